@@ -1,0 +1,179 @@
+"""CPU oracle for the integral-histogram path (Poostchi 2017, arXiv 1711.01656).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product path (the CUDA library and its binding) never does.
+
+The arithmetic lives in plain C (``ih_oracle.c``, FP64 where values are not
+integers); this module only compiles it with gcc and marshals numpy arrays.
+Each wrapper names the passage of the thesis it follows:
+
+* :func:`integral_histogram`  -- Algorithm 5 (sequential recurrence), Eq. 2.15
+* :func:`weighted_integral_histogram` -- Eq. 3.4 with w in {1, c, r, c^2, r^2}
+* :func:`rect_hist`   -- Eq. 2.16's quantity by enumeration of the region
+* :func:`weighted_hist` -- Eq. 3.1 by direct FP64 summation (Sec. 3.1.1)
+* :func:`features`  -- Eq. 2.33 intensity + gradient orientation (Fig. 2.3)
+
+Multi-channel frames concatenate the channels' bins in channel order, so the
+tensor is (sum of bins) x H x W, bin-major (Fig. 5.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ih_oracle.c")
+_LIB = os.path.join(_HERE, "libih_oracle.so")
+
+BIN_UNIFORM8 = 0
+BIN_INDEX = 1
+W_ONE, W_COL, W_ROW, W_COL2, W_ROW2 = 0, 1, 2, 3, 4
+MOMENT_WEIGHTS = (W_COL, W_ROW, W_COL2, W_ROW2)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/libih_oracle.so`` with gcc."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _bind(path: str):
+    lib = ctypes.CDLL(path)
+    i32, i64, p = ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    lib.oracle_bin_of.argtypes = [i32, i32, i32]
+    lib.oracle_bin_of.restype = i32
+    lib.oracle_weighted_ih.argtypes = [p, i64, i32, i32, i32, i32, i32, p, i32]
+    lib.oracle_weighted_ih.restype = i32
+    lib.oracle_ih.argtypes = [p, i64, i32, i32, i32, i32, p, i32]
+    lib.oracle_ih.restype = i32
+    lib.oracle_rect_hist.argtypes = [p, i64, i32, i32, i32, i32, p, i64, p]
+    lib.oracle_rect_hist.restype = i64
+    lib.oracle_weighted_hist.argtypes = [p, i64, i32, i32, i32, i32, p, i64, i32, p]
+    lib.oracle_weighted_hist.restype = i64
+    lib.oracle_kernel_weight.argtypes = [p, i32, i32]
+    lib.oracle_kernel_weight.restype = ctypes.c_double
+    lib.oracle_orientation_bin.argtypes = [i32, i32, i32]
+    lib.oracle_orientation_bin.restype = i32
+    lib.oracle_features.argtypes = [p, i32, i32, p]
+    lib.oracle_features.restype = None
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(build())
+    return _lib
+
+
+def _plane(img) -> np.ndarray:
+    a = np.ascontiguousarray(img, dtype=np.uint8)
+    if a.ndim != 2:
+        raise ValueError("expected an H x W uint8 plane")
+    return a
+
+
+def bin_of(v: int, bins: int, mode: int = BIN_UNIFORM8) -> int:
+    """Eq. 2.15's binning function: the bin value v falls in (-1: none)."""
+    return _load().oracle_bin_of(int(v), int(bins), int(mode))
+
+
+def integral_histogram(img, bins: int, mode: int = BIN_UNIFORM8, threads: int = 1) -> np.ndarray:
+    """Algorithm 5: int32 tensor bins x H x W (inclusive, Eq. 2.15)."""
+    a = _plane(img)
+    h, w = a.shape
+    out = np.empty((bins, h, w), dtype=np.int32)
+    rc = _load().oracle_ih(a.ctypes.data, w, h, w, bins, mode, out.ctypes.data, threads)
+    if rc != 0:
+        raise ArithmeticError("oracle_ih failed (%d)" % rc)
+    return out
+
+
+def weighted_integral_histogram(img, bins: int, weight: int, mode: int = BIN_UNIFORM8,
+                                threads: int = 1) -> np.ndarray:
+    """Eq. 3.4 with w(r,c) in {1, c, r, c^2, r^2}: int64 bins x H x W."""
+    a = _plane(img)
+    h, w = a.shape
+    out = np.empty((bins, h, w), dtype=np.int64)
+    rc = _load().oracle_weighted_ih(a.ctypes.data, w, h, w, bins, mode, weight,
+                                    out.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("oracle_weighted_ih failed (%d)" % rc)
+    return out
+
+
+def _boxes(q) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    if q.ndim != 2 or q.shape[1] != 4:
+        raise ValueError("expected n x 4 int32 (r0, c0, r1, c1)")
+    return q
+
+
+def rect_hist(img, bins: int, rects, mode: int = BIN_UNIFORM8) -> np.ndarray:
+    """Histogram of each inclusive rectangle by enumerating its pixels."""
+    a, q = _plane(img), _boxes(rects)
+    h, w = a.shape
+    out = np.empty((q.shape[0], bins), dtype=np.int32)
+    _load().oracle_rect_hist(a.ctypes.data, w, h, w, bins, mode, q.ctypes.data, q.shape[0],
+                             out.ctypes.data)
+    return out
+
+
+def weighted_hist(img, bins: int, windows, mode: int = BIN_UNIFORM8,
+                  normalize: bool = False) -> np.ndarray:
+    """Eq. 3.1 by direct FP64 summation with the Epanechnikov window kernel."""
+    a, q = _plane(img), _boxes(windows)
+    h, w = a.shape
+    out = np.empty((q.shape[0], bins), dtype=np.float64)
+    _load().oracle_weighted_hist(a.ctypes.data, w, h, w, bins, mode, q.ctypes.data,
+                                 q.shape[0], int(bool(normalize)), out.ctypes.data)
+    return out
+
+
+def kernel_weight(window, r: int, c: int) -> float:
+    """The spatial weight k(r, c) of one pixel inside `window` (FP64)."""
+    q = np.ascontiguousarray(window, dtype=np.int32).reshape(4)
+    return _load().oracle_kernel_weight(q.ctypes.data, int(r), int(c))
+
+
+def orientation_bin(gx: int, gy: int, nbins: int = 9) -> int:
+    """Unsigned gradient-orientation bin of the integer gradient (gx, gy)."""
+    return _load().oracle_orientation_bin(int(gx), int(gy), int(nbins))
+
+
+def features(rgb) -> np.ndarray:
+    """7 uint8 planes (R, G, B, I, HoG s=1, s=2, s=4) from 3 x H x W RGB."""
+    a = np.ascontiguousarray(rgb, dtype=np.uint8)
+    if a.ndim != 3 or a.shape[0] != 3:
+        raise ValueError("expected 3 x H x W uint8")
+    _, h, w = a.shape
+    out = np.empty((7, h, w), dtype=np.uint8)
+    _load().oracle_features(a.ctypes.data, h, w, out.ctypes.data)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# multi-channel frames: channels' bins concatenated in channel order
+
+
+def frame_integral_histogram(planes, chans, threads: int = 1) -> np.ndarray:
+    """Algorithm 5 per channel; chans is a list of (bins, mode)."""
+    return np.concatenate([integral_histogram(p, b, m, threads) for p, (b, m) in zip(planes, chans)],
+                          axis=0)
+
+
+def frame_rect_hist(planes, chans, rects) -> np.ndarray:
+    return np.concatenate([rect_hist(p, b, rects, m) for p, (b, m) in zip(planes, chans)], axis=1)

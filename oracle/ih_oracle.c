@@ -1,0 +1,285 @@
+/*
+ * ih_oracle.c -- plain, slow, obviously-correct CPU oracle for the
+ * integral-histogram path of Poostchi (2017), arXiv 1711.01656.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the test suite, the smoke check of __graft_entry__ and
+ * the cpu_baseline / reference leg of bench.py use it.  It shares no code,
+ * header, table or constant with the CUDA path.
+ *
+ * Every routine below follows one passage of the thesis, in its order and
+ * notation, with no blocking, fusion or reordering:
+ *   - binning function Q                         Eq. 2.15 (and Eq. 3.1's Q(f))
+ *   - integral histogram by the sequential
+ *     recurrence H(k,x,y)=H(k,x-1,y)+H(k,x,y-1)
+ *                 -H(k,x-1,y-1)+Q(k,I(x,y))       Algorithm 5, Sec. 5 intro
+ *   - weighted integral histogram IH_w            Eq. 3.4 (same recurrence,
+ *                                                 the increment times w)
+ *   - rectangle histogram by enumeration of the
+ *     region's pixels                             Eq. 2.15 + Eq. 2.16 (definition)
+ *   - spatially weighted local histogram by
+ *     direct summation (the brute force)          Eq. 3.1, Sec. 3.1.1
+ *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
+ *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
+ *
+ * Readings where the thesis is silent (listed with reasons in the design doc):
+ *   - uniform binning of 8-bit values into B bins over [0,256):
+ *     Q(v) = floor(v*B/256); "index" channels carry the bin itself and a
+ *     value >= B belongs to no bin;
+ *   - the integral histogram is inclusive (Eq. 2.15, Alg. 5), 0-based,
+ *     r = row (the thesis's x), c = column (the thesis's y);
+ *   - a rectangle is inclusive [r0,r1] x [c0,c1]; an invalid one (outside
+ *     the frame or r0>r1 / c0>c1) yields a row of -1;
+ *   - the spatial kernel of Eq. 3.1 is an Epanechnikov profile whose
+ *     ellipse passes through the window's outer corners:
+ *       k(r,c) = 1 - (2c-(c0+c1))^2/(2w^2) - (2r-(r0+r1))^2/(2h^2),
+ *     w = c1-c0+1, h = r1-r0+1 (every pixel centre has k > 0);
+ *   - intensity rounds down; gradient orientation is unsigned, in
+ *     [0,180) degrees, 9 bins of 20 degrees, central differences at step
+ *     s with replicated borders, (0,0) -> bin 0.
+ *
+ * Floating point is FP64 throughout; counts are exact integers (int64
+ * accumulation, checked to fit int32 where the output is int32).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_BIN_UNIFORM8 0
+#define OR_BIN_INDEX 1
+
+/* weight functions w(r,c) of Eq. 3.4 used for moment planes */
+#define OR_W_ONE 0
+#define OR_W_COL 1    /* w = c   */
+#define OR_W_ROW 2    /* w = r   */
+#define OR_W_COL2 3   /* w = c^2 */
+#define OR_W_ROW2 4   /* w = r^2 */
+
+/* Eq. 2.15: Q(I(r,c), b) is 1 iff the pixel value falls in bin b.  Returns
+ * the bin the value falls in, or -1 if it falls in none. */
+int oracle_bin_of(int v, int B, int mode)
+{
+    if (mode == OR_BIN_UNIFORM8) {
+        /* B equal-width bins over [0,256): bin b holds [256b/B, 256(b+1)/B) */
+        return (v * B) / 256;
+    }
+    return (v >= 0 && v < B) ? v : -1;
+}
+
+static int64_t weight_of(int w, int64_t r, int64_t c)
+{
+    switch (w) {
+    case OR_W_ONE: return 1;
+    case OR_W_COL: return c;
+    case OR_W_ROW: return r;
+    case OR_W_COL2: return c * c;
+    case OR_W_ROW2: return r * r;
+    }
+    return 0;
+}
+
+/* Algorithm 5 with the increment Q(k, I(x,y)) replaced by
+ * Q(k, I(x,y)) * w(x,y): this is Eq. 3.4's weighted integral histogram, and
+ * with w = 1 exactly Algorithm 5.  Output is bin-major b x h x w (Fig. 5.1),
+ * packed. H(k,-1,.) = H(k,.,-1) = 0. */
+static void alg5_weighted(const uint8_t *img, int64_t pitch, int h, int w,
+                          int b, int mode, int wk, int64_t *out, int k_lo,
+                          int k_hi)
+{
+    for (int k = k_lo; k < k_hi; k++) {
+        int64_t *Hk = out + (int64_t)k * h * w;
+        for (int x = 0; x < h; x++) {
+            for (int y = 0; y < w; y++) {
+                int64_t up = x > 0 ? Hk[(int64_t)(x - 1) * w + y] : 0;
+                int64_t left = y > 0 ? Hk[(int64_t)x * w + (y - 1)] : 0;
+                int64_t diag = (x > 0 && y > 0) ? Hk[(int64_t)(x - 1) * w + (y - 1)] : 0;
+                int q = oracle_bin_of(img[(int64_t)x * pitch + y], b, mode) == k;
+                Hk[(int64_t)x * w + y] = up + left - diag + (q ? weight_of(wk, x, y) : 0);
+            }
+        }
+    }
+}
+
+typedef struct {
+    const uint8_t *img;
+    int64_t pitch;
+    int h, w, b, mode, wk;
+    int64_t *out;
+    int k_lo, k_hi;
+} alg5_job;
+
+static void *alg5_thread(void *p)
+{
+    alg5_job *j = (alg5_job *)p;
+    alg5_weighted(j->img, j->pitch, j->h, j->w, j->b, j->mode, j->wk, j->out,
+                  j->k_lo, j->k_hi);
+    return NULL;
+}
+
+/* Algorithm 5 / Eq. 3.4 for bins [0,b), split over `threads` host threads by
+ * bin (the bins are independent, Sec. 5.1.2).  out: int64 b x h x w. */
+int oracle_weighted_ih(const uint8_t *img, int64_t pitch, int h, int w, int b,
+                       int mode, int wk, int64_t *out, int threads)
+{
+    if (h < 0 || w < 0 || b < 1 || pitch < w) return -1;
+    if (threads < 1) threads = 1;
+    if (threads > b) threads = b;
+    if (threads == 1) {
+        alg5_weighted(img, pitch, h, w, b, mode, wk, out, 0, b);
+        return 0;
+    }
+    pthread_t *tid = (pthread_t *)malloc(sizeof(pthread_t) * threads);
+    alg5_job *jobs = (alg5_job *)malloc(sizeof(alg5_job) * threads);
+    for (int t = 0; t < threads; t++) {
+        alg5_job j = {img, pitch, h, w, b, mode, wk, out, b * t / threads,
+                      b * (t + 1) / threads};
+        jobs[t] = j;
+        pthread_create(&tid[t], NULL, alg5_thread, &jobs[t]);
+    }
+    for (int t = 0; t < threads; t++) pthread_join(tid[t], NULL);
+    free(tid);
+    free(jobs);
+    return 0;
+}
+
+/* Algorithm 5 proper: int32 integral histogram b x h x w.  Accumulates in
+ * int64 and returns 1 if any cell does not fit int32 (never for h*w < 2^31). */
+int oracle_ih(const uint8_t *img, int64_t pitch, int h, int w, int b, int mode,
+              int32_t *out, int threads)
+{
+    int64_t n = (int64_t)b * h * w;
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (n > 0 ? n : 1));
+    if (!tmp) return -2;
+    int rc = oracle_weighted_ih(img, pitch, h, w, b, mode, OR_W_ONE, tmp, threads);
+    if (rc == 0) {
+        for (int64_t i = 0; i < n; i++) {
+            if (tmp[i] > INT32_MAX) rc = 1;
+            out[i] = (int32_t)tmp[i];
+        }
+    }
+    free(tmp);
+    return rc;
+}
+
+static int rect_valid(int h, int w, const int32_t *q)
+{
+    return q[0] >= 0 && q[1] >= 0 && q[0] <= q[2] && q[1] <= q[3] && q[2] < h &&
+           q[3] < w;
+}
+
+/* Histogram of rectangle R = [r0,r1] x [c0,c1] (inclusive) by enumerating
+ * its pixels: the quantity Eq. 2.16 evaluates from four corners, taken here
+ * from its definition (Eq. 2.15 summed over R).  rects: n x 4 (r0,c0,r1,c1);
+ * out: n x b int32.  Returns the number of invalid rectangles (row of -1). */
+int64_t oracle_rect_hist(const uint8_t *img, int64_t pitch, int h, int w, int b,
+                         int mode, const int32_t *rects, int64_t n,
+                         int32_t *out)
+{
+    int64_t bad = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const int32_t *q = rects + 4 * i;
+        int32_t *o = out + i * b;
+        if (!rect_valid(h, w, q)) {
+            for (int k = 0; k < b; k++) o[k] = -1;
+            bad++;
+            continue;
+        }
+        for (int k = 0; k < b; k++) o[k] = 0;
+        for (int r = q[0]; r <= q[2]; r++)
+            for (int c = q[1]; c <= q[3]; c++) {
+                int k = oracle_bin_of(img[(int64_t)r * pitch + c], b, mode);
+                if (k >= 0) o[k]++;
+            }
+    }
+    return bad;
+}
+
+/* The spatial kernel of Eq. 3.1 for window [r0,r1] x [c0,c1] (Epanechnikov
+ * profile through the window's outer corners), in FP64. */
+double oracle_kernel_weight(const int32_t *q, int r, int c)
+{
+    double wdt = (double)(q[3] - q[1] + 1), hgt = (double)(q[2] - q[0] + 1);
+    double dc = 2.0 * c - (double)(q[1] + q[3]);
+    double dr = 2.0 * r - (double)(q[0] + q[2]);
+    return 1.0 - dc * dc / (2.0 * wdt * wdt) - dr * dr / (2.0 * hgt * hgt);
+}
+
+/* Eq. 3.1 by direct summation (the brute force of Sec. 3.1.1):
+ *   H(T, b_i) = sum_{(x,y) in T} delta(Q(f(x,y)) - b_i) * w(x,y)
+ * in FP64.  normalize != 0 divides every bin by sum_{T} w(x,y), the
+ * normalisation step of the SWIH flow (Ch. 3 introduction).  out: n x b
+ * double; an invalid window yields a row of -1.  Returns #invalid. */
+int64_t oracle_weighted_hist(const uint8_t *img, int64_t pitch, int h, int w,
+                             int b, int mode, const int32_t *wins, int64_t n,
+                             int normalize, double *out)
+{
+    int64_t bad = 0;
+    for (int64_t i = 0; i < n; i++) {
+        const int32_t *q = wins + 4 * i;
+        double *o = out + i * b;
+        if (!rect_valid(h, w, q)) {
+            for (int k = 0; k < b; k++) o[k] = -1.0;
+            bad++;
+            continue;
+        }
+        double wsum = 0.0;
+        for (int k = 0; k < b; k++) o[k] = 0.0;
+        for (int r = q[0]; r <= q[2]; r++)
+            for (int c = q[1]; c <= q[3]; c++) {
+                double wt = oracle_kernel_weight(q, r, c);
+                int k = oracle_bin_of(img[(int64_t)r * pitch + c], b, mode);
+                if (k >= 0) o[k] += wt;
+                wsum += wt;
+            }
+        if (normalize)
+            for (int k = 0; k < b; k++) o[k] /= wsum;
+    }
+    return bad;
+}
+
+/* Gradient orientation bin (Fig. 2.3, Algorithm 2): unsigned
+ * orientation theta = atan2(gy, gx) folded into [0, pi), quantised into nb
+ * equal bins; (0,0) -> bin 0.  FP64. */
+int oracle_orientation_bin(int gx, int gy, int nb)
+{
+    if (gy < 0 || (gy == 0 && gx < 0)) {
+        gx = -gx;
+        gy = -gy;
+    }
+    if (gx == 0 && gy == 0) return 0;
+    double th = atan2((double)gy, (double)gx); /* in [0, pi) after the fold */
+    int k = (int)floor(th / (M_PI / nb));
+    if (k >= nb) k = nb - 1;
+    if (k < 0) k = 0;
+    return k;
+}
+
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* The 7 feature channels of the tracker's descriptor set: R, G, B, intensity
+ * I = (R+G+B)/3 (Eq. 2.33) and three gradient-orientation index planes of I
+ * at central-difference steps s = 1, 2, 4 (9 bins).  rgb: 3 planes of h x w;
+ * out: 7 planes of h x w (uint8), packed. */
+void oracle_features(const uint8_t *rgb, int h, int w, uint8_t *out)
+{
+    int64_t n = (int64_t)h * w;
+    const uint8_t *R = rgb, *G = rgb + n, *B = rgb + 2 * n;
+    uint8_t *I = out + 3 * n;
+    memcpy(out, rgb, (size_t)(3 * n));
+    for (int64_t i = 0; i < n; i++) I[i] = (uint8_t)(((int)R[i] + G[i] + B[i]) / 3);
+    const int steps[3] = {1, 2, 4};
+    for (int l = 0; l < 3; l++) {
+        int s = steps[l];
+        uint8_t *O = out + (4 + l) * n;
+        for (int r = 0; r < h; r++)
+            for (int c = 0; c < w; c++) {
+                int gx = (int)I[(int64_t)r * w + clampi(c + s, 0, w - 1)] -
+                         (int)I[(int64_t)r * w + clampi(c - s, 0, w - 1)];
+                int gy = (int)I[(int64_t)clampi(r + s, 0, h - 1) * w + c] -
+                         (int)I[(int64_t)clampi(r - s, 0, h - 1) * w + c];
+                O[(int64_t)r * w + c] = (uint8_t)oracle_orientation_bin(gx, gy, 9);
+            }
+    }
+}

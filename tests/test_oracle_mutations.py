@@ -1,0 +1,57 @@
+"""The pins bite: plant one plausible mistake at a time in a copy of the
+oracle's C source (on the CPU), rebuild it, and check that the pins of
+test_oracle_pins.py reject the mutant.  The oracle itself is untouched."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "ih_oracle.c")
+
+# (name, original text, mutated text, pin tests that must fail)
+MUTANTS = [
+    ("alg5_diag_sign", "up + left - diag", "up + left + diag",
+     [lambda: pins.test_alg5_equals_enumeration(5, 6, 2, 3)]),
+    ("alg5_drop_up", "up + left - diag", "left - diag",
+     [lambda: pins.test_alg5_constant_image(128)]),
+    ("bin_denominator", "(v * B) / 256", "(v * B) / 255",
+     [lambda: pins.test_uniform_binning_matches_edges(3)]),
+    ("rect_row_exclusive", "o[k] = 0;\n        for (int r = q[0]; r <= q[2]; r++)",
+     "o[k] = 0;\n        for (int r = q[0]; r < q[2]; r++)",
+     [pins.test_rect_hist_is_bincount_of_slice, pins.test_four_corner_identity_all_rects]),
+    ("kernel_transposed_axes", "dc * dc / (2.0 * wdt * wdt)", "dc * dc / (2.0 * hgt * hgt)",
+     [pins.test_weighted_single_pixel_values]),
+    ("kernel_sign", "return 1.0 - dc * dc", "return 1.0 + dc * dc",
+     [lambda: pins.test_weighted_constant_image_closed_form((8, 8))]),
+    ("kernel_centre_off_by_one", "double dc = 2.0 * c - (double)(q[1] + q[3]);",
+     "double dc = 2.0 * c - (double)(q[1] + q[3] + 1);",
+     [pins.test_weighted_mirror_symmetry]),
+    ("weight_axes_swapped", "case OR_W_COL: return c;", "case OR_W_COL: return r;",
+     [lambda: pins.test_weighted_ih_equals_cumsum(oracle.W_COL)]),
+    ("orientation_fold", "if (gy < 0 || (gy == 0 && gx < 0)) {", "if (gy < 0) {",
+     [lambda: pins.test_orientation_known((-1, 0), 0)]),
+    ("orientation_step", "th / (M_PI / nb)", "th / (M_PI / (nb + 1))",
+     [pins.test_orientation_exhaustive_vs_exact_integer_test]),
+    ("intensity_rounding", "G[i] + B[i]) / 3)", "G[i] + B[i] + 1) / 3)",
+     [pins.test_intensity_is_floor_mean]),
+    ("hog_stencil_step", "clampi(c + s, 0, w - 1)", "clampi(c + 1, 0, w - 1)",
+     [pins.test_hog_stencil_replicated_borders]),
+]
+
+
+@pytest.mark.parametrize("name,old,new,checks", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_reject_mutant(tmp_path, monkeypatch, name, old, new, checks):
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor must be unique: %r" % old
+    msrc = tmp_path / "mutant.c"
+    msrc.write_text(src.replace(old, new))
+    so = tmp_path / "mutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o",
+                           str(so), str(msrc), "-lm", "-lpthread"])
+    monkeypatch.setattr(oracle, "_lib", oracle._bind(str(so)))
+    for check in checks:
+        with pytest.raises(AssertionError):
+            check()

@@ -1,0 +1,362 @@
+"""Pins of the CPU oracle to facts other than itself.
+
+Each test checks one oracle routine against something the thesis or the
+mathematics fixes: the hand-worked example (tests/golden), closed forms,
+invariants, special cases that reduce to a library routine, and brute force
+on tiny inputs.  A wrong sign, index, dropped term or transposed operand in
+the oracle fails at least one of them (see test_oracle_mutations.py).
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1711_01656_gb300 import synth
+
+
+def _bins_by_edges(img, bins):
+    """Uniform binning over [0,256) by searching the bin edges 256*b/bins:
+    an independent route to Eq. 2.15's Q (searchsorted, not the formula)."""
+    edges = np.array([Fraction(256 * b, bins) for b in range(1, bins)], dtype=object)
+    flat = np.asarray(img, dtype=np.int64).ravel()
+    idx = np.array([int(np.searchsorted(edges.astype(float), v, side="right")) for v in flat])
+    return idx.reshape(np.shape(img))
+
+
+def _prefix_by_enumeration(q, bins):
+    """H(b, r, c) = #{(r', c') : r' <= r, c' <= c, q = b}, pure Python loops."""
+    h, w = q.shape
+    out = np.zeros((bins, h, w), dtype=np.int64)
+    for r in range(h):
+        for c in range(w):
+            for rr in range(r + 1):
+                for cc in range(c + 1):
+                    b = q[rr, cc]
+                    if 0 <= b < bins:
+                        out[b, r, c] += 1
+    return out
+
+
+# ---------------------------------------------------------------- hand example
+
+def test_hand_example(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "hand_2x3.json")))
+    img = np.array(g["image"], dtype=np.uint8)
+    ih = oracle.integral_histogram(img, g["bins"])
+    assert ih.tolist() == g["ih"]
+    rh = oracle.rect_hist(img, g["bins"], [g["rect"]["box"]])
+    assert rh.tolist() == [g["rect"]["hist"]]
+    wd = g["weighted"]
+    wh = oracle.weighted_hist(img, g["bins"], [wd["window"]])
+    for k in range(g["bins"]):
+        assert wh[0, k] == pytest.approx(wd["hist_num"][k] / wd["hist_den"], rel=1e-15)
+    for r in range(2):
+        for c in range(3):
+            assert oracle.kernel_weight(wd["window"], r, c) == pytest.approx(wd["k_rows"][r][c], rel=1e-15)
+    whn = oracle.weighted_hist(img, g["bins"], [wd["window"]], normalize=True)
+    assert whn[0].tolist() == pytest.approx([157 / 314, 157 / 314], rel=1e-15)
+
+
+# ---------------------------------------------------------------- binning
+
+@pytest.mark.parametrize("bins", [1, 2, 3, 7, 9, 16, 32, 40, 91, 256])
+def test_uniform_binning_matches_edges(bins):
+    v = np.arange(256).reshape(16, 16)
+    got = np.array([[oracle.bin_of(x, bins) for x in row] for row in v])
+    assert (got == _bins_by_edges(v, bins)).all()
+    # every bin of a uniform binning over [0,256) holds floor or ceil of 256/bins values
+    counts = np.bincount(got.ravel(), minlength=bins)
+    assert counts.min() >= 256 // bins and counts.max() <= -(-256 // bins)
+
+
+def test_index_binning():
+    assert [oracle.bin_of(v, 9, oracle.BIN_INDEX) for v in range(12)] == list(range(9)) + [-1] * 3
+
+
+# ---------------------------------------------------------------- Algorithm 5
+
+@pytest.mark.parametrize("h,w,bins,seed", [(1, 1, 1, 0), (1, 7, 3, 1), (6, 1, 4, 2), (5, 6, 2, 3),
+                                           (7, 5, 16, 4), (4, 9, 40, 5)])
+def test_alg5_equals_enumeration(h, w, bins, seed):
+    img = synth.uniform_plane(h, w, seed)
+    got = oracle.integral_histogram(img, bins)
+    ref = _prefix_by_enumeration(_bins_by_edges(img, bins), bins)
+    assert (got == ref).all()
+
+
+@pytest.mark.parametrize("bins", list(range(1, 41)))
+def test_alg5_equals_cumsum_of_onehot(bins):
+    img = synth.uniform_plane(23, 31, 100 + bins)
+    q = _bins_by_edges(img, bins)
+    onehot = (q[None, :, :] == np.arange(bins)[:, None, None]).astype(np.int64)
+    ref = np.cumsum(np.cumsum(onehot, axis=1), axis=2)
+    assert (oracle.integral_histogram(img, bins) == ref).all()
+
+
+@pytest.mark.parametrize("h,w,bins", [(17, 29, 16), (64, 48, 32), (9, 64, 9)])
+def test_alg5_invariants(h, w, bins):
+    img = synth.blob_plane(h, w, 7)
+    H = oracle.integral_histogram(img, bins).astype(np.int64)
+    # the full-image histogram sums to H*W
+    assert H[:, -1, -1].sum() == h * w
+    # every prefix holds (r+1)(c+1) pixels in total
+    rr, cc = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    assert (H.sum(axis=0) == (rr + 1) * (cc + 1)).all()
+    # monotone non-decreasing along rows and columns
+    assert (np.diff(H, axis=1) >= 0).all() and (np.diff(H, axis=2) >= 0).all()
+    # full-image histogram equals numpy's bincount of the bins
+    assert (H[:, -1, -1] == np.bincount(_bins_by_edges(img, bins).ravel(), minlength=bins)).all()
+
+
+@pytest.mark.parametrize("v", [0, 1, 127, 128, 200, 255])
+def test_alg5_constant_image(v):
+    h, w, bins = 13, 11, 16
+    H = oracle.integral_histogram(np.full((h, w), v, np.uint8), bins)
+    b = v * bins // 256
+    rr, cc = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    assert (H[b] == (rr + 1) * (cc + 1)).all()
+    assert (np.delete(H, b, axis=0) == 0).all()
+
+
+def test_alg5_bin_subsets_are_slices():
+    img = synth.uniform_plane(20, 24, 11)
+    full = oracle.integral_histogram(img, 16)
+    # a 16-bin build is the 4-bin build of (v >> 2) refined: bins 4k..4k+3 sum to 4-bin bin k
+    coarse = oracle.integral_histogram(img, 4)
+    assert (full.reshape(4, 4, 20, 24).sum(axis=1) == coarse).all()
+
+
+def test_alg5_index_mode_skips_out_of_range():
+    img = np.array([[0, 1, 9, 2], [3, 200, 8, 8]], np.uint8)
+    H = oracle.integral_histogram(img, 9, oracle.BIN_INDEX)
+    assert H[:, -1, -1].sum() == 6  # 9 and 200 are in no bin
+    assert H[8, -1, -1] == 2 and H[0, -1, -1] == 1
+
+
+def test_alg5_threads_agree():
+    img = synth.uniform_plane(40, 50, 3)
+    assert (oracle.integral_histogram(img, 16, threads=1) ==
+            oracle.integral_histogram(img, 16, threads=5)).all()
+
+
+# ---------------------------------------------------------------- Eq. 2.16
+
+def test_four_corner_identity_all_rects():
+    h, w, bins = 10, 12, 5
+    img = synth.uniform_plane(h, w, 21)
+    H = np.pad(oracle.integral_histogram(img, bins).astype(np.int64), ((0, 0), (1, 0), (1, 0)))
+    rects = [(r0, c0, r1, c1) for r0 in range(h) for r1 in range(r0, h)
+             for c0 in range(w) for c1 in range(c0, w)]
+    rects = np.array(rects, np.int32)
+    brute = oracle.rect_hist(img, bins, rects)
+    r0, c0, r1, c1 = (rects[:, i] for i in range(4))
+    four = (H[:, r1 + 1, c1 + 1] - H[:, r0, c1 + 1] - H[:, r1 + 1, c0] + H[:, r0, c0]).T
+    assert (brute == four).all()
+
+
+def test_rect_hist_is_bincount_of_slice():
+    img = synth.blob_plane(40, 37, 5)
+    rects = synth.rects_uniform_corners(40, 37, 300, 9)
+    got = oracle.rect_hist(img, 16, rects)
+    q = _bins_by_edges(img, 16)
+    for (r0, c0, r1, c1), row in zip(rects, got):
+        assert (row == np.bincount(q[r0:r1 + 1, c0:c1 + 1].ravel(), minlength=16)).all()
+        assert row.sum() == (r1 - r0 + 1) * (c1 - c0 + 1)
+
+
+def test_rect_hist_invalid_rows():
+    img = synth.uniform_plane(8, 8, 1)
+    bad = [[-1, 0, 3, 3], [0, 0, 8, 3], [4, 0, 3, 3], [0, 5, 3, 4], [0, 0, 3, 8]]
+    out = oracle.rect_hist(img, 4, bad + [[0, 0, 7, 7]])
+    assert (out[:5] == -1).all() and out[5].sum() == 64
+
+
+# ---------------------------------------------------------------- Eq. 3.1
+
+def _K_closed_form(w, h):
+    """sum over a w x h window of k(r,c) = 1 - d_c^2/(2w^2) - d_r^2/(2h^2),
+    d = 2*offset - (span-1): sum of d^2 over an axis of length n is
+    (n-1)n(n+1)/3 (sum of squares of n values spaced by 2, symmetric)."""
+    sx = Fraction((w - 1) * w * (w + 1), 3)
+    sy = Fraction((h - 1) * h * (h + 1), 3)
+    return w * h - h * sx / (2 * w * w) - w * sy / (2 * h * h)
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (1, 5), (4, 1), (3, 2), (8, 8), (33, 17), (64, 100)])
+def test_weighted_constant_image_closed_form(wh):
+    w, h = wh
+    img = np.full((h + 3, w + 2), 77, np.uint8)
+    win = [[1, 2, h, w + 1]]
+    out = oracle.weighted_hist(img, 16, win)
+    K = float(_K_closed_form(w, h))
+    assert out[0, 77 * 16 // 256] == pytest.approx(K, rel=1e-13)
+    assert np.count_nonzero(out[0]) == 1
+
+
+def test_weighted_sum_over_bins_is_K_and_normalized_sums_to_one():
+    img = synth.blob_plane(60, 70, 3)
+    wins = synth.rects_side_range(60, 70, 50, 1, 40, 4)
+    out = oracle.weighted_hist(img, 16, wins)
+    outn = oracle.weighted_hist(img, 16, wins, normalize=True)
+    for (r0, c0, r1, c1), row, rown in zip(wins, out, outn):
+        assert row.sum() == pytest.approx(float(_K_closed_form(c1 - c0 + 1, r1 - r0 + 1)), rel=1e-12)
+        assert rown.sum() == pytest.approx(1.0, rel=1e-12)
+
+
+def test_weighted_translation_invariance():
+    """The weights depend on the position relative to the window only (Sec. 3.1.3)."""
+    patch = synth.uniform_plane(9, 14, 8)
+    a = synth.uniform_plane(30, 40, 1)
+    b = synth.uniform_plane(30, 40, 2)
+    a[3:12, 5:19] = patch
+    b[20:29, 22:36] = patch
+    oa = oracle.weighted_hist(a, 8, [[3, 5, 11, 18]])
+    ob = oracle.weighted_hist(b, 8, [[20, 22, 28, 35]])
+    assert np.array_equal(oa, ob)
+
+
+def test_weighted_mirror_symmetry():
+    img = synth.uniform_plane(11, 16, 5)
+    win = [[0, 0, 10, 15]]
+    base = oracle.weighted_hist(img, 8, win)
+    assert oracle.weighted_hist(img[:, ::-1].copy(), 8, win) == pytest.approx(base, rel=1e-14)
+    assert oracle.weighted_hist(img[::-1, :].copy(), 8, win) == pytest.approx(base, rel=1e-14)
+
+
+def test_weighted_single_pixel_values():
+    """One pixel of bin 1 in a bin-0 background isolates k at that pixel."""
+    h, w = 7, 9  # odd: the centre pixel has weight exactly 1
+    for (r, c) in [(3, 4), (0, 0), (6, 8), (2, 7)]:
+        img = np.zeros((h, w), np.uint8)
+        img[r, c] = 255
+        out = oracle.weighted_hist(img, 2, [[0, 0, h - 1, w - 1]])
+        k = 1 - Fraction((2 * c - (w - 1)) ** 2, 2 * w * w) - Fraction((2 * r - (h - 1)) ** 2, 2 * h * h)
+        assert out[0, 1] == pytest.approx(float(k), rel=1e-15)
+        if (r, c) == (3, 4):
+            assert out[0, 1] == 1.0
+        assert out[0, 1] > 0
+
+
+def test_weighted_equals_exact_rational_sum():
+    img = synth.uniform_plane(12, 10, 6)
+    win = (2, 1, 10, 8)
+    r0, c0, r1, c1 = win
+    w, h = c1 - c0 + 1, r1 - r0 + 1
+    exact = [Fraction(0)] * 4
+    for r in range(r0, r1 + 1):
+        for c in range(c0, c1 + 1):
+            k = 1 - Fraction((2 * c - c0 - c1) ** 2, 2 * w * w) - Fraction((2 * r - r0 - r1) ** 2, 2 * h * h)
+            exact[int(img[r, c]) >> 6] += k
+    out = oracle.weighted_hist(img, 4, [win])
+    assert out[0].tolist() == pytest.approx([float(x) for x in exact], rel=1e-14)
+
+
+# ---------------------------------------------------------------- Eq. 3.4 moment planes
+
+@pytest.mark.parametrize("weight", [oracle.W_ONE] + list(oracle.MOMENT_WEIGHTS))
+def test_weighted_ih_equals_cumsum(weight):
+    h, w, bins = 19, 23, 6
+    img = synth.uniform_plane(h, w, 40 + weight)
+    q = _bins_by_edges(img, bins)
+    rr, cc = np.meshgrid(np.arange(h, dtype=np.int64), np.arange(w, dtype=np.int64), indexing="ij")
+    wt = {oracle.W_ONE: np.ones_like(rr), oracle.W_COL: cc, oracle.W_ROW: rr,
+          oracle.W_COL2: cc * cc, oracle.W_ROW2: rr * rr}[weight]
+    f = (q[None] == np.arange(bins)[:, None, None]) * wt[None]
+    ref = np.cumsum(np.cumsum(f, axis=1), axis=2)
+    assert (oracle.weighted_integral_histogram(img, bins, weight) == ref).all()
+
+
+def test_weighted_ih_small_enumeration():
+    img = synth.uniform_plane(4, 5, 77)
+    q = _bins_by_edges(img, 3)
+    got = oracle.weighted_integral_histogram(img, 3, oracle.W_COL2)
+    for b in range(3):
+        for r in range(4):
+            for c in range(5):
+                s = sum(cc * cc for rr in range(r + 1) for cc in range(c + 1) if q[rr, cc] == b)
+                assert got[b, r, c] == s
+
+
+# ---------------------------------------------------------------- features
+
+def test_intensity_is_floor_mean():
+    rgb = synth.blob_rgb(21, 33, 5)
+    f = oracle.features(rgb)
+    assert (f[:3] == rgb).all()
+    assert (f[3] == rgb.astype(np.int64).sum(0) // 3).all()
+    # special cases
+    x = np.array([[[0, 255, 1, 2]], [[0, 255, 1, 2]], [[0, 255, 0, 1]]], np.uint8)
+    assert oracle.features(x)[3].tolist() == [[0, 255, 0, 1]]
+
+
+# (gx, gy) -> bin; angles: atan(84/100) = 40.03, atan(83/100) = 39.69,
+# atan(36/100) = 19.80, atan(37/100) = 20.30 degrees; bins are 20 degrees wide
+KNOWN_ORIENTATIONS = [((1, 0), 0), ((0, 1), 4), ((1, 1), 2), ((-1, 1), 6), ((-1, 0), 0), ((0, -1), 4),
+                      ((0, 0), 0), ((-1, -1), 2), ((1, -1), 6), ((255, 1), 0), ((-255, 1), 8),
+                      ((1, 255), 4), ((100, 84), 2), ((100, 83), 1), ((100, 36), 0), ((100, 37), 1)]
+
+
+@pytest.mark.parametrize("g,b", KNOWN_ORIENTATIONS)
+def test_orientation_known(g, b):
+    assert oracle.orientation_bin(*g) == b
+
+
+def _orientation_exact_table():
+    """Bins of all 511^2 integer gradients by exact integer half-plane tests:
+    theta >= 20j deg  <=>  cos(20j) gy - sin(20j) gx >= 0 for the folded
+    vector.  The unit vectors are scaled by 2^52 and rounded from 40-digit
+    values, so the integer cross products carry an error below 2^8 while the
+    true ones, never zero (tan 20j deg is irrational), exceed 2^30."""
+    import mpmath
+    mpmath.mp.dps = 40
+    U = [(int(mpmath.nint(mpmath.cos(mpmath.pi * j / 9) * 2 ** 52)),
+          int(mpmath.nint(mpmath.sin(mpmath.pi * j / 9) * 2 ** 52))) for j in range(1, 9)]
+    gx, gy = np.meshgrid(np.arange(-255, 256, dtype=np.int64), np.arange(-255, 256, dtype=np.int64),
+                         indexing="ij")
+    flip = (gy < 0) | ((gy == 0) & (gx < 0))
+    fx, fy = np.where(flip, -gx, gx), np.where(flip, -gy, gy)
+    b = np.zeros_like(fx)
+    for ux, uy in U:
+        cross = ux * fy - uy * fx
+        assert (np.abs(cross[(fx != 0) | (fy != 0)]) > 2 ** 30).all()
+        b += (cross >= 0)
+    b[(fx == 0) & (fy == 0)] = 0
+    return gx, gy, b
+
+
+def test_orientation_exhaustive_vs_exact_integer_test():
+    gx, gy, b = _orientation_exact_table()
+    got = np.array([oracle.orientation_bin(int(x), int(y)) for x, y in zip(gx.ravel(), gy.ravel())])
+    assert (got == b.ravel()).all()
+
+
+def test_orientation_margin_to_bin_boundaries():
+    """No integer gradient in [-255,255]^2 lies within 1e-5 rad of a bin
+    boundary, so an FP64 atan2 decides every bin without ambiguity."""
+    gx, gy = np.meshgrid(np.arange(-255, 256), np.arange(-255, 256), indexing="ij")
+    flip = (gy < 0) | ((gy == 0) & (gx < 0))
+    fx, fy = np.where(flip, -gx, gx), np.where(flip, -gy, gy)
+    nz = (fx != 0) | (fy != 0)
+    th = np.arctan2(fy[nz], fx[nz])
+    step = math.pi / 9
+    frac = th / step - np.floor(th / step)
+    gap = np.minimum(frac, 1 - frac) * step
+    gap = gap[th > 1e-12]  # theta = 0 exactly (gy == 0) sits on bin 0's lower edge by definition
+    assert gap.min() > 1e-5
+
+
+def test_hog_stencil_replicated_borders():
+    rgb = synth.blob_rgb(13, 17, 9)
+    f = oracle.features(rgb)
+    I = f[3].astype(np.int64)
+    for li, s in enumerate((1, 2, 4)):
+        P = np.pad(I, s, mode="edge")
+        gx = P[s:-s, 2 * s:] - P[s:-s, :-2 * s]
+        gy = P[2 * s:, s:-s] - P[:-2 * s, s:-s]
+        exp = np.array([[oracle.orientation_bin(int(x), int(y)) for x, y in zip(rx, ry)]
+                        for rx, ry in zip(gx, gy)])
+        assert (f[4 + li] == exp).all()
