@@ -1,0 +1,203 @@
+/*
+ * ih.h -- C ABI of the GB300 integral-histogram engine.
+ *
+ * The engine computes, on one GPU, the data-parallel path of the integral
+ * histogram of Poostchi (2017), arXiv 1711.01656:
+ *
+ *   Q      binning of uint8 feature channels into one-hot bins     Eq. 2.15
+ *   H      H(b,r,c) = sum_{r'<=r, c'<=c} Q(I(r',c'), b), inclusive Eq. 2.15,
+ *          the tensor of Algorithm 5 (b x h x w, Fig. 5.1)
+ *   h(R)   rectangle histogram from four corners of H               Eq. 2.16
+ *   IH_w   weighted integral histograms (moment planes w = c, r,
+ *          c^2, r^2)                                                 Eq. 3.4
+ *   S(T)   spatially weighted local histogram of a window in O(1)   Eq. 3.1,
+ *          evaluated from the moment planes (SWIH, Sec. 3.1.3)
+ *
+ * Conventions used by every call:
+ *   - r is the row (the thesis's x), c the column (its y), both 0-based,
+ *     origin top-left (Fig. 2.8).
+ *   - A rectangle or window is four int32 (r0, c0, r1, c1), inclusive.
+ *   - "device" pointers are CUDA device (or managed) addresses on the
+ *     context's device; "host" pointers are ordinary CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Every call that takes a stream only enqueues work on it and returns;
+ *     results are ready when the stream reaches that point.
+ *   - The caller owns every buffer it passes in (pixels, rectangles,
+ *     outputs).  The context owns the integral-histogram tensors it builds
+ *     until ih_release() or ih_destroy().
+ *   - Argument errors are detected on the host before anything is
+ *     enqueued and return IH_EINVAL (or IH_EBUDGET / IH_ENOMEM); nothing is
+ *     launched then.  Errors found on the device (an invalid rectangle, a
+ *     CUDA launch failure) are recorded in the context and returned by the
+ *     next ih_sync().  ih_last_error() gives a one-line message.
+ *   - A context may be used from several host threads; calls are
+ *     serialised internally.
+ */
+#ifndef IH_H
+#define IH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ih_ctx ih_ctx;
+
+typedef enum {
+    IH_OK = 0,
+    IH_EINVAL = 1,    /* invalid argument (host check) or invalid query (device) */
+    IH_ENOMEM = 2,    /* device allocation failed */
+    IH_EBUDGET = 3,   /* the build would exceed the context's HBM budget */
+    IH_ECUDA = 4,     /* a CUDA runtime call or launch failed */
+    IH_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    IH_ENOTBUILT = 6, /* the handle names no live frame */
+} ih_status;
+
+/* Binning function Q of one channel (Eq. 2.15). */
+typedef enum {
+    IH_BIN_UNIFORM8 = 0, /* B equal bins over [0,256): Q(v) = floor(v*B/256) */
+    IH_BIN_INDEX = 1     /* v is the bin; a value >= B falls in no bin       */
+} ih_binmode;
+
+typedef struct {
+    int32_t bins; /* B_c >= 1 (<= 256) */
+    int32_t mode; /* ih_binmode */
+} ih_channel;
+
+/* What the pixels of an ih_frame are. */
+typedef enum {
+    /* `channels` uint8 planes, binned as given by chan[] */
+    IH_INPUT_PLANES = 0,
+    /* 3 uint8 planes R, G, B; the engine derives the tracker's 7 feature
+     * channels R, G, B, I = floor((R+G+B)/3) (Eq. 2.33) and the gradient
+     * orientation index of I at central-difference steps 1, 2, 4 (9
+     * unsigned 20-degree bins, replicated borders; Fig. 2.3) and bins them
+     * as given by chan[0..6] (channels must be 7). */
+    IH_INPUT_RGB_FEATURES = 1
+} ih_input;
+
+/* ih_frame.layout: how the context stores the count tensor. */
+typedef enum {
+    IH_LAYOUT_BIN_MAJOR = 0, /* b x h x pitch, as Fig. 5.1 */
+} ih_layout;
+
+typedef struct {
+    int32_t height, width;      /* H, W >= 1 */
+    int32_t channels;           /* number of binned channels, 1..16 */
+    int32_t input;              /* ih_input */
+    const ih_channel *chan;     /* host array [channels] */
+    const uint8_t *d_pixels;    /* device; planar: plane p, row r starts at
+                                   d_pixels + (p*H + r)*pitch_bytes */
+    int64_t pitch_bytes;        /* >= W */
+    int32_t weighted_channel;   /* -1: no moment planes; else the channel whose
+                                   moment planes (Eq. 3.4) are built for
+                                   ih_query_weighted */
+    int32_t layout;             /* ih_layout */
+} ih_frame;
+
+typedef struct {
+    int32_t device;             /* CUDA device ordinal */
+    uint64_t hbm_budget_bytes;  /* cap on the bytes of live frames; 0 = none */
+    uint32_t flags;             /* reserved, 0 */
+} ih_config;
+
+/* Creates a context on cfg->device.  *out receives the context.
+ * Returns IH_EINVAL for a NULL argument or bad device, IH_ECUDA if the device
+ * cannot be initialised. */
+ih_status ih_create(const ih_config *cfg, ih_ctx **out);
+
+/* Builds the integral histogram (Eq. 2.15; the tensor Algorithm 5 defines)
+ * of each of the n >= 1 frames, plus the moment planes of Eq. 3.4 for a frame
+ * whose weighted_channel >= 0, and enqueues the work on `stream`.
+ * out_handles (host, n entries) receives one handle per frame.  The tensors
+ * are owned by the context.  The pixels must stay valid until the stream
+ * passes the build.  Returns IH_EINVAL for an invalid descriptor,
+ * IH_EBUDGET if the frames' bytes would exceed the HBM budget (no frame is
+ * built then), IH_ENOMEM / IH_ECUDA on allocation or launch failure. */
+ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_handles,
+                   void *stream);
+
+/* Rectangle histograms by the four-corner rule of Eq. 2.16:
+ *   h(R,b) = H(r1,c1,b) - H(r0-1,c1,b) - H(r1,c0-1,b) + H(r0-1,c0-1,b)
+ * with H(-1,.) = H(.,-1) = 0.  d_rects: device, n x 4 int32 (r0,c0,r1,c1);
+ * d_out: device, n x B int32 (B = the frame's total bins, channels'
+ * bins in channel order).  An invalid rectangle (outside the frame, r0>r1 or
+ * c0>c1) gets a row of -1 and makes the next ih_sync() return IH_EINVAL.
+ * n may be 0. */
+ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, int64_t n,
+                         int32_t *d_out, void *stream);
+
+/* Spatial kernels for ih_query_weighted. */
+typedef enum {
+    /* Epanechnikov profile whose ellipse passes through the window's outer
+     * corners: k(r,c) = 1 - (2c-c0-c1)^2/(2w^2) - (2r-r0-r1)^2/(2h^2),
+     * w = c1-c0+1, h = r1-r0+1 (every pixel of the window has k > 0) */
+    IH_K_EPANECHNIKOV = 0
+} ih_kernel;
+
+enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
+
+/* Spatially weighted local histograms (Eq. 3.1) of n windows on the frame's
+ * weighted channel, in O(1) each from the moment planes (Sec. 3.1.3):
+ * every bin's weighted sum is an exact integer numerator (int64) over the
+ * window's integer denominator, rounded once to float.  d_windows: device,
+ * n x 4 int32; d_out: device, n x B_w float (B_w = bins of the weighted
+ * channel).  Windows must have sides <= 32768.  Invalid windows give a row
+ * of -1 and IH_EINVAL at the next ih_sync().  IH_EINVAL (host) if the frame
+ * has no moment planes. */
+ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_windows, int64_t n,
+                            uint32_t kernel, uint32_t flags, float *d_out, void *stream);
+
+/* Frees every tensor the context owns and the context.  NULL-safe.
+ * Synchronises the device first. */
+ih_status ih_destroy(ih_ctx *ctx);
+
+/* ---- helpers ---------------------------------------------------------- */
+
+/* Frees the frame's tensors (stream-ordered on `stream`); the handle may be
+ * reused by a later build. */
+ih_status ih_release(ih_ctx *ctx, int32_t handle, void *stream);
+
+/* Waits for `stream`, then returns the first device-side error recorded since
+ * the previous ih_sync (and clears it), else IH_OK. */
+ih_status ih_sync(ih_ctx *ctx, void *stream);
+
+typedef struct {
+    int32_t height, width, channels, total_bins;
+    int32_t weighted_channel, weighted_bins;
+    int64_t pitch_elems;        /* row pitch of the count tensor, elements */
+    int64_t count_bytes;        /* bytes of the count tensor */
+    int64_t moment_bytes;       /* bytes of the moment planes (0 if none) */
+} ih_frame_info;
+
+/* Host copy of a live frame's geometry. */
+ih_status ih_info(ih_ctx *ctx, int32_t handle, ih_frame_info *out);
+
+/* Copies the count tensor to d_dst (device, B x H x W int32, packed,
+ * bin-major as Algorithm 5's output), enqueued on `stream`. */
+ih_status ih_export(ih_ctx *ctx, int32_t handle, int32_t *d_dst, void *stream);
+
+/* Copies moment plane `plane` (0: w=c, 1: w=r, 2: w=c^2, 3: w=r^2; Eq. 3.4)
+ * to d_dst (device, B_w x H x W int64, packed). */
+ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t *d_dst,
+                            void *stream);
+
+/* The feature pre-pass alone: 3 planes R,G,B (device, H rows of pitch_bytes,
+ * plane stride H*pitch_bytes) -> 7 planes (device, packed H x W each) as
+ * described for IH_INPUT_RGB_FEATURES. */
+ih_status ih_features(ih_ctx *ctx, const uint8_t *d_rgb, int32_t height, int32_t width,
+                      int64_t pitch_bytes, uint8_t *d_out, void *stream);
+
+/* Kernel launches issued by this context since it was created (all of them
+ * are this library's own kernels). */
+int64_t ih_launch_count(ih_ctx *ctx);
+
+/* One-line description of the last error of this context ("" if none). */
+const char *ih_last_error(ih_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IH_H */

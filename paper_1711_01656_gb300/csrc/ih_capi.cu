@@ -1,0 +1,507 @@
+// ih_capi.cu -- the C ABI of include/ih.h: contexts, frame table, HBM
+// budget, stream-ordered device memory and the launch plan of a build.
+//
+// Memory: every tensor and every scratch buffer comes from a per-context
+// CUDA memory pool through cudaMallocFromPoolAsync / cudaFreeAsync on the
+// caller's stream, so a build never synchronises the device and freed
+// memory is reused by later builds in stream order.  The pool keeps what it
+// has reserved (release threshold = max), which makes steady-state builds
+// allocation-free at the driver level.
+#include <cstdarg>
+#include <mutex>
+#include <string>
+#include <vector>
+#include <cstdio>
+#include <cstring>
+
+#include "../../include/ih.h"
+#include "ih_internal.cuh"
+#include "ih_plan.h"
+
+using namespace ih;
+
+namespace {
+
+struct FrameRec {
+    bool live = false;
+    int H = 0, W = 0, nchan = 0, B = 0;
+    int bins[kMaxChannels] = {0};
+    int bin_off[kMaxChannels] = {0};
+    int64_t P = 0;
+    int32_t *d_ih = nullptr;
+    int wch = -1, Bw = 0;
+    int64_t *d_mom = nullptr;
+    int64_t count_bytes = 0, moment_bytes = 0;
+};
+
+}  // namespace
+
+struct ih_ctx {
+    int device = 0;
+    uint64_t budget = 0;
+    uint64_t used = 0;
+    cudaMemPool_t pool = nullptr;
+    std::vector<FrameRec> frames;
+    int *d_err = nullptr;
+    std::recursive_mutex mu;
+    std::string last_error;
+    int64_t launches = 0;
+    int nsm = 0;
+};
+
+namespace {
+
+ih_status fail(ih_ctx *ctx, ih_status s, const char *fmt, ...)
+{
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->last_error = buf;
+    }
+    return s;
+}
+
+ih_status cuda_fail(ih_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, IH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T>
+cudaError_t pool_alloc(ih_ctx *ctx, T **p, size_t bytes, cudaStream_t st)
+{
+    void *v = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&v, bytes ? bytes : 16, ctx->pool, st);
+    *p = static_cast<T *>(v);
+    return e;
+}
+
+ih_status validate(ih_ctx *ctx, const ih_frame &f)
+{
+    if (f.height < 1 || f.width < 1) return fail(ctx, IH_EINVAL, "frame size %dx%d", f.height, f.width);
+    if ((int64_t)f.height * f.width > (int64_t)1 << 31)
+        return fail(ctx, IH_EINVAL, "frame of %d x %d pixels is above 2^31", f.height, f.width);
+    if (f.channels < 1 || f.channels > kMaxChannels)
+        return fail(ctx, IH_EINVAL, "channels = %d (1..%d)", f.channels, kMaxChannels);
+    if (!f.chan || !f.d_pixels) return fail(ctx, IH_EINVAL, "NULL chan or pixels");
+    if (f.pitch_bytes < f.width) return fail(ctx, IH_EINVAL, "pitch_bytes %lld < width", (long long)f.pitch_bytes);
+    if (f.input != IH_INPUT_PLANES && f.input != IH_INPUT_RGB_FEATURES)
+        return fail(ctx, IH_EINVAL, "input kind %d", f.input);
+    if (f.input == IH_INPUT_RGB_FEATURES && f.channels != 7)
+        return fail(ctx, IH_EINVAL, "IH_INPUT_RGB_FEATURES needs 7 channels");
+    if (f.layout != IH_LAYOUT_BIN_MAJOR) return fail(ctx, IH_EINVAL, "layout %d", f.layout);
+    for (int c = 0; c < f.channels; ++c) {
+        if (f.chan[c].bins < 1 || f.chan[c].bins > 256)
+            return fail(ctx, IH_EINVAL, "channel %d bins = %d (1..256)", c, f.chan[c].bins);
+        if (f.chan[c].mode != IH_BIN_UNIFORM8 && f.chan[c].mode != IH_BIN_INDEX)
+            return fail(ctx, IH_EINVAL, "channel %d mode = %d", c, f.chan[c].mode);
+    }
+    if (f.weighted_channel < -1 || f.weighted_channel >= f.channels)
+        return fail(ctx, IH_EINVAL, "weighted_channel = %d", f.weighted_channel);
+    return IH_OK;
+}
+
+// Bin groups: split each channel's bins evenly into groups of <= cap.
+int make_groups(const int *bins, int nchan, int cap, GroupDev *out, int max_out)
+{
+    int n = 0;
+    for (int c = 0; c < nchan; ++c) {
+        const int ng = (bins[c] + cap - 1) / cap;
+        for (int g = 0; g < ng; ++g) {
+            if (n >= max_out) return -1;
+            const int lo = bins[c] * g / ng, hi = bins[c] * (g + 1) / ng;
+            out[n].chan = (int16_t)c;
+            out[n].b_lo = (int16_t)lo;
+            out[n].nb = (int16_t)(hi - lo);
+            out[n].pad = 0;
+            ++n;
+        }
+    }
+    return n;
+}
+
+// Enqueue one plane set (counts over `chans`, or one moment kind over the
+// weighted channel) with its scratch carries.
+ih_status run_plane_set(ih_ctx *ctx, PlaneSet &ps, int kind, cudaStream_t st)
+{
+    const int nbpg = (kind == WK_ONE) ? 8 : 4;
+    const size_t el = (kind == WK_ONE) ? 4 : 8;
+    int bins[kMaxChannels];
+    for (int c = 0; c < ps.nchan; ++c) bins[c] = ps.chan[c].bins;
+    ps.ngroups = make_groups(bins, ps.nchan, nbpg, ps.grp, kMaxGroups);
+    ps.npgroups = make_groups(bins, ps.nchan, kind == WK_ONE ? 32 : 16, ps.pgrp, kMaxGroups);
+    if (ps.ngroups < 0 || ps.npgroups < 0) return fail(ctx, IH_EINVAL, "too many bins for one build");
+    const TileGrid &g = ps.g;
+    void *scratch = nullptr;
+    ps.colsum = ps.rowsum = ps.tilesum = ps.corner = nullptr;
+    if ((int64_t)g.nb * g.ns > 1) {
+        const size_t a = el * ps.B * (size_t)g.W * g.nb;
+        const size_t b = el * ps.B * (size_t)g.H * g.ns;
+        const size_t c = el * ps.B * (size_t)g.nb * g.ns;
+        const size_t a16 = (a + 255) & ~size_t(255), b16 = (b + 255) & ~size_t(255), c16 = (c + 255) & ~size_t(255);
+        cudaError_t e = pool_alloc(ctx, &scratch, a16 + b16 + 2 * c16, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
+        char *s = static_cast<char *>(scratch);
+        ps.colsum = s;
+        ps.rowsum = s + a16;
+        ps.tilesum = s + a16 + b16;
+        ps.corner = s + a16 + b16 + c16;
+    }
+    const int n = launch_plane_set(ps, kind, nbpg, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    if (n < 0) return cuda_fail(ctx, cudaGetLastError(), "build launch");
+    ctx->launches += n;
+    return IH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ih_status ih_create(const ih_config *cfg, ih_ctx **out)
+{
+    if (!cfg || !out) return IH_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) return IH_EINVAL;
+    ih_ctx *ctx = new ih_ctx();
+    ctx->device = cfg->device;
+    ctx->budget = cfg->hbm_budget_bytes;
+    DevGuard dg(ctx->device);
+    cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = ctx->device;
+    cudaError_t e = cudaMemPoolCreate(&ctx->pool, &props);
+    if (e == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        e = cudaMalloc(&ctx->d_err, sizeof(int));
+    }
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+        delete ctx;
+        return IH_ECUDA;
+    }
+    *out = ctx;
+    return IH_OK;
+}
+
+ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_handles, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!frames || !out_handles || n < 1) return fail(ctx, IH_EINVAL, "ih_build: bad arguments");
+    DevGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // host validation and budget of all frames first: all or nothing
+    uint64_t need = 0;
+    std::vector<FrameRec> recs(n);
+    for (int k = 0; k < n; ++k) {
+        const ih_frame &f = frames[k];
+        ih_status s = validate(ctx, f);
+        if (s != IH_OK) return s;
+        FrameRec &fr = recs[k];
+        fr.H = f.height;
+        fr.W = f.width;
+        fr.nchan = f.channels;
+        fr.P = (f.width + 3) & ~3;
+        int off = 0;
+        for (int c = 0; c < f.channels; ++c) {
+            fr.bins[c] = f.chan[c].bins;
+            fr.bin_off[c] = off;
+            off += f.chan[c].bins;
+        }
+        fr.B = off;
+        fr.wch = f.weighted_channel;
+        fr.Bw = fr.wch >= 0 ? fr.bins[fr.wch] : 0;
+        fr.count_bytes = (int64_t)fr.B * fr.H * fr.P * 4;
+        fr.moment_bytes = (int64_t)4 * fr.Bw * fr.H * fr.P * 8;
+        need += fr.count_bytes + fr.moment_bytes;
+    }
+    if (ctx->budget && ctx->used + need > ctx->budget)
+        return fail(ctx, IH_EBUDGET, "ih_build: %llu bytes live + %llu needed > budget %llu",
+                    (unsigned long long)ctx->used, (unsigned long long)need,
+                    (unsigned long long)ctx->budget);
+    for (int k = 0; k < n; ++k) {
+        const ih_frame &f = frames[k];
+        FrameRec &fr = recs[k];
+        cudaError_t e = pool_alloc(ctx, &fr.d_ih, fr.count_bytes, st);
+        if (e == cudaSuccess && fr.Bw) e = pool_alloc(ctx, &fr.d_mom, fr.moment_bytes, st);
+        if (e != cudaSuccess) {
+            if (fr.d_ih) cudaFreeAsync(fr.d_ih, st);
+            for (int kk = 0; kk < k; ++kk) {
+                cudaFreeAsync(recs[kk].d_ih, st);
+                if (recs[kk].d_mom) cudaFreeAsync(recs[kk].d_mom, st);
+            }
+            return cuda_fail(ctx, e, "tensor allocation");
+        }
+        // channel planes
+        const uint8_t *planes[kMaxChannels];
+        uint8_t *feat = nullptr;
+        int64_t cpitch[kMaxChannels];
+        const int64_t plane_stride = (int64_t)f.height * f.pitch_bytes;
+        if (f.input == IH_INPUT_RGB_FEATURES) {
+            const int64_t fp = (f.width + 15) & ~15;
+            e = pool_alloc(ctx, &feat, (size_t)4 * fp * f.height, st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "feature scratch allocation");
+            const uint8_t *R = f.d_pixels, *G = R + plane_stride, *Bp = G + plane_stride;
+            if (launch_features(R, G, Bp, f.pitch_bytes, f.height, f.width, nullptr, feat,
+                                feat + fp * f.height, fp, st) < 0)
+                return cuda_fail(ctx, cudaGetLastError(), "feature launch");
+            ctx->launches += 1;
+            for (int c = 0; c < 3; ++c) {
+                planes[c] = f.d_pixels + c * plane_stride;
+                cpitch[c] = f.pitch_bytes;
+            }
+            for (int c = 3; c < 7; ++c) {
+                planes[c] = feat + (c - 3) * fp * f.height;
+                cpitch[c] = fp;
+            }
+        } else {
+            for (int c = 0; c < f.channels; ++c) {
+                planes[c] = f.d_pixels + c * plane_stride;
+                cpitch[c] = f.pitch_bytes;
+            }
+        }
+        // counts over all channels
+        PlaneSet ps;
+        memset(&ps, 0, sizeof ps);
+        ps.g = choose_grid(fr.H, fr.W, fr.B, WK_ONE, ctx->nsm);
+        ps.g.P = fr.P;
+        ps.B = fr.B;
+        ps.nchan = fr.nchan;
+        for (int c = 0; c < fr.nchan; ++c) {
+            ps.chan[c].plane = planes[c];
+            ps.chan[c].pitch = cpitch[c];
+            ps.chan[c].bins = f.chan[c].bins;
+            ps.chan[c].mode = f.chan[c].mode;
+            ps.chan[c].bin_off = fr.bin_off[c];
+        }
+        ps.out = fr.d_ih;
+        ih_status s = run_plane_set(ctx, ps, WK_ONE, st);
+        // moment planes of the weighted channel
+        for (int m = 0; s == IH_OK && fr.Bw && m < 4; ++m) {
+            static const int kinds[4] = {WK_COL, WK_ROW, WK_COL2, WK_ROW2};
+            PlaneSet pm;
+            memset(&pm, 0, sizeof pm);
+            pm.g = choose_grid(fr.H, fr.W, fr.Bw, kinds[m], ctx->nsm);
+            pm.g.P = fr.P;
+            pm.B = fr.Bw;
+            pm.nchan = 1;
+            pm.chan[0] = ps.chan[fr.wch];
+            pm.chan[0].bin_off = 0;
+            pm.out = fr.d_mom + (int64_t)m * fr.Bw * fr.H * fr.P;
+            s = run_plane_set(ctx, pm, kinds[m], st);
+        }
+        if (feat) cudaFreeAsync(feat, st);
+        if (s != IH_OK) return s;
+    }
+    // publish handles
+    for (int k = 0; k < n; ++k) {
+        int h = -1;
+        for (size_t i = 0; i < ctx->frames.size(); ++i)
+            if (!ctx->frames[i].live) {
+                h = (int)i;
+                break;
+            }
+        if (h < 0) {
+            h = (int)ctx->frames.size();
+            ctx->frames.emplace_back();
+        }
+        recs[k].live = true;
+        ctx->frames[h] = recs[k];
+        ctx->used += recs[k].count_bytes + recs[k].moment_bytes;
+        out_handles[k] = h;
+    }
+    return IH_OK;
+}
+
+static FrameRec *get_frame(ih_ctx *ctx, int32_t handle)
+{
+    if (handle < 0 || handle >= (int32_t)ctx->frames.size() || !ctx->frames[handle].live) return nullptr;
+    return &ctx->frames[handle];
+}
+
+ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, int64_t n, int32_t *d_out,
+                         void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    if (n < 0 || (n > 0 && (!d_rects || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_rects: bad arguments");
+    DevGuard dg(ctx->device);
+    CountView v{fr->d_ih, fr->B, fr->H, fr->W, fr->P};
+    const int k = launch_query_rects(v, d_rects, n, d_out, ctx->d_err, static_cast<cudaStream_t>(stream));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_windows, int64_t n, uint32_t kernel,
+                            uint32_t flags, float *d_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    if (!fr->Bw) return fail(ctx, IH_EINVAL, "frame %d has no moment planes", handle);
+    if (kernel != IH_K_EPANECHNIKOV || (flags & ~(uint32_t)IH_NORMALIZE))
+        return fail(ctx, IH_EINVAL, "kernel %u / flags %u", kernel, flags);
+    if (n < 0 || (n > 0 && (!d_windows || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_weighted: bad arguments");
+    DevGuard dg(ctx->device);
+    MomentView v{fr->d_ih + (int64_t)fr->bin_off[fr->wch] * fr->H * fr->P, fr->d_mom, fr->Bw, fr->H, fr->W, fr->P};
+    const int k = launch_query_weighted(v, d_windows, n, (flags & IH_NORMALIZE) ? 1 : 0, d_out, ctx->d_err,
+                                        static_cast<cudaStream_t>(stream));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_release(ih_ctx *ctx, int32_t handle, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaFreeAsync(fr->d_ih, st);
+    if (fr->d_mom) cudaFreeAsync(fr->d_mom, st);
+    ctx->used -= fr->count_bytes + fr->moment_bytes;
+    *fr = FrameRec();
+    return IH_OK;
+}
+
+ih_status ih_sync(ih_ctx *ctx, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    DevGuard dg(ctx->device);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    int h = 0;
+    e = cudaMemcpy(&h, ctx->d_err, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "error word read");
+    if (h) {
+        cudaMemset(ctx->d_err, 0, sizeof(int));
+        if (h & 1) return fail(ctx, IH_EINVAL, "a query named a rectangle outside the frame or empty");
+        return fail(ctx, IH_ETIMEOUT, "a device-side wait gave up");
+    }
+    return IH_OK;
+}
+
+ih_status ih_info(ih_ctx *ctx, int32_t handle, ih_frame_info *out)
+{
+    if (!ctx || !out) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    out->height = fr->H;
+    out->width = fr->W;
+    out->channels = fr->nchan;
+    out->total_bins = fr->B;
+    out->weighted_channel = fr->wch;
+    out->weighted_bins = fr->Bw;
+    out->pitch_elems = fr->P;
+    out->count_bytes = fr->count_bytes;
+    out->moment_bytes = fr->moment_bytes;
+    return IH_OK;
+}
+
+ih_status ih_export(ih_ctx *ctx, int32_t handle, int32_t *d_dst, void *stream)
+{
+    if (!ctx || !d_dst) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    DevGuard dg(ctx->device);
+    cudaError_t e = cudaMemcpy2DAsync(d_dst, (size_t)fr->W * 4, fr->d_ih, (size_t)fr->P * 4, (size_t)fr->W * 4,
+                                      (size_t)fr->B * fr->H, cudaMemcpyDeviceToDevice,
+                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? IH_OK : cuda_fail(ctx, e, "export copy");
+}
+
+ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t *d_dst, void *stream)
+{
+    if (!ctx || !d_dst) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    if (!fr->Bw || plane < 0 || plane > 3) return fail(ctx, IH_EINVAL, "no moment plane %d", plane);
+    DevGuard dg(ctx->device);
+    const int64_t *src = fr->d_mom + (int64_t)plane * fr->Bw * fr->H * fr->P;
+    cudaError_t e = cudaMemcpy2DAsync(d_dst, (size_t)fr->W * 8, src, (size_t)fr->P * 8, (size_t)fr->W * 8,
+                                      (size_t)fr->Bw * fr->H, cudaMemcpyDeviceToDevice,
+                                      static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? IH_OK : cuda_fail(ctx, e, "export copy");
+}
+
+ih_status ih_features(ih_ctx *ctx, const uint8_t *d_rgb, int32_t height, int32_t width, int64_t pitch_bytes,
+                      uint8_t *d_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!d_rgb || !d_out || height < 1 || width < 1 || pitch_bytes < width)
+        return fail(ctx, IH_EINVAL, "ih_features: bad arguments");
+    DevGuard dg(ctx->device);
+    const int64_t ps = (int64_t)height * pitch_bytes, po = (int64_t)height * width;
+    if (launch_features(d_rgb, d_rgb + ps, d_rgb + 2 * ps, pitch_bytes, height, width, d_out, d_out + 3 * po,
+                        d_out + 4 * po, width, static_cast<cudaStream_t>(stream)) < 0)
+        return cuda_fail(ctx, cudaGetLastError(), "feature launch");
+    ctx->launches += 1;
+    return IH_OK;
+}
+
+ih_status ih_destroy(ih_ctx *ctx)
+{
+    if (!ctx) return IH_OK;
+    {
+        std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+        DevGuard dg(ctx->device);
+        cudaDeviceSynchronize();
+        for (auto &f : ctx->frames)
+            if (f.live) {
+                cudaFreeAsync(f.d_ih, 0);
+                if (f.d_mom) cudaFreeAsync(f.d_mom, 0);
+            }
+        cudaDeviceSynchronize();
+        if (ctx->d_err) cudaFree(ctx->d_err);
+        if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+    }
+    delete ctx;
+    return IH_OK;
+}
+
+int64_t ih_launch_count(ih_ctx *ctx)
+{
+    if (!ctx) return 0;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    return ctx->launches;
+}
+
+const char *ih_last_error(ih_ctx *ctx)
+{
+    if (!ctx) return "NULL context";
+    return ctx->last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// k_features.cu -- the tracker's feature channels from planar RGB.
+//
+// Intensity I = floor((R+G+B)/3) (Eq. 2.33) and, for central-difference
+// steps s = 1, 2, 4 with replicated borders, the unsigned gradient
+// orientation of I quantised into 9 bins of 20 degrees (the orientation
+// channel of Fig. 2.3 / Algorithm 2, at three cell levels).
+//
+// The orientation bin is decided without trigonometry: after folding the
+// gradient into the upper half plane, theta >= 20j degrees iff the cross
+// product of the unit vector at 20j degrees with (gx, gy) is >= 0, so the bin
+// is the number of the 8 inner boundaries the gradient lies at or beyond.
+// The unit vectors are scaled by 2^30 and rounded; for integer gradients in
+// [-255,255]^2 the angle to the nearest boundary is > 1e-5 rad, so the
+// products' sign (error < 2^-29 |g|, true magnitude > 1e-5 * 2^30 |g|) is
+// exact in int64.
+//
+// One CTA computes a 32 x 32 tile; it stages I for the tile plus a 4-pixel
+// halo in shared memory, clamping coordinates when it loads, which gives the
+// replicated borders.
+#include "ih_internal.cuh"
+
+namespace ih {
+
+namespace {
+
+constexpr int kT = 32, kHalo = 4, kS = kT + 2 * kHalo;
+
+// round(2^30 cos(20j deg)), round(2^30 sin(20j deg)), j = 1..8
+__constant__ long long kUx[8] = {1008987269LL, 822533958LL, 536870912LL, 186453311LL,
+                                 -186453311LL, -536870912LL, -822533958LL, -1008987269LL};
+__constant__ long long kUy[8] = {367241333LL, 690187940LL, 929887697LL, 1057429273LL,
+                                 1057429273LL, 929887697LL, 690187940LL, 367241333LL};
+
+__device__ __forceinline__ int orientation_bin9(int gx, int gy)
+{
+    if (gy < 0 || (gy == 0 && gx < 0)) {
+        gx = -gx;
+        gy = -gy;
+    }
+    if ((gx | gy) == 0) return 0;
+    int b = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) b += (kUx[k] * gy - kUy[k] * gx >= 0) ? 1 : 0;
+    return b;
+}
+
+__global__ void __launch_bounds__(256) k_features(const uint8_t *__restrict__ pr,
+                                                  const uint8_t *__restrict__ pg,
+                                                  const uint8_t *__restrict__ pb, int64_t pitch,
+                                                  int H, int W, uint8_t *out_rgb, uint8_t *out_i,
+                                                  uint8_t *out_hog, int64_t opitch)
+{
+    __shared__ uint8_t sI[kS][kS + 4];
+    const int r0 = blockIdx.y * kT, c0 = blockIdx.x * kT;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int k = tid; k < kS * kS; k += blockDim.x * blockDim.y) {
+        const int sr = k / kS, sc = k % kS;
+        const int r = min(max(r0 - kHalo + sr, 0), H - 1);
+        const int c = min(max(c0 - kHalo + sc, 0), W - 1);
+        const int64_t o = (int64_t)r * pitch + c;
+        sI[sr][sc] = (uint8_t)(((int)__ldg(pr + o) + (int)__ldg(pg + o) + (int)__ldg(pb + o)) / 3);
+    }
+    __syncthreads();
+    const int64_t plane = (int64_t)H * opitch;
+    for (int rr = threadIdx.y; rr < kT; rr += blockDim.y) {
+        const int r = r0 + rr, c = c0 + threadIdx.x;
+        if (r >= H || c >= W) continue;
+        const int sr = rr + kHalo, sc = threadIdx.x + kHalo;
+        const int64_t o = (int64_t)r * opitch + c;
+        out_i[o] = sI[sr][sc];
+#pragma unroll
+        for (int l = 0; l < 3; ++l) {
+            const int s = 1 << l;
+            // clamped neighbours: the halo already holds replicated borders,
+            // but a neighbour past the frame edge must read the edge pixel
+            const int cl = max(c - s, 0) - c0 + kHalo, cr = min(c + s, W - 1) - c0 + kHalo;
+            const int ru = max(r - s, 0) - r0 + kHalo, rd = min(r + s, H - 1) - r0 + kHalo;
+            const int gx = (int)sI[sr][cr] - (int)sI[sr][cl];
+            const int gy = (int)sI[rd][sc] - (int)sI[ru][sc];
+            out_hog[l * plane + o] = (uint8_t)orientation_bin9(gx, gy);
+        }
+        if (out_rgb) {
+            const int64_t oi = (int64_t)r * pitch + c;
+            out_rgb[o] = __ldg(pr + oi);
+            out_rgb[plane + o] = __ldg(pg + oi);
+            out_rgb[2 * plane + o] = __ldg(pb + oi);
+        }
+    }
+}
+
+}  // namespace
+
+int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_t pitch, int H,
+                    int W, uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog, int64_t out_pitch,
+                    cudaStream_t st)
+{
+    dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT);
+    k_features<<<grid, dim3(kT, 8), 0, st>>>(r, g, b, pitch, H, W, out_rgb, out_i, out_hog, out_pitch);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace ih

@@ -1,0 +1,140 @@
+// k_query.cu -- O(1) region queries on a built integral histogram.
+//
+// Rectangle histograms by the four-corner rule of Eq. 2.16 and spatially
+// weighted local histograms (Eq. 3.1) from the moment planes of Eq. 3.4.
+//
+// Weighted histogram, Epanechnikov window kernel.  For window
+// [r0,r1] x [c0,c1] with w = c1-c0+1, h = r1-r0+1, mc = c0+c1, mr = r0+r1:
+//     k(r,c) = 1 - (2c-mc)^2 / (2w^2) - (2r-mr)^2 / (2h^2)
+// so for bin b, with N, Sc, Sr, Scc, Srr the four-corner sums of the count
+// plane and of the planes weighted by c, r, c^2, r^2:
+//     X2 = sum (2c-mc)^2 = 4 Scc - 4 mc Sc + mc^2 N      (exact int64)
+//     Y2 = sum (2r-mr)^2 = 4 Srr - 4 mr Sr + mr^2 N
+//     S_b = N - X2/(2w^2) - Y2/(2h^2).
+// The integer parts of the two quotients are taken exactly; the remaining
+// fraction (< 2) is an exact uint64 ratio; S_b is then an integer plus one
+// fraction in (0,1] and is rounded to float with at most a few roundings
+// (relative error < 4e-7).  No step needs FP64.
+// The window's total weight has the closed form
+//     K = (4 w^2 h^2 + w^2 + h^2) / (6 w h),
+// used by IH_NORMALIZE.
+#include "ih_internal.cuh"
+
+namespace ih {
+
+namespace {
+
+__device__ __forceinline__ bool box_ok(int r0, int c0, int r1, int c1, int H, int W)
+{
+    return r0 >= 0 && c0 >= 0 && r0 <= r1 && c0 <= c1 && r1 < H && c1 < W;
+}
+
+template <typename T>
+__device__ __forceinline__ long long four_corner(const T *p, int64_t P, int r0, int c0, int r1, int c1)
+{
+    const long long a = __ldg(p + (int64_t)r1 * P + c1);
+    const long long b = r0 > 0 ? (long long)__ldg(p + (int64_t)(r0 - 1) * P + c1) : 0;
+    const long long c = c0 > 0 ? (long long)__ldg(p + (int64_t)r1 * P + (c0 - 1)) : 0;
+    const long long d = (r0 > 0 && c0 > 0) ? (long long)__ldg(p + (int64_t)(r0 - 1) * P + (c0 - 1)) : 0;
+    return a - b - c + d;
+}
+
+__global__ void __launch_bounds__(256) k_query_rects(const CountView v, const int32_t *__restrict__ rects,
+                                                     int64_t n, int32_t *__restrict__ out, int *err)
+{
+    const int64_t total = n * v.B;
+    const int64_t plane = (int64_t)v.H * v.P;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = t / v.B;
+        const int b = (int)(t - qi * v.B);
+        const int r0 = __ldg(rects + 4 * qi), c0 = __ldg(rects + 4 * qi + 1);
+        const int r1 = __ldg(rects + 4 * qi + 2), c1 = __ldg(rects + 4 * qi + 3);
+        if (!box_ok(r0, c0, r1, c1, v.H, v.W)) {
+            out[t] = -1;
+            if (b == 0) atomicOr(err, 1);
+            continue;
+        }
+        out[t] = (int32_t)four_corner(v.d + b * plane, v.P, r0, c0, r1, c1);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_query_weighted(const MomentView v, const int32_t *__restrict__ wins,
+                                                        int64_t n, int normalize, float *__restrict__ out,
+                                                        int *err)
+{
+    const int64_t total = n * v.Bw;
+    const int64_t plane = (int64_t)v.H * v.P;
+    const int64_t mplane = (int64_t)v.Bw * plane;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t qi = t / v.Bw;
+        const int b = (int)(t - qi * v.Bw);
+        const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
+        const int r1 = __ldg(wins + 4 * qi + 2), c1 = __ldg(wins + 4 * qi + 3);
+        if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= 32768 || c1 - c0 >= 32768) {
+            out[t] = -1.0f;
+            if (b == 0) atomicOr(err, 1);
+            continue;
+        }
+        const long long N = four_corner(v.n + b * plane, v.P, r0, c0, r1, c1);
+        const int64_t mo = b * plane;
+        const long long Sc = four_corner(v.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Sr = four_corner(v.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Scc = four_corner(v.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Srr = four_corner(v.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
+        const long long mc = c0 + c1, mr = r0 + r1;
+        const long long X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
+        const long long Y2 = 4 * Srr - 4 * mr * Sr + mr * mr * N;
+        const long long A = 2 * w * w, Bh = 2 * h * h;
+        const long long qx = X2 / A, rx = X2 - qx * A;
+        const long long qy = Y2 / Bh, ry = Y2 - qy * Bh;
+        long long I = N - qx - qy;
+        unsigned long long F = (unsigned long long)rx * (unsigned long long)Bh +
+                               (unsigned long long)ry * (unsigned long long)A;
+        const unsigned long long Den = (unsigned long long)A * (unsigned long long)Bh;
+        if (F >= Den) {
+            I -= 1;
+            F -= Den;
+        }
+        // S = I - F/Den, with S > 0 whenever N > 0, so I >= 1 when F > 0
+        float s;
+        if (F == 0)
+            s = (float)I;
+        else
+            s = (float)(I - 1) + (float)(Den - F) / (float)Den;
+        if (normalize) {
+            const float K = (4.0f * (float)(w * w) * (float)(h * h) + (float)(w * w) + (float)(h * h)) /
+                            (6.0f * (float)w * (float)h);
+            s = s / K;
+        }
+        out[t] = s;
+    }
+}
+
+unsigned grid_for(int64_t total)
+{
+    const int64_t b = (total + 255) / 256;
+    return (unsigned)(b < 152 * 32 ? (b > 0 ? b : 1) : 152 * 32);
+}
+
+}  // namespace
+
+int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out, int *err,
+                       cudaStream_t st)
+{
+    if (n == 0) return 0;
+    k_query_rects<<<grid_for(n * v.B), 256, 0, st>>>(v, rects, n, out, err);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_query_weighted(const MomentView &v, const int32_t *wins, int64_t n, int normalize, float *out,
+                          int *err, cudaStream_t st)
+{
+    if (n == 0) return 0;
+    k_query_weighted<<<grid_for(n * v.Bw), 256, 0, st>>>(v, wins, n, normalize, out, err);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+}  // namespace ih

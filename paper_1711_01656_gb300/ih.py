@@ -1,0 +1,224 @@
+"""Python binding of the C ABI in include/ih.h (ctypes; argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device buffers
+are torch CUDA tensors; streams default to torch's current stream.  Every
+step of the integral-histogram path runs in the CUDA library ``libih.so``:
+this module computes nothing, and it raises if the library is missing
+rather than falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libih.so")
+
+IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT = range(7)
+IH_BIN_UNIFORM8, IH_BIN_INDEX = 0, 1
+IH_INPUT_PLANES, IH_INPUT_RGB_FEATURES = 0, 1
+IH_LAYOUT_BIN_MAJOR = 0
+IH_K_EPANECHNIKOV = 0
+IH_NORMALIZE = 1
+
+STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: "IH_ECUDA",
+                5: "IH_ETIMEOUT", 6: "IH_ENOTBUILT"}
+
+# The exported C symbols (include/ih.h), checked by the test suite.
+C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih_destroy",
+             "ih_release", "ih_sync", "ih_info", "ih_export", "ih_export_moments", "ih_features",
+             "ih_launch_count", "ih_last_error")
+
+
+class IHError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class ih_channel(ctypes.Structure):
+    _fields_ = [("bins", ctypes.c_int32), ("mode", ctypes.c_int32)]
+
+
+class ih_frame(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int32), ("width", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("input", ctypes.c_int32), ("chan", ctypes.POINTER(ih_channel)),
+                ("d_pixels", ctypes.c_void_p), ("pitch_bytes", ctypes.c_int64),
+                ("weighted_channel", ctypes.c_int32), ("layout", ctypes.c_int32)]
+
+
+class ih_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
+                ("flags", ctypes.c_uint32)]
+
+
+class ih_frame_info(ctypes.Structure):
+    _fields_ = [("height", ctypes.c_int32), ("width", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("total_bins", ctypes.c_int32), ("weighted_channel", ctypes.c_int32),
+                ("weighted_bins", ctypes.c_int32), ("pitch_elems", ctypes.c_int64),
+                ("count_bytes", ctypes.c_int64), ("moment_bytes", ctypes.c_int64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libih.so (built by __graft_entry__.build()); raise if it is absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise ImportError("libih.so not found at %s: build it with __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        p, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        sig = {
+            "ih_create": ([ctypes.POINTER(ih_config), ctypes.POINTER(p)], i32),
+            "ih_build": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(i32), p], i32),
+            "ih_query_rects": ([p, i32, p, i64, p, p], i32),
+            "ih_query_weighted": ([p, i32, p, i64, u32, u32, p, p], i32),
+            "ih_destroy": ([p], i32),
+            "ih_release": ([p, i32, p], i32),
+            "ih_sync": ([p, p], i32),
+            "ih_info": ([p, i32, ctypes.POINTER(ih_frame_info)], i32),
+            "ih_export": ([p, i32, p, p], i32),
+            "ih_export_moments": ([p, i32, i32, p, p], i32),
+            "ih_features": ([p, p, i32, i32, i64, p, p], i32),
+            "ih_launch_count": ([p], i64),
+            "ih_last_error": ([p], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+        return lib
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _check(ctx, status):
+    if status != IH_OK:
+        msg = load_library().ih_last_error(ctx).decode() if ctx else ""
+        raise IHError(status, msg)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+# ---------------------------------------------------------------- contexts
+
+def ih_create(device: int = 0, hbm_budget_bytes: int = 0):
+    lib = load_library()
+    cfg = ih_config(int(device), int(hbm_budget_bytes), 0)
+    out = ctypes.c_void_p()
+    st = lib.ih_create(ctypes.byref(cfg), ctypes.byref(out))
+    if st != IH_OK:
+        raise IHError(st, "ih_create(device=%d)" % device)
+    return out
+
+
+def ih_destroy(ctx):
+    _check(None, load_library().ih_destroy(ctx))
+
+
+class Frame:
+    """One frame to build: `pixels` is a uint8 CUDA tensor of shape (P, H, W)
+    (P planes; rows may be padded: stride(1) is the row pitch); `channels` a
+    list of (bins, mode) pairs, one per binned channel."""
+
+    def __init__(self, pixels, channels, input=IH_INPUT_PLANES, weighted_channel=-1,
+                 layout=IH_LAYOUT_BIN_MAJOR):
+        if pixels.dtype.itemsize != 1 or pixels.dim() != 3 or not pixels.is_cuda:
+            raise ValueError("pixels must be a (planes, H, W) uint8 CUDA tensor")
+        if pixels.stride(2) != 1 or pixels.stride(0) != pixels.shape[1] * pixels.stride(1):
+            raise ValueError("pixels: planes must be H rows of a common pitch")
+        self.pixels = pixels
+        self.channels = [(int(b), int(m)) for b, m in channels]
+        self.input = int(input)
+        self.weighted_channel = int(weighted_channel)
+        self.layout = int(layout)
+
+    def _c(self):
+        arr = (ih_channel * len(self.channels))(*[ih_channel(b, m) for b, m in self.channels])
+        f = ih_frame(self.pixels.shape[1], self.pixels.shape[2], len(self.channels), self.input,
+                     ctypes.cast(arr, ctypes.POINTER(ih_channel)), self.pixels.data_ptr(),
+                     self.pixels.stride(1), self.weighted_channel, self.layout)
+        return f, arr
+
+
+def ih_build(ctx, frames, stream=None):
+    """Build each Frame; returns the list of handles."""
+    if isinstance(frames, Frame):
+        frames = [frames]
+    cs = [f._c() for f in frames]
+    arr = (ih_frame * len(cs))(*[c[0] for c in cs])
+    handles = (ctypes.c_int32 * len(cs))()
+    _check(ctx, load_library().ih_build(ctx, arr, len(cs), handles, _stream(stream)))
+    return list(handles)
+
+
+def ih_query_rects(ctx, handle, rects, out, stream=None):
+    """rects: (n, 4) int32 CUDA tensor; out: (n, B) int32 CUDA tensor."""
+    n = 0 if rects is None else rects.shape[0]
+    _check(ctx, load_library().ih_query_rects(ctx, int(handle), _ptr(rects), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_query_weighted(ctx, handle, windows, out, kernel=IH_K_EPANECHNIKOV, flags=0, stream=None):
+    """windows: (n, 4) int32 CUDA tensor; out: (n, B_w) float32 CUDA tensor."""
+    n = 0 if windows is None else windows.shape[0]
+    _check(ctx, load_library().ih_query_weighted(ctx, int(handle), _ptr(windows), n, int(kernel),
+                                                 int(flags), _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_release(ctx, handle, stream=None):
+    _check(ctx, load_library().ih_release(ctx, int(handle), _stream(stream)))
+
+
+def ih_sync(ctx, stream=None):
+    _check(ctx, load_library().ih_sync(ctx, _stream(stream)))
+
+
+def ih_info(ctx, handle):
+    info = ih_frame_info()
+    _check(ctx, load_library().ih_info(ctx, int(handle), ctypes.byref(info)))
+    return {k: getattr(info, k) for k, _ in ih_frame_info._fields_}
+
+
+def ih_export(ctx, handle, out, stream=None):
+    """out: (B, H, W) int32 CUDA tensor."""
+    _check(ctx, load_library().ih_export(ctx, int(handle), _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_export_moments(ctx, handle, plane, out, stream=None):
+    """out: (B_w, H, W) int64 CUDA tensor; plane 0..3 = weights c, r, c^2, r^2."""
+    _check(ctx, load_library().ih_export_moments(ctx, int(handle), int(plane), _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_features(ctx, rgb, out, stream=None):
+    """rgb: (3, H, W) uint8 CUDA tensor; out: (7, H, W) uint8 CUDA tensor."""
+    _check(ctx, load_library().ih_features(ctx, _ptr(rgb), rgb.shape[1], rgb.shape[2], rgb.stride(1),
+                                           _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_launch_count(ctx) -> int:
+    return int(load_library().ih_launch_count(ctx))
+
+
+def ih_last_error(ctx) -> str:
+    return load_library().ih_last_error(ctx).decode()

@@ -16,3 +16,21 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return os.path.join(ROOT, "tests", "golden")
+
+
+@pytest.fixture(scope="session")
+def ihlib():
+    """The built CUDA library (built on demand); a missing library fails."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1711_01656_gb300 import ih
+    return ih
+
+
+@pytest.fixture(scope="module")
+def ctx(ihlib):
+    import torch
+    assert torch.cuda.is_available(), "a gpu-marked test needs a CUDA device"
+    c = ihlib.ih_create(0)
+    yield c
+    ihlib.ih_destroy(c)

@@ -1,0 +1,350 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Counts, indices and int64 moment planes must be bit-exact; weighted
+histograms (FP32) within 1e-5 relative of the FP64 oracle and exactly 0
+where the oracle is 0.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1711_01656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+WTOL = 1e-5
+
+
+def _build(ih, ctx, planes, chans, weighted=-1, pitch=None):
+    planes = np.asarray(planes, dtype=np.uint8)
+    if planes.ndim == 2:
+        planes = planes[None]
+    p, h, w = planes.shape
+    if pitch is not None and pitch > w:
+        buf = torch.zeros((p, h, pitch), dtype=torch.uint8, device=DEV)
+        buf[:, :, :w] = torch.from_numpy(planes).to(DEV)
+        pix = buf[:, :, :w]
+    else:
+        pix = torch.from_numpy(planes).to(DEV)
+    hdl, = ih.ih_build(ctx, ih.Frame(pix, chans, weighted_channel=weighted))
+    return hdl, pix
+
+
+def _export(ih, ctx, hdl):
+    info = ih.ih_info(ctx, hdl)
+    out = torch.empty((info["total_bins"], info["height"], info["width"]), dtype=torch.int32, device=DEV)
+    ih.ih_export(ctx, hdl, out)
+    ih.ih_sync(ctx)
+    return out.cpu().numpy()
+
+
+def _assert_weighted(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    zero = ref == 0
+    assert np.array_equal(got[zero], ref[zero]), "non-zero where the oracle is 0"
+    rel = np.abs(got[~zero] - ref[~zero]) / np.abs(ref[~zero])
+    assert rel.size == 0 or rel.max() <= WTOL, "max rel err %g" % rel.max()
+
+
+# ---------------------------------------------------------------- counts
+
+
+SHAPES = [(1, 1), (1, 7), (7, 1), (2, 3), (37, 53), (33, 129), (64, 128), (65, 257), (130, 300),
+          (200, 611), (257, 1030)]
+
+
+@pytest.mark.parametrize("h,w", SHAPES)
+@pytest.mark.parametrize("bins", [1, 3, 16, 32])
+def test_counts_exact(ihlib, ctx, h, w, bins):
+    img = synth.uniform_plane(h, w, h * 1000 + w + bins)
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)])
+    got = _export(ihlib, ctx, hdl)
+    ih_ref = oracle.integral_histogram(img, bins)
+    assert np.array_equal(got, ih_ref)
+    ihlib.ih_release(ctx, hdl)
+
+
+@pytest.mark.parametrize("bins", [2, 7, 9, 40, 64, 200, 256])
+def test_counts_exact_bin_counts(ihlib, ctx, bins):
+    img = synth.blob_plane(150, 260, bins)
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)])
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.integral_histogram(img, bins))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_counts_index_mode_and_out_of_range(ihlib, ctx):
+    g = np.random.Generator(np.random.PCG64(5))
+    img = g.integers(0, 12, size=(90, 301)).astype(np.uint8)  # values 9..11 are in no bin
+    hdl, _ = _build(ihlib, ctx, img, [(9, 1)])
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.integral_histogram(img, 9, oracle.BIN_INDEX))
+    ihlib.ih_release(ctx, hdl)
+
+
+@pytest.mark.parametrize("pitch", [None, 301, 304, 512])
+def test_counts_pitched_input(ihlib, ctx, pitch):
+    img = synth.uniform_plane(77, 299, 3)
+    hdl, _ = _build(ihlib, ctx, img, [(16, 0)], pitch=pitch)
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.integral_histogram(img, 16))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_counts_multichannel(ihlib, ctx):
+    h, w = 123, 517
+    planes = np.stack([synth.uniform_plane(h, w, 10 + k) for k in range(4)])
+    planes[3] %= 9
+    chans = [(16, 0), (5, 0), (32, 0), (9, 1)]
+    hdl, _ = _build(ihlib, ctx, planes, chans)
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.frame_integral_histogram(planes, chans))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_counts_deterministic(ihlib, ctx):
+    img = synth.uniform_plane(300, 700, 1)
+    a, _ = _build(ihlib, ctx, img, [(16, 0)])
+    b, _ = _build(ihlib, ctx, img, [(16, 0)])
+    assert np.array_equal(_export(ihlib, ctx, a), _export(ihlib, ctx, b))
+    ihlib.ih_release(ctx, a)
+    ihlib.ih_release(ctx, b)
+
+
+# ---------------------------------------------------------------- features
+
+
+def _plus_pattern_rgb():
+    """A gray image whose 3x3 blocks realise every integer gradient
+    (gx, gy) in [-255,255]^2 at step 1 in their centre pixel."""
+    n = 511
+    img = np.zeros((3 * n, 3 * n), np.uint8)
+    g = np.arange(-255, 256)
+    gx, gy = np.meshgrid(g, g, indexing="ij")
+    cr = 3 * np.arange(n)[:, None] + 1 + np.zeros((1, n), int)
+    cc = 3 * np.arange(n)[None, :] + 1 + np.zeros((n, 1), int)
+    left = np.maximum(0, -gx)
+    up = np.maximum(0, -gy)
+    img[cr, cc - 1] = left
+    img[cr, cc + 1] = left + gx
+    img[cr - 1, cc] = up
+    img[cr + 1, cc] = up + gy
+    img[cr, cc] = 100
+    return np.stack([img, img, img]), gx, gy
+
+
+def test_features_exhaustive_orientations(ihlib, ctx):
+    rgb, gx, gy = _plus_pattern_rgb()
+    d = torch.from_numpy(rgb).to(DEV)
+    out = torch.empty((7,) + rgb.shape[1:], dtype=torch.uint8, device=DEV)
+    ihlib.ih_features(ctx, d, out)
+    ihlib.ih_sync(ctx)
+    got = out.cpu().numpy()
+    ref = oracle.features(rgb)
+    assert np.array_equal(got, ref)
+    # every one of the 261,121 gradients occurs at a block centre
+    centres = got[4][1::3, 1::3]
+    exp = np.vectorize(oracle.orientation_bin)(gx, gy)
+    assert np.array_equal(centres, exp)
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (3, 2), (5, 9), (33, 31), (100, 257), (1080, 1920)])
+def test_features_exact(ihlib, ctx, h, w):
+    rgb = synth.blob_rgb(h, w, h + w)
+    d = torch.from_numpy(rgb).to(DEV)
+    out = torch.empty((7, h, w), dtype=torch.uint8, device=DEV)
+    ihlib.ih_features(ctx, d, out)
+    ihlib.ih_sync(ctx)
+    assert np.array_equal(out.cpu().numpy(), oracle.features(rgb))
+
+
+def test_rgb_feature_frame_build(ihlib, ctx):
+    h, w = 130, 270
+    rgb = synth.blob_rgb(h, w, 2)
+    chans = synth.FMV_CHANNELS
+    hdl, = ihlib.ih_build(ctx, ihlib.Frame(torch.from_numpy(rgb).to(DEV), chans,
+                                           input=ihlib.IH_INPUT_RGB_FEATURES))
+    ref = oracle.frame_integral_histogram(oracle.features(rgb), chans)
+    assert np.array_equal(_export(ihlib, ctx, hdl), ref)
+    ihlib.ih_release(ctx, hdl)
+
+
+# ---------------------------------------------------------------- rect queries
+
+
+def _rects_gpu(ihlib, ctx, hdl, rects, B):
+    d_r = torch.from_numpy(np.ascontiguousarray(rects, dtype=np.int32)).to(DEV)
+    out = torch.empty((len(rects), B), dtype=torch.int32, device=DEV)
+    ihlib.ih_query_rects(ctx, hdl, d_r, out)
+    return out
+
+
+def test_rects_all_of_small_frame(ihlib, ctx):
+    h, w, bins = 14, 19, 5
+    img = synth.uniform_plane(h, w, 4)
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)])
+    rects = np.array([(r0, c0, r1, c1) for r0 in range(h) for r1 in range(r0, h)
+                      for c0 in range(w) for c1 in range(c0, w)], np.int32)
+    got = _rects_gpu(ihlib, ctx, hdl, rects, bins)
+    ihlib.ih_sync(ctx)
+    assert np.array_equal(got.cpu().numpy(), oracle.rect_hist(img, bins, rects))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_rects_invalid_rows_and_status(ihlib, ctx):
+    img = synth.uniform_plane(20, 30, 4)
+    hdl, _ = _build(ihlib, ctx, img, [(4, 0)])
+    rects = np.array([[0, 0, 19, 29], [-1, 0, 3, 3], [0, 0, 20, 3], [5, 0, 4, 3], [0, 9, 3, 8], [0, 0, 3, 30]],
+                     np.int32)
+    got = _rects_gpu(ihlib, ctx, hdl, rects, 4)
+    with pytest.raises(ihlib.IHError) as ei:
+        ihlib.ih_sync(ctx)
+    assert ei.value.status == ihlib.IH_EINVAL
+    g = got.cpu().numpy()
+    assert (g[1:] == -1).all() and g[0].sum() == 600
+    ihlib.ih_sync(ctx)  # the error word was cleared
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_rects_empty_query(ihlib, ctx):
+    img = synth.uniform_plane(8, 8, 4)
+    hdl, _ = _build(ihlib, ctx, img, [(4, 0)])
+    out = torch.empty((0, 4), dtype=torch.int32, device=DEV)
+    ihlib.ih_query_rects(ctx, hdl, torch.empty((0, 4), dtype=torch.int32, device=DEV), out)
+    ihlib.ih_sync(ctx)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_plain_frame_640x480_all_rects(ihlib, ctx):
+    """One 640x480 uniform frame, 16 bins, 10,000 rectangles with uniform
+    corners: the full tensor and every query against the oracle."""
+    h, w = 480, 640
+    img = synth.uniform_plane(h, w, synth.config_seed(1))
+    rects = synth.rects_uniform_corners(h, w, 10000, synth.config_seed(1) + 100)
+    hdl, _ = _build(ihlib, ctx, img, [(16, 0)])
+    got = _rects_gpu(ihlib, ctx, hdl, rects, 16)
+    tens = _export(ihlib, ctx, hdl)
+    assert np.array_equal(tens, oracle.integral_histogram(img, 16, threads=8))
+    assert np.array_equal(got.cpu().numpy(), oracle.rect_hist(img, 16, rects))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_fmv_frame_1920x1080_features(ihlib, ctx):
+    """One 1920x1080 RGB frame, 7 feature channels (91 bins): the full
+    tensor vs Algorithm 5 and 100,000 rectangles (a seeded 2,000 by
+    enumeration, all by four corners of the oracle's own tensor)."""
+    h, w = 1080, 1920
+    rgb = synth.blob_rgb(h, w, synth.config_seed(2))
+    chans = synth.FMV_CHANNELS
+    B = sum(b for b, _ in chans)
+    hdl, = ihlib.ih_build(ctx, ihlib.Frame(torch.from_numpy(rgb).to(DEV), chans,
+                                           input=ihlib.IH_INPUT_RGB_FEATURES))
+    rects = synth.rects_uniform_corners(h, w, 100000, synth.config_seed(2) + 100)
+    got = _rects_gpu(ihlib, ctx, hdl, rects, B).cpu().numpy()
+    tens = _export(ihlib, ctx, hdl)
+    feats = oracle.features(rgb)
+    ref = oracle.frame_integral_histogram(feats, chans, threads=8)
+    assert np.array_equal(tens, ref)
+    P = np.pad(ref.astype(np.int64), ((0, 0), (1, 0), (1, 0)))
+    r0, c0, r1, c1 = (rects[:, i] for i in range(4))
+    four = (P[:, r1 + 1, c1 + 1] - P[:, r0, c1 + 1] - P[:, r1 + 1, c0] + P[:, r0, c0]).T
+    assert np.array_equal(got, four)
+    sub = np.random.Generator(np.random.PCG64(9)).choice(len(rects), 2000, replace=False)
+    assert np.array_equal(got[sub], oracle.frame_rect_hist(feats, chans, rects[sub]))
+    ihlib.ih_release(ctx, hdl)
+
+
+# ---------------------------------------------------------------- moments + weighted
+
+
+@pytest.mark.parametrize("h,w,bins", [(1, 1, 2), (5, 7, 3), (64, 128, 16), (131, 389, 16), (260, 520, 8)])
+def test_moment_planes_exact(ihlib, ctx, h, w, bins):
+    img = synth.blob_plane(h, w, h + w)
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)], weighted=0)
+    for plane, wk in enumerate(oracle.MOMENT_WEIGHTS):
+        out = torch.empty((bins, h, w), dtype=torch.int64, device=DEV)
+        ihlib.ih_export_moments(ctx, hdl, plane, out)
+        ihlib.ih_sync(ctx)
+        ref = oracle.weighted_integral_histogram(img, bins, wk)
+        assert np.array_equal(out.cpu().numpy(), ref), "moment plane %d" % plane
+    ihlib.ih_release(ctx, hdl)
+
+
+def _weighted_gpu(ihlib, ctx, hdl, wins, Bw, normalize=False):
+    d = torch.from_numpy(np.ascontiguousarray(wins, dtype=np.int32)).to(DEV)
+    out = torch.empty((len(wins), Bw), dtype=torch.float32, device=DEV)
+    ihlib.ih_query_weighted(ctx, hdl, d, out, flags=ihlib.IH_NORMALIZE if normalize else 0)
+    ihlib.ih_sync(ctx)
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("normalize", [False, True])
+def test_weighted_vs_direct_sum(ihlib, ctx, normalize):
+    h, w = 300, 400
+    img = synth.blob_plane(h, w, 12)
+    hdl, _ = _build(ihlib, ctx, img, [(16, 0)], weighted=0)
+    wins = np.concatenate([synth.rects_side_range(h, w, 1500, 1, 64, 3),
+                           synth.rects_side_range(h, w, 100, 32, 256, 4),
+                           np.array([[0, 0, h - 1, w - 1], [0, 0, 0, 0], [h - 1, w - 1, h - 1, w - 1]])])
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, 16, normalize)
+    ref = oracle.weighted_hist(img, 16, wins, normalize=normalize)
+    _assert_weighted(got, ref)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_weighted_hand_example(ihlib, ctx):
+    img = np.array([[0, 200, 100], [255, 50, 130]], np.uint8)
+    hdl, _ = _build(ihlib, ctx, img, [(2, 0)], weighted=0)
+    got = _weighted_gpu(ihlib, ctx, hdl, [[0, 0, 1, 2]], 2)
+    assert np.allclose(got[0], [157 / 72, 157 / 72], rtol=1e-6, atol=0)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_weighted_on_feature_channel(ihlib, ctx):
+    h, w = 200, 330
+    rgb = synth.blob_rgb(h, w, 8)
+    chans = synth.FMV_CHANNELS
+    hdl, = ihlib.ih_build(ctx, ihlib.Frame(torch.from_numpy(rgb).to(DEV), chans,
+                                           input=ihlib.IH_INPUT_RGB_FEATURES, weighted_channel=3))
+    wins = synth.rects_side_range(h, w, 500, 2, 150, 5)
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, 16)
+    ref = oracle.weighted_hist(oracle.features(rgb)[3], 16, wins)
+    _assert_weighted(got, ref)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_weighted_requires_moments(ihlib, ctx):
+    img = synth.uniform_plane(10, 10, 1)
+    hdl, _ = _build(ihlib, ctx, img, [(4, 0)])
+    with pytest.raises(ihlib.IHError):
+        _weighted_gpu(ihlib, ctx, hdl, [[0, 0, 3, 3]], 4)
+    ihlib.ih_release(ctx, hdl)
+
+
+# ---------------------------------------------------------------- host-side errors
+
+
+def test_budget_refuses_and_builds_nothing(ihlib):
+    c = ihlib.ih_create(0, hbm_budget_bytes=1 << 20)
+    try:
+        img = torch.zeros((1, 512, 512), dtype=torch.uint8, device=DEV)
+        with pytest.raises(ihlib.IHError) as ei:
+            ihlib.ih_build(c, ihlib.Frame(img, [(16, 0)]))
+        assert ei.value.status == ihlib.IH_EBUDGET
+        small = torch.zeros((1, 64, 64), dtype=torch.uint8, device=DEV)
+        h, = ihlib.ih_build(c, ihlib.Frame(small, [(16, 0)]))
+        ihlib.ih_release(c, h)
+    finally:
+        ihlib.ih_destroy(c)
+
+
+def test_invalid_descriptors(ihlib, ctx):
+    img = torch.zeros((1, 8, 8), dtype=torch.uint8, device=DEV)
+    for chans in ([(0, 0)], [(257, 0)], [(4, 2)]):
+        with pytest.raises(ihlib.IHError) as ei:
+            ihlib.ih_build(ctx, ihlib.Frame(img, chans))
+        assert ei.value.status == ihlib.IH_EINVAL
+    with pytest.raises(ihlib.IHError) as ei:
+        ihlib.ih_build(ctx, ihlib.Frame(img, [(4, 0)], weighted_channel=1))
+    assert ei.value.status == ihlib.IH_EINVAL
+    with pytest.raises(ihlib.IHError) as ei:
+        ihlib.ih_query_rects(ctx, 12345, None, torch.empty(0, device=DEV))
+    assert ei.value.status == ihlib.IH_ENOTBUILT
