@@ -141,9 +141,14 @@ class Frame:
                  layout=IH_LAYOUT_BIN_MAJOR):
         if pixels.dtype.itemsize != 1 or pixels.dim() != 3 or not pixels.is_cuda:
             raise ValueError("pixels must be a (planes, H, W) uint8 CUDA tensor")
-        if pixels.stride(2) != 1 or pixels.stride(0) != pixels.shape[1] * pixels.stride(1):
-            raise ValueError("pixels: planes must be H rows of a common pitch")
+        planes, h, w = pixels.shape
+        pitch = pixels.stride(1) if h > 1 else w
+        ok = (pixels.stride(2) == 1 or w == 1) and pitch >= w and (planes == 1 or pixels.stride(0) == h * pitch)
+        if not ok:
+            pixels = pixels.contiguous()
+            pitch = w
         self.pixels = pixels
+        self.pitch = pitch
         self.channels = [(int(b), int(m)) for b, m in channels]
         self.input = int(input)
         self.weighted_channel = int(weighted_channel)
@@ -153,7 +158,7 @@ class Frame:
         arr = (ih_channel * len(self.channels))(*[ih_channel(b, m) for b, m in self.channels])
         f = ih_frame(self.pixels.shape[1], self.pixels.shape[2], len(self.channels), self.input,
                      ctypes.cast(arr, ctypes.POINTER(ih_channel)), self.pixels.data_ptr(),
-                     self.pixels.stride(1), self.weighted_channel, self.layout)
+                     self.pitch, self.weighted_channel, self.layout)
         return f, arr
 
 
@@ -211,7 +216,8 @@ def ih_export_moments(ctx, handle, plane, out, stream=None):
 
 def ih_features(ctx, rgb, out, stream=None):
     """rgb: (3, H, W) uint8 CUDA tensor; out: (7, H, W) uint8 CUDA tensor."""
-    _check(ctx, load_library().ih_features(ctx, _ptr(rgb), rgb.shape[1], rgb.shape[2], rgb.stride(1),
+    rgb = rgb.contiguous()
+    _check(ctx, load_library().ih_features(ctx, _ptr(rgb), rgb.shape[1], rgb.shape[2], rgb.shape[2],
                                            _ptr(out), _stream(stream)))
     return out
 

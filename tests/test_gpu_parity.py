@@ -21,6 +21,7 @@ def _build(ih, ctx, planes, chans, weighted=-1, pitch=None):
     planes = np.asarray(planes, dtype=np.uint8)
     if planes.ndim == 2:
         planes = planes[None]
+    planes = np.ascontiguousarray(planes)
     p, h, w = planes.shape
     if pitch is not None and pitch > w:
         buf = torch.zeros((p, h, pitch), dtype=torch.uint8, device=DEV)
