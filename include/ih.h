@@ -99,8 +99,12 @@ typedef struct {
 typedef struct {
     int32_t device;             /* CUDA device ordinal */
     uint64_t hbm_budget_bytes;  /* cap on the bytes of live frames; 0 = none */
-    uint32_t flags;             /* reserved, 0 */
+    uint32_t flags;             /* IH_CFG_* */
 } ih_config;
+
+/* ih_config.flags: record a CUDA event pair around every kernel launch on
+ * the launching stream, read back by ih_profile_read(). */
+enum { IH_CFG_PROFILE = 1 };
 
 /* Creates a context on cfg->device.  *out receives the context.
  * Returns IH_EINVAL for a NULL argument or bad device, IH_ECUDA if the device
@@ -140,8 +144,9 @@ enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
 
 /* Spatially weighted local histograms (Eq. 3.1) of n windows on the frame's
  * weighted channel, in O(1) each from the moment planes (Sec. 3.1.3):
- * every bin's weighted sum is an exact integer numerator (int64) over the
- * window's integer denominator, rounded once to float.  d_windows: device,
+ * every bin's weighted sum is an exact rational number (integer part and
+ * remainder computed exactly in int64/uint64) converted to float with a
+ * relative error below 4e-7; no step uses FP64.  d_windows: device,
  * n x 4 int32; d_out: device, n x B_w float (B_w = bins of the weighted
  * channel).  Windows must have sides <= 32768.  Invalid windows give a row
  * of -1 and IH_EINVAL at the next ih_sync().  IH_EINVAL (host) if the frame
@@ -188,6 +193,19 @@ ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t 
  * described for IH_INPUT_RGB_FEATURES. */
 ih_status ih_features(ih_ctx *ctx, const uint8_t *d_rgb, int32_t height, int32_t width,
                       int64_t pitch_bytes, uint8_t *d_out, void *stream);
+
+/* Per-kernel launch statistics of a context created with IH_CFG_PROFILE. */
+typedef struct {
+    char name[40];      /* e.g. "tiles/count", "tiles/moment_c2", "query_rects" */
+    int64_t launches;   /* launches since the last reset */
+    double total_ms;    /* sum of the event-timed durations */
+} ih_kernel_stat;
+
+/* Waits for the recorded events, then copies up to `max` statistics (one per
+ * kernel that ran) to `out` (host) and their number to *count (host).
+ * reset != 0 clears them afterwards.  IH_EINVAL without IH_CFG_PROFILE. */
+ih_status ih_profile_read(ih_ctx *ctx, ih_kernel_stat *out, int32_t max, int32_t *count,
+                          int32_t reset);
 
 /* Kernel launches issued by this context since it was created (all of them
  * are this library's own kernels). */

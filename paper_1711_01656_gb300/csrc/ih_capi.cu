@@ -36,8 +36,21 @@ struct FrameRec {
 
 }  // namespace
 
+struct ProfRec {
+    int kid;
+    cudaEvent_t a, b;
+};
+
 struct ih_ctx {
     int device = 0;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<ProfRec> prof_pending;
+    int prof_open_kid = -1;
+    cudaEvent_t prof_open = nullptr;
+    int64_t prof_launches[KID_COUNT] = {0};
+    double prof_ms[KID_COUNT] = {0};
+    Prof prof;
     uint64_t budget = 0;
     uint64_t used = 0;
     cudaMemPool_t pool = nullptr;
@@ -67,6 +80,56 @@ ih_status fail(ih_ctx *ctx, ih_status s, const char *fmt, ...)
 ih_status cuda_fail(ih_ctx *ctx, cudaError_t e, const char *what)
 {
     return fail(ctx, IH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaEvent_t take_event(ih_ctx *ctx)
+{
+    if (!ctx->ev_free.empty()) {
+        cudaEvent_t e = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_mark_cb(void *p, int kid, int phase, cudaStream_t st)
+{
+    ih_ctx *ctx = static_cast<ih_ctx *>(p);
+    cudaEvent_t e = take_event(ctx);
+    cudaEventRecord(e, st);
+    if (phase == 0) {
+        ctx->prof_open = e;
+        ctx->prof_open_kid = kid;
+    } else if (ctx->prof_open && ctx->prof_open_kid == kid) {
+        ctx->prof_pending.push_back({kid, ctx->prof_open, e});
+        ctx->prof_open = nullptr;
+        ctx->prof_open_kid = -1;
+    } else {
+        ctx->ev_free.push_back(e);
+    }
+}
+
+const Prof *prof_of(ih_ctx *ctx) { return ctx->profiling ? &ctx->prof : nullptr; }
+
+const char *kernel_name(int kid)
+{
+    static const char *kinds[5] = {"count", "moment_c", "moment_r", "moment_c2", "moment_r2"};
+    static char names[KID_COUNT][40];
+    static bool init = false;
+    if (!init) {
+        snprintf(names[KID_FEATURES], 40, "features");
+        for (int k = 0; k < 5; ++k) {
+            snprintf(names[kid_sums(k)], 40, "tile_sums/%s", kinds[k]);
+            snprintf(names[kid_scan(k)], 40, "carry_scan/%s", kinds[k]);
+            snprintf(names[kid_tiles(k)], 40, "tiles/%s", kinds[k]);
+        }
+        snprintf(names[KID_QUERY_RECTS], 40, "query_rects");
+        snprintf(names[KID_QUERY_WEIGHTED], 40, "query_weighted");
+        init = true;
+    }
+    return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
 struct DevGuard {
@@ -162,7 +225,7 @@ ih_status run_plane_set(ih_ctx *ctx, PlaneSet &ps, int kind, cudaStream_t st)
         ps.tilesum = s + a16 + b16;
         ps.corner = s + a16 + b16 + c16;
     }
-    const int n = launch_plane_set(ps, kind, nbpg, st);
+    const int n = launch_plane_set(ps, kind, st, prof_of(ctx));
     if (scratch) cudaFreeAsync(scratch, st);
     if (n < 0) return cuda_fail(ctx, cudaGetLastError(), "build launch");
     ctx->launches += n;
@@ -181,6 +244,9 @@ ih_status ih_create(const ih_config *cfg, ih_ctx **out)
     ih_ctx *ctx = new ih_ctx();
     ctx->device = cfg->device;
     ctx->budget = cfg->hbm_budget_bytes;
+    ctx->profiling = (cfg->flags & IH_CFG_PROFILE) != 0;
+    ctx->prof.ctx = ctx;
+    ctx->prof.mark = prof_mark_cb;
     DevGuard dg(ctx->device);
     cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
     cudaMemPoolProps props;
@@ -264,7 +330,7 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
             if (e != cudaSuccess) return cuda_fail(ctx, e, "feature scratch allocation");
             const uint8_t *R = f.d_pixels, *G = R + plane_stride, *Bp = G + plane_stride;
             if (launch_features(R, G, Bp, f.pitch_bytes, f.height, f.width, nullptr, feat,
-                                feat + fp * f.height, fp, st) < 0)
+                                feat + fp * f.height, fp, st, prof_of(ctx)) < 0)
                 return cuda_fail(ctx, cudaGetLastError(), "feature launch");
             ctx->launches += 1;
             for (int c = 0; c < 3; ++c) {
@@ -350,7 +416,8 @@ ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, in
     if (n < 0 || (n > 0 && (!d_rects || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_rects: bad arguments");
     DevGuard dg(ctx->device);
     CountView v{fr->d_ih, fr->B, fr->H, fr->W, fr->P};
-    const int k = launch_query_rects(v, d_rects, n, d_out, ctx->d_err, static_cast<cudaStream_t>(stream));
+    const int k = launch_query_rects(v, d_rects, n, d_out, ctx->d_err, static_cast<cudaStream_t>(stream),
+                                     prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
     ctx->launches += k;
     return IH_OK;
@@ -370,7 +437,7 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
     DevGuard dg(ctx->device);
     MomentView v{fr->d_ih + (int64_t)fr->bin_off[fr->wch] * fr->H * fr->P, fr->d_mom, fr->Bw, fr->H, fr->W, fr->P};
     const int k = launch_query_weighted(v, d_windows, n, (flags & IH_NORMALIZE) ? 1 : 0, d_out, ctx->d_err,
-                                        static_cast<cudaStream_t>(stream));
+                                        static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
     ctx->launches += k;
     return IH_OK;
@@ -465,7 +532,7 @@ ih_status ih_features(ih_ctx *ctx, const uint8_t *d_rgb, int32_t height, int32_t
     DevGuard dg(ctx->device);
     const int64_t ps = (int64_t)height * pitch_bytes, po = (int64_t)height * width;
     if (launch_features(d_rgb, d_rgb + ps, d_rgb + 2 * ps, pitch_bytes, height, width, d_out, d_out + 3 * po,
-                        d_out + 4 * po, width, static_cast<cudaStream_t>(stream)) < 0)
+                        d_out + 4 * po, width, static_cast<cudaStream_t>(stream), prof_of(ctx)) < 0)
         return cuda_fail(ctx, cudaGetLastError(), "feature launch");
     ctx->launches += 1;
     return IH_OK;
@@ -485,9 +552,53 @@ ih_status ih_destroy(ih_ctx *ctx)
             }
         cudaDeviceSynchronize();
         if (ctx->d_err) cudaFree(ctx->d_err);
+        for (auto &r : ctx->prof_pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        for (auto e : ctx->ev_free) cudaEventDestroy(e);
+        if (ctx->prof_open) cudaEventDestroy(ctx->prof_open);
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
+    return IH_OK;
+}
+
+ih_status ih_profile_read(ih_ctx *ctx, ih_kernel_stat *out, int32_t max, int32_t *count, int32_t reset)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!ctx->profiling) return fail(ctx, IH_EINVAL, "context was created without IH_CFG_PROFILE");
+    if (!count || (max > 0 && !out)) return fail(ctx, IH_EINVAL, "ih_profile_read: bad arguments");
+    DevGuard dg(ctx->device);
+    for (const ProfRec &r : ctx->prof_pending) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "profile events");
+        ctx->prof_launches[r.kid] += 1;
+        ctx->prof_ms[r.kid] += ms;
+        ctx->ev_free.push_back(r.a);
+        ctx->ev_free.push_back(r.b);
+    }
+    ctx->prof_pending.clear();
+    int n = 0;
+    for (int k = 0; k < KID_COUNT; ++k) {
+        if (!ctx->prof_launches[k]) continue;
+        if (n < max) {
+            memset(&out[n], 0, sizeof out[n]);
+            snprintf(out[n].name, sizeof out[n].name, "%s", kernel_name(k));
+            out[n].launches = ctx->prof_launches[k];
+            out[n].total_ms = ctx->prof_ms[k];
+        }
+        ++n;
+    }
+    *count = n < max ? n : max;
+    if (reset)
+        for (int k = 0; k < KID_COUNT; ++k) {
+            ctx->prof_launches[k] = 0;
+            ctx->prof_ms[k] = 0;
+        }
     return IH_OK;
 }
 

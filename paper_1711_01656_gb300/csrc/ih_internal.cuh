@@ -31,6 +31,24 @@ constexpr int kMaxBandRows = 128;
 
 enum WeightKind { WK_ONE = 0, WK_COL = 1, WK_ROW = 2, WK_COL2 = 3, WK_ROW2 = 4 };
 
+// Kernel ids for the optional per-launch event timing.  Plane-set kernels
+// of weight kind k have ids kid_sums(k), kid_scan(k), kid_tiles(k).
+enum KernelId { KID_FEATURES = 0, KID_QUERY_RECTS = 16, KID_QUERY_WEIGHTED = 17, KID_COUNT = 18 };
+inline int kid_sums(int kind) { return 1 + 3 * kind; }
+inline int kid_scan(int kind) { return 2 + 3 * kind; }
+inline int kid_tiles(int kind) { return 3 + 3 * kind; }
+
+// Optional launch hook: mark(ctx, kid, 0, st) is called before a kernel is
+// launched on st and mark(ctx, kid, 1, st) right after.
+struct Prof {
+    void *ctx;
+    void (*mark)(void *ctx, int kid, int phase, cudaStream_t st);
+};
+inline void prof_mark(const Prof *p, int kid, int phase, cudaStream_t st)
+{
+    if (p && p->mark) p->mark(p->ctx, kid, phase, st);
+}
+
 struct ChanDev {
     const uint8_t *plane;  // row r starts at plane + r * pitch
     int64_t pitch;
@@ -69,14 +87,15 @@ struct PlaneSet {
 
 // Launchers (k_build.cu).  Each returns the number of kernels launched, or
 // -1 with the CUDA error left pending.
-int launch_plane_set(const PlaneSet &ps, int kind, int nb_per_group, cudaStream_t st);
+int launch_plane_set(const PlaneSet &ps, int kind, cudaStream_t st, const Prof *prof);
 size_t tile_sums_smem_bytes(const PlaneSet &ps, int kind);
 
 // Feature pre-pass (k_features.cu): intensity and three orientation planes
 // (and optionally a copy of R, G, B) from planar RGB.
 int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_t pitch, int H,
                     int W, uint8_t *out_rgb /* nullable: 3 planes */, uint8_t *out_i,
-                    uint8_t *out_hog /* 3 planes */, int64_t out_pitch, cudaStream_t st);
+                    uint8_t *out_hog /* 3 planes */, int64_t out_pitch, cudaStream_t st,
+                    const Prof *prof);
 
 // Queries (k_query.cu).
 struct CountView {
@@ -91,8 +110,8 @@ struct MomentView {
     int64_t P;
 };
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out,
-                       int *err, cudaStream_t st);
+                       int *err, cudaStream_t st, const Prof *prof);
 int launch_query_weighted(const MomentView &v, const int32_t *wins, int64_t n, int normalize,
-                          float *out, int *err, cudaStream_t st);
+                          float *out, int *err, cudaStream_t st, const Prof *prof);
 
 }  // namespace ih

@@ -300,7 +300,7 @@ void set_smem_attr(size_t bytes)
 }
 
 template <int K, int NB>
-int launch_kind(const PlaneSet &ps, cudaStream_t st)
+int launch_kind(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 {
     constexpr int BW = (K == WK_ONE) ? 32 : 16;
     int n = 0;
@@ -308,15 +308,21 @@ int launch_kind(const PlaneSet &ps, cudaStream_t st)
     if (ps.colsum) {
         const size_t smem = tile_sums_smem_bytes(ps, K);
         if (smem > 48 * 1024) set_smem_attr<K, BW>(smem);
+        prof_mark(prof, kid_sums(K), 0, st);
         k_tile_sums<K, BW><<<dim3(g.ns, g.nb, ps.npgroups), 256, smem, st>>>(ps);
+        prof_mark(prof, kid_sums(K), 1, st);
         ++n;
         const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.ns * ps.B;
         const int64_t blocks = (tot + 255) / 256;
+        prof_mark(prof, kid_scan(K), 0, st);
         k_carry_scan<K><<<(unsigned)(blocks < 4864 ? blocks : 4864), 256, 0, st>>>(ps);
+        prof_mark(prof, kid_scan(K), 1, st);
         ++n;
     }
     const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
+    prof_mark(prof, kid_tiles(K), 0, st);
     k_ih_tiles<K, NB><<<(unsigned)((units + 3) / 4), 128, 0, st>>>(ps);
+    prof_mark(prof, kid_tiles(K), 1, st);
     ++n;
     return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
@@ -330,15 +336,14 @@ size_t tile_sums_smem_bytes(const PlaneSet &ps, int kind)
     return (ps.g.R * bw + bw * kSumCols) * el;
 }
 
-int launch_plane_set(const PlaneSet &ps, int kind, int nb_per_group, cudaStream_t st)
+int launch_plane_set(const PlaneSet &ps, int kind, cudaStream_t st, const Prof *prof)
 {
-    (void)nb_per_group;
     switch (kind) {
-    case WK_ONE: return launch_kind<WK_ONE, 8>(ps, st);
-    case WK_COL: return launch_kind<WK_COL, 4>(ps, st);
-    case WK_ROW: return launch_kind<WK_ROW, 4>(ps, st);
-    case WK_COL2: return launch_kind<WK_COL2, 4>(ps, st);
-    case WK_ROW2: return launch_kind<WK_ROW2, 4>(ps, st);
+    case WK_ONE: return launch_kind<WK_ONE, 8>(ps, st, prof);
+    case WK_COL: return launch_kind<WK_COL, 4>(ps, st, prof);
+    case WK_ROW: return launch_kind<WK_ROW, 4>(ps, st, prof);
+    case WK_COL2: return launch_kind<WK_COL2, 4>(ps, st, prof);
+    case WK_ROW2: return launch_kind<WK_ROW2, 4>(ps, st, prof);
     }
     return -1;
 }

@@ -92,10 +92,12 @@ __global__ void __launch_bounds__(256) k_features(const uint8_t *__restrict__ pr
 
 int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_t pitch, int H,
                     int W, uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog, int64_t out_pitch,
-                    cudaStream_t st)
+                    cudaStream_t st, const Prof *prof)
 {
     dim3 grid((W + kT - 1) / kT, (H + kT - 1) / kT);
+    prof_mark(prof, KID_FEATURES, 0, st);
     k_features<<<grid, dim3(kT, 8), 0, st>>>(r, g, b, pitch, H, W, out_rgb, out_i, out_hog, out_pitch);
+    prof_mark(prof, KID_FEATURES, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

@@ -122,18 +122,22 @@ unsigned grid_for(int64_t total)
 }  // namespace
 
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out, int *err,
-                       cudaStream_t st)
+                       cudaStream_t st, const Prof *prof)
 {
     if (n == 0) return 0;
+    prof_mark(prof, KID_QUERY_RECTS, 0, st);
     k_query_rects<<<grid_for(n * v.B), 256, 0, st>>>(v, rects, n, out, err);
+    prof_mark(prof, KID_QUERY_RECTS, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_query_weighted(const MomentView &v, const int32_t *wins, int64_t n, int normalize, float *out,
-                          int *err, cudaStream_t st)
+                          int *err, cudaStream_t st, const Prof *prof)
 {
     if (n == 0) return 0;
+    prof_mark(prof, KID_QUERY_WEIGHTED, 0, st);
     k_query_weighted<<<grid_for(n * v.Bw), 256, 0, st>>>(v, wins, n, normalize, out, err);
+    prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

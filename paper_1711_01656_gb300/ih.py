@@ -28,7 +28,8 @@ STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: 
 # The exported C symbols (include/ih.h), checked by the test suite.
 C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih_destroy",
              "ih_release", "ih_sync", "ih_info", "ih_export", "ih_export_moments", "ih_features",
-             "ih_launch_count", "ih_last_error")
+             "ih_profile_read", "ih_launch_count", "ih_last_error")
+IH_CFG_PROFILE = 1
 
 
 class IHError(RuntimeError):
@@ -51,6 +52,10 @@ class ih_frame(ctypes.Structure):
 class ih_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
                 ("flags", ctypes.c_uint32)]
+
+
+class ih_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
 
 class ih_frame_info(ctypes.Structure):
@@ -86,6 +91,7 @@ def load_library(path: str = LIB_PATH):
             "ih_export": ([p, i32, p, p], i32),
             "ih_export_moments": ([p, i32, i32, p, p], i32),
             "ih_features": ([p, p, i32, i32, i64, p, p], i32),
+            "ih_profile_read": ([p, ctypes.POINTER(ih_kernel_stat), i32, ctypes.POINTER(i32), i32], i32),
             "ih_launch_count": ([p], i64),
             "ih_last_error": ([p], ctypes.c_char_p),
         }
@@ -118,9 +124,9 @@ def _ptr(t):
 
 # ---------------------------------------------------------------- contexts
 
-def ih_create(device: int = 0, hbm_budget_bytes: int = 0):
+def ih_create(device: int = 0, hbm_budget_bytes: int = 0, flags: int = 0):
     lib = load_library()
-    cfg = ih_config(int(device), int(hbm_budget_bytes), 0)
+    cfg = ih_config(int(device), int(hbm_budget_bytes), int(flags))
     out = ctypes.c_void_p()
     st = lib.ih_create(ctypes.byref(cfg), ctypes.byref(out))
     if st != IH_OK:
@@ -220,6 +226,14 @@ def ih_features(ctx, rgb, out, stream=None):
     _check(ctx, load_library().ih_features(ctx, _ptr(rgb), rgb.shape[1], rgb.shape[2], rgb.shape[2],
                                            _ptr(out), _stream(stream)))
     return out
+
+
+def ih_profile_read(ctx, reset=True):
+    """{kernel name: (launches, total_ms)} of a context created with IH_CFG_PROFILE."""
+    arr = (ih_kernel_stat * 64)()
+    n = ctypes.c_int32()
+    _check(ctx, load_library().ih_profile_read(ctx, arr, 64, ctypes.byref(n), int(bool(reset))))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
 
 
 def ih_launch_count(ctx) -> int:
