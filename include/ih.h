@@ -52,6 +52,8 @@ typedef enum {
     IH_ECUDA = 4,     /* a CUDA runtime call or launch failed */
     IH_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
     IH_ENOTBUILT = 6, /* the handle names no live frame */
+    IH_ETOOBIG = 7,   /* ih_build_counts_static: the frame needs more carry
+                         scratch than IH_STATIC_SCRATCH_BYTES */
 } ih_status;
 
 /* Binning function Q of one channel (Eq. 2.15). */
@@ -213,6 +215,35 @@ int64_t ih_launch_count(ih_ctx *ctx);
 
 /* One-line description of the last error of this context ("" if none). */
 const char *ih_last_error(ih_ctx *ctx);
+
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* The thesis has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory while they run (a real-time loop whose
+ * device memory is reserved up front by its own arena, where a cudaMalloc
+ * would synchronise the device, or an application whose allocator owns all
+ * device memory).
+ *
+ * Builds the count integral histogram (Eq. 2.15) of ONE uint8 channel on the
+ * CURRENT device, enqueued on `stream`, without allocating anything:
+ *   d_pixels  device, H rows of pitch_bytes (>= W) bytes;
+ *   bins      1..256, mode an ih_binmode;
+ *   d_out     device, caller-owned, bins x H x out_pitch int32, bin-major;
+ *             out_pitch >= W and a multiple of 4, d_out 16-byte aligned;
+ *             columns W..out_pitch-1 receive unspecified values.
+ * Tile carries live in one device array of IH_STATIC_SCRATCH_BYTES that the
+ * library holds on every GPU that loads it until the process exits.  The
+ * array's device address is looked up on the first call made on each device;
+ * make that first call before any stream capture begins.  All calls share the
+ * array: calls whose work overlaps on the GPU race on it and must be ordered
+ * by the caller (one stream, or events).  Returns IH_EINVAL for bad arguments,
+ * IH_ETOOBIG when even the largest tiles need more than the array holds
+ * (about 4*bins*(W*ceil(H/128) + H*ceil(W/1024)) bytes: a 1920x1080 channel
+ * fits up to 107 bins), IH_ECUDA on a CUDA error. */
+#define IH_STATIC_SCRATCH_BYTES (8u << 20)
+ih_status ih_build_counts_static(const uint8_t *d_pixels, int32_t height, int32_t width,
+                                 int64_t pitch_bytes, int32_t bins, int32_t mode, int32_t *d_out,
+                                 int64_t out_pitch, void *stream);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,124 @@
+// ih_static.cu -- ih_build_counts_static: the count build of one channel
+// without any device allocation.
+//
+// Who needs it: callers that must not allocate device memory once they are
+// running -- a real-time tracking loop whose device memory is reserved up
+// front by its own arena (a cudaMalloc there would synchronise the device and
+// stall every stream), or a host application whose allocator owns all device
+// memory.  ih_build allocates its tensors and its carry scratch from a
+// context's memory pool; this entry point writes into the caller's buffer and
+// keeps the carries (column, row and corner sums of the tiles) in one
+// statically sized device array of this library.
+//
+// The array lives in every GPU that loads the library until the process
+// exits.  Its device address is looked up with cudaGetSymbolAddress on the
+// first call made on each device (with that device current) and cached; that
+// first call should be made before any stream capture begins.  Every call
+// shares the array: calls whose work overlaps on the GPU (on different
+// streams, or on one device from several threads) race on it.  Every carry
+// cell a call reads is written earlier by the same call, so nothing needs
+// clearing between calls.
+#include <mutex>
+
+#include "../../include/ih.h"
+#include "ih_internal.cuh"
+#include "ih_plan.h"
+
+using namespace ih;
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // IH_STATIC_SCRATCH_BYTES
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_mu;
+void *g_static_addr[kMaxDevices] = {nullptr};
+
+cudaError_t static_scratch_address(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_static_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t carry_bytes(const TileGrid &g, int B)
+{
+    if ((int64_t)g.nb * g.ns <= 1) return 0;
+    return round256(4ull * B * g.W * g.nb) + round256(4ull * B * g.H * g.ns) + 2 * round256(4ull * B * g.nb * g.ns);
+}
+
+int split_groups(int bins, int cap, GroupDev *out)
+{
+    const int ng = (bins + cap - 1) / cap;
+    for (int g = 0; g < ng; ++g) {
+        out[g].chan = 0;
+        out[g].b_lo = (int16_t)(bins * g / ng);
+        out[g].nb = (int16_t)(bins * (g + 1) / ng - bins * g / ng);
+        out[g].pad = 0;
+    }
+    return ng;
+}
+
+}  // namespace
+
+extern "C" ih_status ih_build_counts_static(const uint8_t *d_pixels, int32_t height, int32_t width,
+                                            int64_t pitch_bytes, int32_t bins, int32_t mode,
+                                            int32_t *d_out, int64_t out_pitch, void *stream)
+{
+    if (!d_pixels || !d_out || height < 1 || width < 1 || pitch_bytes < width || bins < 1 || bins > 256 ||
+        (mode != IH_BIN_UNIFORM8 && mode != IH_BIN_INDEX) || out_pitch < width || (out_pitch & 3) ||
+        (reinterpret_cast<uintptr_t>(d_out) & 15) || (int64_t)height * width > ((int64_t)1 << 31))
+        return IH_EINVAL;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return IH_ECUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IH_ECUDA;
+
+    PlaneSet ps{};
+    ps.g = choose_grid(height, width, bins, WK_ONE, nsm);
+    if (carry_bytes(ps.g, bins) > kStaticScratchBytes) {
+        // the largest tiles need the least carry scratch
+        TileGrid big = ps.g;
+        big.R = height < kMaxBandRows ? height : kMaxBandRows;
+        big.Wc = 1024;
+        big.nb = (height + big.R - 1) / big.R;
+        big.ns = (width + big.Wc - 1) / big.Wc;
+        if (carry_bytes(big, bins) > kStaticScratchBytes) return IH_ETOOBIG;
+        ps.g = big;
+    }
+    ps.g.P = out_pitch;
+    ps.B = bins;
+    ps.nchan = 1;
+    ps.chan[0].plane = d_pixels;
+    ps.chan[0].pitch = pitch_bytes;
+    ps.chan[0].bins = bins;
+    ps.chan[0].mode = mode;
+    ps.chan[0].bin_off = 0;
+    ps.ngroups = split_groups(bins, 8, ps.grp);
+    ps.npgroups = split_groups(bins, 32, ps.pgrp);
+    ps.out = d_out;
+    if ((int64_t)ps.g.nb * ps.g.ns > 1) {
+        void *base = nullptr;
+        if (static_scratch_address(dev, &base) != cudaSuccess) return IH_ECUDA;
+        char *s = static_cast<char *>(base);
+        const size_t a = round256(4ull * bins * ps.g.W * ps.g.nb);
+        const size_t b = round256(4ull * bins * ps.g.H * ps.g.ns);
+        const size_t c = round256(4ull * bins * ps.g.nb * ps.g.ns);
+        ps.colsum = s;
+        ps.rowsum = s + a;
+        ps.tilesum = s + a + b;
+        ps.corner = s + a + b + c;
+    }
+    if (launch_plane_set(ps, WK_ONE, static_cast<cudaStream_t>(stream), nullptr) < 0) return IH_ECUDA;
+    return IH_OK;
+}

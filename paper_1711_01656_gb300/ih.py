@@ -15,7 +15,7 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libih.so")
 
-IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT = range(7)
+IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT, IH_ETOOBIG = range(8)
 IH_BIN_UNIFORM8, IH_BIN_INDEX = 0, 1
 IH_INPUT_PLANES, IH_INPUT_RGB_FEATURES = 0, 1
 IH_LAYOUT_BIN_MAJOR = 0
@@ -23,12 +23,12 @@ IH_K_EPANECHNIKOV = 0
 IH_NORMALIZE = 1
 
 STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: "IH_ECUDA",
-                5: "IH_ETIMEOUT", 6: "IH_ENOTBUILT"}
+                5: "IH_ETIMEOUT", 6: "IH_ENOTBUILT", 7: "IH_ETOOBIG"}
 
 # The exported C symbols (include/ih.h), checked by the test suite.
 C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih_destroy",
              "ih_release", "ih_sync", "ih_info", "ih_export", "ih_export_moments", "ih_features",
-             "ih_profile_read", "ih_launch_count", "ih_last_error")
+             "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_build_counts_static")
 IH_CFG_PROFILE = 1
 
 
@@ -94,6 +94,7 @@ def load_library(path: str = LIB_PATH):
             "ih_profile_read": ([p, ctypes.POINTER(ih_kernel_stat), i32, ctypes.POINTER(i32), i32], i32),
             "ih_launch_count": ([p], i64),
             "ih_last_error": ([p], ctypes.c_char_p),
+            "ih_build_counts_static": ([p, i32, i32, i64, i32, i32, p, i64, p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -242,3 +243,18 @@ def ih_launch_count(ctx) -> int:
 
 def ih_last_error(ctx) -> str:
     return load_library().ih_last_error(ctx).decode()
+
+
+def ih_build_counts_static(pixels, bins, mode, out, stream=None):
+    """Allocation-free count build of one channel into `out`.
+
+    pixels: (H, W) uint8 CUDA tensor (rows may be padded); out: (bins, H, P)
+    int32 CUDA tensor, P >= W a multiple of 4.  Uses the library's static
+    carry array: calls that overlap on the GPU race (see include/ih.h)."""
+    h, w = pixels.shape
+    pitch = pixels.stride(0) if h > 1 else w
+    st = load_library().ih_build_counts_static(_ptr(pixels), h, w, pitch, int(bins), int(mode), _ptr(out),
+                                                out.shape[2], _stream(stream))
+    if st != IH_OK:
+        raise IHError(st, "ih_build_counts_static(%dx%d, %d bins)" % (h, w, bins))
+    return out
