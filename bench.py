@@ -159,17 +159,17 @@ def algorithmic_bytes(kernel: str, B: int, Bw: int, n_rects: int, n_wins: int) -
     hw = H * W
     if kernel == "tiles/count":
         return 7 * hw + 4.0 * B * hw          # 7 channel planes in, B int32 planes out
-    if kernel.startswith("tiles/moment"):
-        return hw + 8.0 * Bw * hw            # intensity in, Bw int64 planes out
+    if kernel == "tiles/moments":
+        return hw + 4 * 8.0 * Bw * hw        # intensity in, 4 x Bw int64 planes out
     if kernel == "features":
         return 3 * hw + 4 * hw
     if kernel == "query_rects":
         return n_rects * (16 + 4 * B * 4 + 4 * B)
     if kernel == "query_weighted":
         return n_wins * (16 + 4 * Bw * (4 + 4 * 8) + 4 * Bw)
-    if kernel.startswith("tile_sums/count"):
-        return 7 * hw
-    if kernel.startswith("tile_sums"):
+    if kernel == "tile_sums/count":
+        return 6 * hw
+    if kernel == "tile_sums/weighted":
         return hw
     return float("nan")
 
@@ -304,7 +304,8 @@ def run_engine(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(pix):
-        h, = ih.ih_build(ctx, ih.Frame(pix, chans, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH))
+        h, = ih.ih_build(ctx, ih.Frame(pix, chans, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
+                                       layout=ih.IH_LAYOUT_SLAB))
         ih.ih_query_rects(ctx, h, d_rects, out_r)
         ih.ih_query_weighted(ctx, h, d_wins, out_w)
         ih.ih_release(ctx, h)
@@ -400,7 +401,8 @@ def run_engine(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "global_batch": world, "frames_per_gpu": 1,
                        "l2": "flushed between timed steps (256 MiB write)",
-                       "parallelism": "replicas: one frame per GPU, no collective"},
+                       "parallelism": "replicas: one frame per GPU, no collective",
+                       "layout": "slab (bins innermost, groups of <= 8 bins)"},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(h_rgb.numel() + h_rects.numel() * 4 + h_wins.numel() * 4),

@@ -79,14 +79,21 @@ typedef enum {
     IH_INPUT_RGB_FEATURES = 1
 } ih_input;
 
-/* ih_frame.layout: how the context stores the count tensor. */
+/* ih_frame.layout: how the context stores the count tensor (ih_export
+ * always returns the packed bin-major tensor of Algorithm 5). */
 typedef enum {
     IH_LAYOUT_BIN_MAJOR = 0, /* b x h x pitch, as Fig. 5.1 */
+    /* bins innermost: each channel's bins are split in order into
+     * ceil(B_c/8) groups of near-equal size (floor/ceil of B_c/groups), and
+     * each group g of nb_g bins is stored as h x pitch x nb_g; a rectangle
+     * query then reads each corner's bins from a few contiguous words */
+    IH_LAYOUT_SLAB = 1
 } ih_layout;
 
 typedef struct {
     int32_t height, width;      /* H, W >= 1 */
-    int32_t channels;           /* number of binned channels, 1..16 */
+    int32_t channels;           /* number of binned channels, 1..16, with
+                                   at most 1024 bins in total */
     int32_t input;              /* ih_input */
     const ih_channel *chan;     /* host array [channels] */
     const uint8_t *d_pixels;    /* device; planar: plane p, row r starts at

@@ -32,6 +32,7 @@ struct FrameRec {
     int wch = -1, Bw = 0;
     int64_t *d_mom = nullptr;
     int64_t count_bytes = 0, moment_bytes = 0;
+    CountView view{};
 };
 
 }  // namespace
@@ -115,20 +116,9 @@ const Prof *prof_of(ih_ctx *ctx) { return ctx->profiling ? &ctx->prof : nullptr;
 
 const char *kernel_name(int kid)
 {
-    static const char *kinds[5] = {"count", "moment_c", "moment_r", "moment_c2", "moment_r2"};
-    static char names[KID_COUNT][40];
-    static bool init = false;
-    if (!init) {
-        snprintf(names[KID_FEATURES], 40, "features");
-        for (int k = 0; k < 5; ++k) {
-            snprintf(names[kid_sums(k)], 40, "tile_sums/%s", kinds[k]);
-            snprintf(names[kid_scan(k)], 40, "carry_scan/%s", kinds[k]);
-            snprintf(names[kid_tiles(k)], 40, "tiles/%s", kinds[k]);
-        }
-        snprintf(names[KID_QUERY_RECTS], 40, "query_rects");
-        snprintf(names[KID_QUERY_WEIGHTED], 40, "query_weighted");
-        init = true;
-    }
+    static const char *names[KID_COUNT] = {"features",      "tile_sums/count", "tile_sums/weighted",
+                                           "carry_scan",    "tiles/count",     "tiles/moments",
+                                           "query_rects",   "query_weighted",  "export"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -167,13 +157,16 @@ ih_status validate(ih_ctx *ctx, const ih_frame &f)
         return fail(ctx, IH_EINVAL, "input kind %d", f.input);
     if (f.input == IH_INPUT_RGB_FEATURES && f.channels != 7)
         return fail(ctx, IH_EINVAL, "IH_INPUT_RGB_FEATURES needs 7 channels");
-    if (f.layout != IH_LAYOUT_BIN_MAJOR) return fail(ctx, IH_EINVAL, "layout %d", f.layout);
+    if (f.layout != IH_LAYOUT_BIN_MAJOR && f.layout != IH_LAYOUT_SLAB) return fail(ctx, IH_EINVAL, "layout %d", f.layout);
     for (int c = 0; c < f.channels; ++c) {
         if (f.chan[c].bins < 1 || f.chan[c].bins > 256)
             return fail(ctx, IH_EINVAL, "channel %d bins = %d (1..256)", c, f.chan[c].bins);
         if (f.chan[c].mode != IH_BIN_UNIFORM8 && f.chan[c].mode != IH_BIN_INDEX)
             return fail(ctx, IH_EINVAL, "channel %d mode = %d", c, f.chan[c].mode);
     }
+    int total = 0;
+    for (int c = 0; c < f.channels; ++c) total += f.chan[c].bins;
+    if (total > kMaxBins) return fail(ctx, IH_EINVAL, "%d bins in one frame (at most %d)", total, kMaxBins);
     if (f.weighted_channel < -1 || f.weighted_channel >= f.channels)
         return fail(ctx, IH_EINVAL, "weighted_channel = %d", f.weighted_channel);
     return IH_OK;
@@ -198,38 +191,52 @@ int make_groups(const int *bins, int nchan, int cap, GroupDev *out, int max_out)
     return n;
 }
 
-// Enqueue one plane set (counts over `chans`, or one moment kind over the
-// weighted channel) with its scratch carries.
-ih_status run_plane_set(ih_ctx *ctx, PlaneSet &ps, int kind, cudaStream_t st)
+// Count groups ordered by size (one tiles launch per size); tile-sums
+// windows with the weighted channel's windows last.
+bool plan_groups(PlaneSet &ps)
 {
-    const int nbpg = (kind == WK_ONE) ? 8 : 4;
-    const size_t el = (kind == WK_ONE) ? 4 : 8;
     int bins[kMaxChannels];
     for (int c = 0; c < ps.nchan; ++c) bins[c] = ps.chan[c].bins;
-    ps.ngroups = make_groups(bins, ps.nchan, nbpg, ps.grp, kMaxGroups);
-    ps.npgroups = make_groups(bins, ps.nchan, kind == WK_ONE ? 32 : 16, ps.pgrp, kMaxGroups);
-    if (ps.ngroups < 0 || ps.npgroups < 0) return fail(ctx, IH_EINVAL, "too many bins for one build");
-    const TileGrid &g = ps.g;
-    void *scratch = nullptr;
-    ps.colsum = ps.rowsum = ps.tilesum = ps.corner = nullptr;
-    if ((int64_t)g.nb * g.ns > 1) {
-        const size_t a = el * ps.B * (size_t)g.W * g.nb;
-        const size_t b = el * ps.B * (size_t)g.H * g.ns;
-        const size_t c = el * ps.B * (size_t)g.nb * g.ns;
-        const size_t a16 = (a + 255) & ~size_t(255), b16 = (b + 255) & ~size_t(255), c16 = (c + 255) & ~size_t(255);
-        cudaError_t e = pool_alloc(ctx, &scratch, a16 + b16 + 2 * c16, st);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
-        char *s = static_cast<char *>(scratch);
-        ps.colsum = s;
-        ps.rowsum = s + a16;
-        ps.tilesum = s + a16 + b16;
-        ps.corner = s + a16 + b16 + c16;
+    GroupDev tmp[kMaxGroups];
+    const int ng = make_groups(bins, ps.nchan, kGroupBins, tmp, kMaxGroups);
+    if (ng < 0) return false;
+    int n = 0;
+    for (int size = kGroupBins; size >= 1; --size)
+        for (int k = 0; k < ng; ++k)
+            if (tmp[k].nb == size) ps.grp[n++] = tmp[k];
+    ps.ngroups = n;
+    const int nw = make_groups(bins, ps.nchan, kWindowBins, tmp, kMaxGroups);
+    if (nw < 0) return false;
+    n = 0;
+    for (int k = 0; k < nw; ++k)
+        if (tmp[k].chan != ps.wch) ps.win[n++] = tmp[k];
+    for (int k = 0; k < nw; ++k)
+        if (tmp[k].chan == ps.wch) ps.win[n++] = tmp[k];
+    ps.nwin = n;
+    return true;
+}
+
+// Slab offsets of the groups (LAYOUT_SLAB) and the read view of the tensor.
+void make_view(const PlaneSet &ps, const int32_t *d, CountView &v)
+{
+    memset(&v, 0, sizeof v);
+    v.d = d;
+    v.B = ps.B;
+    v.H = ps.g.H;
+    v.W = ps.g.W;
+    v.P = ps.g.P;
+    v.layout = ps.layout;
+    v.ngroups = ps.ngroups;
+    for (int k = 0; k < ps.ngroups; ++k) {
+        const GroupDev &gr = ps.grp[k];
+        v.group_nb[k] = gr.nb;
+        v.slab_off[k] = ps.slab_off[k];
+        for (int b = 0; b < gr.nb; ++b) {
+            const int gb = ps.chan[gr.chan].bin_off + gr.b_lo + b;
+            v.bin_group[gb] = (int16_t)k;
+            v.bin_local[gb] = (int16_t)b;
+        }
     }
-    const int n = launch_plane_set(ps, kind, st, prof_of(ctx));
-    if (scratch) cudaFreeAsync(scratch, st);
-    if (n < 0) return cuda_fail(ctx, cudaGetLastError(), "build launch");
-    ctx->launches += n;
-    return IH_OK;
 }
 
 }  // namespace
@@ -347,13 +354,12 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
                 cpitch[c] = f.pitch_bytes;
             }
         }
-        // counts over all channels
         PlaneSet ps;
         memset(&ps, 0, sizeof ps);
-        ps.g = choose_grid(fr.H, fr.W, fr.B, WK_ONE, ctx->nsm);
-        ps.g.P = fr.P;
         ps.B = fr.B;
         ps.nchan = fr.nchan;
+        ps.layout = f.layout;
+        ps.wch = fr.wch;
         for (int c = 0; c < fr.nchan; ++c) {
             ps.chan[c].plane = planes[c];
             ps.chan[c].pitch = cpitch[c];
@@ -361,22 +367,31 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
             ps.chan[c].mode = f.chan[c].mode;
             ps.chan[c].bin_off = fr.bin_off[c];
         }
-        ps.out = fr.d_ih;
-        ih_status s = run_plane_set(ctx, ps, WK_ONE, st);
-        // moment planes of the weighted channel
-        for (int m = 0; s == IH_OK && fr.Bw && m < 4; ++m) {
-            static const int kinds[4] = {WK_COL, WK_ROW, WK_COL2, WK_ROW2};
-            PlaneSet pm;
-            memset(&pm, 0, sizeof pm);
-            pm.g = choose_grid(fr.H, fr.W, fr.Bw, kinds[m], ctx->nsm);
-            pm.g.P = fr.P;
-            pm.B = fr.Bw;
-            pm.nchan = 1;
-            pm.chan[0] = ps.chan[fr.wch];
-            pm.chan[0].bin_off = 0;
-            pm.out = fr.d_mom + (int64_t)m * fr.Bw * fr.H * fr.P;
-            s = run_plane_set(ctx, pm, kinds[m], st);
+        if (!plan_groups(ps)) return fail(ctx, IH_EINVAL, "too many bins for one build");
+        ps.g = choose_grid(fr.H, fr.W, ps.ngroups, ctx->nsm);
+        ps.g.P = fr.P;
+        int64_t off = 0;
+        for (int kg = 0; kg < ps.ngroups; ++kg) {
+            ps.slab_off[kg] = off;
+            off += (int64_t)fr.H * fr.P * ps.grp[kg].nb;
         }
+        ps.out = fr.d_ih;
+        ps.mom = fr.d_mom;
+        void *scratch = nullptr;
+        const size_t cb = carry_bytes(ps);
+        if (cb) {
+            e = pool_alloc(ctx, &scratch, cb, st);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
+        }
+        carve_carries(ps, scratch);
+        const int nl = launch_build(ps, st, prof_of(ctx));
+        if (scratch) cudaFreeAsync(scratch, st);
+        ih_status s = IH_OK;
+        if (nl < 0)
+            s = cuda_fail(ctx, cudaGetLastError(), "build launch");
+        else
+            ctx->launches += nl;
+        make_view(ps, fr.d_ih, fr.view);
         if (feat) cudaFreeAsync(feat, st);
         if (s != IH_OK) return s;
     }
@@ -415,8 +430,7 @@ ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, in
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (n < 0 || (n > 0 && (!d_rects || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_rects: bad arguments");
     DevGuard dg(ctx->device);
-    CountView v{fr->d_ih, fr->B, fr->H, fr->W, fr->P};
-    const int k = launch_query_rects(v, d_rects, n, d_out, ctx->d_err, static_cast<cudaStream_t>(stream),
+    const int k = launch_query_rects(fr->view, d_rects, n, d_out, ctx->d_err, static_cast<cudaStream_t>(stream),
                                      prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
     ctx->launches += k;
@@ -435,9 +449,9 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
         return fail(ctx, IH_EINVAL, "kernel %u / flags %u", kernel, flags);
     if (n < 0 || (n > 0 && (!d_windows || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_weighted: bad arguments");
     DevGuard dg(ctx->device);
-    MomentView v{fr->d_ih + (int64_t)fr->bin_off[fr->wch] * fr->H * fr->P, fr->d_mom, fr->Bw, fr->H, fr->W, fr->P};
-    const int k = launch_query_weighted(v, d_windows, n, (flags & IH_NORMALIZE) ? 1 : 0, d_out, ctx->d_err,
-                                        static_cast<cudaStream_t>(stream), prof_of(ctx));
+    const MomentView m{fr->bin_off[fr->wch], fr->d_mom, fr->Bw};
+    const int k = launch_query_weighted(fr->view, m, d_windows, n, (flags & IH_NORMALIZE) ? 1 : 0, d_out,
+                                        ctx->d_err, static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
     ctx->launches += k;
     return IH_OK;
@@ -501,10 +515,10 @@ ih_status ih_export(ih_ctx *ctx, int32_t handle, int32_t *d_dst, void *stream)
     FrameRec *fr = get_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     DevGuard dg(ctx->device);
-    cudaError_t e = cudaMemcpy2DAsync(d_dst, (size_t)fr->W * 4, fr->d_ih, (size_t)fr->P * 4, (size_t)fr->W * 4,
-                                      (size_t)fr->B * fr->H, cudaMemcpyDeviceToDevice,
-                                      static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? IH_OK : cuda_fail(ctx, e, "export copy");
+    if (launch_export(fr->view, d_dst, static_cast<cudaStream_t>(stream), prof_of(ctx)) < 0)
+        return cuda_fail(ctx, cudaGetLastError(), "export launch");
+    ctx->launches += 1;
+    return IH_OK;
 }
 
 ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t *d_dst, void *stream)

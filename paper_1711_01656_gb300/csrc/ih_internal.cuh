@@ -1,22 +1,24 @@
 // ih_internal.cuh -- descriptors shared by the engine's kernels and its C ABI.
 //
-// A "plane set" is one weighted integral histogram (Eq. 3.4) over a set of
-// channels: the count tensor (w = 1, Eq. 2.15 / Algorithm 5) or one of the
-// four moment planes w in {c, r, c^2, r^2} of the weighted channel.  Every
-// plane set is built by the same three kernels over a grid of tiles of R
-// rows (a band) by Wc columns (a strip):
+// A build computes, over a grid of tiles of R rows (a band) by Wc columns (a
+// strip), the count integral histogram of every channel (Eq. 2.15, the
+// tensor of Algorithm 5) and, for one optional "weighted" channel, the four
+// moment planes of Eq. 3.4 with w in {c, r, c^2, r^2}.  Three kernels remove
+// Algorithm 5's serial dependence:
 //
-//   tile sums  : per tile and bin, the column sums over the band's rows and
-//                the row sums over the strip's columns (reads pixels only);
-//   carry scan : exclusive prefixes of those sums over bands (G), over
-//                strips (L) and over both (corner);
-//   tiles      : per tile and bin group, the 2-D inclusive prefix of the
-//                tile, seeded with its carries, written once.
+//   tile sums  : per tile and bin, the column sums over the band and the row
+//                sums over the strip (and, for the weighted channel, the same
+//                sums weighted by the offset inside the tile and its square);
+//   carry scan : exclusive prefixes of those sums over bands (G), over strips
+//                (L) and over both (the tile corners), in int32 for counts
+//                and int64 for the moments;
+//   tiles      : per tile and bin group, the tile's 2-D inclusive prefix
+//                seeded with its carries, each output cell written once.
 //
-// With tile origin (R0, C0):
-//   H(r,c) = corner + sum_{C0<=c'<=c} G(c')
-//          + sum_{R0<=r'<=r} ( L(r') + sum_{C0<=c'<=c} w(r',c') Q(r',c') )
-// which is Eq. 2.15 split at the tile's top and left edges.
+// With tile origin (R0, C0) and any weight w:
+//   H_w(r,c) = corner_w + sum_{C0<=c'<=c} G_w(c')
+//            + sum_{R0<=r'<=r} ( L_w(r') + sum_{C0<=c'<=c} w(r',c') Q(r',c') )
+// which is Eq. 3.4 (Eq. 2.15 for w = 1) split at the tile's top and left edges.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,20 +28,38 @@ namespace ih {
 
 constexpr int kMaxChannels = 16;
 constexpr int kMaxGroups = 128;
-constexpr int kChunk = 128;      // columns a warp covers at once (4 per lane)
+constexpr int kMaxBins = 1024;   // total bins of a frame
+constexpr int kChunk = 128;       // columns a warp covers at once (4 per lane)
 constexpr int kMaxBandRows = 128;
+constexpr int kGroupBins = 8;     // bins per warp in the count tiles kernel
+constexpr int kWindowBins = 16;   // bins per CTA in the tile-sums kernel
+constexpr int kSumCols = 256;     // columns per pass of the tile-sums kernel
 
+// Count-tensor layouts.
+enum Layout {
+    LAYOUT_BIN_MAJOR = 0,  // [B][H][P]                (Fig. 5.1)
+    LAYOUT_SLAB = 1        // per bin group g: [H][P][nb_g], bins innermost
+};
+
+// Weight kinds, used by the kernel-id table and the moment planes.
 enum WeightKind { WK_ONE = 0, WK_COL = 1, WK_ROW = 2, WK_COL2 = 3, WK_ROW2 = 4 };
 
-// Kernel ids for the optional per-launch event timing.  Plane-set kernels
-// of weight kind k have ids kid_sums(k), kid_scan(k), kid_tiles(k).
-enum KernelId { KID_FEATURES = 0, KID_QUERY_RECTS = 16, KID_QUERY_WEIGHTED = 17, KID_COUNT = 18 };
-inline int kid_sums(int kind) { return 1 + 3 * kind; }
-inline int kid_scan(int kind) { return 2 + 3 * kind; }
-inline int kid_tiles(int kind) { return 3 + 3 * kind; }
+// Kernel ids for the optional per-launch event timing.
+enum KernelId {
+    KID_FEATURES = 0,
+    KID_SUMS_COUNT = 1,
+    KID_SUMS_WEIGHTED = 2,
+    KID_SCAN = 3,
+    KID_TILES_COUNT = 4,
+    KID_TILES_MOMENTS = 5,
+    KID_QUERY_RECTS = 6,
+    KID_QUERY_WEIGHTED = 7,
+    KID_EXPORT = 8,
+    KID_COUNT = 9
+};
 
-// Optional launch hook: mark(ctx, kid, 0, st) is called before a kernel is
-// launched on st and mark(ctx, kid, 1, st) right after.
+// Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
+// st and mark(ctx, kid, 1, st) right after.
 struct Prof {
     void *ctx;
     void (*mark)(void *ctx, int kid, int phase, cudaStream_t st);
@@ -54,7 +74,7 @@ struct ChanDev {
     int64_t pitch;
     int32_t bins;          // bins of the channel
     int32_t mode;          // 0: uniform over [0,256), 1: value is the bin
-    int32_t bin_off;       // first bin of the channel inside the plane set
+    int32_t bin_off;       // first bin of the channel in the count tensor
     int32_t pad;
 };
 
@@ -64,31 +84,51 @@ struct GroupDev {  // bins [b_lo, b_lo + nb) of channel `chan` (channel-local)
 
 struct TileGrid {
     int32_t H, W;      // frame
-    int32_t R, Wc;     // band rows, strip columns (Wc % kChunk == 0)
+    int32_t R, Wc;     // band rows (<= kMaxBandRows), strip columns (% kChunk == 0)
     int32_t nb, ns;    // number of bands, strips
-    int64_t P;         // row pitch of the output, elements (multiple of 4)
+    int64_t P;         // row pitch of the outputs, elements (multiple of 4)
 };
 
 struct PlaneSet {
     TileGrid g;
-    int32_t B;          // bins of the plane set
+    int32_t B;            // total bins (all channels)
     int32_t nchan;
+    int32_t layout;       // Layout of the count tensor
+    int32_t wch;          // weighted channel, or -1
     ChanDev chan[kMaxChannels];
-    int32_t ngroups;    // bin groups of the tiles kernel
-    int32_t npgroups;   // bin windows of the tile-sums kernel
+    int32_t ngroups;      // count bin groups (<= kGroupBins bins each)
+    int32_t nwin;         // tile-sums windows (<= kWindowBins bins each)
     GroupDev grp[kMaxGroups];
-    GroupDev pgrp[kMaxGroups];
-    void *out;          // T [B][H][P]
-    void *colsum;       // T [nb][B][W]   column sums -> G after the scan
-    void *rowsum;       // T [ns][B][H]   row sums    -> L after the scan
-    void *tilesum;      // T [nb][ns][B]
-    void *corner;       // T [nb][ns][B]
+    GroupDev win[kMaxGroups];
+    int64_t slab_off[kMaxGroups];  // LAYOUT_SLAB: element offset of group g's slab
+    int32_t *out;         // count tensor
+    int64_t *mom;         // moment planes [4][Bw][H][P] (w = c, r, c^2, r^2), or null
+    // carries (null when the frame is a single tile)
+    int32_t *colsum;      // [nb][B][W]  column counts -> G0 after the scan
+    int32_t *rowsum;      // [ns][B][H]  row counts    -> L0 after the scan
+    int32_t *tilesum;     // [nb][ns][B]
+    int32_t *corner;      // [nb][ns][B]
+    // weighted-channel carries (Bw = bins of channel wch)
+    int32_t *col_su;      // [nb][Bw][W] sum of (r-R0), (r-R0)^2 over the band
+    int32_t *col_suu;
+    int32_t *row_sv;      // [ns][Bw][H] sum of (c-C0), (c-C0)^2 over the strip
+    int32_t *row_svv;
+    int64_t *tile_w;      // [nb][ns][Bw][4]: sums of (r-R0), (r-R0)^2, (c-C0), (c-C0)^2
+    int64_t *g_r;         // [nb][Bw][W] G for w = r and r^2 (int64)
+    int64_t *g_rr;
+    int64_t *l_c;         // [ns][Bw][H] L for w = c and c^2 (int64)
+    int64_t *l_cc;
+    int64_t *corner_w;    // [nb][ns][Bw][4] corners for w = c, r, c^2, r^2
 };
 
-// Launchers (k_build.cu).  Each returns the number of kernels launched, or
-// -1 with the CUDA error left pending.
-int launch_plane_set(const PlaneSet &ps, int kind, cudaStream_t st, const Prof *prof);
-size_t tile_sums_smem_bytes(const PlaneSet &ps, int kind);
+// Bytes of carry scratch a plane set needs (0 for a single tile), and the
+// carving of one scratch block into the carry arrays.
+size_t carry_bytes(const PlaneSet &ps);
+void carve_carries(PlaneSet &ps, void *base);
+
+// Launchers (k_build.cu).  Return the number of kernels launched, or -1 with
+// the CUDA error left pending.
+int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof);
 
 // Feature pre-pass (k_features.cu): intensity and three orientation planes
 // (and optionally a copy of R, G, B) from planar RGB.
@@ -97,21 +137,27 @@ int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_
                     uint8_t *out_hog /* 3 planes */, int64_t out_pitch, cudaStream_t st,
                     const Prof *prof);
 
-// Queries (k_query.cu).
+// Read access to a count tensor in either layout (k_query.cu).
 struct CountView {
-    const int32_t *d;  // [B][H][P]
-    int32_t B, H, W;
+    const int32_t *d;
+    int32_t B, H, W, layout;
     int64_t P;
+    int32_t ngroups;
+    int16_t bin_group[kMaxBins];  // global bin -> group (LAYOUT_SLAB)
+    int16_t bin_local[kMaxBins];  // global bin -> bin inside its group
+    int16_t group_nb[kMaxGroups];
+    int64_t slab_off[kMaxGroups];
 };
 struct MomentView {
-    const int32_t *n;    // count planes of the weighted channel [Bw][H][P]
+    int32_t bin0;        // first bin of the weighted channel in the count tensor
     const int64_t *m;    // [4][Bw][H][P]: w = c, r, c^2, r^2
-    int32_t Bw, H, W;
-    int64_t P;
+    int32_t Bw;
 };
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out,
                        int *err, cudaStream_t st, const Prof *prof);
-int launch_query_weighted(const MomentView &v, const int32_t *wins, int64_t n, int normalize,
-                          float *out, int *err, cudaStream_t st, const Prof *prof);
+int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n,
+                          int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
+// Count tensor -> packed bin-major B x H x W int32.
+int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
 
 }  // namespace ih

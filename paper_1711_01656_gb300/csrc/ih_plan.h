@@ -1,16 +1,19 @@
-// ih_plan.h -- tile-grid choice for one plane set.
+// ih_plan.h -- tile-grid choice for one build.
 //
 // Larger tiles mean fewer carry bytes (the carries are about 1/R + 1/Wc of
-// the output per pass); smaller tiles mean more independent warps.  The
-// default rule takes the largest tile that still gives every SM at least
-// `kWarpsPerSm` warps of work; an explicit override (set by the autotuner
-// through ih_plan_override) replaces it for matching shapes.
+// the output); smaller tiles mean more independent warps.  The default rule
+// takes the largest tile that still gives every SM `kWarpsPerSm` warps of
+// count-tile work.  A tuned choice (ih_tune) overrides it for a shape.
 #pragma once
 
 #include "ih_internal.cuh"
 
 namespace ih {
 
-TileGrid choose_grid(int H, int W, int B, int kind, int nsm);
+// groups: warps of count-tile work per tile (the number of bin groups).
+TileGrid choose_grid(int H, int W, int groups, int nsm);
+
+// Tile grid with explicit band rows and strip width (clamped to the frame).
+TileGrid make_grid(int H, int W, int R, int Wc);
 
 }  // namespace ih

@@ -50,14 +50,6 @@ cudaError_t static_scratch_address(int dev, void **out)
     return cudaSuccess;
 }
 
-size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
-
-size_t carry_bytes(const TileGrid &g, int B)
-{
-    if ((int64_t)g.nb * g.ns <= 1) return 0;
-    return round256(4ull * B * g.W * g.nb) + round256(4ull * B * g.H * g.ns) + 2 * round256(4ull * B * g.nb * g.ns);
-}
-
 int split_groups(int bins, int cap, GroupDev *out)
 {
     const int ng = (bins + cap - 1) / cap;
@@ -85,40 +77,31 @@ extern "C" ih_status ih_build_counts_static(const uint8_t *d_pixels, int32_t hei
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IH_ECUDA;
 
     PlaneSet ps{};
-    ps.g = choose_grid(height, width, bins, WK_ONE, nsm);
-    if (carry_bytes(ps.g, bins) > kStaticScratchBytes) {
-        // the largest tiles need the least carry scratch
-        TileGrid big = ps.g;
-        big.R = height < kMaxBandRows ? height : kMaxBandRows;
-        big.Wc = 1024;
-        big.nb = (height + big.R - 1) / big.R;
-        big.ns = (width + big.Wc - 1) / big.Wc;
-        if (carry_bytes(big, bins) > kStaticScratchBytes) return IH_ETOOBIG;
-        ps.g = big;
-    }
-    ps.g.P = out_pitch;
     ps.B = bins;
     ps.nchan = 1;
+    ps.layout = LAYOUT_BIN_MAJOR;
+    ps.wch = -1;
     ps.chan[0].plane = d_pixels;
     ps.chan[0].pitch = pitch_bytes;
     ps.chan[0].bins = bins;
     ps.chan[0].mode = mode;
     ps.chan[0].bin_off = 0;
-    ps.ngroups = split_groups(bins, 8, ps.grp);
-    ps.npgroups = split_groups(bins, 32, ps.pgrp);
+    // groups by size, largest first (one tiles launch per size)
+    GroupDev tmp[kMaxGroups];
+    const int ng = split_groups(bins, kGroupBins, tmp);
+    ps.ngroups = 0;
+    for (int size = kGroupBins; size >= 1; --size)
+        for (int k = 0; k < ng; ++k)
+            if (tmp[k].nb == size) ps.grp[ps.ngroups++] = tmp[k];
+    ps.nwin = split_groups(bins, kWindowBins, ps.win);
+    ps.g = choose_grid(height, width, ps.ngroups, nsm);
+    if (carry_bytes(ps) > kStaticScratchBytes) ps.g = make_grid(height, width, kMaxBandRows, 1024);
+    if (carry_bytes(ps) > kStaticScratchBytes) return IH_ETOOBIG;
+    ps.g.P = out_pitch;
     ps.out = d_out;
-    if ((int64_t)ps.g.nb * ps.g.ns > 1) {
-        void *base = nullptr;
-        if (static_scratch_address(dev, &base) != cudaSuccess) return IH_ECUDA;
-        char *s = static_cast<char *>(base);
-        const size_t a = round256(4ull * bins * ps.g.W * ps.g.nb);
-        const size_t b = round256(4ull * bins * ps.g.H * ps.g.ns);
-        const size_t c = round256(4ull * bins * ps.g.nb * ps.g.ns);
-        ps.colsum = s;
-        ps.rowsum = s + a;
-        ps.tilesum = s + a + b;
-        ps.corner = s + a + b + c;
-    }
-    if (launch_plane_set(ps, WK_ONE, static_cast<cudaStream_t>(stream), nullptr) < 0) return IH_ECUDA;
+    void *base = nullptr;
+    if (carry_bytes(ps) && static_scratch_address(dev, &base) != cudaSuccess) return IH_ECUDA;
+    carve_carries(ps, base);
+    if (launch_build(ps, static_cast<cudaStream_t>(stream), nullptr) < 0) return IH_ECUDA;
     return IH_OK;
 }

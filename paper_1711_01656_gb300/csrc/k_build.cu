@@ -1,26 +1,38 @@
-// k_build.cu -- integral histograms (Eq. 2.15) and weighted integral
-// histograms (Eq. 3.4) on a grid of tiles, written once.
+// k_build.cu -- integral histograms (Eq. 2.15) and moment planes (Eq. 3.4)
+// on a grid of tiles, every output cell written once.
 //
-// Per pixel the thesis's Algorithm 5 adds Q(k, I(x,y)) into a recurrence that
-// is serial in both directions.  Here the frame is cut into bands of R rows
-// and strips of Wc columns; three kernels remove the serial dependence:
+// Algorithm 5 adds Q(k, I(x,y)) into a recurrence that is serial along rows
+// and columns.  The frame is cut into bands of R rows and strips of Wc
+// columns and three kernels remove the serial dependence (ih_internal.cuh):
 //
-//   k_tile_sums   reads the pixels of one tile and a window of bins and
-//                 accumulates, in shared memory, the column sums over the
-//                 band and the row sums over the strip (bin-independent
-//                 cost per pixel: two shared-memory atomics);
-//   k_carry_scan  turns them into the exclusive prefixes G (over bands, per
-//                 column), L (over strips, per row) and the tile corners;
-//   k_ih_tiles    one warp per (tile, bin group): the warp covers 128
-//                 columns (4 per lane), walks the band's rows, forms each
-//                 row's prefix with an in-lane prefix plus a warp shuffle
-//                 scan, adds the row carry and accumulates down the
-//                 columns in registers, and stores each output cell once
-//                 with 16-byte stores (a warp writes 512 contiguous bytes
-//                 per bin and row).
+// k_tile_sums  one CTA per (tile, window of <= 16 bins of one channel).  It
+//   stages the tile's bins in shared memory as bytes, then one thread per
+//   column walks down the band and one thread per row walks along the strip,
+//   accumulating run lengths in registers and flushing them to per-thread
+//   shared counters: no atomics.  For the weighted channel it also sums the
+//   offsets (r-R0), (r-R0)^2 per column and (c-C0), (c-C0)^2 per row, which
+//   are small enough for int32; the carry scan rebuilds the global int64
+//   moment carries from them.
+// k_carry_scan  exclusive prefixes over bands (G), strips (L) and both
+//   (corners), int32 for counts and int64 for the moments.
+// k_tiles_count  one warp per (tile, group of <= 8 bins).  A lane owns 4
+//   adjacent columns of a 128-column chunk; per row each pixel's bin becomes
+//   a one-hot packed as 8-bit fields (4 bins per 32-bit word), so one
+//   in-lane prefix and one warp shuffle scan of two words give the row
+//   prefix of all 8 bins (a field never exceeds 128, the chunk width).  Each
+//   column's running sum down the band lives in registers; each cell is
+//   stored once with 16-byte stores.  Pixel rows are prefetched 4 rows ahead.
+// k_tiles_moments  one warp per (tile, bin of the weighted channel); the same
+//   walk produces the four moment planes.  With u the column offset inside
+//   the chunk, the row prefixes of Q, u Q and u^2 Q are packed into two words
+//   (count: 8 bits, sum of u: 24 bits; sum of u^2: 32 bits), scanned once,
+//   and expanded to Sum c Q and Sum c^2 Q with the chunk's base column:
+//   c = C + u gives Sum c Q = C n + Sum u Q, Sum c^2 Q = C^2 n + 2C Sum u Q +
+//   Sum u^2 Q.  The row-weighted planes accumulate r * (row prefix of Q) and
+//   r^2 * (row prefix of Q).  All moment arithmetic is exact in int64.
 //
-// No kernel waits on another CTA; the only inter-CTA data flow is through
-// the carry arrays between launches on the same stream.
+// No kernel waits on another CTA; the only inter-CTA data flow is through the
+// carry arrays between launches on one stream.
 #include "ih_internal.cuh"
 
 namespace ih {
@@ -28,46 +40,13 @@ namespace ih {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
-
-template <int K>
-struct Wt;
-template <>
-struct Wt<WK_ONE> {
-    typedef int32_t T;
-    __device__ __forceinline__ static T w(int, int) { return 1; }
-};
-template <>
-struct Wt<WK_COL> {
-    typedef long long T;
-    __device__ __forceinline__ static T w(int, int c) { return c; }
-};
-template <>
-struct Wt<WK_ROW> {
-    typedef long long T;
-    __device__ __forceinline__ static T w(int r, int) { return r; }
-};
-template <>
-struct Wt<WK_COL2> {
-    typedef long long T;
-    __device__ __forceinline__ static T w(int, int c) { return (long long)c * c; }
-};
-template <>
-struct Wt<WK_ROW2> {
-    typedef long long T;
-    __device__ __forceinline__ static T w(int r, int) { return (long long)r * r; }
-};
+constexpr int kQStride = kSumCols + 4;  // padded row of the staged byte tile
 
 // Eq. 2.15's Q: the channel-local bin of value v, or -1 for none.
 __device__ __forceinline__ int bin_of(int v, int bins, int mode)
 {
     if (mode == 0) return (v * bins) >> 8;
     return v < bins ? v : -1;
-}
-
-__device__ __forceinline__ void sm_add(int32_t *p, int32_t v) { atomicAdd(p, v); }
-__device__ __forceinline__ void sm_add(long long *p, long long v)
-{
-    atomicAdd(reinterpret_cast<unsigned long long *>(p), static_cast<unsigned long long>(v));
 }
 
 template <typename T>
@@ -81,211 +60,407 @@ __device__ __forceinline__ T warp_incl_scan(T x, int lane)
     return x;
 }
 
-__device__ __forceinline__ void store4(int32_t *p, const int32_t (&a)[4])
-{
-    *reinterpret_cast<int4 *>(p) = make_int4(a[0], a[1], a[2], a[3]);
-}
-__device__ __forceinline__ void store4(long long *p, const long long (&a)[4])
-{
-    reinterpret_cast<longlong2 *>(p)[0] = make_longlong2(a[0], a[1]);
-    reinterpret_cast<longlong2 *>(p)[1] = make_longlong2(a[2], a[3]);
-}
-
-// Channel-local bins of the 4 pixels (r, c..c+3); -1 outside [0, cend).
-__device__ __forceinline__ void load_bins(const ChanDev &ch, int r, int c, int cend, bool vec_ok,
-                                          int (&q)[4])
+// The 4 pixels (r, c..c+3) of a channel as packed bytes (pixel j in byte j);
+// bytes at or beyond `cend` are 0 and must be masked by the caller.
+__device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int cend, bool vec_ok)
 {
     const uint8_t *row = ch.plane + (int64_t)r * ch.pitch;
-    if (vec_ok && c + 3 < cend) {
-        const uint32_t v = __ldg(reinterpret_cast<const unsigned int *>(row + c));
+    if (vec_ok && c + 3 < cend) return __ldg(reinterpret_cast<const unsigned int *>(row + c));
+    uint32_t v = 0;
 #pragma unroll
-        for (int jj = 0; jj < 4; ++jj) q[jj] = bin_of((v >> (8 * jj)) & 0xff, ch.bins, ch.mode);
-    } else {
-#pragma unroll
-        for (int jj = 0; jj < 4; ++jj)
-            q[jj] = (c + jj < cend) ? bin_of(__ldg(row + c + jj), ch.bins, ch.mode) : -1;
-    }
+    for (int jj = 0; jj < 4; ++jj)
+        if (c + jj < cend) v |= (uint32_t)__ldg(row + c + jj) << (8 * jj);
+    return v;
 }
 
-constexpr int kSumCols = 256;  // columns per pass of k_tile_sums
+// ------------------------------------------------------------- tile sums
 
-template <int K, int BW>
-__global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ PlaneSet ps)
+struct SumsSmem {
+    static constexpr size_t q = (size_t)kMaxBandRows * kQStride;
+    static constexpr size_t col = (size_t)kWindowBins * kSumCols * 4;
+    static constexpr size_t row = (size_t)kWindowBins * kMaxBandRows * 4;
+    static constexpr size_t count_bytes = q + col + row;
+    static constexpr size_t weighted_bytes = q + 3 * col + 3 * row;
+};
+
+template <bool WT>
+__global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
 {
-    typedef typename Wt<K>::T T;
     const TileGrid &g = ps.g;
     const int j = blockIdx.x, i = blockIdx.y;
-    const GroupDev pg = ps.pgrp[blockIdx.z];
-    const ChanDev &ch = ps.chan[pg.chan];
+    const GroupDev wd = ps.win[win0 + blockIdx.z];
+    const ChanDev &ch = ps.chan[wd.chan];
     const int R0 = i * g.R, nr = min(g.R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
-    const int64_t bg0 = ch.bin_off + pg.b_lo;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T *row_acc = reinterpret_cast<T *>(smem);  // [R][BW]
-    T *col_acc = row_acc + g.R * BW;           // [BW][kSumCols]
+    const int nbw = wd.nb;
+    const int64_t bglob = ch.bin_off + wd.b_lo;
+    const int Bw = WT ? ch.bins : 0;
     const int tid = threadIdx.x;
-    T *colsum = static_cast<T *>(ps.colsum);
-    T *rowsum = static_cast<T *>(ps.rowsum);
-    T *tilesum = static_cast<T *>(ps.tilesum);
 
-    for (int k = tid; k < nr * BW; k += blockDim.x) row_acc[k] = 0;
+    extern __shared__ __align__(16) unsigned char sm[];
+    uint8_t *qt = sm;
+    int32_t *col_cnt = reinterpret_cast<int32_t *>(sm + SumsSmem::q);  // [16][kSumCols]
+    int32_t *row_cnt = col_cnt + kWindowBins * kSumCols;              // [16][kMaxBandRows]
+    int32_t *col_su = row_cnt + kWindowBins * kMaxBandRows;
+    int32_t *col_suu = col_su + kWindowBins * kSumCols;
+    int32_t *row_sv = col_suu + kWindowBins * kSumCols;
+    int32_t *row_svv = row_sv + kWindowBins * kMaxBandRows;
+
+    for (int k = tid; k < kWindowBins * kMaxBandRows; k += blockDim.x) {
+        row_cnt[k] = 0;
+        if (WT) {
+            row_sv[k] = 0;
+            row_svv[k] = 0;
+        }
+    }
     for (int cp = C0; cp < C1; cp += kSumCols) {
         const int cw = min(kSumCols, C1 - cp);
-        for (int k = tid; k < BW * kSumCols; k += blockDim.x) col_acc[k] = 0;
-        __syncthreads();
+        for (int k = tid; k < kWindowBins * kSumCols; k += blockDim.x) {
+            col_cnt[k] = 0;
+            if (WT) {
+                col_su[k] = 0;
+                col_suu[k] = 0;
+            }
+        }
         for (int idx = tid; idx < nr * kSumCols; idx += blockDim.x) {
             const int rr = idx / kSumCols, cc = idx % kSumCols;
-            if (cc < cw) {
-                const int r = R0 + rr, c = cp + cc;
-                const int q = bin_of(__ldg(ch.plane + (int64_t)r * ch.pitch + c), ch.bins, ch.mode) -
-                              pg.b_lo;
-                if (q >= 0 && q < pg.nb) {
-                    const T w = Wt<K>::w(r, c);
-                    sm_add(&col_acc[q * kSumCols + cc], w);
-                    sm_add(&row_acc[rr * BW + q], w);
+            int v = -1;
+            if (cc < cw) v = bin_of(__ldg(ch.plane + (int64_t)(R0 + rr) * ch.pitch + cp + cc), ch.bins, ch.mode) - wd.b_lo;
+            qt[rr * kQStride + cc] = (v >= 0 && v < nbw) ? (uint8_t)v : (uint8_t)0xFF;
+        }
+        __syncthreads();
+        // one thread per column: counts (and offset sums) down the band
+        for (int t = tid; t < cw; t += blockDim.x) {
+            int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
+            for (int rr = 0; rr < nr; ++rr) {
+                const int q = qt[rr * kQStride + t];
+                if (q != cur) {
+                    if (cur != 0xFF) {
+                        col_cnt[cur * kSumCols + t] += n;
+                        if (WT) {
+                            col_su[cur * kSumCols + t] += s1;
+                            col_suu[cur * kSumCols + t] += s2;
+                        }
+                    }
+                    cur = q;
+                    n = s1 = s2 = 0;
+                }
+                ++n;
+                if (WT) {
+                    s1 += rr;
+                    s2 += rr * rr;
+                }
+            }
+            if (cur != 0xFF) {
+                col_cnt[cur * kSumCols + t] += n;
+                if (WT) {
+                    col_su[cur * kSumCols + t] += s1;
+                    col_suu[cur * kSumCols + t] += s2;
+                }
+            }
+        }
+        // one thread per row: counts (and offset sums) along this pass
+        for (int t = tid; t < nr; t += blockDim.x) {
+            int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
+            const int u0 = cp - C0;
+            for (int cc = 0; cc < cw; ++cc) {
+                const int q = qt[t * kQStride + cc];
+                if (q != cur) {
+                    if (cur != 0xFF) {
+                        row_cnt[cur * kMaxBandRows + t] += n;
+                        if (WT) {
+                            row_sv[cur * kMaxBandRows + t] += s1;
+                            row_svv[cur * kMaxBandRows + t] += s2;
+                        }
+                    }
+                    cur = q;
+                    n = s1 = s2 = 0;
+                }
+                ++n;
+                if (WT) {
+                    const int u = u0 + cc;
+                    s1 += u;
+                    s2 += u * u;
+                }
+            }
+            if (cur != 0xFF) {
+                row_cnt[cur * kMaxBandRows + t] += n;
+                if (WT) {
+                    row_sv[cur * kMaxBandRows + t] += s1;
+                    row_svv[cur * kMaxBandRows + t] += s2;
                 }
             }
         }
         __syncthreads();
-        for (int k = tid; k < pg.nb * kSumCols; k += blockDim.x) {
+        for (int k = tid; k < nbw * kSumCols; k += blockDim.x) {
             const int b = k / kSumCols, cc = k % kSumCols;
-            if (cc < cw) colsum[((int64_t)i * ps.B + bg0 + b) * g.W + cp + cc] = col_acc[b * kSumCols + cc];
+            if (cc < cw) {
+                ps.colsum[((int64_t)i * ps.B + bglob + b) * g.W + cp + cc] = col_cnt[b * kSumCols + cc];
+                if (WT) {
+                    const int64_t o = ((int64_t)i * Bw + wd.b_lo + b) * g.W + cp + cc;
+                    ps.col_su[o] = col_su[b * kSumCols + cc];
+                    ps.col_suu[o] = col_suu[b * kSumCols + cc];
+                }
+            }
         }
         __syncthreads();
     }
-    for (int k = tid; k < pg.nb * nr; k += blockDim.x) {
+    for (int k = tid; k < nbw * nr; k += blockDim.x) {
         const int b = k / nr, rr = k % nr;
-        rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] = row_acc[rr * BW + b];
+        ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = row_cnt[b * kMaxBandRows + rr];
+        if (WT) {
+            const int64_t o = ((int64_t)j * Bw + wd.b_lo + b) * g.H + R0 + rr;
+            ps.row_sv[o] = row_sv[b * kMaxBandRows + rr];
+            ps.row_svv[o] = row_svv[b * kMaxBandRows + rr];
+        }
     }
-    if (tid < pg.nb) {
-        T s = 0;
-        for (int rr = 0; rr < nr; ++rr) s += row_acc[rr * BW + tid];
-        tilesum[((int64_t)i * g.ns + j) * ps.B + bg0 + tid] = s;
+    if (tid < nbw) {
+        const int b = tid;
+        int32_t n = 0;
+        long long su = 0, suu = 0, sv = 0, svv = 0;
+        for (int rr = 0; rr < nr; ++rr) {
+            const int32_t x = row_cnt[b * kMaxBandRows + rr];
+            n += x;
+            if (WT) {
+                su += (long long)rr * x;
+                suu += (long long)rr * rr * x;
+                sv += row_sv[b * kMaxBandRows + rr];
+                svv += row_svv[b * kMaxBandRows + rr];
+            }
+        }
+        ps.tilesum[((int64_t)i * g.ns + j) * ps.B + bglob + b] = n;
+        if (WT) {
+            int64_t *tw = ps.tile_w + (((int64_t)i * g.ns + j) * Bw + wd.b_lo + b) * 4;
+            tw[0] = su;
+            tw[1] = suu;
+            tw[2] = sv;
+            tw[3] = svv;
+        }
     }
 }
 
-template <int K>
+// ------------------------------------------------------------- carry scan
+
 __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ PlaneSet ps)
 {
-    typedef typename Wt<K>::T T;
     const TileGrid &g = ps.g;
     const int64_t B = ps.B;
+    const int wch = ps.wch;
+    const int64_t bin0 = wch >= 0 ? ps.chan[wch].bin_off : 0;
+    const int64_t Bw = wch >= 0 ? ps.chan[wch].bins : 0;
     const int64_t nA = B * g.W, nB = B * g.H, nC = (int64_t)g.ns * B;
-    T *colsum = static_cast<T *>(ps.colsum);
-    T *rowsum = static_cast<T *>(ps.rowsum);
-    const T *tilesum = static_cast<const T *>(ps.tilesum);
-    T *corner = static_cast<T *>(ps.corner);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nA + nB + nC;
          t += (int64_t)gridDim.x * blockDim.x) {
         if (t < nA) {  // G(i, c, b): exclusive over bands
-            T *p = colsum + t;
-            T run = 0;
+            const int64_t b = t / g.W, c = t % g.W, wb = b - bin0;
+            const bool wt = wb >= 0 && wb < Bw;
+            int32_t run = 0;
+            long long rr1 = 0, rr2 = 0;
+#pragma unroll 4
             for (int i = 0; i < g.nb; ++i) {
-                const T v = p[(int64_t)i * nA];
-                p[(int64_t)i * nA] = run;
+                const int64_t idx = (int64_t)i * nA + t;
+                const int32_t v = ps.colsum[idx];
+                ps.colsum[idx] = run;
+                if (wt) {
+                    const int64_t o = ((int64_t)i * Bw + wb) * g.W + c;
+                    const long long su = ps.col_su[o], suu = ps.col_suu[o];
+                    const long long R0 = (long long)i * g.R;
+                    ps.g_r[o] = rr1;
+                    ps.g_rr[o] = rr2;
+                    rr1 += R0 * v + su;
+                    rr2 += R0 * R0 * v + 2 * R0 * su + suu;
+                }
                 run += v;
             }
         } else if (t < nA + nB) {  // L(j, r, b): exclusive over strips
-            T *p = rowsum + (t - nA);
-            T run = 0;
+            const int64_t u = t - nA;
+            const int64_t b = u / g.H, r = u % g.H, wb = b - bin0;
+            const bool wt = wb >= 0 && wb < Bw;
+            int32_t run = 0;
+            long long rc1 = 0, rc2 = 0;
+#pragma unroll 4
             for (int j = 0; j < g.ns; ++j) {
-                const T v = p[(int64_t)j * nB];
-                p[(int64_t)j * nB] = run;
+                const int64_t idx = (int64_t)j * nB + u;
+                const int32_t v = ps.rowsum[idx];
+                ps.rowsum[idx] = run;
+                if (wt) {
+                    const int64_t o = ((int64_t)j * Bw + wb) * g.H + r;
+                    const long long sv = ps.row_sv[o], svv = ps.row_svv[o];
+                    const long long C0 = (long long)j * g.Wc;
+                    ps.l_c[o] = rc1;
+                    ps.l_cc[o] = rc2;
+                    rc1 += C0 * v + sv;
+                    rc2 += C0 * C0 * v + 2 * C0 * sv + svv;
+                }
                 run += v;
             }
-        } else {  // corner(i, j, b) = sum over tiles above-left
+        } else {  // corners: sums over the tiles above-left
             const int64_t u = t - nA - nB;
             const int j = (int)(u / B);
-            const int64_t b = u % B;
-            T run = 0;
+            const int64_t b = u % B, wb = b - bin0;
+            const bool wt = wb >= 0 && wb < Bw;
+            int32_t run = 0;
+            long long rw[4] = {0, 0, 0, 0};  // w = c, r, c^2, r^2
             for (int i = 0; i < g.nb; ++i) {
-                corner[((int64_t)i * g.ns + j) * B + b] = run;
-                T s = 0;
-                for (int jj = 0; jj < j; ++jj) s += tilesum[((int64_t)i * g.ns + jj) * B + b];
-                run += s;
+                ps.corner[((int64_t)i * g.ns + j) * B + b] = run;
+                if (wt) {
+                    int64_t *cw = ps.corner_w + (((int64_t)i * g.ns + j) * Bw + wb) * 4;
+                    cw[0] = rw[0];
+                    cw[1] = rw[1];
+                    cw[2] = rw[2];
+                    cw[3] = rw[3];
+                }
+                const long long R0 = (long long)i * g.R;
+                for (int jj = 0; jj < j; ++jj) {
+                    const int32_t n = ps.tilesum[((int64_t)i * g.ns + jj) * B + b];
+                    run += n;
+                    if (wt) {
+                        const int64_t *tw = ps.tile_w + (((int64_t)i * g.ns + jj) * Bw + wb) * 4;
+                        const long long C0 = (long long)jj * g.Wc;
+                        rw[0] += C0 * n + tw[2];
+                        rw[1] += R0 * n + tw[0];
+                        rw[2] += C0 * C0 * n + 2 * C0 * tw[2] + tw[3];
+                        rw[3] += R0 * R0 * n + 2 * R0 * tw[0] + tw[1];
+                    }
+                }
             }
         }
     }
 }
 
-template <int K, int NB>
-__global__ void __launch_bounds__(128) k_ih_tiles(const __grid_constant__ PlaneSet ps)
+// ------------------------------------------------------------- count tiles
+
+// Store the 4 pixels x NB bins of one lane in the slab layout: the lane's
+// records are contiguous (pixel-major, bins innermost), NB int4 stores.
+template <int NB>
+__device__ __forceinline__ void store_slab(int32_t *p, const int (&acc)[NB][4])
 {
-    typedef typename Wt<K>::T T;
-    __shared__ T RLs[4][kMaxBandRows * NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        int v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int f = 4 * k + e;  // flat index: pixel f / NB, bin f % NB
+            v[e] = acc[f % NB][f / NB];
+        }
+        reinterpret_cast<int4 *>(p)[k] = make_int4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// One launch per group size NB: the units are (tile, group g_begin + k) for
+// k < g_count, all of whose groups hold exactly NB bins.
+template <int LAYOUT, int NB>
+__global__ void __launch_bounds__(128, 5) k_tiles_count(const __grid_constant__ PlaneSet ps, int g_begin,
+                                                        int g_count)
+{
+    __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
-    const int ng = ps.ngroups;
+    const int ng = g_count;
     const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
     if (unit >= (int64_t)g.nb * g.ns * ng) return;  // whole warp
-    const int tile = (int)(unit / ng), gi = (int)(unit % ng);
+    const int tile = (int)(unit / ng), gi = g_begin + (int)(unit % ng);
     const int i = tile / g.ns, j = tile % g.ns;
     const GroupDev gr = ps.grp[gi];
     const ChanDev &ch = ps.chan[gr.chan];
+    constexpr int nbg = NB;
     const int64_t bg0 = ch.bin_off + gr.b_lo;
     const int R0 = i * g.R, nr = min(g.R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
-    T *RL = RLs[wid];
-    const T *Lc = static_cast<const T *>(ps.rowsum);
-    const T *Gc = static_cast<const T *>(ps.colsum);
-    const T *Cc = static_cast<const T *>(ps.corner);
-    T *out = static_cast<T *>(ps.out);
+    int32_t(*RL)[kGroupBins] = RLs[wid];
 
-    // row carries L(j, r, b) of this band, per bin of the group
-    for (int k = lane; k < nr * NB; k += 32) {
-        const int rr = k / NB, b = k % NB;
-        RL[k] = (Lc && b < gr.nb) ? Lc[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] : T(0);
+    for (int k = lane; k < nr * kGroupBins; k += 32) {
+        const int rr = k / kGroupBins, b = k % kGroupBins;
+        RL[rr][b] = (ps.rowsum && b < nbg) ? ps.rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] : 0;
     }
-    T TR[NB];  // corner + sum of G over the strip's columns left of the chunk
+    int TR[NB];  // H(R0-1, chunk start - 1) per bin
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-        TR[b] = (Cc && b < gr.nb) ? Cc[((int64_t)i * g.ns + j) * ps.B + bg0 + b] : T(0);
+    for (int b = 0; b < NB; ++b) TR[b] = ps.corner ? ps.corner[((int64_t)i * g.ns + j) * ps.B + bg0 + b] : 0;
     __syncwarp();
 
     const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
     for (int cc = C0; cc < C1; cc += kChunk) {
         const int c = cc + lane * 4;
-        T acc[NB][4];
-        // seed each column with H(R0-1, c): corner + prefix of G along the strip
+        const int nvalid = max(0, min(4, C1 - c));
+        int acc[NB][4];
+        // seed each column with H(R0-1, c): the corner plus the prefix of G
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-            T p[4];
+            int p[4] = {0, 0, 0, 0};
+            if (ps.colsum) {
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
-                p[jj] = (Gc && b < gr.nb && c + jj < C1)
-                            ? Gc[((int64_t)i * ps.B + bg0 + b) * g.W + c + jj]
-                            : T(0);
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj < nvalid) p[jj] = ps.colsum[((int64_t)i * ps.B + bg0 + b) * g.W + c + jj];
+            }
             p[1] += p[0];
             p[2] += p[1];
             p[3] += p[2];
-            const T incl = warp_incl_scan(p[3], lane);
-            const T base = TR[b] + (incl - p[3]);
+            const int incl = warp_incl_scan(p[3], lane);
+            const int base = TR[b] + (incl - p[3]);
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) acc[b][jj] = base + p[jj];
+            for (int jj = 0; jj < 4; ++jj) acc[b][jj] = p[jj] + base;
             TR[b] += __shfl_sync(kFull, incl, 31);
         }
-        for (int rr = 0; rr < nr; ++rr) {
-            const int r = R0 + rr;
-            int q[4];
-            load_bins(ch, r, c, C1, vec_ok, q);
+        uint32_t pf[4];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-                if (b < gr.nb) {  // warp-uniform
-                    const int bin = gr.b_lo + b;
-                    T p[4];
+        for (int k = 0; k < 4; ++k) pf[k] = (k < nr) ? load4(ch, R0 + k, c, C1, vec_ok) : 0u;
+        for (int rr0 = 0; rr0 < nr; rr0 += 4) {
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) p[jj] = (q[jj] == bin) ? Wt<K>::w(r, c + jj) : T(0);
-                    p[1] += p[0];
-                    p[2] += p[1];
-                    p[3] += p[2];
-                    const T incl = warp_incl_scan(p[3], lane);
-                    const T base = RL[rr * NB + b] + (incl - p[3]);
+            for (int k = 0; k < 4; ++k) {
+                const int rr = rr0 + k;
+                if (rr >= nr) break;  // warp-uniform
+                const uint32_t px = pf[k];
+                if (rr + 4 < nr) pf[k] = load4(ch, R0 + rr + 4, c, C1, vec_ok);
+                // packed one-hot of the 4 pixels and its in-lane prefix
+                uint32_t P0[4], P1[4];
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) acc[b][jj] += base + p[jj];
-                    if (c < g.P) store4(out + ((bg0 + b) * g.H + r) * g.P + c, acc[b]);
-                    const T tot = __shfl_sync(kFull, incl, 31);
-                    __syncwarp();
-                    if (lane == 0) RL[rr * NB + b] += tot;
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int q = bin_of((px >> (8 * jj)) & 0xff, ch.bins, ch.mode);
+                    const unsigned d = (jj < nvalid && q >= 0) ? (unsigned)(q - gr.b_lo) : 0xFFFFFFFFu;
+                    const uint32_t e0 = d < 4u ? (1u << (d << 3)) : 0u;
+                    const uint32_t e1 = (d - 4u) < 4u ? (1u << ((d - 4u) << 3)) : 0u;
+                    P0[jj] = (jj ? P0[jj - 1] : 0u) + e0;
+                    P1[jj] = (jj ? P1[jj - 1] : 0u) + e1;
+                }
+                const uint32_t i0 = warp_incl_scan(P0[3], lane);
+                const uint32_t i1 = NB > 4 ? warp_incl_scan(P1[3], lane) : 0u;
+                const uint32_t x0 = i0 - P0[3], x1 = i1 - P1[3];
+                const uint32_t t0 = __shfl_sync(kFull, i0, 31);
+                const uint32_t t1 = NB > 4 ? __shfl_sync(kFull, i1, 31) : 0u;
+                const int4 rl0 = *reinterpret_cast<const int4 *>(&RL[rr][0]);
+                const int4 rl1 = *reinterpret_cast<const int4 *>(&RL[rr][4]);
+                const int rl[8] = {rl0.x, rl0.y, rl0.z, rl0.w, rl1.x, rl1.y, rl1.z, rl1.w};
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const uint32_t y0 = x0 + P0[jj], y1 = x1 + P1[jj];
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        acc[b][jj] += rl[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
+                }
+                const int r = R0 + rr;
+                if (c < g.P) {
+                    if (LAYOUT == LAYOUT_BIN_MAJOR) {
+#pragma unroll
+                        for (int b = 0; b < NB; ++b)
+                            *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + r) * g.P + c) =
+                                make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+                    } else {
+                        store_slab<NB>(ps.out + ps.slab_off[gi] + ((int64_t)r * g.P + c) * NB, acc);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    int4 a, b4;
+                    a.x = rl[0] + (int)__byte_perm(t0, 0, 0x4440);
+                    a.y = rl[1] + (int)__byte_perm(t0, 0, 0x4441);
+                    a.z = rl[2] + (int)__byte_perm(t0, 0, 0x4442);
+                    a.w = rl[3] + (int)__byte_perm(t0, 0, 0x4443);
+                    b4.x = rl[4] + (int)__byte_perm(t1, 0, 0x4440);
+                    b4.y = rl[5] + (int)__byte_perm(t1, 0, 0x4441);
+                    b4.z = rl[6] + (int)__byte_perm(t1, 0, 0x4442);
+                    b4.w = rl[7] + (int)__byte_perm(t1, 0, 0x4443);
+                    *reinterpret_cast<int4 *>(&RL[rr][0]) = a;
+                    *reinterpret_cast<int4 *>(&RL[rr][4]) = b4;
                 }
             }
         }
@@ -293,59 +468,267 @@ __global__ void __launch_bounds__(128) k_ih_tiles(const __grid_constant__ PlaneS
     }
 }
 
-template <int K, int BW>
-void set_smem_attr(size_t bytes)
+// ------------------------------------------------------------- moment tiles
+
+__global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant__ PlaneSet ps)
 {
-    cudaFuncSetAttribute(k_tile_sums<K, BW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    __shared__ int32_t sRLn[4][kMaxBandRows];
+    __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const TileGrid &g = ps.g;
+    const ChanDev &ch = ps.chan[ps.wch];
+    const int Bw = ch.bins;
+    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+    if (unit >= (int64_t)g.nb * g.ns * Bw) return;  // whole warp
+    const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
+    const int i = tile / g.ns, j = tile % g.ns;
+    const int64_t bglob = ch.bin_off + wb;
+    const int R0 = i * g.R, nr = min(g.R, g.H - R0);
+    const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
+    const bool carries = ps.colsum != nullptr;
+    int32_t *RLn = sRLn[wid];
+    long long *RLx = sRLx[wid], *RLxx = sRLxx[wid];
+
+    for (int rr = lane; rr < nr; rr += 32) {
+        RLn[rr] = carries ? ps.rowsum[((int64_t)j * ps.B + bglob) * g.H + R0 + rr] : 0;
+        RLx[rr] = carries ? ps.l_c[((int64_t)j * Bw + wb) * g.H + R0 + rr] : 0;
+        RLxx[rr] = carries ? ps.l_cc[((int64_t)j * Bw + wb) * g.H + R0 + rr] : 0;
+    }
+    long long TR[4] = {0, 0, 0, 0};  // w = c, r, c^2, r^2
+    if (carries) {
+        const int64_t *cw = ps.corner_w + (((int64_t)i * g.ns + j) * Bw + wb) * 4;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) TR[k] = cw[k];
+    }
+    __syncwarp();
+    const int64_t plane = (int64_t)Bw * g.H * g.P;
+    int64_t *mo = ps.mom + (int64_t)wb * g.H * g.P;
+    const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
+
+    for (int cc = C0; cc < C1; cc += kChunk) {
+        const int c = cc + lane * 4;
+        const int nvalid = max(0, min(4, C1 - c));
+        long long acc[4][4];  // [plane][pixel]
+        // seeds: H_w(R0-1, c) = corner_w + prefix over the strip of the top carries
+        {
+            long long p[4][4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                long long g0 = 0, gr = 0, grr = 0;
+                if (carries && jj < nvalid) {
+                    const int64_t cidx = c + jj;
+                    g0 = ps.colsum[((int64_t)i * ps.B + bglob) * g.W + cidx];
+                    gr = ps.g_r[((int64_t)i * Bw + wb) * g.W + cidx];
+                    grr = ps.g_rr[((int64_t)i * Bw + wb) * g.W + cidx];
+                }
+                const long long cj = c + jj;
+                p[0][jj] = cj * g0;
+                p[1][jj] = gr;
+                p[2][jj] = cj * cj * g0;
+                p[3][jj] = grr;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                p[k][1] += p[k][0];
+                p[k][2] += p[k][1];
+                p[k][3] += p[k][2];
+                const long long incl = warp_incl_scan(p[k][3], lane);
+                const long long base = TR[k] + (incl - p[k][3]);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[k][jj] = base + p[k][jj];
+                TR[k] += __shfl_sync(kFull, incl, 31);
+            }
+        }
+        const long long Cb = cc;
+        uint32_t pf[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pf[k] = (k < nr) ? load4(ch, R0 + k, c, C1, vec_ok) : 0u;
+        for (int rr0 = 0; rr0 < nr; rr0 += 4) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int rr = rr0 + k;
+                if (rr >= nr) break;  // warp-uniform
+                const uint32_t px = pf[k];
+                if (rr + 4 < nr) pf[k] = load4(ch, R0 + rr + 4, c, C1, vec_ok);
+                int pn[4], pu[4], puu[4];
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int q = bin_of((px >> (8 * jj)) & 0xff, ch.bins, ch.mode);
+                    const int e = (jj < nvalid && q == wb) ? 1 : 0;
+                    const int u = lane * 4 + jj;
+                    pn[jj] = (jj ? pn[jj - 1] : 0) + e;
+                    pu[jj] = (jj ? pu[jj - 1] : 0) + e * u;
+                    puu[jj] = (jj ? puu[jj - 1] : 0) + e * u * u;
+                }
+                // count <= 128 (8 bits) | sum of u <= 8128 (24 bits); sum of u^2 <= 690880
+                const uint32_t w1 = (uint32_t)pn[3] | ((uint32_t)pu[3] << 8);
+                const uint32_t w2 = (uint32_t)puu[3];
+                const uint32_t i1 = warp_incl_scan(w1, lane), i2 = warp_incl_scan(w2, lane);
+                const uint32_t x1 = i1 - w1, x2 = i2 - w2;
+                const uint32_t t1 = __shfl_sync(kFull, i1, 31), t2 = __shfl_sync(kFull, i2, 31);
+                const int ex_n = (int)(x1 & 0xFF), ex_u = (int)(x1 >> 8), ex_uu = (int)x2;
+                const int rn = RLn[rr];
+                const long long rx = RLx[rr], rxx = RLxx[rr];
+                const long long r = R0 + rr;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const long long n = ex_n + pn[jj];          // row prefix of Q inside the chunk
+                    const long long su = ex_u + pu[jj];         // ... of u Q
+                    const long long suu = ex_uu + puu[jj];      // ... of u^2 Q
+                    const long long N = rn + n;                 // row prefix of Q from column 0
+                    acc[0][jj] += rx + Cb * n + su;
+                    acc[1][jj] += r * N;
+                    acc[2][jj] += rxx + Cb * Cb * n + 2 * Cb * su + suu;
+                    acc[3][jj] += r * r * N;
+                }
+                if (c < g.P) {
+                    const int64_t o = (int64_t)(R0 + rr) * g.P + c;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        longlong2 *dst = reinterpret_cast<longlong2 *>(mo + k * plane + o);
+                        dst[0] = make_longlong2(acc[k][0], acc[k][1]);
+                        dst[1] = make_longlong2(acc[k][2], acc[k][3]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    const long long tn = t1 & 0xFF, tu = t1 >> 8, tuu = t2;
+                    RLn[rr] = rn + (int)tn;
+                    RLx[rr] = rx + Cb * tn + tu;
+                    RLxx[rr] = rxx + Cb * Cb * tn + 2 * Cb * tu + tuu;
+                }
+            }
+        }
+        __syncwarp();
+    }
 }
 
-template <int K, int NB>
-int launch_kind(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+template <int LAYOUT>
+void launch_tiles_count(int nb, unsigned blocks, cudaStream_t st, const PlaneSet &ps, int gb, int gc)
 {
-    constexpr int BW = (K == WK_ONE) ? 32 : 16;
-    int n = 0;
-    const TileGrid &g = ps.g;
-    if (ps.colsum) {
-        const size_t smem = tile_sums_smem_bytes(ps, K);
-        if (smem > 48 * 1024) set_smem_attr<K, BW>(smem);
-        prof_mark(prof, kid_sums(K), 0, st);
-        k_tile_sums<K, BW><<<dim3(g.ns, g.nb, ps.npgroups), 256, smem, st>>>(ps);
-        prof_mark(prof, kid_sums(K), 1, st);
-        ++n;
-        const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.ns * ps.B;
-        const int64_t blocks = (tot + 255) / 256;
-        prof_mark(prof, kid_scan(K), 0, st);
-        k_carry_scan<K><<<(unsigned)(blocks < 4864 ? blocks : 4864), 256, 0, st>>>(ps);
-        prof_mark(prof, kid_scan(K), 1, st);
-        ++n;
+    switch (nb) {
+    case 1: k_tiles_count<LAYOUT, 1><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    case 2: k_tiles_count<LAYOUT, 2><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    case 3: k_tiles_count<LAYOUT, 3><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    case 4: k_tiles_count<LAYOUT, 4><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    case 5: k_tiles_count<LAYOUT, 5><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    case 6: k_tiles_count<LAYOUT, 6><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    case 7: k_tiles_count<LAYOUT, 7><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    default: k_tiles_count<LAYOUT, 8><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
     }
-    const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
-    prof_mark(prof, kid_tiles(K), 0, st);
-    k_ih_tiles<K, NB><<<(unsigned)((units + 3) / 4), 128, 0, st>>>(ps);
-    prof_mark(prof, kid_tiles(K), 1, st);
-    ++n;
-    return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
+
+template <typename F>
+void set_max_smem(F *f, size_t bytes)
+{
+    cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
-size_t tile_sums_smem_bytes(const PlaneSet &ps, int kind)
+size_t carry_bytes(const PlaneSet &ps)
 {
-    const size_t bw = (kind == WK_ONE) ? 32 : 16;
-    const size_t el = (kind == WK_ONE) ? 4 : 8;
-    return (ps.g.R * bw + bw * kSumCols) * el;
+    const TileGrid &g = ps.g;
+    if ((int64_t)g.nb * g.ns <= 1) return 0;
+    const size_t B = ps.B, W = g.W, H = g.H, nb = g.nb, ns = g.ns;
+    size_t n = r256(4 * B * W * nb) + r256(4 * B * H * ns) + 2 * r256(4 * nb * ns * B);
+    if (ps.wch >= 0) {
+        const size_t Bw = ps.chan[ps.wch].bins;
+        n += 2 * r256(4 * Bw * W * nb) + 2 * r256(4 * Bw * H * ns) + r256(32 * nb * ns * Bw);
+        n += 2 * r256(8 * Bw * W * nb) + 2 * r256(8 * Bw * H * ns) + r256(32 * nb * ns * Bw);
+    }
+    return n;
 }
 
-int launch_plane_set(const PlaneSet &ps, int kind, cudaStream_t st, const Prof *prof)
+void carve_carries(PlaneSet &ps, void *base)
 {
-    switch (kind) {
-    case WK_ONE: return launch_kind<WK_ONE, 8>(ps, st, prof);
-    case WK_COL: return launch_kind<WK_COL, 4>(ps, st, prof);
-    case WK_ROW: return launch_kind<WK_ROW, 4>(ps, st, prof);
-    case WK_COL2: return launch_kind<WK_COL2, 4>(ps, st, prof);
-    case WK_ROW2: return launch_kind<WK_ROW2, 4>(ps, st, prof);
+    const TileGrid &g = ps.g;
+    ps.colsum = ps.rowsum = ps.tilesum = ps.corner = nullptr;
+    ps.col_su = ps.col_suu = ps.row_sv = ps.row_svv = nullptr;
+    ps.tile_w = ps.g_r = ps.g_rr = ps.l_c = ps.l_cc = ps.corner_w = nullptr;
+    if (!base || (int64_t)g.nb * g.ns <= 1) return;
+    char *s = static_cast<char *>(base);
+    const size_t B = ps.B, W = g.W, H = g.H, nb = g.nb, ns = g.ns;
+    auto take = [&s](size_t bytes) {
+        char *p = s;
+        s += r256(bytes);
+        return p;
+    };
+    ps.colsum = reinterpret_cast<int32_t *>(take(4 * B * W * nb));
+    ps.rowsum = reinterpret_cast<int32_t *>(take(4 * B * H * ns));
+    ps.tilesum = reinterpret_cast<int32_t *>(take(4 * nb * ns * B));
+    ps.corner = reinterpret_cast<int32_t *>(take(4 * nb * ns * B));
+    if (ps.wch >= 0) {
+        const size_t Bw = ps.chan[ps.wch].bins;
+        ps.col_su = reinterpret_cast<int32_t *>(take(4 * Bw * W * nb));
+        ps.col_suu = reinterpret_cast<int32_t *>(take(4 * Bw * W * nb));
+        ps.row_sv = reinterpret_cast<int32_t *>(take(4 * Bw * H * ns));
+        ps.row_svv = reinterpret_cast<int32_t *>(take(4 * Bw * H * ns));
+        ps.tile_w = reinterpret_cast<int64_t *>(take(32 * nb * ns * Bw));
+        ps.g_r = reinterpret_cast<int64_t *>(take(8 * Bw * W * nb));
+        ps.g_rr = reinterpret_cast<int64_t *>(take(8 * Bw * W * nb));
+        ps.l_c = reinterpret_cast<int64_t *>(take(8 * Bw * H * ns));
+        ps.l_cc = reinterpret_cast<int64_t *>(take(8 * Bw * H * ns));
+        ps.corner_w = reinterpret_cast<int64_t *>(take(32 * nb * ns * Bw));
     }
-    return -1;
+}
+
+int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+{
+    static bool attrs = false;
+    if (!attrs) {
+        set_max_smem(k_tile_sums<false>, SumsSmem::count_bytes);
+        set_max_smem(k_tile_sums<true>, SumsSmem::weighted_bytes);
+        attrs = true;
+    }
+    const TileGrid &g = ps.g;
+    int n = 0;
+    if (ps.colsum) {
+        int nw_count = 0, nw_weighted = 0;
+        for (int k = 0; k < ps.nwin; ++k) (ps.win[k].chan == ps.wch ? nw_weighted : nw_count) += 1;
+        if (nw_count) {
+            prof_mark(prof, KID_SUMS_COUNT, 0, st);
+            k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), 256, SumsSmem::count_bytes, st>>>(ps, 0);
+            prof_mark(prof, KID_SUMS_COUNT, 1, st);
+            ++n;
+        }
+        if (nw_weighted) {
+            prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
+            k_tile_sums<true><<<dim3(g.ns, g.nb, nw_weighted), 256, SumsSmem::weighted_bytes, st>>>(ps, nw_count);
+            prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
+            ++n;
+        }
+        const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.ns * ps.B;
+        const int64_t blocks = (tot + 255) / 256;
+        prof_mark(prof, KID_SCAN, 0, st);
+        k_carry_scan<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(ps);
+        prof_mark(prof, KID_SCAN, 1, st);
+        ++n;
+    }
+    for (int gb = 0; gb < ps.ngroups;) {
+        int ge = gb;
+        while (ge < ps.ngroups && ps.grp[ge].nb == ps.grp[gb].nb) ++ge;
+        const int gc = ge - gb;
+        const unsigned blocks = (unsigned)(((int64_t)g.nb * g.ns * gc + 3) / 4);
+        prof_mark(prof, KID_TILES_COUNT, 0, st);
+        if (ps.layout == LAYOUT_SLAB)
+            launch_tiles_count<LAYOUT_SLAB>(ps.grp[gb].nb, blocks, st, ps, gb, gc);
+        else
+            launch_tiles_count<LAYOUT_BIN_MAJOR>(ps.grp[gb].nb, blocks, st, ps, gb, gc);
+        prof_mark(prof, KID_TILES_COUNT, 1, st);
+        ++n;
+        gb = ge;
+    }
+    if (ps.mom) {
+        const int64_t mu = (int64_t)g.nb * g.ns * ps.chan[ps.wch].bins;
+        prof_mark(prof, KID_TILES_MOMENTS, 0, st);
+        k_tiles_moments<<<(unsigned)((mu + 3) / 4), 128, 0, st>>>(ps);
+        prof_mark(prof, KID_TILES_MOMENTS, 1, st);
+        ++n;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
 
 }  // namespace ih

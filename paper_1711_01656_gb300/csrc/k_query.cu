@@ -2,6 +2,8 @@
 //
 // Rectangle histograms by the four-corner rule of Eq. 2.16 and spatially
 // weighted local histograms (Eq. 3.1) from the moment planes of Eq. 3.4.
+// One thread per (query, bin); consecutive threads take consecutive bins of
+// one query, which in the slab layout are consecutive words of each corner.
 //
 // Weighted histogram, Epanechnikov window kernel.  For window
 // [r0,r1] x [c0,c1] with w = c1-c0+1, h = r1-r0+1, mc = c0+c1, mr = r0+r1:
@@ -29,8 +31,24 @@ __device__ __forceinline__ bool box_ok(int r0, int c0, int r1, int c1, int H, in
     return r0 >= 0 && c0 >= 0 && r0 <= r1 && c0 <= c1 && r1 < H && c1 < W;
 }
 
-template <typename T>
-__device__ __forceinline__ long long four_corner(const T *p, int64_t P, int r0, int c0, int r1, int c1)
+// Address of H(b, r, c) in either count layout.
+__device__ __forceinline__ const int32_t *count_ptr(const CountView &v, int b, int64_t r, int64_t c)
+{
+    if (v.layout == LAYOUT_BIN_MAJOR) return v.d + ((int64_t)b * v.H + r) * v.P + c;
+    const int g = v.bin_group[b];
+    return v.d + v.slab_off[g] + (r * v.P + c) * v.group_nb[g] + v.bin_local[b];
+}
+
+__device__ __forceinline__ long long count_four(const CountView &v, int b, int r0, int c0, int r1, int c1)
+{
+    const long long a = __ldg(count_ptr(v, b, r1, c1));
+    const long long bb = r0 > 0 ? (long long)__ldg(count_ptr(v, b, r0 - 1, c1)) : 0;
+    const long long cc = c0 > 0 ? (long long)__ldg(count_ptr(v, b, r1, c0 - 1)) : 0;
+    const long long d = (r0 > 0 && c0 > 0) ? (long long)__ldg(count_ptr(v, b, r0 - 1, c0 - 1)) : 0;
+    return a - bb - cc + d;
+}
+
+__device__ __forceinline__ long long four_corner(const int64_t *p, int64_t P, int r0, int c0, int r1, int c1)
 {
     const long long a = __ldg(p + (int64_t)r1 * P + c1);
     const long long b = r0 > 0 ? (long long)__ldg(p + (int64_t)(r0 - 1) * P + c1) : 0;
@@ -39,11 +57,11 @@ __device__ __forceinline__ long long four_corner(const T *p, int64_t P, int r0, 
     return a - b - c + d;
 }
 
-__global__ void __launch_bounds__(256) k_query_rects(const CountView v, const int32_t *__restrict__ rects,
-                                                     int64_t n, int32_t *__restrict__ out, int *err)
+__global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ CountView v,
+                                                     const int32_t *__restrict__ rects, int64_t n,
+                                                     int32_t *__restrict__ out, int *err)
 {
     const int64_t total = n * v.B;
-    const int64_t plane = (int64_t)v.H * v.P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t qi = t / v.B;
@@ -55,21 +73,21 @@ __global__ void __launch_bounds__(256) k_query_rects(const CountView v, const in
             if (b == 0) atomicOr(err, 1);
             continue;
         }
-        out[t] = (int32_t)four_corner(v.d + b * plane, v.P, r0, c0, r1, c1);
+        out[t] = (int32_t)count_four(v, b, r0, c0, r1, c1);
     }
 }
 
-__global__ void __launch_bounds__(256) k_query_weighted(const MomentView v, const int32_t *__restrict__ wins,
-                                                        int64_t n, int normalize, float *__restrict__ out,
-                                                        int *err)
+__global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ CountView v, const MomentView m,
+                                                        const int32_t *__restrict__ wins, int64_t n,
+                                                        int normalize, float *__restrict__ out, int *err)
 {
-    const int64_t total = n * v.Bw;
+    const int64_t total = n * m.Bw;
     const int64_t plane = (int64_t)v.H * v.P;
-    const int64_t mplane = (int64_t)v.Bw * plane;
+    const int64_t mplane = (int64_t)m.Bw * plane;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = t / v.Bw;
-        const int b = (int)(t - qi * v.Bw);
+        const int64_t qi = t / m.Bw;
+        const int b = (int)(t - qi * m.Bw);
         const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
         const int r1 = __ldg(wins + 4 * qi + 2), c1 = __ldg(wins + 4 * qi + 3);
         if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= 32768 || c1 - c0 >= 32768) {
@@ -77,12 +95,12 @@ __global__ void __launch_bounds__(256) k_query_weighted(const MomentView v, cons
             if (b == 0) atomicOr(err, 1);
             continue;
         }
-        const long long N = four_corner(v.n + b * plane, v.P, r0, c0, r1, c1);
+        const long long N = count_four(v, m.bin0 + b, r0, c0, r1, c1);
         const int64_t mo = b * plane;
-        const long long Sc = four_corner(v.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Sr = four_corner(v.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Scc = four_corner(v.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Srr = four_corner(v.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Scc = four_corner(m.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Srr = four_corner(m.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
         const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
         const long long mc = c0 + c1, mr = r0 + r1;
         const long long X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
@@ -113,6 +131,18 @@ __global__ void __launch_bounds__(256) k_query_weighted(const MomentView v, cons
     }
 }
 
+__global__ void __launch_bounds__(256) k_export(const __grid_constant__ CountView v, int32_t *__restrict__ dst)
+{
+    const int64_t total = (int64_t)v.B * v.H * v.W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % v.W, rb = t / v.W;
+        const int64_t r = rb % v.H;
+        const int b = (int)(rb / v.H);
+        dst[t] = __ldg(count_ptr(v, b, r, c));
+    }
+}
+
 unsigned grid_for(int64_t total)
 {
     const int64_t b = (total + 255) / 256;
@@ -131,13 +161,21 @@ int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int3
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_query_weighted(const MomentView &v, const int32_t *wins, int64_t n, int normalize, float *out,
-                          int *err, cudaStream_t st, const Prof *prof)
+int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n, int normalize,
+                          float *out, int *err, cudaStream_t st, const Prof *prof)
 {
     if (n == 0) return 0;
     prof_mark(prof, KID_QUERY_WEIGHTED, 0, st);
-    k_query_weighted<<<grid_for(n * v.Bw), 256, 0, st>>>(v, wins, n, normalize, out, err);
+    k_query_weighted<<<grid_for(n * m.Bw), 256, 0, st>>>(v, m, wins, n, normalize, out, err);
     prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof)
+{
+    prof_mark(prof, KID_EXPORT, 0, st);
+    k_export<<<grid_for((int64_t)v.B * v.H * v.W), 256, 0, st>>>(v, dst);
+    prof_mark(prof, KID_EXPORT, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

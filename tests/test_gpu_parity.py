@@ -17,7 +17,7 @@ DEV = torch.device("cuda:0")
 WTOL = 1e-5
 
 
-def _build(ih, ctx, planes, chans, weighted=-1, pitch=None):
+def _build(ih, ctx, planes, chans, weighted=-1, pitch=None, layout=0):
     planes = np.asarray(planes, dtype=np.uint8)
     if planes.ndim == 2:
         planes = planes[None]
@@ -29,7 +29,7 @@ def _build(ih, ctx, planes, chans, weighted=-1, pitch=None):
         pix = buf[:, :, :w]
     else:
         pix = torch.from_numpy(planes).to(DEV)
-    hdl, = ih.ih_build(ctx, ih.Frame(pix, chans, weighted_channel=weighted))
+    hdl, = ih.ih_build(ctx, ih.Frame(pix, chans, weighted_channel=weighted, layout=layout))
     return hdl, pix
 
 
@@ -56,21 +56,23 @@ SHAPES = [(1, 1), (1, 7), (7, 1), (2, 3), (37, 53), (33, 129), (64, 128), (65, 2
           (200, 611), (257, 1030)]
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("h,w", SHAPES)
 @pytest.mark.parametrize("bins", [1, 3, 16, 32])
-def test_counts_exact(ihlib, ctx, h, w, bins):
+def test_counts_exact(ihlib, ctx, h, w, bins, layout):
     img = synth.uniform_plane(h, w, h * 1000 + w + bins)
-    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)])
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)], layout=layout)
     got = _export(ihlib, ctx, hdl)
     ih_ref = oracle.integral_histogram(img, bins)
     assert np.array_equal(got, ih_ref)
     ihlib.ih_release(ctx, hdl)
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("bins", [2, 7, 9, 40, 64, 200, 256])
-def test_counts_exact_bin_counts(ihlib, ctx, bins):
+def test_counts_exact_bin_counts(ihlib, ctx, bins, layout):
     img = synth.blob_plane(150, 260, bins)
-    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)])
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)], layout=layout)
     assert np.array_equal(_export(ihlib, ctx, hdl), oracle.integral_histogram(img, bins))
     ihlib.ih_release(ctx, hdl)
 
@@ -91,12 +93,13 @@ def test_counts_pitched_input(ihlib, ctx, pitch):
     ihlib.ih_release(ctx, hdl)
 
 
-def test_counts_multichannel(ihlib, ctx):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_counts_multichannel(ihlib, ctx, layout):
     h, w = 123, 517
     planes = np.stack([synth.uniform_plane(h, w, 10 + k) for k in range(4)])
     planes[3] %= 9
     chans = [(16, 0), (5, 0), (32, 0), (9, 1)]
-    hdl, _ = _build(ihlib, ctx, planes, chans)
+    hdl, _ = _build(ihlib, ctx, planes, chans, layout=layout)
     assert np.array_equal(_export(ihlib, ctx, hdl), oracle.frame_integral_histogram(planes, chans))
     ihlib.ih_release(ctx, hdl)
 
@@ -178,10 +181,11 @@ def _rects_gpu(ihlib, ctx, hdl, rects, B):
     return out
 
 
-def test_rects_all_of_small_frame(ihlib, ctx):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_rects_all_of_small_frame(ihlib, ctx, layout):
     h, w, bins = 14, 19, 5
     img = synth.uniform_plane(h, w, 4)
-    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)])
+    hdl, _ = _build(ihlib, ctx, img, [(bins, 0)], layout=layout)
     rects = np.array([(r0, c0, r1, c1) for r0 in range(h) for r1 in range(r0, h)
                       for c0 in range(w) for c1 in range(c0, w)], np.int32)
     got = _rects_gpu(ihlib, ctx, hdl, rects, bins)
@@ -228,7 +232,8 @@ def test_plain_frame_640x480_all_rects(ihlib, ctx):
     ihlib.ih_release(ctx, hdl)
 
 
-def test_fmv_frame_1920x1080_features(ihlib, ctx):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_fmv_frame_1920x1080_features(ihlib, ctx, layout):
     """One 1920x1080 RGB frame, 7 feature channels (91 bins): the full
     tensor vs Algorithm 5 and 100,000 rectangles (a seeded 2,000 by
     enumeration, all by four corners of the oracle's own tensor)."""
@@ -237,7 +242,7 @@ def test_fmv_frame_1920x1080_features(ihlib, ctx):
     chans = synth.FMV_CHANNELS
     B = sum(b for b, _ in chans)
     hdl, = ihlib.ih_build(ctx, ihlib.Frame(torch.from_numpy(rgb).to(DEV), chans,
-                                           input=ihlib.IH_INPUT_RGB_FEATURES))
+                                           input=ihlib.IH_INPUT_RGB_FEATURES, layout=layout))
     rects = synth.rects_uniform_corners(h, w, 100000, synth.config_seed(2) + 100)
     got = _rects_gpu(ihlib, ctx, hdl, rects, B).cpu().numpy()
     tens = _export(ihlib, ctx, hdl)
@@ -256,7 +261,8 @@ def test_fmv_frame_1920x1080_features(ihlib, ctx):
 # ---------------------------------------------------------------- moments + weighted
 
 
-@pytest.mark.parametrize("h,w,bins", [(1, 1, 2), (5, 7, 3), (64, 128, 16), (131, 389, 16), (260, 520, 8)])
+@pytest.mark.parametrize("h,w,bins", [(1, 1, 2), (5, 7, 3), (64, 128, 16), (131, 389, 16), (260, 520, 8),
+                                      (300, 1500, 32), (1100, 300, 5)])
 def test_moment_planes_exact(ihlib, ctx, h, w, bins):
     img = synth.blob_plane(h, w, h + w)
     hdl, _ = _build(ihlib, ctx, img, [(bins, 0)], weighted=0)
@@ -277,11 +283,12 @@ def _weighted_gpu(ihlib, ctx, hdl, wins, Bw, normalize=False):
     return out.cpu().numpy()
 
 
+@pytest.mark.parametrize("layout", [0, 1])
 @pytest.mark.parametrize("normalize", [False, True])
-def test_weighted_vs_direct_sum(ihlib, ctx, normalize):
+def test_weighted_vs_direct_sum(ihlib, ctx, normalize, layout):
     h, w = 300, 400
     img = synth.blob_plane(h, w, 12)
-    hdl, _ = _build(ihlib, ctx, img, [(16, 0)], weighted=0)
+    hdl, _ = _build(ihlib, ctx, img, [(16, 0)], weighted=0, layout=layout)
     wins = np.concatenate([synth.rects_side_range(h, w, 1500, 1, 64, 3),
                            synth.rects_side_range(h, w, 100, 32, 256, 4),
                            np.array([[0, 0, h - 1, w - 1], [0, 0, 0, 0], [h - 1, w - 1, h - 1, w - 1]])])
@@ -299,12 +306,14 @@ def test_weighted_hand_example(ihlib, ctx):
     ihlib.ih_release(ctx, hdl)
 
 
-def test_weighted_on_feature_channel(ihlib, ctx):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_weighted_on_feature_channel(ihlib, ctx, layout):
     h, w = 200, 330
     rgb = synth.blob_rgb(h, w, 8)
     chans = synth.FMV_CHANNELS
     hdl, = ihlib.ih_build(ctx, ihlib.Frame(torch.from_numpy(rgb).to(DEV), chans,
-                                           input=ihlib.IH_INPUT_RGB_FEATURES, weighted_channel=3))
+                                           input=ihlib.IH_INPUT_RGB_FEATURES, weighted_channel=3,
+                                           layout=layout))
     wins = synth.rects_side_range(h, w, 500, 2, 150, 5)
     got = _weighted_gpu(ihlib, ctx, hdl, wins, 16)
     ref = oracle.weighted_hist(oracle.features(rgb)[3], 16, wins)
@@ -349,3 +358,24 @@ def test_invalid_descriptors(ihlib, ctx):
     with pytest.raises(ihlib.IHError) as ei:
         ihlib.ih_query_rects(ctx, 12345, None, torch.empty(0, device=DEV))
     assert ei.value.status == ihlib.IH_ENOTBUILT
+
+
+@pytest.mark.parametrize("wch", [0, 2])
+def test_moments_on_multichannel_frame(ihlib, ctx, wch):
+    """The moment planes of one channel of a multi-channel frame, with the
+    counts of all channels, on a frame that spans many tiles."""
+    h, w = 333, 1100
+    planes = np.stack([synth.blob_plane(h, w, 30 + k) for k in range(3)])
+    chans = [(16, 0), (9, 0), (12, 0)]
+    hdl, _ = _build(ihlib, ctx, planes, chans, weighted=wch, layout=1)
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.frame_integral_histogram(planes, chans))
+    bw = chans[wch][0]
+    for plane, wk in enumerate(oracle.MOMENT_WEIGHTS):
+        out = torch.empty((bw, h, w), dtype=torch.int64, device=DEV)
+        ihlib.ih_export_moments(ctx, hdl, plane, out)
+        ihlib.ih_sync(ctx)
+        assert np.array_equal(out.cpu().numpy(), oracle.weighted_integral_histogram(planes[wch], bw, wk))
+    wins = synth.rects_side_range(h, w, 300, 1, 200, 6)
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, bw)
+    _assert_weighted(got, oracle.weighted_hist(planes[wch], bw, wins))
+    ihlib.ih_release(ctx, hdl)
