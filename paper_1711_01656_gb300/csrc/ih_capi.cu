@@ -230,6 +230,7 @@ void make_view(const PlaneSet &ps, const int32_t *d, CountView &v)
     for (int k = 0; k < ps.ngroups; ++k) {
         const GroupDev &gr = ps.grp[k];
         v.group_nb[k] = gr.nb;
+        v.group_bin0[k] = (int16_t)(ps.chan[gr.chan].bin_off + gr.b_lo);
         v.slab_off[k] = ps.slab_off[k];
         for (int b = 0; b < gr.nb; ++b) {
             const int gb = ps.chan[gr.chan].bin_off + gr.b_lo + b;

@@ -33,7 +33,7 @@ constexpr int kChunk = 128;       // columns a warp covers at once (4 per lane)
 constexpr int kMaxBandRows = 128;
 constexpr int kGroupBins = 8;     // bins per warp in the count tiles kernel
 constexpr int kWindowBins = 16;   // bins per CTA in the tile-sums kernel
-constexpr int kSumCols = 256;     // columns per pass of the tile-sums kernel
+constexpr int kSumCols = 128;     // columns per pass of the tile-sums kernel
 
 // Count-tensor layouts.
 enum Layout {
@@ -146,6 +146,7 @@ struct CountView {
     int16_t bin_group[kMaxBins];  // global bin -> group (LAYOUT_SLAB)
     int16_t bin_local[kMaxBins];  // global bin -> bin inside its group
     int16_t group_nb[kMaxGroups];
+    int16_t group_bin0[kMaxGroups];  // first global bin of each group
     int64_t slab_off[kMaxGroups];
 };
 struct MomentView {

@@ -33,6 +33,8 @@
 //
 // No kernel waits on another CTA; the only inter-CTA data flow is through the
 // carry arrays between launches on one stream.
+#include <algorithm>
+
 #include "ih_internal.cuh"
 
 namespace ih {
@@ -75,6 +77,8 @@ __device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int c
 
 // ------------------------------------------------------------- tile sums
 
+constexpr int kSumThreads = 128;
+
 struct SumsSmem {
     static constexpr size_t q = (size_t)kMaxBandRows * kQStride;
     static constexpr size_t col = (size_t)kWindowBins * kSumCols * 4;
@@ -83,8 +87,20 @@ struct SumsSmem {
     static constexpr size_t weighted_bytes = q + 3 * col + 3 * row;
 };
 
+// Bins of 4 pixels packed in a word, as window-local bytes (0xFF: none).
+__device__ __forceinline__ uint32_t window_bins4(uint32_t px, const ChanDev &ch, int b_lo, int nbw, int valid)
+{
+    uint32_t out = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int v = k < valid ? bin_of((px >> (8 * k)) & 0xff, ch.bins, ch.mode) - b_lo : -1;
+        out |= (uint32_t)((v >= 0 && v < nbw) ? v : 0xFF) << (8 * k);
+    }
+    return out;
+}
+
 template <bool WT>
-__global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
+__global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
 {
     const TileGrid &g = ps.g;
     const int j = blockIdx.x, i = blockIdx.y;
@@ -96,6 +112,7 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
     const int64_t bglob = ch.bin_off + wd.b_lo;
     const int Bw = WT ? ch.bins : 0;
     const int tid = threadIdx.x;
+    const bool vec16 = ((ch.pitch & 15) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 15) == 0);
 
     extern __shared__ __align__(16) unsigned char sm[];
     uint8_t *qt = sm;
@@ -106,7 +123,7 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
     int32_t *row_sv = col_suu + kWindowBins * kSumCols;
     int32_t *row_svv = row_sv + kWindowBins * kMaxBandRows;
 
-    for (int k = tid; k < kWindowBins * kMaxBandRows; k += blockDim.x) {
+    for (int k = tid; k < kWindowBins * kMaxBandRows; k += kSumThreads) {
         row_cnt[k] = 0;
         if (WT) {
             row_sv[k] = 0;
@@ -115,22 +132,48 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
     }
     for (int cp = C0; cp < C1; cp += kSumCols) {
         const int cw = min(kSumCols, C1 - cp);
-        for (int k = tid; k < kWindowBins * kSumCols; k += blockDim.x) {
+        for (int k = tid; k < kWindowBins * kSumCols; k += kSumThreads) {
             col_cnt[k] = 0;
             if (WT) {
                 col_su[k] = 0;
                 col_suu[k] = 0;
             }
         }
-        for (int idx = tid; idx < nr * kSumCols; idx += blockDim.x) {
-            const int rr = idx / kSumCols, cc = idx % kSumCols;
-            int v = -1;
-            if (cc < cw) v = bin_of(__ldg(ch.plane + (int64_t)(R0 + rr) * ch.pitch + cp + cc), ch.bins, ch.mode) - wd.b_lo;
-            qt[rr * kQStride + cc] = (v >= 0 && v < nbw) ? (uint8_t)v : (uint8_t)0xFF;
+        // stage the window-local bins of the nr x kSumCols pass, 16 pixels per
+        // item; all of a thread's loads are issued before any is used
+        constexpr int kSeg = kSumCols / 16;
+        constexpr int kItems = kMaxBandRows * kSeg / kSumThreads;
+        uint4 v[kItems];
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int idx = tid + k * kSumThreads, rr = idx / kSeg, c16 = (idx % kSeg) * 16;
+            v[k] = make_uint4(0, 0, 0, 0);
+            if (rr < nr && c16 < cw) {
+                const uint8_t *src = ch.plane + (int64_t)(R0 + rr) * ch.pitch + cp + c16;
+                if (vec16 && c16 + 16 <= cw) {
+                    v[k] = __ldg(reinterpret_cast<const uint4 *>(src));
+                } else {
+                    uint32_t w[4] = {0, 0, 0, 0};
+                    for (int e = 0; e < 16 && c16 + e < cw; ++e) w[e >> 2] |= (uint32_t)__ldg(src + e) << (8 * (e & 3));
+                    v[k] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int idx = tid + k * kSumThreads, rr = idx / kSeg, c16 = (idx % kSeg) * 16;
+            if (rr < nr) {
+                const int valid = cw - c16;
+                uint32_t *dst = reinterpret_cast<uint32_t *>(qt + rr * kQStride + c16);
+                dst[0] = window_bins4(v[k].x, ch, wd.b_lo, nbw, valid);
+                dst[1] = window_bins4(v[k].y, ch, wd.b_lo, nbw, valid - 4);
+                dst[2] = window_bins4(v[k].z, ch, wd.b_lo, nbw, valid - 8);
+                dst[3] = window_bins4(v[k].w, ch, wd.b_lo, nbw, valid - 12);
+            }
         }
         __syncthreads();
         // one thread per column: counts (and offset sums) down the band
-        for (int t = tid; t < cw; t += blockDim.x) {
+        for (int t = tid; t < cw; t += kSumThreads) {
             int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
             for (int rr = 0; rr < nr; ++rr) {
                 const int q = qt[rr * kQStride + t];
@@ -160,27 +203,32 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
             }
         }
         // one thread per row: counts (and offset sums) along this pass
-        for (int t = tid; t < nr; t += blockDim.x) {
+        for (int t = tid; t < nr; t += kSumThreads) {
             int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
             const int u0 = cp - C0;
-            for (int cc = 0; cc < cw; ++cc) {
-                const int q = qt[t * kQStride + cc];
-                if (q != cur) {
-                    if (cur != 0xFF) {
-                        row_cnt[cur * kMaxBandRows + t] += n;
-                        if (WT) {
-                            row_sv[cur * kMaxBandRows + t] += s1;
-                            row_svv[cur * kMaxBandRows + t] += s2;
+            const uint32_t *rowq = reinterpret_cast<const uint32_t *>(qt + t * kQStride);
+            for (int c4 = 0; c4 < cw; c4 += 4) {
+                const uint32_t w4 = rowq[c4 >> 2];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int q = (w4 >> (8 * e)) & 0xff;
+                    if (q != cur) {
+                        if (cur != 0xFF) {
+                            row_cnt[cur * kMaxBandRows + t] += n;
+                            if (WT) {
+                                row_sv[cur * kMaxBandRows + t] += s1;
+                                row_svv[cur * kMaxBandRows + t] += s2;
+                            }
                         }
+                        cur = q;
+                        n = s1 = s2 = 0;
                     }
-                    cur = q;
-                    n = s1 = s2 = 0;
-                }
-                ++n;
-                if (WT) {
-                    const int u = u0 + cc;
-                    s1 += u;
-                    s2 += u * u;
+                    ++n;
+                    if (WT) {
+                        const int u = u0 + c4 + e;
+                        s1 += u;
+                        s2 += u * u;
+                    }
                 }
             }
             if (cur != 0xFF) {
@@ -192,7 +240,7 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
             }
         }
         __syncthreads();
-        for (int k = tid; k < nbw * kSumCols; k += blockDim.x) {
+        for (int k = tid; k < nbw * kSumCols; k += kSumThreads) {
             const int b = k / kSumCols, cc = k % kSumCols;
             if (cc < cw) {
                 ps.colsum[((int64_t)i * ps.B + bglob + b) * g.W + cp + cc] = col_cnt[b * kSumCols + cc];
@@ -205,7 +253,7 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
         }
         __syncthreads();
     }
-    for (int k = tid; k < nbw * nr; k += blockDim.x) {
+    for (int k = tid; k < nbw * nr; k += kSumThreads) {
         const int b = k / nr, rr = k % nr;
         ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = row_cnt[b * kMaxBandRows + rr];
         if (WT) {
@@ -240,6 +288,13 @@ __global__ void __launch_bounds__(256) k_tile_sums(const __grid_constant__ Plane
 }
 
 // ------------------------------------------------------------- carry scan
+//
+// G and L are exclusive prefixes over bands and strips.  The tile corners
+// are split in two: here, per (band i, bin), the exclusive prefix over strips
+// of the tile sums ("corner" then holds sum_{j'<j} tilesum(i, j')); the tiles
+// kernels add these up over the bands above their own (a warp reduction).
+
+constexpr int kScanBatch = 8;
 
 __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ PlaneSet ps)
 {
@@ -248,7 +303,7 @@ __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ Plan
     const int wch = ps.wch;
     const int64_t bin0 = wch >= 0 ? ps.chan[wch].bin_off : 0;
     const int64_t Bw = wch >= 0 ? ps.chan[wch].bins : 0;
-    const int64_t nA = B * g.W, nB = B * g.H, nC = (int64_t)g.ns * B;
+    const int64_t nA = B * g.W, nB = B * g.H, nC = (int64_t)g.nb * B;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nA + nB + nC;
          t += (int64_t)gridDim.x * blockDim.x) {
         if (t < nA) {  // G(i, c, b): exclusive over bands
@@ -256,21 +311,38 @@ __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ Plan
             const bool wt = wb >= 0 && wb < Bw;
             int32_t run = 0;
             long long rr1 = 0, rr2 = 0;
-#pragma unroll 4
-            for (int i = 0; i < g.nb; ++i) {
-                const int64_t idx = (int64_t)i * nA + t;
-                const int32_t v = ps.colsum[idx];
-                ps.colsum[idx] = run;
+            for (int i0 = 0; i0 < g.nb; i0 += kScanBatch) {
+                const int ni = min(kScanBatch, g.nb - i0);
+                int32_t v[kScanBatch];
+#pragma unroll
+                for (int k = 0; k < kScanBatch; ++k)
+                    if (k < ni) v[k] = ps.colsum[(int64_t)(i0 + k) * nA + t];
+                int32_t su[kScanBatch], suu[kScanBatch];
                 if (wt) {
-                    const int64_t o = ((int64_t)i * Bw + wb) * g.W + c;
-                    const long long su = ps.col_su[o], suu = ps.col_suu[o];
-                    const long long R0 = (long long)i * g.R;
-                    ps.g_r[o] = rr1;
-                    ps.g_rr[o] = rr2;
-                    rr1 += R0 * v + su;
-                    rr2 += R0 * R0 * v + 2 * R0 * su + suu;
+#pragma unroll
+                    for (int k = 0; k < kScanBatch; ++k)
+                        if (k < ni) {
+                            const int64_t o = ((int64_t)(i0 + k) * Bw + wb) * g.W + c;
+                            su[k] = ps.col_su[o];
+                            suu[k] = ps.col_suu[o];
+                        }
                 }
-                run += v;
+#pragma unroll
+                for (int k = 0; k < kScanBatch; ++k) {
+                    if (k < ni) {
+                        const int i = i0 + k;
+                        ps.colsum[(int64_t)i * nA + t] = run;
+                        if (wt) {
+                            const int64_t o = ((int64_t)i * Bw + wb) * g.W + c;
+                            const long long R0 = (long long)i * g.R;
+                            ps.g_r[o] = rr1;
+                            ps.g_rr[o] = rr2;
+                            rr1 += R0 * v[k] + su[k];
+                            rr2 += R0 * R0 * v[k] + 2 * R0 * su[k] + suu[k];
+                        }
+                        run += v[k];
+                    }
+                }
             }
         } else if (t < nA + nB) {  // L(j, r, b): exclusive over strips
             const int64_t u = t - nA;
@@ -278,54 +350,80 @@ __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ Plan
             const bool wt = wb >= 0 && wb < Bw;
             int32_t run = 0;
             long long rc1 = 0, rc2 = 0;
-#pragma unroll 4
-            for (int j = 0; j < g.ns; ++j) {
-                const int64_t idx = (int64_t)j * nB + u;
-                const int32_t v = ps.rowsum[idx];
-                ps.rowsum[idx] = run;
+            for (int j0 = 0; j0 < g.ns; j0 += kScanBatch) {
+                const int nj = min(kScanBatch, g.ns - j0);
+                int32_t v[kScanBatch], sv[kScanBatch], svv[kScanBatch];
+#pragma unroll
+                for (int k = 0; k < kScanBatch; ++k)
+                    if (k < nj) v[k] = ps.rowsum[(int64_t)(j0 + k) * nB + u];
                 if (wt) {
-                    const int64_t o = ((int64_t)j * Bw + wb) * g.H + r;
-                    const long long sv = ps.row_sv[o], svv = ps.row_svv[o];
-                    const long long C0 = (long long)j * g.Wc;
-                    ps.l_c[o] = rc1;
-                    ps.l_cc[o] = rc2;
-                    rc1 += C0 * v + sv;
-                    rc2 += C0 * C0 * v + 2 * C0 * sv + svv;
+#pragma unroll
+                    for (int k = 0; k < kScanBatch; ++k)
+                        if (k < nj) {
+                            const int64_t o = ((int64_t)(j0 + k) * Bw + wb) * g.H + r;
+                            sv[k] = ps.row_sv[o];
+                            svv[k] = ps.row_svv[o];
+                        }
                 }
-                run += v;
+#pragma unroll
+                for (int k = 0; k < kScanBatch; ++k) {
+                    if (k < nj) {
+                        const int jj = j0 + k;
+                        ps.rowsum[(int64_t)jj * nB + u] = run;
+                        if (wt) {
+                            const int64_t o = ((int64_t)jj * Bw + wb) * g.H + r;
+                            const long long C0 = (long long)jj * g.Wc;
+                            ps.l_c[o] = rc1;
+                            ps.l_cc[o] = rc2;
+                            rc1 += C0 * v[k] + sv[k];
+                            rc2 += C0 * C0 * v[k] + 2 * C0 * sv[k] + svv[k];
+                        }
+                        run += v[k];
+                    }
+                }
             }
-        } else {  // corners: sums over the tiles above-left
+        } else {  // per band: exclusive prefix over strips of the tile sums
             const int64_t u = t - nA - nB;
-            const int j = (int)(u / B);
+            const int i = (int)(u / B);
             const int64_t b = u % B, wb = b - bin0;
             const bool wt = wb >= 0 && wb < Bw;
+            const long long R0 = (long long)i * g.R;
             int32_t run = 0;
             long long rw[4] = {0, 0, 0, 0};  // w = c, r, c^2, r^2
-            for (int i = 0; i < g.nb; ++i) {
-                ps.corner[((int64_t)i * g.ns + j) * B + b] = run;
+            for (int j = 0; j < g.ns; ++j) {
+                const int64_t ti = ((int64_t)i * g.ns + j) * B + b;
+                const int32_t n = ps.tilesum[ti];
+                ps.corner[ti] = run;
+                run += n;
                 if (wt) {
-                    int64_t *cw = ps.corner_w + (((int64_t)i * g.ns + j) * Bw + wb) * 4;
+                    const int64_t wi = (((int64_t)i * g.ns + j) * Bw + wb) * 4;
+                    const int64_t *tw = ps.tile_w + wi;
+                    int64_t *cw = ps.corner_w + wi;
                     cw[0] = rw[0];
                     cw[1] = rw[1];
                     cw[2] = rw[2];
                     cw[3] = rw[3];
-                }
-                const long long R0 = (long long)i * g.R;
-                for (int jj = 0; jj < j; ++jj) {
-                    const int32_t n = ps.tilesum[((int64_t)i * g.ns + jj) * B + b];
-                    run += n;
-                    if (wt) {
-                        const int64_t *tw = ps.tile_w + (((int64_t)i * g.ns + jj) * Bw + wb) * 4;
-                        const long long C0 = (long long)jj * g.Wc;
-                        rw[0] += C0 * n + tw[2];
-                        rw[1] += R0 * n + tw[0];
-                        rw[2] += C0 * C0 * n + 2 * C0 * tw[2] + tw[3];
-                        rw[3] += R0 * R0 * n + 2 * R0 * tw[0] + tw[1];
-                    }
+                    const long long C0 = (long long)j * g.Wc;
+                    rw[0] += C0 * n + tw[2];
+                    rw[1] += R0 * n + tw[0];
+                    rw[2] += C0 * C0 * n + 2 * C0 * tw[2] + tw[3];
+                    rw[3] += R0 * R0 * n + 2 * R0 * tw[0] + tw[1];
                 }
             }
         }
     }
+}
+
+// Sum over the bands above band i of a per-band value (the corner's second
+// half): lanes take bands i' = lane, lane + 32, ... < i, then a warp reduction.
+template <typename T, typename F>
+__device__ __forceinline__ T sum_bands_above(int i, int lane, F at)
+{
+    T s = 0;
+    for (int ib = lane; ib < i; ib += 32) s += at(ib);
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(kFull, s, d);
+    return s;
 }
 
 // ------------------------------------------------------------- count tiles
@@ -347,35 +445,29 @@ __device__ __forceinline__ void store_slab(int32_t *p, const int (&acc)[NB][4])
     }
 }
 
-// One launch per group size NB: the units are (tile, group g_begin + k) for
-// k < g_count, all of whose groups hold exactly NB bins.
+// One warp-unit of the count tiles: tile (i, j), group gi of exactly NB bins.
 template <int LAYOUT, int NB>
-__global__ void __launch_bounds__(128, 5) k_tiles_count(const __grid_constant__ PlaneSet ps, int g_begin,
-                                                        int g_count)
+__device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int j, int gi, int lane,
+                                                 int32_t (*RL)[kGroupBins])
 {
-    __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
-    const int ng = g_count;
-    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
-    if (unit >= (int64_t)g.nb * g.ns * ng) return;  // whole warp
-    const int tile = (int)(unit / ng), gi = g_begin + (int)(unit % ng);
-    const int i = tile / g.ns, j = tile % g.ns;
     const GroupDev gr = ps.grp[gi];
     const ChanDev &ch = ps.chan[gr.chan];
-    constexpr int nbg = NB;
     const int64_t bg0 = ch.bin_off + gr.b_lo;
     const int R0 = i * g.R, nr = min(g.R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
-    int32_t(*RL)[kGroupBins] = RLs[wid];
 
+    __syncwarp();
     for (int k = lane; k < nr * kGroupBins; k += 32) {
         const int rr = k / kGroupBins, b = k % kGroupBins;
-        RL[rr][b] = (ps.rowsum && b < nbg) ? ps.rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] : 0;
+        RL[rr][b] = (ps.rowsum && b < NB) ? ps.rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] : 0;
     }
-    int TR[NB];  // H(R0-1, chunk start - 1) per bin
+    int TR[NB];  // H(R0-1, chunk start - 1) per bin: the tile corner to begin with
 #pragma unroll
-    for (int b = 0; b < NB; ++b) TR[b] = ps.corner ? ps.corner[((int64_t)i * g.ns + j) * ps.B + bg0 + b] : 0;
+    for (int b = 0; b < NB; ++b)
+        TR[b] = ps.corner ? sum_bands_above<int>(i, lane, [&](int ib) {
+            return ps.corner[((int64_t)ib * g.ns + j) * ps.B + bg0 + b];
+        }) : 0;
     __syncwarp();
 
     const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
@@ -468,37 +560,60 @@ __global__ void __launch_bounds__(128, 5) k_tiles_count(const __grid_constant__ 
     }
 }
 
+// Persistent over units: warp w of the grid takes units w, w + total, ...;
+// unit = tile * ngroups + group, so a warp's units spread over tiles and
+// groups of every size.
+template <int LAYOUT>
+__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 5 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
+{
+    __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const TileGrid &g = ps.g;
+    const int ng = ps.ngroups;
+    const int64_t units = (int64_t)g.nb * g.ns * ng;
+    const int64_t stride = (int64_t)gridDim.x * 4;
+    for (int64_t unit = (int64_t)blockIdx.x * 4 + wid; unit < units; unit += stride) {
+        const int tile = (int)(unit / ng), gi = (int)(unit % ng);
+        const int i = tile / g.ns, j = tile % g.ns;
+        switch (ps.grp[gi].nb) {
+        case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 2: tiles_count_unit<LAYOUT, 2>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 3: tiles_count_unit<LAYOUT, 3>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 4: tiles_count_unit<LAYOUT, 4>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 5: tiles_count_unit<LAYOUT, 5>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 6: tiles_count_unit<LAYOUT, 6>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 7: tiles_count_unit<LAYOUT, 7>(ps, i, j, gi, lane, RLs[wid]); break;
+        default: tiles_count_unit<LAYOUT, 8>(ps, i, j, gi, lane, RLs[wid]); break;
+        }
+    }
+}
+
 // ------------------------------------------------------------- moment tiles
 
-__global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant__ PlaneSet ps)
+__device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, int j, int wb, int lane,
+                                                   int32_t *RLn, long long *RLx, long long *RLxx)
 {
-    __shared__ int32_t sRLn[4][kMaxBandRows];
-    __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
     const ChanDev &ch = ps.chan[ps.wch];
     const int Bw = ch.bins;
-    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
-    if (unit >= (int64_t)g.nb * g.ns * Bw) return;  // whole warp
-    const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
-    const int i = tile / g.ns, j = tile % g.ns;
     const int64_t bglob = ch.bin_off + wb;
     const int R0 = i * g.R, nr = min(g.R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
     const bool carries = ps.colsum != nullptr;
-    int32_t *RLn = sRLn[wid];
-    long long *RLx = sRLx[wid], *RLxx = sRLxx[wid];
 
+    __syncwarp();
     for (int rr = lane; rr < nr; rr += 32) {
         RLn[rr] = carries ? ps.rowsum[((int64_t)j * ps.B + bglob) * g.H + R0 + rr] : 0;
         RLx[rr] = carries ? ps.l_c[((int64_t)j * Bw + wb) * g.H + R0 + rr] : 0;
         RLxx[rr] = carries ? ps.l_cc[((int64_t)j * Bw + wb) * g.H + R0 + rr] : 0;
     }
-    long long TR[4] = {0, 0, 0, 0};  // w = c, r, c^2, r^2
+    long long TR[4] = {0, 0, 0, 0};  // w = c, r, c^2, r^2: the tile corners to begin with
     if (carries) {
-        const int64_t *cw = ps.corner_w + (((int64_t)i * g.ns + j) * Bw + wb) * 4;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) TR[k] = cw[k];
+        for (int k = 0; k < 4; ++k)
+            TR[k] = sum_bands_above<long long>(i, lane, [&](int ib) {
+                return (long long)ps.corner_w[(((int64_t)ib * g.ns + j) * Bw + wb) * 4 + k];
+            });
     }
     __syncwarp();
     const int64_t plane = (int64_t)Bw * g.H * g.P;
@@ -603,18 +718,18 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant_
     }
 }
 
-template <int LAYOUT>
-void launch_tiles_count(int nb, unsigned blocks, cudaStream_t st, const PlaneSet &ps, int gb, int gc)
+__global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant__ PlaneSet ps)
 {
-    switch (nb) {
-    case 1: k_tiles_count<LAYOUT, 1><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    case 2: k_tiles_count<LAYOUT, 2><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    case 3: k_tiles_count<LAYOUT, 3><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    case 4: k_tiles_count<LAYOUT, 4><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    case 5: k_tiles_count<LAYOUT, 5><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    case 6: k_tiles_count<LAYOUT, 6><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    case 7: k_tiles_count<LAYOUT, 7><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
-    default: k_tiles_count<LAYOUT, 8><<<blocks, 128, 0, st>>>(ps, gb, gc); break;
+    __shared__ int32_t sRLn[4][kMaxBandRows];
+    __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const TileGrid &g = ps.g;
+    const int Bw = ps.chan[ps.wch].bins;
+    const int64_t units = (int64_t)g.nb * g.ns * Bw;
+    const int64_t stride = (int64_t)gridDim.x * 4;
+    for (int64_t unit = (int64_t)blockIdx.x * 4 + wid; unit < units; unit += stride) {
+        const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
+        tiles_moments_unit(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
     }
 }
 
@@ -625,6 +740,8 @@ void set_max_smem(F *f, size_t bytes)
 }
 
 size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int g_nsm = 148;
 
 }  // namespace
 
@@ -681,6 +798,9 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     if (!attrs) {
         set_max_smem(k_tile_sums<false>, SumsSmem::count_bytes);
         set_max_smem(k_tile_sums<true>, SumsSmem::weighted_bytes);
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
         attrs = true;
     }
     const TileGrid &g = ps.g;
@@ -690,41 +810,38 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         for (int k = 0; k < ps.nwin; ++k) (ps.win[k].chan == ps.wch ? nw_weighted : nw_count) += 1;
         if (nw_count) {
             prof_mark(prof, KID_SUMS_COUNT, 0, st);
-            k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), 256, SumsSmem::count_bytes, st>>>(ps, 0);
+            k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), kSumThreads, SumsSmem::count_bytes, st>>>(ps, 0);
             prof_mark(prof, KID_SUMS_COUNT, 1, st);
             ++n;
         }
         if (nw_weighted) {
             prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-            k_tile_sums<true><<<dim3(g.ns, g.nb, nw_weighted), 256, SumsSmem::weighted_bytes, st>>>(ps, nw_count);
+            k_tile_sums<true><<<dim3(g.ns, g.nb, nw_weighted), kSumThreads, SumsSmem::weighted_bytes, st>>>(ps, nw_count);
             prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
             ++n;
         }
-        const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.ns * ps.B;
+        const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.nb * ps.B;
         const int64_t blocks = (tot + 255) / 256;
         prof_mark(prof, KID_SCAN, 0, st);
         k_carry_scan<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(ps);
         prof_mark(prof, KID_SCAN, 1, st);
         ++n;
     }
-    for (int gb = 0; gb < ps.ngroups;) {
-        int ge = gb;
-        while (ge < ps.ngroups && ps.grp[ge].nb == ps.grp[gb].nb) ++ge;
-        const int gc = ge - gb;
-        const unsigned blocks = (unsigned)(((int64_t)g.nb * g.ns * gc + 3) / 4);
-        prof_mark(prof, KID_TILES_COUNT, 0, st);
-        if (ps.layout == LAYOUT_SLAB)
-            launch_tiles_count<LAYOUT_SLAB>(ps.grp[gb].nb, blocks, st, ps, gb, gc);
-        else
-            launch_tiles_count<LAYOUT_BIN_MAJOR>(ps.grp[gb].nb, blocks, st, ps, gb, gc);
-        prof_mark(prof, KID_TILES_COUNT, 1, st);
-        ++n;
-        gb = ge;
-    }
+    const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
+    const int64_t cap = (int64_t)g_nsm * 5;  // resident CTAs of 4 warps
+    const unsigned blocks = (unsigned)std::min<int64_t>((units + 3) / 4, cap);
+    prof_mark(prof, KID_TILES_COUNT, 0, st);
+    if (ps.layout == LAYOUT_SLAB)
+        k_tiles_count<LAYOUT_SLAB><<<blocks, 128, 0, st>>>(ps);
+    else
+        k_tiles_count<LAYOUT_BIN_MAJOR><<<blocks, 128, 0, st>>>(ps);
+    prof_mark(prof, KID_TILES_COUNT, 1, st);
+    ++n;
     if (ps.mom) {
         const int64_t mu = (int64_t)g.nb * g.ns * ps.chan[ps.wch].bins;
+        const unsigned mblocks = (unsigned)std::min<int64_t>((mu + 3) / 4, (int64_t)g_nsm * 4);
         prof_mark(prof, KID_TILES_MOMENTS, 0, st);
-        k_tiles_moments<<<(unsigned)((mu + 3) / 4), 128, 0, st>>>(ps);
+        k_tiles_moments<<<mblocks, 128, 0, st>>>(ps);
         prof_mark(prof, KID_TILES_MOMENTS, 1, st);
         ++n;
     }

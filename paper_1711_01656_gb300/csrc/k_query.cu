@@ -2,8 +2,8 @@
 //
 // Rectangle histograms by the four-corner rule of Eq. 2.16 and spatially
 // weighted local histograms (Eq. 3.1) from the moment planes of Eq. 3.4.
-// One thread per (query, bin); consecutive threads take consecutive bins of
-// one query, which in the slab layout are consecutive words of each corner.
+// Rectangles: one thread per (rectangle, bin group); weighted windows: one
+// thread per (window, bin).
 //
 // Weighted histogram, Epanechnikov window kernel.  For window
 // [r0,r1] x [c0,c1] with w = c1-c0+1, h = r1-r0+1, mc = c0+c1, mr = r0+r1:
@@ -39,15 +39,6 @@ __device__ __forceinline__ const int32_t *count_ptr(const CountView &v, int b, i
     return v.d + v.slab_off[g] + (r * v.P + c) * v.group_nb[g] + v.bin_local[b];
 }
 
-__device__ __forceinline__ long long count_four(const CountView &v, int b, int r0, int c0, int r1, int c1)
-{
-    const long long a = __ldg(count_ptr(v, b, r1, c1));
-    const long long bb = r0 > 0 ? (long long)__ldg(count_ptr(v, b, r0 - 1, c1)) : 0;
-    const long long cc = c0 > 0 ? (long long)__ldg(count_ptr(v, b, r1, c0 - 1)) : 0;
-    const long long d = (r0 > 0 && c0 > 0) ? (long long)__ldg(count_ptr(v, b, r0 - 1, c0 - 1)) : 0;
-    return a - bb - cc + d;
-}
-
 __device__ __forceinline__ long long four_corner(const int64_t *p, int64_t P, int r0, int c0, int r1, int c1)
 {
     const long long a = __ldg(p + (int64_t)r1 * P + c1);
@@ -57,23 +48,56 @@ __device__ __forceinline__ long long four_corner(const int64_t *p, int64_t P, in
     return a - b - c + d;
 }
 
+// One thread per (rectangle, bin group): the group's bins of each corner
+// are nb_g contiguous words in the slab layout.  The group table is copied
+// to shared memory so that threads of different groups do not serialise on
+// the kernel-parameter bank.
 __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ CountView v,
                                                      const int32_t *__restrict__ rects, int64_t n,
                                                      int32_t *__restrict__ out, int *err)
 {
-    const int64_t total = n * v.B;
+    __shared__ int64_t s_off[kMaxGroups];
+    __shared__ int s_nb[kMaxGroups], s_b0[kMaxGroups];
+    for (int k = threadIdx.x; k < v.ngroups; k += blockDim.x) {
+        s_off[k] = v.slab_off[k];
+        s_nb[k] = v.group_nb[k];
+        s_b0[k] = v.group_bin0[k];
+    }
+    __syncthreads();
+    const int ng = v.ngroups;
+    const int64_t total = n * ng;
+    const int64_t plane = (int64_t)v.H * v.P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = t / v.B;
-        const int b = (int)(t - qi * v.B);
+        const int64_t qi = t / ng;
+        const int gi = (int)(t - qi * ng);
+        const int nb = s_nb[gi], b0 = s_b0[gi];
+        int32_t *o = out + qi * v.B + b0;
         const int r0 = __ldg(rects + 4 * qi), c0 = __ldg(rects + 4 * qi + 1);
         const int r1 = __ldg(rects + 4 * qi + 2), c1 = __ldg(rects + 4 * qi + 3);
         if (!box_ok(r0, c0, r1, c1, v.H, v.W)) {
-            out[t] = -1;
-            if (b == 0) atomicOr(err, 1);
+            for (int b = 0; b < nb; ++b) o[b] = -1;
+            if (gi == 0) atomicOr(err, 1);
             continue;
         }
-        out[t] = (int32_t)count_four(v, b, r0, c0, r1, c1);
+        // corner offsets (element index of bin 0 of the group) and strides
+        const bool slab = v.layout == LAYOUT_SLAB;
+        const int64_t base = slab ? s_off[gi] : (int64_t)b0 * plane;
+        const int64_t px = slab ? nb : 1, bs = slab ? 1 : plane;
+        const int64_t a = base + ((int64_t)r1 * v.P + c1) * px;
+        const int64_t bq = base + ((int64_t)(r0 - 1) * v.P + c1) * px;
+        const int64_t cq = base + ((int64_t)r1 * v.P + (c0 - 1)) * px;
+        const int64_t dq = base + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px;
+        const bool top = r0 > 0, left = c0 > 0;
+#pragma unroll 8
+        for (int b = 0; b < nb; ++b) {
+            const int64_t ob = b * bs;
+            int32_t s = __ldg(v.d + a + ob);
+            if (top) s -= __ldg(v.d + bq + ob);
+            if (left) s -= __ldg(v.d + cq + ob);
+            if (top && left) s += __ldg(v.d + dq + ob);
+            o[b] = s;
+        }
     }
 }
 
@@ -81,6 +105,20 @@ __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ 
                                                         const int32_t *__restrict__ wins, int64_t n,
                                                         int normalize, float *__restrict__ out, int *err)
 {
+    // element offset and stride of each weighted bin's count plane
+    __shared__ int64_t s_base[256], s_px[256];
+    for (int b = threadIdx.x; b < m.Bw; b += blockDim.x) {
+        const int gb = m.bin0 + b;
+        if (v.layout == LAYOUT_SLAB) {
+            const int g = v.bin_group[gb];
+            s_base[b] = v.slab_off[g] + v.bin_local[gb];
+            s_px[b] = v.group_nb[g];
+        } else {
+            s_base[b] = (int64_t)gb * v.H * v.P;
+            s_px[b] = 1;
+        }
+    }
+    __syncthreads();
     const int64_t total = n * m.Bw;
     const int64_t plane = (int64_t)v.H * v.P;
     const int64_t mplane = (int64_t)m.Bw * plane;
@@ -95,7 +133,12 @@ __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ 
             if (b == 0) atomicOr(err, 1);
             continue;
         }
-        const long long N = count_four(v, m.bin0 + b, r0, c0, r1, c1);
+        const int32_t *cp = v.d + s_base[b];
+        const int64_t px = s_px[b];
+        const long long N = (long long)__ldg(cp + ((int64_t)r1 * v.P + c1) * px) -
+                            (r0 > 0 ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + c1) * px) : 0) -
+                            (c0 > 0 ? (long long)__ldg(cp + ((int64_t)r1 * v.P + (c0 - 1)) * px) : 0) +
+                            ((r0 > 0 && c0 > 0) ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px) : 0);
         const int64_t mo = b * plane;
         const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
         const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
@@ -156,7 +199,7 @@ int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int3
 {
     if (n == 0) return 0;
     prof_mark(prof, KID_QUERY_RECTS, 0, st);
-    k_query_rects<<<grid_for(n * v.B), 256, 0, st>>>(v, rects, n, out, err);
+    k_query_rects<<<grid_for(n * v.ngroups), 256, 0, st>>>(v, rects, n, out, err);
     prof_mark(prof, KID_QUERY_RECTS, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
