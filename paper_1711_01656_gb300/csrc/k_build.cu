@@ -497,62 +497,104 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
 #pragma unroll
         for (int k = 0; k < 4; ++k) pf[k] = (k < nr) ? load4(ch, R0 + k, c, C1, vec_ok) : 0u;
         for (int rr0 = 0; rr0 < nr; rr0 += 4) {
+            // two rows at a time: their shuffle scans are independent
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int rr = rr0 + k;
-                if (rr >= nr) break;  // warp-uniform
-                const uint32_t px = pf[k];
-                if (rr + 4 < nr) pf[k] = load4(ch, R0 + rr + 4, c, C1, vec_ok);
-                // packed one-hot of the 4 pixels and its in-lane prefix
-                uint32_t P0[4], P1[4];
+            for (int h = 0; h < 2; ++h) {
+                const int ra = rr0 + 2 * h, rb = ra + 1;
+                if (ra >= nr) break;  // warp-uniform
+                const bool hasb = rb < nr;
+                const uint32_t pxa = pf[2 * h], pxb = pf[2 * h + 1];
+                if (ra + 4 < nr) pf[2 * h] = load4(ch, R0 + ra + 4, c, C1, vec_ok);
+                if (rb + 4 < nr) pf[2 * h + 1] = load4(ch, R0 + rb + 4, c, C1, vec_ok);
+                // packed one-hot of each row's 4 pixels and its in-lane prefix
+                uint32_t Pa0[4], Pa1[4], Pb0[4], Pb1[4];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const int q = bin_of((px >> (8 * jj)) & 0xff, ch.bins, ch.mode);
-                    const unsigned d = (jj < nvalid && q >= 0) ? (unsigned)(q - gr.b_lo) : 0xFFFFFFFFu;
-                    const uint32_t e0 = d < 4u ? (1u << (d << 3)) : 0u;
-                    const uint32_t e1 = (d - 4u) < 4u ? (1u << ((d - 4u) << 3)) : 0u;
-                    P0[jj] = (jj ? P0[jj - 1] : 0u) + e0;
-                    P1[jj] = (jj ? P1[jj - 1] : 0u) + e1;
+                    const int qa = bin_of((pxa >> (8 * jj)) & 0xff, ch.bins, ch.mode);
+                    const int qb = bin_of((pxb >> (8 * jj)) & 0xff, ch.bins, ch.mode);
+                    const unsigned da = (jj < nvalid && qa >= 0) ? (unsigned)(qa - gr.b_lo) : 0xFFFFFFFFu;
+                    const unsigned db = (jj < nvalid && qb >= 0 && hasb) ? (unsigned)(qb - gr.b_lo) : 0xFFFFFFFFu;
+                    Pa0[jj] = (jj ? Pa0[jj - 1] : 0u) + (da < 4u ? (1u << (da << 3)) : 0u);
+                    Pa1[jj] = (jj ? Pa1[jj - 1] : 0u) + ((da - 4u) < 4u ? (1u << ((da - 4u) << 3)) : 0u);
+                    Pb0[jj] = (jj ? Pb0[jj - 1] : 0u) + (db < 4u ? (1u << (db << 3)) : 0u);
+                    Pb1[jj] = (jj ? Pb1[jj - 1] : 0u) + ((db - 4u) < 4u ? (1u << ((db - 4u) << 3)) : 0u);
                 }
-                const uint32_t i0 = warp_incl_scan(P0[3], lane);
-                const uint32_t i1 = NB > 4 ? warp_incl_scan(P1[3], lane) : 0u;
-                const uint32_t x0 = i0 - P0[3], x1 = i1 - P1[3];
-                const uint32_t t0 = __shfl_sync(kFull, i0, 31);
-                const uint32_t t1 = NB > 4 ? __shfl_sync(kFull, i1, 31) : 0u;
-                const int4 rl0 = *reinterpret_cast<const int4 *>(&RL[rr][0]);
-                const int4 rl1 = *reinterpret_cast<const int4 *>(&RL[rr][4]);
-                const int rl[8] = {rl0.x, rl0.y, rl0.z, rl0.w, rl1.x, rl1.y, rl1.z, rl1.w};
+                const uint32_t ia0 = warp_incl_scan(Pa0[3], lane);
+                const uint32_t ib0 = warp_incl_scan(Pb0[3], lane);
+                const uint32_t ia1 = NB > 4 ? warp_incl_scan(Pa1[3], lane) : 0u;
+                const uint32_t ib1 = NB > 4 ? warp_incl_scan(Pb1[3], lane) : 0u;
+                const uint32_t xa0 = ia0 - Pa0[3], xa1 = ia1 - Pa1[3];
+                const uint32_t xb0 = ib0 - Pb0[3], xb1 = ib1 - Pb1[3];
+                const int4 la0 = *reinterpret_cast<const int4 *>(&RL[ra][0]);
+                const int4 la1 = *reinterpret_cast<const int4 *>(&RL[ra][4]);
+                const int4 lb0 = *reinterpret_cast<const int4 *>(&RL[rb][0]);
+                const int4 lb1 = *reinterpret_cast<const int4 *>(&RL[rb][4]);
+                const int rla[8] = {la0.x, la0.y, la0.z, la0.w, la1.x, la1.y, la1.z, la1.w};
+                const int rlb[8] = {lb0.x, lb0.y, lb0.z, lb0.w, lb1.x, lb1.y, lb1.z, lb1.w};
+                // row a
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const uint32_t y0 = x0 + P0[jj], y1 = x1 + P1[jj];
+                    const uint32_t y0 = xa0 + Pa0[jj], y1 = xa1 + Pa1[jj];
 #pragma unroll
                     for (int b = 0; b < NB; ++b)
-                        acc[b][jj] += rl[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
+                        acc[b][jj] += rla[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
                 }
-                const int r = R0 + rr;
                 if (c < g.P) {
                     if (LAYOUT == LAYOUT_BIN_MAJOR) {
 #pragma unroll
                         for (int b = 0; b < NB; ++b)
-                            *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + r) * g.P + c) =
+                            *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + ra) * g.P + c) =
                                 make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
                     } else {
-                        store_slab<NB>(ps.out + ps.slab_off[gi] + ((int64_t)r * g.P + c) * NB, acc);
+                        store_slab<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + ra) * g.P + c) * NB, acc);
                     }
                 }
+                // row b
+                if (hasb) {
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const uint32_t y0 = xb0 + Pb0[jj], y1 = xb1 + Pb1[jj];
+#pragma unroll
+                        for (int b = 0; b < NB; ++b)
+                            acc[b][jj] += rlb[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
+                    }
+                    if (c < g.P) {
+                        if (LAYOUT == LAYOUT_BIN_MAJOR) {
+#pragma unroll
+                            for (int b = 0; b < NB; ++b)
+                                *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + rb) * g.P + c) =
+                                    make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+                        } else {
+                            store_slab<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + rb) * g.P + c) * NB, acc);
+                        }
+                    }
+                }
+                // the last lane's inclusive sums are the chunk's row totals
                 __syncwarp();
-                if (lane == 0) {
+                if (lane == 31) {
                     int4 a, b4;
-                    a.x = rl[0] + (int)__byte_perm(t0, 0, 0x4440);
-                    a.y = rl[1] + (int)__byte_perm(t0, 0, 0x4441);
-                    a.z = rl[2] + (int)__byte_perm(t0, 0, 0x4442);
-                    a.w = rl[3] + (int)__byte_perm(t0, 0, 0x4443);
-                    b4.x = rl[4] + (int)__byte_perm(t1, 0, 0x4440);
-                    b4.y = rl[5] + (int)__byte_perm(t1, 0, 0x4441);
-                    b4.z = rl[6] + (int)__byte_perm(t1, 0, 0x4442);
-                    b4.w = rl[7] + (int)__byte_perm(t1, 0, 0x4443);
-                    *reinterpret_cast<int4 *>(&RL[rr][0]) = a;
-                    *reinterpret_cast<int4 *>(&RL[rr][4]) = b4;
+                    a.x = rla[0] + (int)__byte_perm(ia0, 0, 0x4440);
+                    a.y = rla[1] + (int)__byte_perm(ia0, 0, 0x4441);
+                    a.z = rla[2] + (int)__byte_perm(ia0, 0, 0x4442);
+                    a.w = rla[3] + (int)__byte_perm(ia0, 0, 0x4443);
+                    b4.x = rla[4] + (int)__byte_perm(ia1, 0, 0x4440);
+                    b4.y = rla[5] + (int)__byte_perm(ia1, 0, 0x4441);
+                    b4.z = rla[6] + (int)__byte_perm(ia1, 0, 0x4442);
+                    b4.w = rla[7] + (int)__byte_perm(ia1, 0, 0x4443);
+                    *reinterpret_cast<int4 *>(&RL[ra][0]) = a;
+                    *reinterpret_cast<int4 *>(&RL[ra][4]) = b4;
+                    if (hasb) {
+                        a.x = rlb[0] + (int)__byte_perm(ib0, 0, 0x4440);
+                        a.y = rlb[1] + (int)__byte_perm(ib0, 0, 0x4441);
+                        a.z = rlb[2] + (int)__byte_perm(ib0, 0, 0x4442);
+                        a.w = rlb[3] + (int)__byte_perm(ib0, 0, 0x4443);
+                        b4.x = rlb[4] + (int)__byte_perm(ib1, 0, 0x4440);
+                        b4.y = rlb[5] + (int)__byte_perm(ib1, 0, 0x4441);
+                        b4.z = rlb[6] + (int)__byte_perm(ib1, 0, 0x4442);
+                        b4.w = rlb[7] + (int)__byte_perm(ib1, 0, 0x4443);
+                        *reinterpret_cast<int4 *>(&RL[rb][0]) = a;
+                        *reinterpret_cast<int4 *>(&RL[rb][4]) = b4;
+                    }
                 }
             }
         }
@@ -560,20 +602,20 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
     }
 }
 
-// Persistent over units: warp w of the grid takes units w, w + total, ...;
-// unit = tile * ngroups + group, so a warp's units spread over tiles and
-// groups of every size.
+// One warp per unit; unit = group * tiles + tile with the groups sorted by
+// size, so the CTAs dispatched first carry the largest groups and the tail of
+// the grid is made of the cheapest units.
 template <int LAYOUT>
-__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 5 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
+__global__ void __launch_bounds__(128, 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
 {
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
-    const int ng = ps.ngroups;
-    const int64_t units = (int64_t)g.nb * g.ns * ng;
+    const int64_t ntiles = (int64_t)g.nb * g.ns;
+    const int64_t units = ntiles * ps.ngroups;
     const int64_t stride = (int64_t)gridDim.x * 4;
     for (int64_t unit = (int64_t)blockIdx.x * 4 + wid; unit < units; unit += stride) {
-        const int tile = (int)(unit / ng), gi = (int)(unit % ng);
+        const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
         const int i = tile / g.ns, j = tile % g.ns;
         switch (ps.grp[gi].nb) {
         case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RLs[wid]); break;
@@ -828,8 +870,7 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         ++n;
     }
     const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
-    const int64_t cap = (int64_t)g_nsm * 5;  // resident CTAs of 4 warps
-    const unsigned blocks = (unsigned)std::min<int64_t>((units + 3) / 4, cap);
+    const unsigned blocks = (unsigned)std::min<int64_t>((units + 3) / 4, (int64_t)1 << 30);
     prof_mark(prof, KID_TILES_COUNT, 0, st);
     if (ps.layout == LAYOUT_SLAB)
         k_tiles_count<LAYOUT_SLAB><<<blocks, 128, 0, st>>>(ps);
@@ -839,7 +880,7 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     ++n;
     if (ps.mom) {
         const int64_t mu = (int64_t)g.nb * g.ns * ps.chan[ps.wch].bins;
-        const unsigned mblocks = (unsigned)std::min<int64_t>((mu + 3) / 4, (int64_t)g_nsm * 4);
+        const unsigned mblocks = (unsigned)std::min<int64_t>((mu + 3) / 4, (int64_t)1 << 30);
         prof_mark(prof, KID_TILES_MOMENTS, 0, st);
         k_tiles_moments<<<mblocks, 128, 0, st>>>(ps);
         prof_mark(prof, KID_TILES_MOMENTS, 1, st);

@@ -89,6 +89,39 @@ __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ Cou
         const int64_t cq = base + ((int64_t)r1 * v.P + (c0 - 1)) * px;
         const int64_t dq = base + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px;
         const bool top = r0 > 0, left = c0 > 0;
+        if (slab && (nb & 3) == 0) {
+            // nb a multiple of 4: each corner's record is nb/4 aligned int4s;
+            // all loads are issued before the sums
+            for (int b = 0; b < nb; b += 8) {
+                const bool two = b + 4 < nb;
+                int4 A0 = __ldg(reinterpret_cast<const int4 *>(v.d + a + b)), A1 = A0;
+                int4 B0 = make_int4(0, 0, 0, 0), B1 = B0, C0 = B0, C1 = B0, D0 = B0, D1 = B0;
+                if (two) A1 = __ldg(reinterpret_cast<const int4 *>(v.d + a + b + 4));
+                if (top) {
+                    B0 = __ldg(reinterpret_cast<const int4 *>(v.d + bq + b));
+                    if (two) B1 = __ldg(reinterpret_cast<const int4 *>(v.d + bq + b + 4));
+                }
+                if (left) {
+                    C0 = __ldg(reinterpret_cast<const int4 *>(v.d + cq + b));
+                    if (two) C1 = __ldg(reinterpret_cast<const int4 *>(v.d + cq + b + 4));
+                }
+                if (top && left) {
+                    D0 = __ldg(reinterpret_cast<const int4 *>(v.d + dq + b));
+                    if (two) D1 = __ldg(reinterpret_cast<const int4 *>(v.d + dq + b + 4));
+                }
+                o[b + 0] = A0.x - B0.x - C0.x + D0.x;
+                o[b + 1] = A0.y - B0.y - C0.y + D0.y;
+                o[b + 2] = A0.z - B0.z - C0.z + D0.z;
+                o[b + 3] = A0.w - B0.w - C0.w + D0.w;
+                if (two) {
+                    o[b + 4] = A1.x - B1.x - C1.x + D1.x;
+                    o[b + 5] = A1.y - B1.y - C1.y + D1.y;
+                    o[b + 6] = A1.z - B1.z - C1.z + D1.z;
+                    o[b + 7] = A1.w - B1.w - C1.w + D1.w;
+                }
+            }
+            continue;
+        }
 #pragma unroll 8
         for (int b = 0; b < nb; ++b) {
             const int64_t ob = b * bs;
