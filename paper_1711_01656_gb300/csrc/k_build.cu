@@ -428,11 +428,23 @@ __device__ __forceinline__ T sum_bands_above(int i, int lane, F at)
 
 // ------------------------------------------------------------- count tiles
 
-// Store the 4 pixels x NB bins of one lane in the slab layout: the lane's
-// records are contiguous (pixel-major, bins innermost), NB int4 stores.
+// Slab-layout row store through a per-warp shared buffer.  Lane L's 4
+// pixel records (NB int4 units) go to units L*S + k, S the smallest odd
+// number > NB, so that both the writes and the reads below hit 8 distinct
+// 16-byte bank groups per 8 lanes; the warp then stores the row segment
+// (32*NB units, contiguous in global memory) with lane L writing units
+// 32m + L: every store instruction covers 512 contiguous bytes.
 template <int NB>
-__device__ __forceinline__ void store_slab(int32_t *p, const int (&acc)[NB][4])
+struct SlabStage {
+    static constexpr int S = (NB + 1) | 1;
+};
+
+template <int NB>
+__device__ __forceinline__ void store_slab_staged(int32_t *seg, int npx, const int (&acc)[NB][4], int4 *stage,
+                                                  int lane)
 {
+    constexpr int S = SlabStage<NB>::S;
+    __syncwarp();
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
         int v[4];
@@ -441,14 +453,22 @@ __device__ __forceinline__ void store_slab(int32_t *p, const int (&acc)[NB][4])
             const int f = 4 * k + e;  // flat index: pixel f / NB, bin f % NB
             v[e] = acc[f % NB][f / NB];
         }
-        reinterpret_cast<int4 *>(p)[k] = make_int4(v[0], v[1], v[2], v[3]);
+        stage[lane * S + k] = make_int4(v[0], v[1], v[2], v[3]);
+    }
+    __syncwarp();
+    // units of pixels below npx (the segment's valid pixels, a multiple of 4)
+    const int nunits = npx / 4 * NB;
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+        const int u = 32 * m + lane;
+        if (u < nunits) reinterpret_cast<int4 *>(seg)[u] = stage[(u / NB) * S + (u % NB)];
     }
 }
 
 // One warp-unit of the count tiles: tile (i, j), group gi of exactly NB bins.
 template <int LAYOUT, int NB>
 __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int j, int gi, int lane,
-                                                 int32_t (*RL)[kGroupBins])
+                                                 int32_t (*RL)[kGroupBins], int4 *stage)
 {
     const TileGrid &g = ps.g;
     const GroupDev gr = ps.grp[gi];
@@ -539,15 +559,16 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                     for (int b = 0; b < NB; ++b)
                         acc[b][jj] += rla[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
                 }
-                if (c < g.P) {
-                    if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                    if (c < g.P) {
 #pragma unroll
                         for (int b = 0; b < NB; ++b)
                             *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + ra) * g.P + c) =
                                 make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
-                    } else {
-                        store_slab<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + ra) * g.P + c) * NB, acc);
                     }
+                } else {
+                    store_slab_staged<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + ra) * g.P + cc) * NB,
+                                          (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
                 }
                 // row b
                 if (hasb) {
@@ -558,15 +579,16 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                         for (int b = 0; b < NB; ++b)
                             acc[b][jj] += rlb[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
                     }
-                    if (c < g.P) {
-                        if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                    if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                        if (c < g.P) {
 #pragma unroll
                             for (int b = 0; b < NB; ++b)
                                 *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + rb) * g.P + c) =
                                     make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
-                        } else {
-                            store_slab<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + rb) * g.P + c) * NB, acc);
                         }
+                    } else {
+                        store_slab_staged<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + rb) * g.P + cc) * NB,
+                                              (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
                     }
                 }
                 // the last lane's inclusive sums are the chunk's row totals
@@ -606,9 +628,10 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
 // size, so the CTAs dispatched first carry the largest groups and the tail of
 // the grid is made of the cheapest units.
 template <int LAYOUT>
-__global__ void __launch_bounds__(128, 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
+__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 3 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
 {
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
+    __shared__ int4 stages[4][LAYOUT == LAYOUT_SLAB ? 32 * SlabStage<kGroupBins>::S : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
     const int64_t ntiles = (int64_t)g.nb * g.ns;
@@ -618,14 +641,14 @@ __global__ void __launch_bounds__(128, 4) k_tiles_count(const __grid_constant__ 
         const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
         const int i = tile / g.ns, j = tile % g.ns;
         switch (ps.grp[gi].nb) {
-        case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RLs[wid]); break;
-        case 2: tiles_count_unit<LAYOUT, 2>(ps, i, j, gi, lane, RLs[wid]); break;
-        case 3: tiles_count_unit<LAYOUT, 3>(ps, i, j, gi, lane, RLs[wid]); break;
-        case 4: tiles_count_unit<LAYOUT, 4>(ps, i, j, gi, lane, RLs[wid]); break;
-        case 5: tiles_count_unit<LAYOUT, 5>(ps, i, j, gi, lane, RLs[wid]); break;
-        case 6: tiles_count_unit<LAYOUT, 6>(ps, i, j, gi, lane, RLs[wid]); break;
-        case 7: tiles_count_unit<LAYOUT, 7>(ps, i, j, gi, lane, RLs[wid]); break;
-        default: tiles_count_unit<LAYOUT, 8>(ps, i, j, gi, lane, RLs[wid]); break;
+        case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        case 2: tiles_count_unit<LAYOUT, 2>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        case 3: tiles_count_unit<LAYOUT, 3>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        case 4: tiles_count_unit<LAYOUT, 4>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        case 5: tiles_count_unit<LAYOUT, 5>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        case 6: tiles_count_unit<LAYOUT, 6>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        case 7: tiles_count_unit<LAYOUT, 7>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
+        default: tiles_count_unit<LAYOUT, 8>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
         }
     }
 }
