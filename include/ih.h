@@ -183,6 +183,8 @@ typedef struct {
     int64_t pitch_elems;        /* row pitch of the count tensor, elements */
     int64_t count_bytes;        /* bytes of the count tensor */
     int64_t moment_bytes;       /* bytes of the moment planes (0 if none) */
+    int32_t tile_rows, tile_cols; /* tile grid the build used (band rows,
+                                     strip columns) */
 } ih_frame_info;
 
 /* Host copy of a live frame's geometry. */
@@ -222,6 +224,55 @@ int64_t ih_launch_count(ih_ctx *ctx);
 
 /* One-line description of the last error of this context ("" if none). */
 const char *ih_last_error(ih_ctx *ctx);
+
+/* ---- batches ---------------------------------------------------------- */
+
+/* A batch builds many frames of uneven size and channel or bin count with ONE
+ * launch of each build kernel over all of them (and one launch of each query
+ * kernel over all their queries), optionally replayed from a CUDA graph. */
+typedef struct ih_batch ih_batch;
+
+typedef struct {
+    const int32_t *d_rects;     /* device: every frame's rectangles (x4 int32),
+                                   frame 0's first; NULL = no rectangle queries */
+    const int64_t *rects;       /* host, n entries: rectangles of frame k */
+    int32_t *d_rect_out;        /* device: frame k's rects[k] x B_k int32 block,
+                                   blocks in frame order */
+    const int32_t *d_windows;   /* device: every frame's weighted windows;
+                                   NULL = no weighted queries */
+    const int64_t *windows;     /* host, n entries: windows of frame k */
+    float *d_weighted_out;      /* device: frame k's windows[k] x B_w,k floats,
+                                   blocks in frame order */
+    uint32_t kernel, flags;     /* as for ih_query_weighted */
+} ih_batch_queries;
+
+enum {
+    IH_BATCH_GRAPH = 1,   /* capture the run's launches in a CUDA graph */
+    IH_BATCH_AUTOTUNE = 2 /* ih_autotune every distinct frame shape first */
+};
+
+/* Plans a batch of n frames: allocates every frame's tensors (the frames are
+ * registered in the context; out_handles, host, n entries; release them with
+ * ih_release), their feature scratch and tile carries, and uploads the
+ * descriptor tables; with IH_BATCH_GRAPH also captures the run in a CUDA
+ * graph.  Pixel, rectangle, window and output pointers are baked into the
+ * plan: each run reads and writes the same buffers.  Synchronous (allocates
+ * and uploads).  Errors as for ih_build. */
+ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const ih_batch_queries *queries,
+                          uint32_t flags, ih_batch **out, int32_t *out_handles);
+
+/* Enqueues one run of the batch on `stream`: the feature pre-pass of every
+ * RGB frame, the build of every frame and the batch's queries. */
+ih_status ih_batch_run(ih_batch *batch, void *stream);
+
+/* Frees the plan (not the frames).  Synchronises the device first. */
+ih_status ih_batch_destroy(ih_batch *batch);
+
+/* Times the build of `frame` on each candidate tile grid (band rows 32, 64,
+ * 128 x strip columns 128..1024) and makes the context build every later
+ * frame of the same shape (size, channels, bins, input kind, weighted
+ * channel, layout) with the fastest.  Synchronous. */
+ih_status ih_autotune(ih_ctx *ctx, const ih_frame *frame, void *stream);
 
 /* ---- allocation-free variant ------------------------------------------ */
 

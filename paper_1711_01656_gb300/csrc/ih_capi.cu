@@ -15,55 +15,13 @@
 #include <cstring>
 
 #include "../../include/ih.h"
+#include "ih_ctx.h"
 #include "ih_internal.cuh"
 #include "ih_plan.h"
 
 using namespace ih;
 
-namespace {
-
-struct FrameRec {
-    bool live = false;
-    int H = 0, W = 0, nchan = 0, B = 0;
-    int bins[kMaxChannels] = {0};
-    int bin_off[kMaxChannels] = {0};
-    int64_t P = 0;
-    int32_t *d_ih = nullptr;
-    int wch = -1, Bw = 0;
-    int64_t *d_mom = nullptr;
-    int64_t count_bytes = 0, moment_bytes = 0;
-    CountView view{};
-};
-
-}  // namespace
-
-struct ProfRec {
-    int kid;
-    cudaEvent_t a, b;
-};
-
-struct ih_ctx {
-    int device = 0;
-    bool profiling = false;
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<ProfRec> prof_pending;
-    int prof_open_kid = -1;
-    cudaEvent_t prof_open = nullptr;
-    int64_t prof_launches[KID_COUNT] = {0};
-    double prof_ms[KID_COUNT] = {0};
-    Prof prof;
-    uint64_t budget = 0;
-    uint64_t used = 0;
-    cudaMemPool_t pool = nullptr;
-    std::vector<FrameRec> frames;
-    int *d_err = nullptr;
-    std::recursive_mutex mu;
-    std::string last_error;
-    int64_t launches = 0;
-    int nsm = 0;
-};
-
-namespace {
+namespace ih {
 
 ih_status fail(ih_ctx *ctx, ih_status s, const char *fmt, ...)
 {
@@ -122,27 +80,6 @@ const char *kernel_name(int kid)
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
-struct DevGuard {
-    int prev = -1;
-    explicit DevGuard(int dev)
-    {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DevGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-template <typename T>
-cudaError_t pool_alloc(ih_ctx *ctx, T **p, size_t bytes, cudaStream_t st)
-{
-    void *v = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&v, bytes ? bytes : 16, ctx->pool, st);
-    *p = static_cast<T *>(v);
-    return e;
-}
 
 ih_status validate(ih_ctx *ctx, const ih_frame &f)
 {
@@ -210,6 +147,7 @@ bool plan_groups(PlaneSet &ps)
     n = 0;
     for (int k = 0; k < nw; ++k)
         if (tmp[k].chan != ps.wch) ps.win[n++] = tmp[k];
+    ps.nwin_count = n;
     for (int k = 0; k < nw; ++k)
         if (tmp[k].chan == ps.wch) ps.win[n++] = tmp[k];
     ps.nwin = n;
@@ -240,7 +178,88 @@ void make_view(const PlaneSet &ps, const int32_t *d, CountView &v)
     }
 }
 
-}  // namespace
+void frame_record(const ih_frame &f, FrameRec &fr)
+{
+    fr.H = f.height;
+    fr.W = f.width;
+    fr.nchan = f.channels;
+    fr.P = (f.width + 3) & ~3;
+    int off = 0;
+    for (int c = 0; c < f.channels; ++c) {
+        fr.bins[c] = f.chan[c].bins;
+        fr.bin_off[c] = off;
+        off += f.chan[c].bins;
+    }
+    fr.B = off;
+    fr.wch = f.weighted_channel;
+    fr.Bw = fr.wch >= 0 ? fr.bins[fr.wch] : 0;
+    fr.count_bytes = (int64_t)fr.B * fr.H * fr.P * 4;
+    fr.moment_bytes = (int64_t)4 * fr.Bw * fr.H * fr.P * 8;
+}
+
+std::string shape_key(const ih_frame &f)
+{
+    std::string k = std::to_string(f.height) + "x" + std::to_string(f.width) + ":" + std::to_string(f.input) + ":" +
+                    std::to_string(f.weighted_channel) + ":" + std::to_string(f.layout);
+    for (int c = 0; c < f.channels; ++c) k += ":" + std::to_string(f.chan[c].bins) + "/" + std::to_string(f.chan[c].mode);
+    return k;
+}
+
+bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uint8_t *const *planes,
+                   const int64_t *cpitch, PlaneSet &ps)
+{
+    memset(&ps, 0, sizeof ps);
+    ps.B = fr.B;
+    ps.nchan = fr.nchan;
+    ps.layout = f.layout;
+    ps.wch = fr.wch;
+    for (int c = 0; c < fr.nchan; ++c) {
+        ps.chan[c].plane = planes[c];
+        ps.chan[c].pitch = cpitch[c];
+        ps.chan[c].bins = f.chan[c].bins;
+        ps.chan[c].mode = f.chan[c].mode;
+        ps.chan[c].bin_off = fr.bin_off[c];
+    }
+    if (!plan_groups(ps)) return false;
+    auto it = ctx->tuned.find(shape_key(f));
+    ps.g = it != ctx->tuned.end() ? make_grid(fr.H, fr.W, it->second.first, it->second.second)
+                                  : choose_grid(fr.H, fr.W, ps.ngroups, ctx->nsm);
+    ps.g.P = fr.P;
+    int64_t off = 0;
+    for (int kg = 0; kg < ps.ngroups; ++kg) {
+        ps.slab_off[kg] = off;
+        off += (int64_t)fr.H * fr.P * ps.grp[kg].nb;
+    }
+    ps.out = fr.d_ih;
+    ps.mom = fr.d_mom;
+    return true;
+}
+
+FrameRec *get_frame(ih_ctx *ctx, int32_t handle)
+{
+    if (handle < 0 || handle >= (int32_t)ctx->frames.size() || !ctx->frames[handle].live) return nullptr;
+    return &ctx->frames[handle];
+}
+
+int publish_frame(ih_ctx *ctx, FrameRec &fr)
+{
+    int h = -1;
+    for (size_t i = 0; i < ctx->frames.size(); ++i)
+        if (!ctx->frames[i].live) {
+            h = (int)i;
+            break;
+        }
+    if (h < 0) {
+        h = (int)ctx->frames.size();
+        ctx->frames.emplace_back();
+    }
+    fr.live = true;
+    ctx->frames[h] = fr;
+    ctx->used += fr.count_bytes + fr.moment_bytes;
+    return h;
+}
+
+}  // namespace ih
 
 extern "C" {
 
@@ -293,21 +312,7 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
         ih_status s = validate(ctx, f);
         if (s != IH_OK) return s;
         FrameRec &fr = recs[k];
-        fr.H = f.height;
-        fr.W = f.width;
-        fr.nchan = f.channels;
-        fr.P = (f.width + 3) & ~3;
-        int off = 0;
-        for (int c = 0; c < f.channels; ++c) {
-            fr.bins[c] = f.chan[c].bins;
-            fr.bin_off[c] = off;
-            off += f.chan[c].bins;
-        }
-        fr.B = off;
-        fr.wch = f.weighted_channel;
-        fr.Bw = fr.wch >= 0 ? fr.bins[fr.wch] : 0;
-        fr.count_bytes = (int64_t)fr.B * fr.H * fr.P * 4;
-        fr.moment_bytes = (int64_t)4 * fr.Bw * fr.H * fr.P * 8;
+        frame_record(f, fr);
         need += fr.count_bytes + fr.moment_bytes;
     }
     if (ctx->budget && ctx->used + need > ctx->budget)
@@ -356,28 +361,7 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
             }
         }
         PlaneSet ps;
-        memset(&ps, 0, sizeof ps);
-        ps.B = fr.B;
-        ps.nchan = fr.nchan;
-        ps.layout = f.layout;
-        ps.wch = fr.wch;
-        for (int c = 0; c < fr.nchan; ++c) {
-            ps.chan[c].plane = planes[c];
-            ps.chan[c].pitch = cpitch[c];
-            ps.chan[c].bins = f.chan[c].bins;
-            ps.chan[c].mode = f.chan[c].mode;
-            ps.chan[c].bin_off = fr.bin_off[c];
-        }
-        if (!plan_groups(ps)) return fail(ctx, IH_EINVAL, "too many bins for one build");
-        ps.g = choose_grid(fr.H, fr.W, ps.ngroups, ctx->nsm);
-        ps.g.P = fr.P;
-        int64_t off = 0;
-        for (int kg = 0; kg < ps.ngroups; ++kg) {
-            ps.slab_off[kg] = off;
-            off += (int64_t)fr.H * fr.P * ps.grp[kg].nb;
-        }
-        ps.out = fr.d_ih;
-        ps.mom = fr.d_mom;
+        if (!make_planeset(ctx, f, fr, planes, cpitch, ps)) return fail(ctx, IH_EINVAL, "too many bins for one build");
         void *scratch = nullptr;
         const size_t cb = carry_bytes(ps);
         if (cb) {
@@ -393,33 +377,13 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
         else
             ctx->launches += nl;
         make_view(ps, fr.d_ih, fr.view);
+        fr.R = ps.g.R;
+        fr.Wc = ps.g.Wc;
         if (feat) cudaFreeAsync(feat, st);
         if (s != IH_OK) return s;
     }
-    // publish handles
-    for (int k = 0; k < n; ++k) {
-        int h = -1;
-        for (size_t i = 0; i < ctx->frames.size(); ++i)
-            if (!ctx->frames[i].live) {
-                h = (int)i;
-                break;
-            }
-        if (h < 0) {
-            h = (int)ctx->frames.size();
-            ctx->frames.emplace_back();
-        }
-        recs[k].live = true;
-        ctx->frames[h] = recs[k];
-        ctx->used += recs[k].count_bytes + recs[k].moment_bytes;
-        out_handles[k] = h;
-    }
+    for (int k = 0; k < n; ++k) out_handles[k] = publish_frame(ctx, recs[k]);
     return IH_OK;
-}
-
-static FrameRec *get_frame(ih_ctx *ctx, int32_t handle)
-{
-    if (handle < 0 || handle >= (int32_t)ctx->frames.size() || !ctx->frames[handle].live) return nullptr;
-    return &ctx->frames[handle];
 }
 
 ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, int64_t n, int32_t *d_out,
@@ -506,6 +470,8 @@ ih_status ih_info(ih_ctx *ctx, int32_t handle, ih_frame_info *out)
     out->pitch_elems = fr->P;
     out->count_bytes = fr->count_bytes;
     out->moment_bytes = fr->moment_bytes;
+    out->tile_rows = fr->R;
+    out->tile_cols = fr->Wc;
     return IH_OK;
 }
 

@@ -98,6 +98,7 @@ struct PlaneSet {
     ChanDev chan[kMaxChannels];
     int32_t ngroups;      // count bin groups (<= kGroupBins bins each)
     int32_t nwin;         // tile-sums windows (<= kWindowBins bins each)
+    int32_t nwin_count;   // the first nwin_count windows are not of channel wch
     GroupDev grp[kMaxGroups];
     GroupDev win[kMaxGroups];
     int64_t slab_off[kMaxGroups];  // LAYOUT_SLAB: element offset of group g's slab
@@ -129,6 +130,25 @@ void carve_carries(PlaneSet &ps, void *base);
 // Launchers (k_build.cu).  Return the number of kernels launched, or -1 with
 // the CUDA error left pending.
 int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof);
+// One-time kernel attributes (shared-memory limits); call before a capture.
+void prepare_kernels();
+
+// Batched build: every kernel runs once over the concatenated work of n
+// frames.  The prefix arrays (n + 1 entries, device) give each frame's first
+// CTA / work item / warp unit of the five kernels.
+struct BatchDev {
+    const PlaneSet *sets;     // device, n entries
+    int32_t n;
+    const int64_t *pre_sums0; // tile sums, windows of unweighted channels (CTAs)
+    const int64_t *pre_sums1; // tile sums, windows of the weighted channel (CTAs)
+    const int64_t *pre_scan;  // carry-scan work items
+    const int64_t *pre_tiles; // count-tile warp units
+    const int64_t *pre_mom;   // moment-tile warp units
+};
+// Work counts of one frame for the five batched kernels (host).
+void batch_counts(const PlaneSet &ps, int64_t *counts5);
+// totals: the five totals over all frames (host).
+int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t st, const Prof *prof);
 
 // Feature pre-pass (k_features.cu): intensity and three orientation planes
 // (and optionally a copy of R, G, B) from planar RGB.
@@ -136,6 +156,18 @@ int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_
                     int W, uint8_t *out_rgb /* nullable: 3 planes */, uint8_t *out_i,
                     uint8_t *out_hog /* 3 planes */, int64_t out_pitch, cudaStream_t st,
                     const Prof *prof);
+
+// One frame of a batched feature pre-pass.
+struct FeatJob {
+    const uint8_t *r, *g, *b;
+    int64_t pitch;
+    int32_t H, W;
+    uint8_t *out_i, *out_hog;  // intensity plane and 3 orientation planes
+    int64_t opitch;
+};
+int64_t feature_tiles(int H, int W);  // CTAs of one frame
+int launch_features_batch(const FeatJob *jobs, const int64_t *pre, int n, int64_t total, cudaStream_t st,
+                          const Prof *prof);
 
 // Read access to a count tensor in either layout (k_query.cu).
 struct CountView {
@@ -156,6 +188,19 @@ struct MomentView {
 };
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out,
                        int *err, cudaStream_t st, const Prof *prof);
+// Queries of one frame of a batch (device table).
+struct QueryJob {
+    const CountView *v;   // device copy of the frame's view
+    MomentView m;
+    const int32_t *rects;
+    int32_t *rect_out;
+    const int32_t *wins;
+    float *wout;
+    int32_t normalize;
+};
+// pre_rects: rect work items (rects x groups), pre_wins: windows x Bw, per frame.
+int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const int64_t *pre_wins, int n,
+                         int64_t total_rects, int64_t total_wins, int *err, cudaStream_t st, const Prof *prof);
 int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n,
                           int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.

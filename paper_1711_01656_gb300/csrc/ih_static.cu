@@ -94,6 +94,7 @@ extern "C" ih_status ih_build_counts_static(const uint8_t *d_pixels, int32_t hei
         for (int k = 0; k < ng; ++k)
             if (tmp[k].nb == size) ps.grp[ps.ngroups++] = tmp[k];
     ps.nwin = split_groups(bins, kWindowBins, ps.win);
+    ps.nwin_count = ps.nwin;
     ps.g = choose_grid(height, width, ps.ngroups, nsm);
     if (carry_bytes(ps) > kStaticScratchBytes) ps.g = make_grid(height, width, kMaxBandRows, 1024);
     if (carry_bytes(ps) > kStaticScratchBytes) return IH_ETOOBIG;

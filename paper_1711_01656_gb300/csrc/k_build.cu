@@ -100,11 +100,10 @@ __device__ __forceinline__ uint32_t window_bins4(uint32_t px, const ChanDev &ch,
 }
 
 template <bool WT>
-__global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
+__device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i, int widx)
 {
     const TileGrid &g = ps.g;
-    const int j = blockIdx.x, i = blockIdx.y;
-    const GroupDev wd = ps.win[win0 + blockIdx.z];
+    const GroupDev wd = ps.win[widx];
     const ChanDev &ch = ps.chan[wd.chan];
     const int R0 = i * g.R, nr = min(g.R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
@@ -287,6 +286,40 @@ __global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant
     }
 }
 
+template <bool WT>
+__global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
+{
+    tile_sums_body<WT>(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
+}
+
+// Largest f in [0, n) with pre[f] <= x (pre is a prefix sum of n counts).
+__device__ __forceinline__ int find_frame(const int64_t *pre, int n, int64_t x)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Batched: one CTA per (frame, window, band, strip), frames concatenated.
+template <bool WT>
+__global__ void __launch_bounds__(kSumThreads) k_tile_sums_b(const BatchDev bd)
+{
+    const int64_t *pre = WT ? bd.pre_sums1 : bd.pre_sums0;
+    const int64_t flat = blockIdx.x;
+    const int f = find_frame(pre, bd.n, flat);
+    const PlaneSet &ps = bd.sets[f];
+    const int64_t local = flat - pre[f];
+    const int64_t per = (int64_t)ps.g.ns * ps.g.nb;
+    const int z = (int)(local / per), rem = (int)(local % per);
+    tile_sums_body<WT>(ps, rem % ps.g.ns, rem / ps.g.ns, (WT ? ps.nwin_count : 0) + z);
+}
+
 // ------------------------------------------------------------- carry scan
 //
 // G and L are exclusive prefixes over bands and strips.  The tile corners
@@ -296,16 +329,20 @@ __global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant
 
 constexpr int kScanBatch = 8;
 
-__global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ PlaneSet ps)
+__device__ __forceinline__ int64_t carry_scan_items(const PlaneSet &ps)
+{
+    return (int64_t)ps.B * ps.g.W + (int64_t)ps.B * ps.g.H + (int64_t)ps.g.nb * ps.B;
+}
+
+__device__ __forceinline__ void carry_scan_item(const PlaneSet &ps, int64_t t)
 {
     const TileGrid &g = ps.g;
     const int64_t B = ps.B;
     const int wch = ps.wch;
     const int64_t bin0 = wch >= 0 ? ps.chan[wch].bin_off : 0;
     const int64_t Bw = wch >= 0 ? ps.chan[wch].bins : 0;
-    const int64_t nA = B * g.W, nB = B * g.H, nC = (int64_t)g.nb * B;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nA + nB + nC;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nA = B * g.W, nB = B * g.H;
+    {
         if (t < nA) {  // G(i, c, b): exclusive over bands
             const int64_t b = t / g.W, c = t % g.W, wb = b - bin0;
             const bool wt = wb >= 0 && wb < Bw;
@@ -411,6 +448,23 @@ __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ Plan
                 }
             }
         }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ PlaneSet ps)
+{
+    const int64_t total = carry_scan_items(ps);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
+        carry_scan_item(ps, t);
+}
+
+__global__ void __launch_bounds__(256) k_carry_scan_b(const BatchDev bd)
+{
+    const int64_t total = bd.pre_scan[bd.n];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int f = find_frame(bd.pre_scan, bd.n, t);
+        carry_scan_item(bd.sets[f], t - bd.pre_scan[f]);
     }
 }
 
@@ -624,33 +678,53 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
     }
 }
 
-// One warp per unit; unit = group * tiles + tile with the groups sorted by
-// size, so the CTAs dispatched first carry the largest groups and the tail of
-// the grid is made of the cheapest units.
+// Unit = group * tiles + tile with the groups sorted by size, so the CTAs
+// dispatched first carry the largest groups and the tail of the grid is made
+// of the cheapest units.
+template <int LAYOUT>
+__device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t unit, int lane,
+                                                     int32_t (*RL)[kGroupBins], int4 *stage)
+{
+    const int64_t ntiles = (int64_t)ps.g.nb * ps.g.ns;
+    const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
+    const int i = tile / ps.g.ns, j = tile % ps.g.ns;
+    switch (ps.grp[gi].nb) {
+    case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RL, stage); break;
+    case 2: tiles_count_unit<LAYOUT, 2>(ps, i, j, gi, lane, RL, stage); break;
+    case 3: tiles_count_unit<LAYOUT, 3>(ps, i, j, gi, lane, RL, stage); break;
+    case 4: tiles_count_unit<LAYOUT, 4>(ps, i, j, gi, lane, RL, stage); break;
+    case 5: tiles_count_unit<LAYOUT, 5>(ps, i, j, gi, lane, RL, stage); break;
+    case 6: tiles_count_unit<LAYOUT, 6>(ps, i, j, gi, lane, RL, stage); break;
+    case 7: tiles_count_unit<LAYOUT, 7>(ps, i, j, gi, lane, RL, stage); break;
+    default: tiles_count_unit<LAYOUT, 8>(ps, i, j, gi, lane, RL, stage); break;
+    }
+}
+
 template <int LAYOUT>
 __global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 3 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
 {
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
     __shared__ int4 stages[4][LAYOUT == LAYOUT_SLAB ? 32 * SlabStage<kGroupBins>::S : 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const TileGrid &g = ps.g;
-    const int64_t ntiles = (int64_t)g.nb * g.ns;
-    const int64_t units = ntiles * ps.ngroups;
-    const int64_t stride = (int64_t)gridDim.x * 4;
-    for (int64_t unit = (int64_t)blockIdx.x * 4 + wid; unit < units; unit += stride) {
-        const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
-        const int i = tile / g.ns, j = tile % g.ns;
-        switch (ps.grp[gi].nb) {
-        case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        case 2: tiles_count_unit<LAYOUT, 2>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        case 3: tiles_count_unit<LAYOUT, 3>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        case 4: tiles_count_unit<LAYOUT, 4>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        case 5: tiles_count_unit<LAYOUT, 5>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        case 6: tiles_count_unit<LAYOUT, 6>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        case 7: tiles_count_unit<LAYOUT, 7>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        default: tiles_count_unit<LAYOUT, 8>(ps, i, j, gi, lane, RLs[wid], stages[wid]); break;
-        }
-    }
+    const int64_t units = (int64_t)ps.g.nb * ps.g.ns * ps.ngroups;
+    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+    if (unit < units) tiles_count_dispatch<LAYOUT>(ps, unit, lane, RLs[wid], stages[wid]);
+}
+
+// Batched: warps over the concatenated units of all frames (any layout).
+__global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
+{
+    __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
+    __shared__ int4 stages[4][32 * SlabStage<kGroupBins>::S];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+    if (unit >= bd.pre_tiles[bd.n]) return;
+    const int f = find_frame(bd.pre_tiles, bd.n, unit);
+    const PlaneSet &ps = bd.sets[f];
+    if (ps.layout == LAYOUT_SLAB)
+        tiles_count_dispatch<LAYOUT_SLAB>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
+    else
+        tiles_count_dispatch<LAYOUT_BIN_MAJOR>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
 }
 
 // ------------------------------------------------------------- moment tiles
@@ -790,12 +864,25 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant_
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
     const int Bw = ps.chan[ps.wch].bins;
-    const int64_t units = (int64_t)g.nb * g.ns * Bw;
-    const int64_t stride = (int64_t)gridDim.x * 4;
-    for (int64_t unit = (int64_t)blockIdx.x * 4 + wid; unit < units; unit += stride) {
-        const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
-        tiles_moments_unit(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
-    }
+    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+    if (unit >= (int64_t)g.nb * g.ns * Bw) return;
+    const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
+    tiles_moments_unit(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+}
+
+__global__ void __launch_bounds__(128, 4) k_tiles_moments_b(const BatchDev bd)
+{
+    __shared__ int32_t sRLn[4][kMaxBandRows];
+    __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+    if (unit >= bd.pre_mom[bd.n]) return;
+    const int f = find_frame(bd.pre_mom, bd.n, unit);
+    const PlaneSet &ps = bd.sets[f];
+    const int Bw = ps.chan[ps.wch].bins;
+    const int64_t local = unit - bd.pre_mom[f];
+    const int tile = (int)(local / Bw), wb = (int)(local % Bw);
+    tiles_moments_unit(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
 }
 
 template <typename F>
@@ -857,22 +944,77 @@ void carve_carries(PlaneSet &ps, void *base)
     }
 }
 
-int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+void prepare_kernels()
 {
     static bool attrs = false;
     if (!attrs) {
         set_max_smem(k_tile_sums<false>, SumsSmem::count_bytes);
         set_max_smem(k_tile_sums<true>, SumsSmem::weighted_bytes);
+        set_max_smem(k_tile_sums_b<false>, SumsSmem::count_bytes);
+        set_max_smem(k_tile_sums_b<true>, SumsSmem::weighted_bytes);
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
         attrs = true;
     }
+}
+
+int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t st, const Prof *prof)
+{
+    prepare_kernels();
+    int n = 0;
+    if (totals[0]) {
+        prof_mark(prof, KID_SUMS_COUNT, 0, st);
+        k_tile_sums_b<false><<<(unsigned)totals[0], kSumThreads, SumsSmem::count_bytes, st>>>(bd);
+        prof_mark(prof, KID_SUMS_COUNT, 1, st);
+        ++n;
+    }
+    if (totals[1]) {
+        prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
+        k_tile_sums_b<true><<<(unsigned)totals[1], kSumThreads, SumsSmem::weighted_bytes, st>>>(bd);
+        prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
+        ++n;
+    }
+    if (totals[2]) {
+        const int64_t blocks = (totals[2] + 255) / 256;
+        prof_mark(prof, KID_SCAN, 0, st);
+        k_carry_scan_b<<<(unsigned)(blocks < 16384 ? blocks : 16384), 256, 0, st>>>(bd);
+        prof_mark(prof, KID_SCAN, 1, st);
+        ++n;
+    }
+    if (totals[3]) {
+        prof_mark(prof, KID_TILES_COUNT, 0, st);
+        k_tiles_count_b<<<(unsigned)((totals[3] + 3) / 4), 128, 0, st>>>(bd);
+        prof_mark(prof, KID_TILES_COUNT, 1, st);
+        ++n;
+    }
+    if (totals[4]) {
+        prof_mark(prof, KID_TILES_MOMENTS, 0, st);
+        k_tiles_moments_b<<<(unsigned)((totals[4] + 3) / 4), 128, 0, st>>>(bd);
+        prof_mark(prof, KID_TILES_MOMENTS, 1, st);
+        ++n;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? n : -1;
+}
+
+void batch_counts(const PlaneSet &ps, int64_t *c)
+{
+    const int64_t tiles = (int64_t)ps.g.nb * ps.g.ns;
+    const bool carries = ps.colsum != nullptr;
+    c[0] = carries ? tiles * ps.nwin_count : 0;
+    c[1] = carries ? tiles * (ps.nwin - ps.nwin_count) : 0;
+    c[2] = carries ? (int64_t)ps.B * ps.g.W + (int64_t)ps.B * ps.g.H + (int64_t)ps.g.nb * ps.B : 0;
+    c[3] = tiles * ps.ngroups;
+    c[4] = ps.mom ? tiles * ps.chan[ps.wch].bins : 0;
+}
+
+int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+{
+    prepare_kernels();
     const TileGrid &g = ps.g;
     int n = 0;
     if (ps.colsum) {
-        int nw_count = 0, nw_weighted = 0;
-        for (int k = 0; k < ps.nwin; ++k) (ps.win[k].chan == ps.wch ? nw_weighted : nw_count) += 1;
+        const int nw_count = ps.nwin_count, nw_weighted = ps.nwin - ps.nwin_count;
         if (nw_count) {
             prof_mark(prof, KID_SUMS_COUNT, 0, st);
             k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), kSumThreads, SumsSmem::count_bytes, st>>>(ps, 0);
@@ -893,7 +1035,7 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         ++n;
     }
     const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
-    const unsigned blocks = (unsigned)std::min<int64_t>((units + 3) / 4, (int64_t)1 << 30);
+    const unsigned blocks = (unsigned)((units + 3) / 4);
     prof_mark(prof, KID_TILES_COUNT, 0, st);
     if (ps.layout == LAYOUT_SLAB)
         k_tiles_count<LAYOUT_SLAB><<<blocks, 128, 0, st>>>(ps);
@@ -903,7 +1045,7 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     ++n;
     if (ps.mom) {
         const int64_t mu = (int64_t)g.nb * g.ns * ps.chan[ps.wch].bins;
-        const unsigned mblocks = (unsigned)std::min<int64_t>((mu + 3) / 4, (int64_t)1 << 30);
+        const unsigned mblocks = (unsigned)((mu + 3) / 4);
         prof_mark(prof, KID_TILES_MOMENTS, 0, st);
         k_tiles_moments<<<mblocks, 128, 0, st>>>(ps);
         prof_mark(prof, KID_TILES_MOMENTS, 1, st);

@@ -44,14 +44,13 @@ __device__ __forceinline__ int orientation_bin9(int gx, int gy)
     return b;
 }
 
-__global__ void __launch_bounds__(256) k_features(const uint8_t *__restrict__ pr,
-                                                  const uint8_t *__restrict__ pg,
-                                                  const uint8_t *__restrict__ pb, int64_t pitch,
-                                                  int H, int W, uint8_t *out_rgb, uint8_t *out_i,
-                                                  uint8_t *out_hog, int64_t opitch)
+__device__ __forceinline__ void features_tile(const uint8_t *__restrict__ pr, const uint8_t *__restrict__ pg,
+                                              const uint8_t *__restrict__ pb, int64_t pitch, int H, int W,
+                                              uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog, int64_t opitch,
+                                              int tr, int tc)
 {
     __shared__ uint8_t sI[kS][kS + 4];
-    const int r0 = blockIdx.y * kT, c0 = blockIdx.x * kT;
+    const int r0 = tr * kT, c0 = tc * kT;
     for (int sr = threadIdx.y; sr < kS; sr += blockDim.y) {
         const int64_t ro = (int64_t)min(max(r0 - kHalo + sr, 0), H - 1) * pitch;
         for (int sc = threadIdx.x; sc < kS; sc += blockDim.x) {
@@ -87,6 +86,33 @@ __global__ void __launch_bounds__(256) k_features(const uint8_t *__restrict__ pr
     }
 }
 
+__global__ void __launch_bounds__(256) k_features(const uint8_t *__restrict__ pr, const uint8_t *__restrict__ pg,
+                                                  const uint8_t *__restrict__ pb, int64_t pitch, int H, int W,
+                                                  uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog, int64_t opitch)
+{
+    features_tile(pr, pg, pb, pitch, H, W, out_rgb, out_i, out_hog, opitch, blockIdx.y, blockIdx.x);
+}
+
+// Batched: one CTA per (frame, 32 x 32 tile), frames concatenated.
+__global__ void __launch_bounds__(256) k_features_b(const FeatJob *__restrict__ jobs, const int64_t *__restrict__ pre,
+                                                    int n)
+{
+    const int64_t flat = blockIdx.x;
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= flat)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    const FeatJob &jb = jobs[lo];
+    const int local = (int)(flat - pre[lo]);
+    const int tcols = (jb.W + kT - 1) / kT;
+    features_tile(jb.r, jb.g, jb.b, jb.pitch, jb.H, jb.W, nullptr, jb.out_i, jb.out_hog, jb.opitch, local / tcols,
+                  local % tcols);
+}
+
 }  // namespace
 
 int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_t pitch, int H,
@@ -100,4 +126,18 @@ int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
+}  // namespace ih
+
+namespace ih {
+int64_t feature_tiles(int H, int W) { return (int64_t)((H + kT - 1) / kT) * ((W + kT - 1) / kT); }
+
+int launch_features_batch(const FeatJob *jobs, const int64_t *pre, int n, int64_t total, cudaStream_t st,
+                          const Prof *prof)
+{
+    if (!total) return 0;
+    prof_mark(prof, KID_FEATURES, 0, st);
+    k_features_b<<<(unsigned)total, dim3(kT, 8), 0, st>>>(jobs, pre, n);
+    prof_mark(prof, KID_FEATURES, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
 }  // namespace ih

@@ -49,9 +49,80 @@ __device__ __forceinline__ long long four_corner(const int64_t *p, int64_t P, in
 }
 
 // One thread per (rectangle, bin group): the group's bins of each corner
-// are nb_g contiguous words in the slab layout.  The group table is copied
-// to shared memory so that threads of different groups do not serialise on
-// the kernel-parameter bank.
+// are nb_g contiguous words in the slab layout.
+template <typename TN>
+__device__ __forceinline__ void rect_item(const CountView &v, const int64_t *g_off, const TN *g_nb, const TN *g_b0,
+                                          const int32_t *__restrict__ rects, int32_t *__restrict__ out, int64_t t,
+                                          int *err)
+{
+    const int ng = v.ngroups;
+    const int64_t plane = (int64_t)v.H * v.P;
+    const int64_t qi = t / ng;
+    const int gi = (int)(t - qi * ng);
+    const int nb = g_nb[gi], b0 = g_b0[gi];
+    int32_t *o = out + qi * v.B + b0;
+    const int r0 = __ldg(rects + 4 * qi), c0 = __ldg(rects + 4 * qi + 1);
+    const int r1 = __ldg(rects + 4 * qi + 2), c1 = __ldg(rects + 4 * qi + 3);
+    if (!box_ok(r0, c0, r1, c1, v.H, v.W)) {
+        for (int b = 0; b < nb; ++b) o[b] = -1;
+        if (gi == 0) atomicOr(err, 1);
+        return;
+    }
+    // corner offsets (element index of bin 0 of the group) and strides
+    const bool slab = v.layout == LAYOUT_SLAB;
+    const int64_t base = slab ? g_off[gi] : (int64_t)b0 * plane;
+    const int64_t px = slab ? nb : 1, bs = slab ? 1 : plane;
+    const int64_t a = base + ((int64_t)r1 * v.P + c1) * px;
+    const int64_t bq = base + ((int64_t)(r0 - 1) * v.P + c1) * px;
+    const int64_t cq = base + ((int64_t)r1 * v.P + (c0 - 1)) * px;
+    const int64_t dq = base + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px;
+    const bool top = r0 > 0, left = c0 > 0;
+    if (slab && (nb & 3) == 0) {
+        // nb a multiple of 4: each corner's record is nb/4 aligned int4s;
+        // all loads are issued before the sums
+        for (int b = 0; b < nb; b += 8) {
+            const bool two = b + 4 < nb;
+            int4 A0 = __ldg(reinterpret_cast<const int4 *>(v.d + a + b)), A1 = A0;
+            int4 B0 = make_int4(0, 0, 0, 0), B1 = B0, C0 = B0, C1 = B0, D0 = B0, D1 = B0;
+            if (two) A1 = __ldg(reinterpret_cast<const int4 *>(v.d + a + b + 4));
+            if (top) {
+                B0 = __ldg(reinterpret_cast<const int4 *>(v.d + bq + b));
+                if (two) B1 = __ldg(reinterpret_cast<const int4 *>(v.d + bq + b + 4));
+            }
+            if (left) {
+                C0 = __ldg(reinterpret_cast<const int4 *>(v.d + cq + b));
+                if (two) C1 = __ldg(reinterpret_cast<const int4 *>(v.d + cq + b + 4));
+            }
+            if (top && left) {
+                D0 = __ldg(reinterpret_cast<const int4 *>(v.d + dq + b));
+                if (two) D1 = __ldg(reinterpret_cast<const int4 *>(v.d + dq + b + 4));
+            }
+            o[b + 0] = A0.x - B0.x - C0.x + D0.x;
+            o[b + 1] = A0.y - B0.y - C0.y + D0.y;
+            o[b + 2] = A0.z - B0.z - C0.z + D0.z;
+            o[b + 3] = A0.w - B0.w - C0.w + D0.w;
+            if (two) {
+                o[b + 4] = A1.x - B1.x - C1.x + D1.x;
+                o[b + 5] = A1.y - B1.y - C1.y + D1.y;
+                o[b + 6] = A1.z - B1.z - C1.z + D1.z;
+                o[b + 7] = A1.w - B1.w - C1.w + D1.w;
+            }
+        }
+        return;
+    }
+#pragma unroll 8
+    for (int b = 0; b < nb; ++b) {
+        const int64_t ob = b * bs;
+        int32_t s = __ldg(v.d + a + ob);
+        if (top) s -= __ldg(v.d + bq + ob);
+        if (left) s -= __ldg(v.d + cq + ob);
+        if (top && left) s += __ldg(v.d + dq + ob);
+        o[b] = s;
+    }
+}
+
+// The group table is copied to shared memory so that threads of different
+// groups do not serialise on the kernel-parameter bank.
 __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ CountView v,
                                                      const int32_t *__restrict__ rects, int64_t n,
                                                      int32_t *__restrict__ out, int *err)
@@ -64,146 +135,127 @@ __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ Cou
         s_b0[k] = v.group_bin0[k];
     }
     __syncthreads();
-    const int ng = v.ngroups;
-    const int64_t total = n * ng;
-    const int64_t plane = (int64_t)v.H * v.P;
+    const int64_t total = n * v.ngroups;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        rect_item(v, s_off, s_nb, s_b0, rects, out, t, err);
+}
+
+// Largest f in [0, n) with pre[f] <= x.
+__device__ __forceinline__ int find_job(const int64_t *pre, int n, int64_t x)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (pre[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Batched: work items of all frames concatenated; tables read from global.
+__global__ void __launch_bounds__(256) k_query_rects_b(const QueryJob *__restrict__ jobs,
+                                                       const int64_t *__restrict__ pre, int n, int *err)
+{
+    const int64_t total = pre[n];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = t / ng;
-        const int gi = (int)(t - qi * ng);
-        const int nb = s_nb[gi], b0 = s_b0[gi];
-        int32_t *o = out + qi * v.B + b0;
-        const int r0 = __ldg(rects + 4 * qi), c0 = __ldg(rects + 4 * qi + 1);
-        const int r1 = __ldg(rects + 4 * qi + 2), c1 = __ldg(rects + 4 * qi + 3);
-        if (!box_ok(r0, c0, r1, c1, v.H, v.W)) {
-            for (int b = 0; b < nb; ++b) o[b] = -1;
-            if (gi == 0) atomicOr(err, 1);
-            continue;
-        }
-        // corner offsets (element index of bin 0 of the group) and strides
-        const bool slab = v.layout == LAYOUT_SLAB;
-        const int64_t base = slab ? s_off[gi] : (int64_t)b0 * plane;
-        const int64_t px = slab ? nb : 1, bs = slab ? 1 : plane;
-        const int64_t a = base + ((int64_t)r1 * v.P + c1) * px;
-        const int64_t bq = base + ((int64_t)(r0 - 1) * v.P + c1) * px;
-        const int64_t cq = base + ((int64_t)r1 * v.P + (c0 - 1)) * px;
-        const int64_t dq = base + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px;
-        const bool top = r0 > 0, left = c0 > 0;
-        if (slab && (nb & 3) == 0) {
-            // nb a multiple of 4: each corner's record is nb/4 aligned int4s;
-            // all loads are issued before the sums
-            for (int b = 0; b < nb; b += 8) {
-                const bool two = b + 4 < nb;
-                int4 A0 = __ldg(reinterpret_cast<const int4 *>(v.d + a + b)), A1 = A0;
-                int4 B0 = make_int4(0, 0, 0, 0), B1 = B0, C0 = B0, C1 = B0, D0 = B0, D1 = B0;
-                if (two) A1 = __ldg(reinterpret_cast<const int4 *>(v.d + a + b + 4));
-                if (top) {
-                    B0 = __ldg(reinterpret_cast<const int4 *>(v.d + bq + b));
-                    if (two) B1 = __ldg(reinterpret_cast<const int4 *>(v.d + bq + b + 4));
-                }
-                if (left) {
-                    C0 = __ldg(reinterpret_cast<const int4 *>(v.d + cq + b));
-                    if (two) C1 = __ldg(reinterpret_cast<const int4 *>(v.d + cq + b + 4));
-                }
-                if (top && left) {
-                    D0 = __ldg(reinterpret_cast<const int4 *>(v.d + dq + b));
-                    if (two) D1 = __ldg(reinterpret_cast<const int4 *>(v.d + dq + b + 4));
-                }
-                o[b + 0] = A0.x - B0.x - C0.x + D0.x;
-                o[b + 1] = A0.y - B0.y - C0.y + D0.y;
-                o[b + 2] = A0.z - B0.z - C0.z + D0.z;
-                o[b + 3] = A0.w - B0.w - C0.w + D0.w;
-                if (two) {
-                    o[b + 4] = A1.x - B1.x - C1.x + D1.x;
-                    o[b + 5] = A1.y - B1.y - C1.y + D1.y;
-                    o[b + 6] = A1.z - B1.z - C1.z + D1.z;
-                    o[b + 7] = A1.w - B1.w - C1.w + D1.w;
-                }
-            }
-            continue;
-        }
-#pragma unroll 8
-        for (int b = 0; b < nb; ++b) {
-            const int64_t ob = b * bs;
-            int32_t s = __ldg(v.d + a + ob);
-            if (top) s -= __ldg(v.d + bq + ob);
-            if (left) s -= __ldg(v.d + cq + ob);
-            if (top && left) s += __ldg(v.d + dq + ob);
-            o[b] = s;
-        }
+        const int f = find_job(pre, n, t);
+        const QueryJob &jb = jobs[f];
+        const CountView &v = *jb.v;
+        rect_item(v, v.slab_off, v.group_nb, v.group_bin0, jb.rects, jb.rect_out, t - pre[f], err);
     }
+}
+
+// Element offset of bin gb's count at (0, 0) and its per-pixel stride.
+__device__ __forceinline__ void count_base(const CountView &v, int gb, int64_t &base, int64_t &px)
+{
+    if (v.layout == LAYOUT_SLAB) {
+        const int g = v.bin_group[gb];
+        base = v.slab_off[g] + v.bin_local[gb];
+        px = v.group_nb[g];
+    } else {
+        base = (int64_t)gb * v.H * v.P;
+        px = 1;
+    }
+}
+
+__device__ __forceinline__ void weighted_item(const CountView &v, const MomentView &m, const int32_t *__restrict__ wins,
+                                              int normalize, float *__restrict__ out, int64_t t, int *err)
+{
+    const int64_t plane = (int64_t)v.H * v.P;
+    const int64_t mplane = (int64_t)m.Bw * plane;
+    const int64_t qi = t / m.Bw;
+    const int b = (int)(t - qi * m.Bw);
+    const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
+    const int r1 = __ldg(wins + 4 * qi + 2), c1 = __ldg(wins + 4 * qi + 3);
+    if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= 32768 || c1 - c0 >= 32768) {
+        out[t] = -1.0f;
+        if (b == 0) atomicOr(err, 1);
+        return;
+    }
+    int64_t cbase, px;
+    count_base(v, m.bin0 + b, cbase, px);
+    const int32_t *cp = v.d + cbase;
+    const long long N = (long long)__ldg(cp + ((int64_t)r1 * v.P + c1) * px) -
+                        (r0 > 0 ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + c1) * px) : 0) -
+                        (c0 > 0 ? (long long)__ldg(cp + ((int64_t)r1 * v.P + (c0 - 1)) * px) : 0) +
+                        ((r0 > 0 && c0 > 0) ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px) : 0);
+    const int64_t mo = b * plane;
+    const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
+    const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
+    const long long Scc = four_corner(m.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
+    const long long Srr = four_corner(m.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
+    const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
+    const long long mc = c0 + c1, mr = r0 + r1;
+    const long long X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
+    const long long Y2 = 4 * Srr - 4 * mr * Sr + mr * mr * N;
+    const long long A = 2 * w * w, Bh = 2 * h * h;
+    const long long qx = X2 / A, rx = X2 - qx * A;
+    const long long qy = Y2 / Bh, ry = Y2 - qy * Bh;
+    long long I = N - qx - qy;
+    unsigned long long F = (unsigned long long)rx * (unsigned long long)Bh +
+                           (unsigned long long)ry * (unsigned long long)A;
+    const unsigned long long Den = (unsigned long long)A * (unsigned long long)Bh;
+    if (F >= Den) {
+        I -= 1;
+        F -= Den;
+    }
+    // S = I - F/Den, with S > 0 whenever N > 0, so I >= 1 when F > 0
+    float s;
+    if (F == 0)
+        s = (float)I;
+    else
+        s = (float)(I - 1) + (float)(Den - F) / (float)Den;
+    if (normalize) {
+        const float K = (4.0f * (float)(w * w) * (float)(h * h) + (float)(w * w) + (float)(h * h)) /
+                        (6.0f * (float)w * (float)h);
+        s = s / K;
+    }
+    out[t] = s;
 }
 
 __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ CountView v, const MomentView m,
                                                         const int32_t *__restrict__ wins, int64_t n,
                                                         int normalize, float *__restrict__ out, int *err)
 {
-    // element offset and stride of each weighted bin's count plane
-    __shared__ int64_t s_base[256], s_px[256];
-    for (int b = threadIdx.x; b < m.Bw; b += blockDim.x) {
-        const int gb = m.bin0 + b;
-        if (v.layout == LAYOUT_SLAB) {
-            const int g = v.bin_group[gb];
-            s_base[b] = v.slab_off[g] + v.bin_local[gb];
-            s_px[b] = v.group_nb[g];
-        } else {
-            s_base[b] = (int64_t)gb * v.H * v.P;
-            s_px[b] = 1;
-        }
-    }
-    __syncthreads();
     const int64_t total = n * m.Bw;
-    const int64_t plane = (int64_t)v.H * v.P;
-    const int64_t mplane = (int64_t)m.Bw * plane;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x)
+        weighted_item(v, m, wins, normalize, out, t, err);
+}
+
+__global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__restrict__ jobs,
+                                                          const int64_t *__restrict__ pre, int n, int *err)
+{
+    const int64_t total = pre[n];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t qi = t / m.Bw;
-        const int b = (int)(t - qi * m.Bw);
-        const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
-        const int r1 = __ldg(wins + 4 * qi + 2), c1 = __ldg(wins + 4 * qi + 3);
-        if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= 32768 || c1 - c0 >= 32768) {
-            out[t] = -1.0f;
-            if (b == 0) atomicOr(err, 1);
-            continue;
-        }
-        const int32_t *cp = v.d + s_base[b];
-        const int64_t px = s_px[b];
-        const long long N = (long long)__ldg(cp + ((int64_t)r1 * v.P + c1) * px) -
-                            (r0 > 0 ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + c1) * px) : 0) -
-                            (c0 > 0 ? (long long)__ldg(cp + ((int64_t)r1 * v.P + (c0 - 1)) * px) : 0) +
-                            ((r0 > 0 && c0 > 0) ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px) : 0);
-        const int64_t mo = b * plane;
-        const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Scc = four_corner(m.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Srr = four_corner(m.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
-        const long long mc = c0 + c1, mr = r0 + r1;
-        const long long X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
-        const long long Y2 = 4 * Srr - 4 * mr * Sr + mr * mr * N;
-        const long long A = 2 * w * w, Bh = 2 * h * h;
-        const long long qx = X2 / A, rx = X2 - qx * A;
-        const long long qy = Y2 / Bh, ry = Y2 - qy * Bh;
-        long long I = N - qx - qy;
-        unsigned long long F = (unsigned long long)rx * (unsigned long long)Bh +
-                               (unsigned long long)ry * (unsigned long long)A;
-        const unsigned long long Den = (unsigned long long)A * (unsigned long long)Bh;
-        if (F >= Den) {
-            I -= 1;
-            F -= Den;
-        }
-        // S = I - F/Den, with S > 0 whenever N > 0, so I >= 1 when F > 0
-        float s;
-        if (F == 0)
-            s = (float)I;
-        else
-            s = (float)(I - 1) + (float)(Den - F) / (float)Den;
-        if (normalize) {
-            const float K = (4.0f * (float)(w * w) * (float)(h * h) + (float)(w * w) + (float)(h * h)) /
-                            (6.0f * (float)w * (float)h);
-            s = s / K;
-        }
-        out[t] = s;
+        const int f = find_job(pre, n, t);
+        const QueryJob &jb = jobs[f];
+        weighted_item(*jb.v, jb.m, jb.wins, jb.normalize, jb.wout, t - pre[f], err);
     }
 }
 
@@ -245,6 +297,25 @@ int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t
     k_query_weighted<<<grid_for(n * m.Bw), 256, 0, st>>>(v, m, wins, n, normalize, out, err);
     prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const int64_t *pre_wins, int n,
+                         int64_t total_rects, int64_t total_wins, int *err, cudaStream_t st, const Prof *prof)
+{
+    int k = 0;
+    if (total_rects) {
+        prof_mark(prof, KID_QUERY_RECTS, 0, st);
+        k_query_rects_b<<<grid_for(total_rects), 256, 0, st>>>(jobs, pre_rects, n, err);
+        prof_mark(prof, KID_QUERY_RECTS, 1, st);
+        ++k;
+    }
+    if (total_wins) {
+        prof_mark(prof, KID_QUERY_WEIGHTED, 0, st);
+        k_query_weighted_b<<<grid_for(total_wins), 256, 0, st>>>(jobs, pre_wins, n, err);
+        prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
+        ++k;
+    }
+    return cudaPeekAtLastError() == cudaSuccess ? k : -1;
 }
 
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof)

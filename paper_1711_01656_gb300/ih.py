@@ -28,7 +28,9 @@ STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: 
 # The exported C symbols (include/ih.h), checked by the test suite.
 C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih_destroy",
              "ih_release", "ih_sync", "ih_info", "ih_export", "ih_export_moments", "ih_features",
-             "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_build_counts_static")
+             "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_batch_create", "ih_batch_run",
+             "ih_batch_destroy", "ih_autotune", "ih_build_counts_static")
+IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
 
@@ -62,7 +64,15 @@ class ih_frame_info(ctypes.Structure):
     _fields_ = [("height", ctypes.c_int32), ("width", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("total_bins", ctypes.c_int32), ("weighted_channel", ctypes.c_int32),
                 ("weighted_bins", ctypes.c_int32), ("pitch_elems", ctypes.c_int64),
-                ("count_bytes", ctypes.c_int64), ("moment_bytes", ctypes.c_int64)]
+                ("count_bytes", ctypes.c_int64), ("moment_bytes", ctypes.c_int64),
+                ("tile_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32)]
+
+
+class ih_batch_queries(ctypes.Structure):
+    _fields_ = [("d_rects", ctypes.c_void_p), ("rects", ctypes.POINTER(ctypes.c_int64)),
+                ("d_rect_out", ctypes.c_void_p), ("d_windows", ctypes.c_void_p),
+                ("windows", ctypes.POINTER(ctypes.c_int64)), ("d_weighted_out", ctypes.c_void_p),
+                ("kernel", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 _lock = threading.Lock()
@@ -95,6 +105,11 @@ def load_library(path: str = LIB_PATH):
             "ih_launch_count": ([p], i64),
             "ih_last_error": ([p], ctypes.c_char_p),
             "ih_build_counts_static": ([p, i32, i32, i64, i32, i32, p, i64, p], i32),
+            "ih_batch_create": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(ih_batch_queries), u32,
+                                 ctypes.POINTER(p), ctypes.POINTER(i32)], i32),
+            "ih_batch_run": ([p, p], i32),
+            "ih_batch_destroy": ([p], i32),
+            "ih_autotune": ([p, ctypes.POINTER(ih_frame), p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -235,6 +250,43 @@ def ih_profile_read(ctx, reset=True):
     n = ctypes.c_int32()
     _check(ctx, load_library().ih_profile_read(ctx, arr, 64, ctypes.byref(n), int(bool(reset))))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def ih_batch_create(ctx, frames, rects=None, rect_counts=None, rect_out=None, windows=None, window_counts=None,
+                    weighted_out=None, kernel=IH_K_EPANECHNIKOV, flags=0, batch_flags=IH_BATCH_GRAPH):
+    """Plan a batch of Frames (see include/ih.h).  rects / windows: (sum, 4)
+    int32 CUDA tensors with per-frame counts; outputs: flat CUDA tensors
+    holding each frame's block in frame order.  Returns (batch, handles)."""
+    cs = [f._c() for f in frames]
+    arr = (ih_frame * len(cs))(*[c[0] for c in cs])
+    handles = (ctypes.c_int32 * len(cs))()
+    q = None
+    keep = []
+    if rects is not None or windows is not None:
+        rc = (ctypes.c_int64 * len(cs))(*(rect_counts or [0] * len(cs)))
+        wc = (ctypes.c_int64 * len(cs))(*(window_counts or [0] * len(cs)))
+        keep += [rc, wc]
+        q = ih_batch_queries(_ptr(rects).value if rects is not None else None, rc,
+                             _ptr(rect_out).value if rect_out is not None else None,
+                             _ptr(windows).value if windows is not None else None, wc,
+                             _ptr(weighted_out).value if weighted_out is not None else None, int(kernel), int(flags))
+    out = ctypes.c_void_p()
+    _check(ctx, load_library().ih_batch_create(ctx, arr, len(cs), ctypes.byref(q) if q is not None else None,
+                                               int(batch_flags), ctypes.byref(out), handles))
+    return out, list(handles)
+
+
+def ih_batch_run(ctx, batch, stream=None):
+    _check(ctx, load_library().ih_batch_run(batch, _stream(stream)))
+
+
+def ih_batch_destroy(batch):
+    _check(None, load_library().ih_batch_destroy(batch))
+
+
+def ih_autotune(ctx, frame, stream=None):
+    f, arr = frame._c()
+    _check(ctx, load_library().ih_autotune(ctx, ctypes.byref(f), _stream(stream)))
 
 
 def ih_launch_count(ctx) -> int:

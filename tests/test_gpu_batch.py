@@ -1,0 +1,158 @@
+"""Batched builds (one launch per kernel over many frames, CUDA graph
+replay, autotuned tile grids) give exactly what per-frame builds give, and
+per-frame builds match the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1711_01656_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def _frames(ih, seed):
+    """Uneven frames: sizes, channel sets, bin counts, layouts and weighted
+    channels all differ."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    specs = []
+    sizes = [(48, 64), (130, 300), (77, 1030), (257, 129), (1, 9), (200, 200)]
+    for k, (h, w) in enumerate(sizes):
+        layout = k % 2
+        if k % 3 == 0:
+            rgb = synth.blob_rgb(h, w, seed + k)
+            pix = torch.from_numpy(rgb).to(DEV)
+            chans = synth.FMV_CHANNELS
+            f = ih.Frame(pix, chans, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=3 if k % 2 == 0 else -1,
+                         layout=layout)
+            planes = oracle.features(rgb)
+        else:
+            nch = 1 + k % 3
+            chans = [(int(g.integers(1, 40)), 0) for _ in range(nch)]
+            planes = np.stack([synth.blob_plane(h, w, seed + 10 * k + c) for c in range(nch)])
+            pix = torch.from_numpy(planes).to(DEV)
+            f = ih.Frame(pix, chans, weighted_channel=(nch - 1) if k % 2 else -1, layout=layout)
+        specs.append((f, planes, chans))
+    return specs
+
+
+def _export(ih, ctx, h):
+    info = ih.ih_info(ctx, h)
+    out = torch.empty((info["total_bins"], info["height"], info["width"]), dtype=torch.int32, device=DEV)
+    ih.ih_export(ctx, h, out)
+    return out
+
+
+def _moments(ih, ctx, h):
+    info = ih.ih_info(ctx, h)
+    if info["weighted_bins"] == 0:
+        return None
+    outs = []
+    for p in range(4):
+        o = torch.empty((info["weighted_bins"], info["height"], info["width"]), dtype=torch.int64, device=DEV)
+        ih.ih_export_moments(ctx, h, p, o)
+        outs.append(o)
+    return torch.stack(outs)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_equals_single_and_oracle(ihlib, ctx, graph):
+    ih = ihlib
+    specs = _frames(ih, 11)
+    frames = [s[0] for s in specs]
+    # queries: rectangles for every frame, weighted windows for weighted frames
+    rc, wc, rects, wins, win_of = [], [], [], [], {}
+    for k, (f, planes, chans) in enumerate(specs):
+        h, w = f.pixels.shape[1], f.pixels.shape[2]
+        r = synth.rects_uniform_corners(h, w, 37, h + w)
+        rects.append(r)
+        rc.append(len(r))
+        if f.weighted_channel >= 0:
+            q = synth.rects_side_range(h, w, 23, 1, 64, h * w)
+            wins.append(q)
+            win_of[k] = q
+            wc.append(len(q))
+        else:
+            wc.append(0)
+    B = [sum(b for b, _ in s[2]) for s in specs]
+    Bw = [s[2][s[0].weighted_channel][0] if s[0].weighted_channel >= 0 else 0 for s in specs]
+    d_rects = torch.from_numpy(np.concatenate(rects)).to(DEV)
+    d_wins = torch.from_numpy(np.concatenate(wins)).to(DEV)
+    rect_out = torch.full((sum(n * b for n, b in zip(rc, B)),), -7, dtype=torch.int32, device=DEV)
+    w_out = torch.full((sum(n * b for n, b in zip(wc, Bw)),), -7.0, dtype=torch.float32, device=DEV)
+    batch, handles = ih.ih_batch_create(ctx, frames, rects=d_rects, rect_counts=rc, rect_out=rect_out,
+                                        windows=d_wins, window_counts=wc, weighted_out=w_out,
+                                        batch_flags=ih.IH_BATCH_GRAPH if graph else 0)
+    try:
+        for run in range(2):  # a second run (graph replay) gives the same results
+            if run:
+                rect_out.fill_(-7)
+                w_out.fill_(-7.0)
+            ih.ih_batch_run(ctx, batch)
+            ih.ih_sync(ctx)
+            ro, wo = 0, 0
+            for k, (f, planes, chans) in enumerate(specs):
+                got = _export(ih, ctx, handles[k])
+                single, = ih.ih_build(ctx, f)
+                ref = _export(ih, ctx, single)
+                ih.ih_sync(ctx)
+                assert torch.equal(got, ref), "frame %d counts" % k
+                if run == 0:
+                    assert np.array_equal(got.cpu().numpy(), oracle.frame_integral_histogram(planes, chans))
+                gm, sm = _moments(ih, ctx, handles[k]), _moments(ih, ctx, single)
+                assert (gm is None) == (sm is None)
+                if gm is not None:
+                    assert torch.equal(gm, sm), "frame %d moments" % k
+                # queries against the single frame's own queries
+                d_r = torch.from_numpy(rects[k]).to(DEV)
+                sr = torch.empty((rc[k], B[k]), dtype=torch.int32, device=DEV)
+                ih.ih_query_rects(ctx, single, d_r, sr)
+                assert torch.equal(rect_out[ro:ro + rc[k] * B[k]].view(rc[k], B[k]), sr), "frame %d rects" % k
+                ro += rc[k] * B[k]
+                if wc[k]:
+                    wi = win_of[k]
+                    sw = torch.empty((wc[k], Bw[k]), dtype=torch.float32, device=DEV)
+                    ih.ih_query_weighted(ctx, single, torch.from_numpy(wi).to(DEV), sw)
+                    assert torch.equal(w_out[wo:wo + wc[k] * Bw[k]].view(wc[k], Bw[k]), sw), "frame %d weighted" % k
+                    wo += wc[k] * Bw[k]
+                ih.ih_sync(ctx)
+                ih.ih_release(ctx, single)
+    finally:
+        ih.ih_batch_destroy(batch)
+        for h in handles:
+            ih.ih_release(ctx, h)
+
+
+def test_autotune_then_build_exact(ihlib, ctx):
+    ih = ihlib
+    h, w = 300, 1100
+    rgb = synth.blob_rgb(h, w, 5)
+    f = ih.Frame(torch.from_numpy(rgb).to(DEV), synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES,
+                 weighted_channel=3, layout=ih.IH_LAYOUT_SLAB)
+    ih.ih_autotune(ctx, f)
+    hdl, = ih.ih_build(ctx, f)
+    info = ih.ih_info(ctx, hdl)
+    assert info["tile_rows"] in (32, 64, 128) and info["tile_cols"] in (128, 256, 512, 1024, 1152)
+    got = _export(ih, ctx, hdl).cpu().numpy()
+    assert np.array_equal(got, oracle.frame_integral_histogram(oracle.features(rgb), synth.FMV_CHANNELS))
+    ih.ih_release(ctx, hdl)
+
+
+def test_batch_autotune_flag(ihlib, ctx):
+    ih = ihlib
+    imgs = [synth.blob_plane(100 + 37 * k, 150 + 91 * k, k) for k in range(3)]
+    frames = [ih.Frame(torch.from_numpy(im).to(DEV)[None], [(16, 0)], weighted_channel=0) for im in imgs]
+    batch, handles = ih.ih_batch_create(ctx, frames, batch_flags=ih.IH_BATCH_AUTOTUNE | ih.IH_BATCH_GRAPH)
+    try:
+        ih.ih_batch_run(ctx, batch)
+        ih.ih_sync(ctx)
+        for im, hdl in zip(imgs, handles):
+            assert np.array_equal(_export(ih, ctx, hdl).cpu().numpy(), oracle.integral_histogram(im, 16))
+            mo = _moments(ih, ctx, hdl).cpu().numpy()
+            for p, wk in enumerate(oracle.MOMENT_WEIGHTS):
+                assert np.array_equal(mo[p], oracle.weighted_integral_histogram(im, 16, wk))
+    finally:
+        ih.ih_batch_destroy(batch)
+        for hdl in handles:
+            ih.ih_release(ctx, hdl)
