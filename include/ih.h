@@ -103,6 +103,12 @@ typedef struct {
                                    moment planes (Eq. 3.4) are built for
                                    ih_query_weighted */
     int32_t layout;             /* ih_layout */
+    int32_t moment_bits;        /* 0 or 64: exact int64 moment planes;
+                                   32: the planes modulo 2^32 (half the bytes),
+                                   which still gives exact weighted histograms
+                                   for windows of side <= 256 (the centred
+                                   sums they need stay below 2^32); larger
+                                   windows are refused */
 } ih_frame;
 
 typedef struct {
@@ -157,9 +163,10 @@ enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
  * remainder computed exactly in int64/uint64) converted to float with a
  * relative error below 4e-7; no step uses FP64.  d_windows: device,
  * n x 4 int32; d_out: device, n x B_w float (B_w = bins of the weighted
- * channel).  Windows must have sides <= 32768.  Invalid windows give a row
- * of -1 and IH_EINVAL at the next ih_sync().  IH_EINVAL (host) if the frame
- * has no moment planes. */
+ * channel).  Windows must have sides <= 32768 (<= 256 when the frame's
+ * moment planes are 32-bit).  Invalid windows give a row of -1 and
+ * IH_EINVAL at the next ih_sync().  IH_EINVAL (host) if the frame has no
+ * moment planes. */
 ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_windows, int64_t n,
                             uint32_t kernel, uint32_t flags, float *d_out, void *stream);
 
@@ -195,7 +202,8 @@ ih_status ih_info(ih_ctx *ctx, int32_t handle, ih_frame_info *out);
 ih_status ih_export(ih_ctx *ctx, int32_t handle, int32_t *d_dst, void *stream);
 
 /* Copies moment plane `plane` (0: w=c, 1: w=r, 2: w=c^2, 3: w=r^2; Eq. 3.4)
- * to d_dst (device, B_w x H x W int64, packed). */
+ * to d_dst (device, B_w x H x W int64, packed); for a frame built with
+ * moment_bits = 32 each value is the plane modulo 2^32. */
 ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t *d_dst,
                             void *stream);
 

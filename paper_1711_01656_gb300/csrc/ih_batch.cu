@@ -300,7 +300,7 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
         QueryJob &j = qj[k];
         memset(&j, 0, sizeof j);
         j.v = d_views + k;
-        j.m = MomentView{fr.wch >= 0 ? fr.bin_off[fr.wch] : 0, fr.d_mom, fr.Bw};
+        j.m = MomentView{fr.wch >= 0 ? fr.bin_off[fr.wch] : 0, fr.d_mom, fr.Bw, fr.mbits == 32};
         const int64_t nr = (q && q->d_rects) ? q->rects[k] : 0;
         const int64_t nw = (q && q->d_windows) ? q->windows[k] : 0;
         if (nr) {

@@ -104,6 +104,8 @@ ih_status validate(ih_ctx *ctx, const ih_frame &f)
     int total = 0;
     for (int c = 0; c < f.channels; ++c) total += f.chan[c].bins;
     if (total > kMaxBins) return fail(ctx, IH_EINVAL, "%d bins in one frame (at most %d)", total, kMaxBins);
+    if (f.moment_bits != 0 && f.moment_bits != 32 && f.moment_bits != 64)
+        return fail(ctx, IH_EINVAL, "moment_bits = %d (0, 32 or 64)", f.moment_bits);
     if (f.weighted_channel < -1 || f.weighted_channel >= f.channels)
         return fail(ctx, IH_EINVAL, "weighted_channel = %d", f.weighted_channel);
     return IH_OK;
@@ -193,8 +195,9 @@ void frame_record(const ih_frame &f, FrameRec &fr)
     fr.B = off;
     fr.wch = f.weighted_channel;
     fr.Bw = fr.wch >= 0 ? fr.bins[fr.wch] : 0;
+    fr.mbits = f.moment_bits == 32 ? 32 : 64;
     fr.count_bytes = (int64_t)fr.B * fr.H * fr.P * 4;
-    fr.moment_bytes = (int64_t)4 * fr.Bw * fr.H * fr.P * 8;
+    fr.moment_bytes = (int64_t)4 * fr.Bw * fr.H * fr.P * (fr.mbits / 8);
 }
 
 std::string shape_key(const ih_frame &f)
@@ -232,6 +235,7 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
     }
     ps.out = fr.d_ih;
     ps.mom = fr.d_mom;
+    ps.mom32 = fr.mbits == 32;
     return true;
 }
 
@@ -414,7 +418,7 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
         return fail(ctx, IH_EINVAL, "kernel %u / flags %u", kernel, flags);
     if (n < 0 || (n > 0 && (!d_windows || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_weighted: bad arguments");
     DevGuard dg(ctx->device);
-    const MomentView m{fr->bin_off[fr->wch], fr->d_mom, fr->Bw};
+    const MomentView m{fr->bin_off[fr->wch], fr->d_mom, fr->Bw, fr->mbits == 32};
     const int k = launch_query_weighted(fr->view, m, d_windows, n, (flags & IH_NORMALIZE) ? 1 : 0, d_out,
                                         ctx->d_err, static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
@@ -496,11 +500,11 @@ ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t 
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (!fr->Bw || plane < 0 || plane > 3) return fail(ctx, IH_EINVAL, "no moment plane %d", plane);
     DevGuard dg(ctx->device);
-    const int64_t *src = fr->d_mom + (int64_t)plane * fr->Bw * fr->H * fr->P;
-    cudaError_t e = cudaMemcpy2DAsync(d_dst, (size_t)fr->W * 8, src, (size_t)fr->P * 8, (size_t)fr->W * 8,
-                                      (size_t)fr->Bw * fr->H, cudaMemcpyDeviceToDevice,
-                                      static_cast<cudaStream_t>(stream));
-    return e == cudaSuccess ? IH_OK : cuda_fail(ctx, e, "export copy");
+    if (launch_export_moments(fr->d_mom, fr->mbits == 32, fr->Bw, fr->H, fr->W, fr->P, plane, d_dst,
+                              static_cast<cudaStream_t>(stream), prof_of(ctx)) < 0)
+        return cuda_fail(ctx, cudaGetLastError(), "export launch");
+    ctx->launches += 1;
+    return IH_OK;
 }
 
 ih_status ih_features(ih_ctx *ctx, const uint8_t *d_rgb, int32_t height, int32_t width, int64_t pitch_bytes,

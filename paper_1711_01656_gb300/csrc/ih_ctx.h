@@ -18,8 +18,8 @@ struct FrameRec {
     int bin_off[kMaxChannels] = {0};
     int64_t P = 0;
     int32_t *d_ih = nullptr;
-    int wch = -1, Bw = 0;
-    int64_t *d_mom = nullptr;
+    int wch = -1, Bw = 0, mbits = 64;
+    int64_t *d_mom = nullptr;  // int64 or uint32 planes (mbits)
     int64_t count_bytes = 0, moment_bytes = 0;
     int R = 0, Wc = 0;  // tile grid used by the build
     CountView view{};

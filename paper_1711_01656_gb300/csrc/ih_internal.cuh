@@ -95,6 +95,7 @@ struct PlaneSet {
     int32_t nchan;
     int32_t layout;       // Layout of the count tensor
     int32_t wch;          // weighted channel, or -1
+    int32_t mom32;        // moment planes stored as uint32
     ChanDev chan[kMaxChannels];
     int32_t ngroups;      // count bin groups (<= kGroupBins bins each)
     int32_t nwin;         // tile-sums windows (<= kWindowBins bins each)
@@ -103,7 +104,8 @@ struct PlaneSet {
     GroupDev win[kMaxGroups];
     int64_t slab_off[kMaxGroups];  // LAYOUT_SLAB: element offset of group g's slab
     int32_t *out;         // count tensor
-    int64_t *mom;         // moment planes [4][Bw][H][P] (w = c, r, c^2, r^2), or null
+    int64_t *mom;         // moment planes [4][Bw][H][P] (w = c, r, c^2, r^2), or null;
+                          // uint32 (values mod 2^32) when mom32
     // carries (null when the frame is a single tile)
     int32_t *colsum;      // [nb][B][W]  column counts -> G0 after the scan
     int32_t *rowsum;      // [ns][B][H]  row counts    -> L0 after the scan
@@ -183,8 +185,9 @@ struct CountView {
 };
 struct MomentView {
     int32_t bin0;        // first bin of the weighted channel in the count tensor
-    const int64_t *m;    // [4][Bw][H][P]: w = c, r, c^2, r^2
+    const int64_t *m;    // [4][Bw][H][P]: w = c, r, c^2, r^2 (uint32 when m32)
     int32_t Bw;
+    int32_t m32;
 };
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out,
                        int *err, cudaStream_t st, const Prof *prof);
@@ -205,5 +208,8 @@ int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t
                           int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
+// Moment plane k of [4][Bw][H][P] (int64, or uint32 when m32) -> packed Bw x H x W int64.
+int launch_export_moments(const void *m, int m32, int Bw, int H, int W, int64_t P, int k, int64_t *dst,
+                          cudaStream_t st, const Prof *prof);
 
 }  // namespace ih

@@ -729,6 +729,7 @@ __global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
 
 // ------------------------------------------------------------- moment tiles
 
+template <bool M32>
 __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, int j, int wb, int lane,
                                                    int32_t *RLn, long long *RLx, long long *RLxx)
 {
@@ -757,6 +758,7 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
     __syncwarp();
     const int64_t plane = (int64_t)Bw * g.H * g.P;
     int64_t *mo = ps.mom + (int64_t)wb * g.H * g.P;
+    uint32_t *mo32 = reinterpret_cast<uint32_t *>(ps.mom) + (int64_t)wb * g.H * g.P;
     const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
 
     for (int cc = C0; cc < C1; cc += kChunk) {
@@ -837,11 +839,20 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                 }
                 if (c < g.P) {
                     const int64_t o = (int64_t)(R0 + rr) * g.P + c;
+                    if (M32) {
+                        // the planes modulo 2^32: one 16-byte store per plane
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        longlong2 *dst = reinterpret_cast<longlong2 *>(mo + k * plane + o);
-                        dst[0] = make_longlong2(acc[k][0], acc[k][1]);
-                        dst[1] = make_longlong2(acc[k][2], acc[k][3]);
+                        for (int k = 0; k < 4; ++k)
+                            *reinterpret_cast<uint4 *>(mo32 + k * plane + o) =
+                                make_uint4((uint32_t)acc[k][0], (uint32_t)acc[k][1], (uint32_t)acc[k][2],
+                                           (uint32_t)acc[k][3]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            longlong2 *dst = reinterpret_cast<longlong2 *>(mo + k * plane + o);
+                            dst[0] = make_longlong2(acc[k][0], acc[k][1]);
+                            dst[1] = make_longlong2(acc[k][2], acc[k][3]);
+                        }
                     }
                 }
                 __syncwarp();
@@ -867,7 +878,10 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant_
     const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
     if (unit >= (int64_t)g.nb * g.ns * Bw) return;
     const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
-    tiles_moments_unit(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+    if (ps.mom32)
+        tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+    else
+        tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
 }
 
 __global__ void __launch_bounds__(128, 4) k_tiles_moments_b(const BatchDev bd)
@@ -882,7 +896,10 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments_b(const BatchDev bd)
     const int Bw = ps.chan[ps.wch].bins;
     const int64_t local = unit - bd.pre_mom[f];
     const int tile = (int)(local / Bw), wb = (int)(local % Bw);
-    tiles_moments_unit(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+    if (ps.mom32)
+        tiles_moments_unit<true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+    else
+        tiles_moments_unit<false>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
 }
 
 template <typename F>

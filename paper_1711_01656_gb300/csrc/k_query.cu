@@ -48,6 +48,15 @@ __device__ __forceinline__ long long four_corner(const int64_t *p, int64_t P, in
     return a - b - c + d;
 }
 
+__device__ __forceinline__ uint32_t four_corner_u32(const uint32_t *p, int64_t P, int r0, int c0, int r1, int c1)
+{
+    const uint32_t a = __ldg(p + (int64_t)r1 * P + c1);
+    const uint32_t b = r0 > 0 ? __ldg(p + (int64_t)(r0 - 1) * P + c1) : 0u;
+    const uint32_t c = c0 > 0 ? __ldg(p + (int64_t)r1 * P + (c0 - 1)) : 0u;
+    const uint32_t d = (r0 > 0 && c0 > 0) ? __ldg(p + (int64_t)(r0 - 1) * P + (c0 - 1)) : 0u;
+    return a - b - c + d;
+}
+
 // One thread per (rectangle, bin group): the group's bins of each corner
 // are nb_g contiguous words in the slab layout.
 template <typename TN>
@@ -191,7 +200,8 @@ __device__ __forceinline__ void weighted_item(const CountView &v, const MomentVi
     const int b = (int)(t - qi * m.Bw);
     const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
     const int r1 = __ldg(wins + 4 * qi + 2), c1 = __ldg(wins + 4 * qi + 3);
-    if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= 32768 || c1 - c0 >= 32768) {
+    const int smax = m.m32 ? 256 : 32768;
+    if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= smax || c1 - c0 >= smax) {
         out[t] = -1.0f;
         if (b == 0) atomicOr(err, 1);
         return;
@@ -204,14 +214,28 @@ __device__ __forceinline__ void weighted_item(const CountView &v, const MomentVi
                         (c0 > 0 ? (long long)__ldg(cp + ((int64_t)r1 * v.P + (c0 - 1)) * px) : 0) +
                         ((r0 > 0 && c0 > 0) ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px) : 0);
     const int64_t mo = b * plane;
-    const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
-    const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
-    const long long Scc = four_corner(m.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
-    const long long Srr = four_corner(m.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
     const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
     const long long mc = c0 + c1, mr = r0 + r1;
-    const long long X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
-    const long long Y2 = 4 * Srr - 4 * mr * Sr + mr * mr * N;
+    long long X2, Y2;
+    if (m.m32) {
+        // planes modulo 2^32: the centred sums X2, Y2 < 2^32 for sides <= 256,
+        // so computing them modulo 2^32 gives them exactly
+        const uint32_t *m32 = reinterpret_cast<const uint32_t *>(m.m);
+        const uint32_t Sc = four_corner_u32(m32 + 0 * mplane + mo, v.P, r0, c0, r1, c1);
+        const uint32_t Sr = four_corner_u32(m32 + 1 * mplane + mo, v.P, r0, c0, r1, c1);
+        const uint32_t Scc = four_corner_u32(m32 + 2 * mplane + mo, v.P, r0, c0, r1, c1);
+        const uint32_t Srr = four_corner_u32(m32 + 3 * mplane + mo, v.P, r0, c0, r1, c1);
+        const uint32_t n32 = (uint32_t)N, mc32 = (uint32_t)mc, mr32 = (uint32_t)mr;
+        X2 = (long long)(uint32_t)(4u * Scc - 4u * mc32 * Sc + mc32 * mc32 * n32);
+        Y2 = (long long)(uint32_t)(4u * Srr - 4u * mr32 * Sr + mr32 * mr32 * n32);
+    } else {
+        const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Scc = four_corner(m.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
+        const long long Srr = four_corner(m.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
+        X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
+        Y2 = 4 * Srr - 4 * mr * Sr + mr * mr * N;
+    }
     const long long A = 2 * w * w, Bh = 2 * h * h;
     const long long qx = X2 / A, rx = X2 - qx * A;
     const long long qy = Y2 / Bh, ry = Y2 - qy * Bh;
@@ -271,6 +295,19 @@ __global__ void __launch_bounds__(256) k_export(const __grid_constant__ CountVie
     }
 }
 
+__global__ void __launch_bounds__(256) k_export_moments(const void *__restrict__ m, int m32, int Bw, int H, int W,
+                                                        int64_t P, int k, int64_t *__restrict__ dst)
+{
+    const int64_t total = (int64_t)Bw * H * W;
+    const int64_t plane = (int64_t)Bw * H * P;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t % W, rb = t / W;
+        const int64_t o = k * plane + rb * P + c;
+        dst[t] = m32 ? (int64_t)__ldg(static_cast<const uint32_t *>(m) + o) : __ldg(static_cast<const int64_t *>(m) + o);
+    }
+}
+
 unsigned grid_for(int64_t total)
 {
     const int64_t b = (total + 255) / 256;
@@ -316,6 +353,15 @@ int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const i
         ++k;
     }
     return cudaPeekAtLastError() == cudaSuccess ? k : -1;
+}
+
+int launch_export_moments(const void *m, int m32, int Bw, int H, int W, int64_t P, int k, int64_t *dst,
+                          cudaStream_t st, const Prof *prof)
+{
+    prof_mark(prof, KID_EXPORT, 0, st);
+    k_export_moments<<<grid_for((int64_t)Bw * H * W), 256, 0, st>>>(m, m32, Bw, H, W, P, k, dst);
+    prof_mark(prof, KID_EXPORT, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof)

@@ -48,7 +48,8 @@ class ih_frame(ctypes.Structure):
     _fields_ = [("height", ctypes.c_int32), ("width", ctypes.c_int32), ("channels", ctypes.c_int32),
                 ("input", ctypes.c_int32), ("chan", ctypes.POINTER(ih_channel)),
                 ("d_pixels", ctypes.c_void_p), ("pitch_bytes", ctypes.c_int64),
-                ("weighted_channel", ctypes.c_int32), ("layout", ctypes.c_int32)]
+                ("weighted_channel", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("moment_bits", ctypes.c_int32)]
 
 
 class ih_config(ctypes.Structure):
@@ -160,7 +161,7 @@ class Frame:
     list of (bins, mode) pairs, one per binned channel."""
 
     def __init__(self, pixels, channels, input=IH_INPUT_PLANES, weighted_channel=-1,
-                 layout=IH_LAYOUT_BIN_MAJOR):
+                 layout=IH_LAYOUT_BIN_MAJOR, moment_bits=64):
         if pixels.dtype.itemsize != 1 or pixels.dim() != 3 or not pixels.is_cuda:
             raise ValueError("pixels must be a (planes, H, W) uint8 CUDA tensor")
         planes, h, w = pixels.shape
@@ -175,12 +176,13 @@ class Frame:
         self.input = int(input)
         self.weighted_channel = int(weighted_channel)
         self.layout = int(layout)
+        self.moment_bits = int(moment_bits)
 
     def _c(self):
         arr = (ih_channel * len(self.channels))(*[ih_channel(b, m) for b, m in self.channels])
         f = ih_frame(self.pixels.shape[1], self.pixels.shape[2], len(self.channels), self.input,
                      ctypes.cast(arr, ctypes.POINTER(ih_channel)), self.pixels.data_ptr(),
-                     self.pitch, self.weighted_channel, self.layout)
+                     self.pitch, self.weighted_channel, self.layout, self.moment_bits)
         return f, arr
 
 

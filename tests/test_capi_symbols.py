@@ -29,8 +29,8 @@ def test_library_exports_all_declared(ihlib):
 
 
 def test_struct_layouts_match_header(ihlib):
-    # ih_frame: 4 int32, 2 pointers, int64, 2 int32 -> 48 bytes on LP64
-    assert ctypes.sizeof(ihlib.ih_frame) == 48
+    # ih_frame: 4 int32, 2 pointers, int64, 3 int32 (+4 padding) -> 56 bytes on LP64
+    assert ctypes.sizeof(ihlib.ih_frame) == 56
     assert ctypes.sizeof(ihlib.ih_frame_info) == 56
     assert ctypes.sizeof(ihlib.ih_batch_queries) == 56
     assert ctypes.sizeof(ihlib.ih_config) == 24

@@ -379,3 +379,28 @@ def test_moments_on_multichannel_frame(ihlib, ctx, wch):
     got = _weighted_gpu(ihlib, ctx, hdl, wins, bw)
     _assert_weighted(got, oracle.weighted_hist(planes[wch], bw, wins))
     ihlib.ih_release(ctx, hdl)
+
+
+def test_moment_planes_u32_and_weighted(ihlib, ctx):
+    """32-bit moment planes hold the int64 planes modulo 2^32 and still give
+    the exact weighted histograms of windows with sides up to 256."""
+    h, w, bins = 700, 900, 16
+    img = synth.blob_plane(h, w, 44)
+    pix = torch.from_numpy(img).to(DEV)[None]
+    hdl, = ihlib.ih_build(ctx, ihlib.Frame(pix, [(bins, 0)], weighted_channel=0, layout=1, moment_bits=32))
+    info = ihlib.ih_info(ctx, hdl)
+    assert info["moment_bytes"] == 4 * bins * h * ((w + 3) // 4 * 4) * 4
+    for plane, wk in enumerate(oracle.MOMENT_WEIGHTS):
+        out = torch.empty((bins, h, w), dtype=torch.int64, device=DEV)
+        ihlib.ih_export_moments(ctx, hdl, plane, out)
+        ihlib.ih_sync(ctx)
+        ref = oracle.weighted_integral_histogram(img, bins, wk) % (1 << 32)
+        assert np.array_equal(out.cpu().numpy(), ref), "plane %d" % plane
+    wins = np.concatenate([synth.rects_side_range(h, w, 800, 1, 256, 7),
+                           np.array([[0, 0, 255, 255], [h - 256, w - 256, h - 1, w - 1]], np.int32)])
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, bins)
+    _assert_weighted(got, oracle.weighted_hist(img, bins, wins))
+    # a window wider than 256 is refused on the device
+    with pytest.raises(ihlib.IHError):
+        _weighted_gpu(ihlib, ctx, hdl, [[0, 0, 10, 256]], bins)
+    ihlib.ih_release(ctx, hdl)
