@@ -282,6 +282,63 @@ ih_status ih_batch_destroy(ih_batch *batch);
  * channel, layout) with the fastest.  Synchronous. */
 ih_status ih_autotune(ih_ctx *ctx, const ih_frame *frame, void *stream);
 
+/* ---- serving ---------------------------------------------------------- */
+
+/* A server runs a request loop for many concurrent tracker streams: each
+ * request is a frame plus its rectangle and weighted queries.  A scheduler
+ * thread admits pending requests as in-flight slots and HBM (the context's
+ * budget) free up, merges the requests admitted together into one batched
+ * build and one batched query launch (a "tick"), and runs ticks on several
+ * CUDA streams so that they overlap on the device.  Each tracker's latest
+ * completed frame stays resident until its next frame completes or memory is
+ * needed for a pending request (least recently completed first). */
+typedef struct ih_server ih_server;
+
+typedef struct {
+    int32_t streams;       /* CUDA streams ticks are spread over (>= 1) */
+    int32_t max_inflight;  /* ticks on the device at once (>= 1) */
+    int32_t max_batch;     /* requests merged into one tick (>= 1, <= 256) */
+    uint32_t flags;        /* reserved, 0 */
+} ih_server_config;
+
+typedef struct {
+    int32_t tracker;             /* tracker stream id, >= 0 */
+    ih_frame frame;              /* chan copied at submit; pixels must stay
+                                    valid until the request completes */
+    ih_channel chan[16];         /* storage the server copies frame.chan into */
+    const int32_t *d_rects;      /* device, n_rects x 4, or NULL */
+    int64_t n_rects;
+    int32_t *d_rect_out;         /* device, n_rects x B int32 */
+    const int32_t *d_windows;    /* device, n_windows x 4, or NULL */
+    int64_t n_windows;
+    float *d_weighted_out;       /* device, n_windows x B_w float */
+    uint32_t weighted_flags;     /* IH_NORMALIZE or 0 */
+    uint64_t user;               /* returned in the completion */
+} ih_request;
+
+typedef struct {
+    uint64_t user;
+    int32_t status;       /* ih_status of the request */
+    int32_t handle;       /* the frame while it stays resident, or -1 */
+    double t_submit;      /* seconds on the server clock (ih_server_clock) */
+    double t_admit;       /* the tick holding the request was enqueued */
+    double t_done;        /* the device finished the request's tick */
+} ih_completion;
+
+/* Starts a server on ctx.  Synchronous. */
+ih_status ih_server_create(ih_ctx *ctx, const ih_server_config *cfg, ih_server **out);
+/* Queues a request (validated now: IH_EINVAL without queueing). */
+ih_status ih_server_submit(ih_server *srv, const ih_request *req);
+/* Copies up to max completions (host) to out, waiting up to wait_ms for the
+ * first one; returns how many were copied. */
+int32_t ih_server_poll(ih_server *srv, ih_completion *out, int32_t max, int32_t wait_ms);
+/* Waits until every submitted request has completed. */
+ih_status ih_server_drain(ih_server *srv);
+/* Seconds since the server started (host monotonic clock). */
+double ih_server_clock(ih_server *srv);
+/* Drains, stops the scheduler and releases the resident frames. */
+ih_status ih_server_destroy(ih_server *srv);
+
 /* ---- allocation-free variant ------------------------------------------ */
 
 /* The thesis has no counterpart to this call; it exists for callers that

@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: 
 C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih_destroy",
              "ih_release", "ih_sync", "ih_info", "ih_export", "ih_export_moments", "ih_features",
              "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_batch_create", "ih_batch_run",
-             "ih_batch_destroy", "ih_autotune", "ih_build_counts_static")
+             "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
+             "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -67,6 +68,23 @@ class ih_frame_info(ctypes.Structure):
                 ("weighted_bins", ctypes.c_int32), ("pitch_elems", ctypes.c_int64),
                 ("count_bytes", ctypes.c_int64), ("moment_bytes", ctypes.c_int64),
                 ("tile_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32)]
+
+
+class ih_server_config(ctypes.Structure):
+    _fields_ = [("streams", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("flags", ctypes.c_uint32)]
+
+
+class ih_request(ctypes.Structure):
+    _fields_ = [("tracker", ctypes.c_int32), ("frame", ih_frame), ("chan", ih_channel * 16),
+                ("d_rects", ctypes.c_void_p), ("n_rects", ctypes.c_int64), ("d_rect_out", ctypes.c_void_p),
+                ("d_windows", ctypes.c_void_p), ("n_windows", ctypes.c_int64), ("d_weighted_out", ctypes.c_void_p),
+                ("weighted_flags", ctypes.c_uint32), ("user", ctypes.c_uint64)]
+
+
+class ih_completion(ctypes.Structure):
+    _fields_ = [("user", ctypes.c_uint64), ("status", ctypes.c_int32), ("handle", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
 
 
 class ih_batch_queries(ctypes.Structure):
@@ -111,6 +129,12 @@ def load_library(path: str = LIB_PATH):
             "ih_batch_run": ([p, p], i32),
             "ih_batch_destroy": ([p], i32),
             "ih_autotune": ([p, ctypes.POINTER(ih_frame), p], i32),
+            "ih_server_create": ([p, ctypes.POINTER(ih_server_config), ctypes.POINTER(p)], i32),
+            "ih_server_submit": ([p, ctypes.POINTER(ih_request)], i32),
+            "ih_server_poll": ([p, ctypes.POINTER(ih_completion), i32, i32], i32),
+            "ih_server_drain": ([p], i32),
+            "ih_server_clock": ([p], ctypes.c_double),
+            "ih_server_destroy": ([p], i32),
         }
         for name, (args, res) in sig.items():
             f = getattr(lib, name)
@@ -289,6 +313,50 @@ def ih_batch_destroy(batch):
 def ih_autotune(ctx, frame, stream=None):
     f, arr = frame._c()
     _check(ctx, load_library().ih_autotune(ctx, ctypes.byref(f), _stream(stream)))
+
+
+def ih_server_create(ctx, streams=4, max_inflight=8, max_batch=32):
+    cfg = ih_server_config(int(streams), int(max_inflight), int(max_batch), 0)
+    out = ctypes.c_void_p()
+    _check(ctx, load_library().ih_server_create(ctx, ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def ih_server_submit(ctx, srv, tracker, frame, rects=None, rect_out=None, windows=None, weighted_out=None,
+                     weighted_flags=0, user=0):
+    """Queue a request; the caller keeps `frame.pixels`, the query tensors and
+    the outputs alive until its completion is polled."""
+    f, arr = frame._c()
+    q = ih_request()
+    q.tracker = int(tracker)
+    q.frame = f
+    q.d_rects = _ptr(rects).value if rects is not None else None
+    q.n_rects = 0 if rects is None else rects.shape[0]
+    q.d_rect_out = _ptr(rect_out).value if rect_out is not None else None
+    q.d_windows = _ptr(windows).value if windows is not None else None
+    q.n_windows = 0 if windows is None else windows.shape[0]
+    q.d_weighted_out = _ptr(weighted_out).value if weighted_out is not None else None
+    q.weighted_flags = int(weighted_flags)
+    q.user = int(user)
+    _check(ctx, load_library().ih_server_submit(srv, ctypes.byref(q)))
+
+
+def ih_server_poll(srv, max=1024, wait_ms=0):
+    arr = (ih_completion * max)()
+    n = load_library().ih_server_poll(srv, arr, max, int(wait_ms))
+    return [{k: getattr(arr[i], k) for k, _ in ih_completion._fields_} for i in range(n)]
+
+
+def ih_server_drain(srv):
+    _check(None, load_library().ih_server_drain(srv))
+
+
+def ih_server_clock(srv) -> float:
+    return float(load_library().ih_server_clock(srv))
+
+
+def ih_server_destroy(srv):
+    _check(None, load_library().ih_server_destroy(srv))
 
 
 def ih_launch_count(ctx) -> int:

@@ -3,6 +3,7 @@ include/ih.h declares (no GPU needed, nothing is computed)."""
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -28,12 +29,29 @@ def test_library_exports_all_declared(ihlib):
     assert sorted(ihlib.C_SYMBOLS) == sorted(_declared())
 
 
-def test_struct_layouts_match_header(ihlib):
-    # ih_frame: 4 int32, 2 pointers, int64, 3 int32 (+4 padding) -> 56 bytes on LP64
-    assert ctypes.sizeof(ihlib.ih_frame) == 56
-    assert ctypes.sizeof(ihlib.ih_frame_info) == 56
-    assert ctypes.sizeof(ihlib.ih_batch_queries) == 56
-    assert ctypes.sizeof(ihlib.ih_config) == 24
+STRUCTS = ["ih_channel", "ih_frame", "ih_config", "ih_frame_info", "ih_kernel_stat", "ih_batch_queries",
+           "ih_server_config", "ih_request", "ih_completion"]
+
+
+def test_struct_layouts_match_header(ihlib, tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    that a C compiler gives the structure of include/ih.h."""
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "ih.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (name, name))
+        for field, _ in getattr(ihlib, name)._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, field, name, field))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    c = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for name in STRUCTS:
+        st = getattr(ihlib, name)
+        assert int(c[name]) == ctypes.sizeof(st), name
+        for field, _ in st._fields_:
+            assert int(c["%s.%s" % (name, field)]) == getattr(st, field).offset, (name, field)
 
 
 def test_binding_refuses_missing_library(tmp_path):
