@@ -389,6 +389,12 @@ def run_engine(args):
                    "gbs": round(algorithmic_bytes(k, B, Bw, N_RECTS, N_WINDOWS) / (v[1] / v[0] / 1e3) / 1e9, 1)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
+    batched = served = None
+    if not args.no_batched:
+        batched = batched_section(ih, ctx, dev)
+    if not args.no_served:
+        served = served_section(ih, dev)
+
     line = None
     if rank == 0:
         cpu = None
@@ -410,12 +416,161 @@ def run_engine(args):
             "gpu_launches": int(launches),
             "clocks": clocks.summary(t_wall0, t_wall1),
             "kernels": kernels,
+            "batched": batched,
+            "served": served,
         }
         print(json.dumps(line))
     ih.ih_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+# ----------------------------------------------------------------- batched / served
+
+def batched_section(ih, ctx, dev, n_frames=64, runs=5):
+    """64 uneven FMV frames (sizes drawn from {640x480, 1280x720, 1920x1080,
+    4096x2160}) with intensity moments and 4,096 weighted windows each: one
+    batched launch per kernel replayed from a CUDA graph with autotuned tile
+    grids, against 64 per-frame builds and queries on one stream."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    sizes = synth.frame_sizes_batched(n_frames, synth.config_seed(4))
+    px = sum(h * w for h, w in sizes)
+    need = px * (91 * 4 + 16 * 32) * 1.1 + px * 3
+    free, _ = torch.cuda.mem_get_info(dev)
+    while need > free * 0.9 and n_frames > 1:  # keep within this GPU's free memory
+        n_frames //= 2
+        sizes = sizes[:n_frames]
+        px = sum(h * w for h, w in sizes)
+        need = px * (91 * 4 + 16 * 32) * 1.1 + px * 3
+    base = {s: synth.blob_rgb(s[0], s[1], 1000 + s[0]) for s in set(sizes)}
+    pix = [torch.from_numpy(np.roll(base[s], 37 * k, axis=2)).to(dev) for k, s in enumerate(sizes)]
+    frames = [ih.Frame(p, synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
+                       layout=ih.IH_LAYOUT_SLAB) for p in pix]
+    nw = 4096
+    wins = torch.from_numpy(np.concatenate([synth.rects_side_range(h, w, nw, 32, 256, 77 + k)
+                                            for k, (h, w) in enumerate(sizes)])).to(dev)
+    w_out = torch.empty(n_frames * nw * 16, dtype=torch.float32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, k):
+        ts = []
+        for _ in range(k):
+            ev[0].record()
+            fn()
+            ev[1].record()
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+        return float(np.median(ts))
+
+    batch, handles = ih.ih_batch_create(ctx, frames, windows=wins, window_counts=[nw] * n_frames,
+                                        weighted_out=w_out, batch_flags=ih.IH_BATCH_GRAPH | ih.IH_BATCH_AUTOTUNE)
+    timed(lambda: ih.ih_batch_run(ctx, batch), 2)
+    l0 = ih.ih_launch_count(ctx)
+    ms_b = timed(lambda: ih.ih_batch_run(ctx, batch), runs)
+    launches_b = (ih.ih_launch_count(ctx) - l0) // runs
+    ih.ih_batch_destroy(batch)
+    for h in handles:
+        ih.ih_release(ctx, h)
+    torch.cuda.synchronize()
+
+    def per_frame():
+        for k, f in enumerate(frames):
+            h, = ih.ih_build(ctx, f)
+            ih.ih_query_weighted(ctx, h, wins[nw * k: nw * (k + 1)], w_out[nw * 16 * k: nw * 16 * (k + 1)].view(nw, 16))
+            ih.ih_release(ctx, h)
+
+    timed(per_frame, 1)
+    l0 = ih.ih_launch_count(ctx)
+    ms_p = timed(per_frame, max(2, runs // 2))
+    launches_p = (ih.ih_launch_count(ctx) - l0) // max(2, runs // 2)
+    ih.ih_sync(ctx)
+    cells = px * 91
+    gbytes = px * (91 * 4 + 16 * 32) / 1e9
+    return {"workload": "%d uneven FMV frames (%s), 91 bins + intensity moments, %d weighted windows each"
+                        % (n_frames, ", ".join("%dx%d:%d" % (w, h, sizes.count((h, w))) for h, w in sorted(set(sizes))), nw),
+            "frames": n_frames, "pixels": px, "output_GB": round(gbytes, 2),
+            "batched_graph_ms": round(ms_b, 3), "per_frame_ms": round(ms_p, 3),
+            "batched_cells_per_s": cells / (ms_b / 1e3), "per_frame_cells_per_s": cells / (ms_p / 1e3),
+            "batched_output_GBs": round(gbytes / (ms_b / 1e3), 1), "speedup_vs_per_frame": round(ms_p / ms_b, 3),
+            "launches_per_batch": int(launches_b), "launches_per_frame_loop": int(launches_p)}
+
+
+def served_section(ih, dev, seconds=2.0, trackers=16, fps=30.0, budget_gb=60):
+    """16 tracker streams with Poisson frame arrivals (30 fps each); frames
+    drawn from the batched workload's sizes (FMV, 91 bins + intensity int64
+    moments) and, with probability 1/16, 8192x8192 WAMI frames (32 bins,
+    32-bit moments); 2,000 rectangles and 2,000 weighted windows per frame;
+    60 GB budget.  The same arrival trace is served with continuous batching
+    (4 streams, 4 ticks in flight, up to 16 requests per tick) and one
+    request at a time."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    g = np.random.Generator(np.random.PCG64(synth.config_seed(5)))
+    rate = trackers * fps
+    n = int(seconds * rate)
+    t = np.cumsum(g.exponential(1.0 / rate, size=n))
+    tracker = g.integers(0, trackers, size=n)
+    sizes = [(480, 640), (720, 1280), (1080, 1920), (2160, 4096)]
+    kind = np.where(g.random(n) < 1.0 / 16, 4, g.integers(0, 4, size=n))
+    # device-resident inputs: two variants per FMV size, one WAMI frame
+    fmv = {s: [torch.from_numpy(synth.blob_rgb(s[0], s[1], 500 + v + s[0])).to(dev) for v in range(2)] for s in sizes}
+    wami = torch.from_numpy(synth.blob_plane(8192, 8192, 555)).to(dev)[None]
+    qs = {}
+    for k, (h, w) in enumerate(sizes + [(8192, 8192)]):
+        qs[k] = (torch.from_numpy(synth.rects_uniform_corners(h, w, 2000, 900 + k)).to(dev),
+                 torch.from_numpy(synth.rects_side_range(h, w, 2000, 32, 256, 950 + k)).to(dev))
+
+    def frame_of(i):
+        if kind[i] == 4:
+            return ih.Frame(wami, [(32, 0)], weighted_channel=0, layout=ih.IH_LAYOUT_SLAB, moment_bits=32), 32, 32, \
+                8192 * 8192
+        s = sizes[kind[i]]
+        return ih.Frame(fmv[s][i % 2], synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
+                        layout=ih.IH_LAYOUT_SLAB), 91, 16, s[0] * s[1]
+
+    def serve(streams, inflight, batch):
+        ctx = ih.ih_create(dev.index or 0, hbm_budget_bytes=int(budget_gb * 1e9))
+        srv = ih.ih_server_create(ctx, streams=streams, max_inflight=inflight, max_batch=batch)
+        keep, lat, cells, done = {}, [], 0, []
+        try:
+            start = ih.ih_server_clock(srv) + 0.05
+            for i in range(n):
+                while ih.ih_server_clock(srv) < start + t[i]:
+                    for c in ih.ih_server_poll(srv, 256, 0):
+                        done.append(c)
+                        keep.pop(c["user"], None)
+                f, B, Bw, npx = frame_of(i)
+                r, w = qs[int(kind[i])]
+                ro = torch.empty((2000, B), dtype=torch.int32, device=dev)
+                wo = torch.empty((2000, Bw), dtype=torch.float32, device=dev)
+                keep[i] = (f, ro, wo)
+                ih.ih_server_submit(ctx, srv, int(tracker[i]), f, rects=r, rect_out=ro, windows=w, weighted_out=wo,
+                                    user=i)
+            ih.ih_server_drain(srv)
+            done += ih.ih_server_poll(srv, n + 16, 0)
+        finally:
+            ih.ih_server_destroy(srv)
+            ih.ih_destroy(ctx)
+        ok = [c for c in done if c["status"] == 0]
+        lat = np.array([c["t_done"] - c["t_submit"] for c in ok]) * 1e3
+        span = max(c["t_done"] for c in ok) - min(c["t_submit"] for c in ok)
+        for c in ok:
+            cells += (91 if kind[c["user"]] < 4 else 32) * (sizes[kind[c["user"]]][0] * sizes[kind[c["user"]]][1]
+                                                           if kind[c["user"]] < 4 else 8192 * 8192)
+        return {"completed": len(ok), "failed": len(done) - len(ok), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3), "mean_ms": round(float(lat.mean()), 3),
+                "cells_per_s": cells / span, "span_s": round(span, 3)}
+
+    cont = serve(4, 4, 16)
+    single = serve(1, 1, 1)
+    return {"workload": "%d trackers x %.0f fps Poisson for %.1f s (%d frames, %d WAMI 8192^2), 2,000 rect + "
+                        "2,000 weighted queries per frame, %d GB budget" % (trackers, fps, seconds, n,
+                                                                            int((kind == 4).sum()), budget_gb),
+            "continuous_batching": cont, "one_request_at_a_time": single}
 
 
 def main(argv=None):
@@ -425,6 +580,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-frame batched comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the serving-loop comparison")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
         ap.error("--warmup must be >= 3")
