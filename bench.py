@@ -391,7 +391,7 @@ def run_engine(args):
 
     batched = served = None
     if not args.no_batched:
-        batched = batched_section(ih, ctx, dev)
+        batched = batched_section(ih, dev)
     if not args.no_served:
         served = served_section(ih, dev)
 
@@ -428,7 +428,7 @@ def run_engine(args):
 
 # ----------------------------------------------------------------- batched / served
 
-def batched_section(ih, ctx, dev, n_frames=64, runs=5):
+def batched_section(ih, dev, n_frames=64, runs=5):
     """64 uneven FMV frames (sizes drawn from {640x480, 1280x720, 1920x1080,
     4096x2160}) with intensity moments and 4,096 weighted windows each: one
     batched launch per kernel replayed from a CUDA graph with autotuned tile
@@ -465,6 +465,7 @@ def batched_section(ih, ctx, dev, n_frames=64, runs=5):
             ts.append(ev[0].elapsed_time(ev[1]))
         return float(np.median(ts))
 
+    ctx = ih.ih_create(dev.index or 0)
     batch, handles = ih.ih_batch_create(ctx, frames, windows=wins, window_counts=[nw] * n_frames,
                                         weighted_out=w_out, batch_flags=ih.IH_BATCH_GRAPH | ih.IH_BATCH_AUTOTUNE)
     timed(lambda: ih.ih_batch_run(ctx, batch), 2)
@@ -487,6 +488,7 @@ def batched_section(ih, ctx, dev, n_frames=64, runs=5):
     ms_p = timed(per_frame, max(2, runs // 2))
     launches_p = (ih.ih_launch_count(ctx) - l0) // max(2, runs // 2)
     ih.ih_sync(ctx)
+    ih.ih_destroy(ctx)
     cells = px * 91
     gbytes = px * (91 * 4 + 16 * 32) / 1e9
     return {"workload": "%d uneven FMV frames (%s), 91 bins + intensity moments, %d weighted windows each"
