@@ -22,7 +22,7 @@
  *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
  *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
  *
- * Readings where the thesis is silent (listed with reasons in the design doc):
+ * Readings where the thesis is silent:
  *   - uniform binning of 8-bit values into B bins over [0,256):
  *     Q(v) = floor(v*B/256); "index" channels carry the bin itself and a
  *     value >= B belongs to no bin;
