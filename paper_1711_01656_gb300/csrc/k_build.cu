@@ -6,10 +6,10 @@
 // columns and three kernels remove the serial dependence (ih_internal.cuh):
 //
 // k_tile_sums  one CTA per (tile, window of <= 16 bins of one channel).  It
-//   stages the tile's bins in shared memory as bytes, then one thread per
-//   column walks down the band and one thread per row walks along the strip,
-//   accumulating run lengths in registers and flushing them to per-thread
-//   shared counters: no atomics.  For the weighted channel it also sums the
+//   stages the tile's bins in shared memory as bytes, then each thread walks
+//   32-pixel pieces of columns (down the band) and of rows (along the strip),
+//   accumulating run lengths in registers and flushing each run to shared
+//   counters with one atomic add.  For the weighted channel it also sums the
 //   offsets (r-R0), (r-R0)^2 per column and (c-C0), (c-C0)^2 per row, which
 //   are small enough for int32; the carry scan rebuilds the global int64
 //   moment carries from them.
@@ -77,15 +77,17 @@ __device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int c
 
 // ------------------------------------------------------------- tile sums
 
-constexpr int kSumThreads = 128;
+constexpr int kSumThreads = 256;
+constexpr int kWalk = 32;  // pixels one thread walks per item
 
-struct SumsSmem {
-    static constexpr size_t q = (size_t)kMaxBandRows * kQStride;
-    static constexpr size_t col = (size_t)kWindowBins * kSumCols * 4;
-    static constexpr size_t row = (size_t)kWindowBins * kMaxBandRows * 4;
-    static constexpr size_t count_bytes = q + col + row;
-    static constexpr size_t weighted_bytes = q + 3 * col + 3 * row;
-};
+// Dynamic shared memory of k_tile_sums for bands of up to R rows: the staged
+// byte tile, the column counters of one pass and the row counters of the
+// strip (and the offset sums of both for the weighted channel).
+__host__ __device__ constexpr size_t sums_q_bytes(int R) { return ((size_t)R * kQStride + 15) & ~size_t(15); }
+__host__ __device__ constexpr size_t sums_smem_bytes(int R, bool weighted)
+{
+    return sums_q_bytes(R) + (weighted ? 3 : 1) * ((size_t)kWindowBins * kSumCols * 4 + (size_t)kWindowBins * R * 4);
+}
 
 // Bins of 4 pixels packed in a word, as window-local bytes (0xFF: none).
 __device__ __forceinline__ uint32_t window_bins4(uint32_t px, const ChanDev &ch, int b_lo, int nbw, int valid)
@@ -99,13 +101,90 @@ __device__ __forceinline__ uint32_t window_bins4(uint32_t px, const ChanDev &ch,
     return out;
 }
 
+// Run-length walks over the staged byte tile.  Each item covers kWalk
+// pixels of one column (down the band) or of one row (along the pass); a run
+// of equal bins is flushed with one shared-memory atomic, so the counters of
+// a column or row shared by several items add up exactly.
+template <bool WT>
+__device__ __forceinline__ void walk_column(const uint8_t *qt, int t, int rlo, int rhi, int32_t *cnt, int32_t *su,
+                                            int32_t *suu)
+{
+    int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
+    for (int rr = rlo; rr < rhi; ++rr) {
+        const int q = qt[rr * kQStride + t];
+        if (q != cur) {
+            if (cur != 0xFF) {
+                atomicAdd(cnt + cur * kSumCols + t, n);
+                if (WT) {
+                    atomicAdd(su + cur * kSumCols + t, s1);
+                    atomicAdd(suu + cur * kSumCols + t, s2);
+                }
+            }
+            cur = q;
+            n = s1 = s2 = 0;
+        }
+        ++n;
+        if (WT) {
+            s1 += rr;
+            s2 += rr * rr;
+        }
+    }
+    if (cur != 0xFF) {
+        atomicAdd(cnt + cur * kSumCols + t, n);
+        if (WT) {
+            atomicAdd(su + cur * kSumCols + t, s1);
+            atomicAdd(suu + cur * kSumCols + t, s2);
+        }
+    }
+}
+
+template <bool WT>
+__device__ __forceinline__ void walk_row(const uint8_t *qt, int t, int clo, int chi, int u0, int R, int32_t *cnt,
+                                         int32_t *sv, int32_t *svv)
+{
+    int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
+    const uint32_t *rowq = reinterpret_cast<const uint32_t *>(qt + t * kQStride);
+    for (int c4 = clo; c4 < chi; c4 += 4) {
+        const uint32_t w4 = rowq[c4 >> 2];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int q = (w4 >> (8 * e)) & 0xff;
+            if (q != cur) {
+                if (cur != 0xFF) {
+                    atomicAdd(cnt + cur * R + t, n);
+                    if (WT) {
+                        atomicAdd(sv + cur * R + t, s1);
+                        atomicAdd(svv + cur * R + t, s2);
+                    }
+                }
+                cur = q;
+                n = s1 = s2 = 0;
+            }
+            ++n;
+            if (WT) {
+                const int u = u0 + c4 + e;
+                s1 += u;
+                s2 += u * u;
+            }
+        }
+    }
+    if (cur != 0xFF) {
+        atomicAdd(cnt + cur * R + t, n);
+        if (WT) {
+            atomicAdd(sv + cur * R + t, s1);
+            atomicAdd(svv + cur * R + t, s2);
+        }
+    }
+}
+
 template <bool WT>
 __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i, int widx)
 {
     const TileGrid &g = ps.g;
     const GroupDev wd = ps.win[widx];
     const ChanDev &ch = ps.chan[wd.chan];
-    const int R0 = i * g.R, nr = min(g.R, g.H - R0);
+    const int R = g.R;
+    const int R0 = i * R, nr = min(R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
     const int nbw = wd.nb;
     const int64_t bglob = ch.bin_off + wd.b_lo;
@@ -115,20 +194,21 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
 
     extern __shared__ __align__(16) unsigned char sm[];
     uint8_t *qt = sm;
-    int32_t *col_cnt = reinterpret_cast<int32_t *>(sm + SumsSmem::q);  // [16][kSumCols]
-    int32_t *row_cnt = col_cnt + kWindowBins * kSumCols;              // [16][kMaxBandRows]
-    int32_t *col_su = row_cnt + kWindowBins * kMaxBandRows;
+    int32_t *col_cnt = reinterpret_cast<int32_t *>(sm + sums_q_bytes(R));  // [16][kSumCols]
+    int32_t *row_cnt = col_cnt + kWindowBins * kSumCols;                   // [16][R]
+    int32_t *col_su = row_cnt + kWindowBins * R;
     int32_t *col_suu = col_su + kWindowBins * kSumCols;
     int32_t *row_sv = col_suu + kWindowBins * kSumCols;
-    int32_t *row_svv = row_sv + kWindowBins * kMaxBandRows;
+    int32_t *row_svv = row_sv + kWindowBins * R;
 
-    for (int k = tid; k < kWindowBins * kMaxBandRows; k += kSumThreads) {
+    for (int k = tid; k < kWindowBins * R; k += kSumThreads) {
         row_cnt[k] = 0;
         if (WT) {
             row_sv[k] = 0;
             row_svv[k] = 0;
         }
     }
+    const int rsegs = (nr + kWalk - 1) / kWalk;
     for (int cp = C0; cp < C1; cp += kSumCols) {
         const int cw = min(kSumCols, C1 - cp);
         for (int k = tid; k < kWindowBins * kSumCols; k += kSumThreads) {
@@ -171,71 +251,19 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
             }
         }
         __syncthreads();
-        // one thread per column: counts (and offset sums) down the band
-        for (int t = tid; t < cw; t += kSumThreads) {
-            int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
-            for (int rr = 0; rr < nr; ++rr) {
-                const int q = qt[rr * kQStride + t];
-                if (q != cur) {
-                    if (cur != 0xFF) {
-                        col_cnt[cur * kSumCols + t] += n;
-                        if (WT) {
-                            col_su[cur * kSumCols + t] += s1;
-                            col_suu[cur * kSumCols + t] += s2;
-                        }
-                    }
-                    cur = q;
-                    n = s1 = s2 = 0;
-                }
-                ++n;
-                if (WT) {
-                    s1 += rr;
-                    s2 += rr * rr;
-                }
-            }
-            if (cur != 0xFF) {
-                col_cnt[cur * kSumCols + t] += n;
-                if (WT) {
-                    col_su[cur * kSumCols + t] += s1;
-                    col_suu[cur * kSumCols + t] += s2;
-                }
-            }
-        }
-        // one thread per row: counts (and offset sums) along this pass
-        for (int t = tid; t < nr; t += kSumThreads) {
-            int cur = 0xFF, n = 0, s1 = 0, s2 = 0;
-            const int u0 = cp - C0;
-            const uint32_t *rowq = reinterpret_cast<const uint32_t *>(qt + t * kQStride);
-            for (int c4 = 0; c4 < cw; c4 += 4) {
-                const uint32_t w4 = rowq[c4 >> 2];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const int q = (w4 >> (8 * e)) & 0xff;
-                    if (q != cur) {
-                        if (cur != 0xFF) {
-                            row_cnt[cur * kMaxBandRows + t] += n;
-                            if (WT) {
-                                row_sv[cur * kMaxBandRows + t] += s1;
-                                row_svv[cur * kMaxBandRows + t] += s2;
-                            }
-                        }
-                        cur = q;
-                        n = s1 = s2 = 0;
-                    }
-                    ++n;
-                    if (WT) {
-                        const int u = u0 + c4 + e;
-                        s1 += u;
-                        s2 += u * u;
-                    }
-                }
-            }
-            if (cur != 0xFF) {
-                row_cnt[cur * kMaxBandRows + t] += n;
-                if (WT) {
-                    row_sv[cur * kMaxBandRows + t] += s1;
-                    row_svv[cur * kMaxBandRows + t] += s2;
-                }
+        // column items: (row segment, column), consecutive threads take
+        // consecutive columns; row items: (column segment, row), consecutive
+        // threads take consecutive rows (the padded row stride avoids bank
+        // conflicts)
+        const int csegs = (cw + kWalk - 1) / kWalk;
+        const int ncol = rsegs * cw, nrow = csegs * nr;
+        for (int it = tid; it < ncol + nrow; it += kSumThreads) {
+            if (it < ncol) {
+                const int seg = it / cw, t = it - seg * cw;
+                walk_column<WT>(qt, t, seg * kWalk, min(nr, seg * kWalk + kWalk), col_cnt, col_su, col_suu);
+            } else {
+                const int k = it - ncol, seg = k / nr, t = k - seg * nr;
+                walk_row<WT>(qt, t, seg * kWalk, min(cw, seg * kWalk + kWalk), cp - C0, R, row_cnt, row_sv, row_svv);
             }
         }
         __syncthreads();
@@ -254,11 +282,11 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
     }
     for (int k = tid; k < nbw * nr; k += kSumThreads) {
         const int b = k / nr, rr = k % nr;
-        ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = row_cnt[b * kMaxBandRows + rr];
+        ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = row_cnt[b * R + rr];
         if (WT) {
             const int64_t o = ((int64_t)j * Bw + wd.b_lo + b) * g.H + R0 + rr;
-            ps.row_sv[o] = row_sv[b * kMaxBandRows + rr];
-            ps.row_svv[o] = row_svv[b * kMaxBandRows + rr];
+            ps.row_sv[o] = row_sv[b * R + rr];
+            ps.row_svv[o] = row_svv[b * R + rr];
         }
     }
     if (tid < nbw) {
@@ -266,13 +294,13 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
         int32_t n = 0;
         long long su = 0, suu = 0, sv = 0, svv = 0;
         for (int rr = 0; rr < nr; ++rr) {
-            const int32_t x = row_cnt[b * kMaxBandRows + rr];
+            const int32_t x = row_cnt[b * R + rr];
             n += x;
             if (WT) {
                 su += (long long)rr * x;
                 suu += (long long)rr * rr * x;
-                sv += row_sv[b * kMaxBandRows + rr];
-                svv += row_svv[b * kMaxBandRows + rr];
+                sv += row_sv[b * R + rr];
+                svv += row_svv[b * R + rr];
             }
         }
         ps.tilesum[((int64_t)i * g.ns + j) * ps.B + bglob + b] = n;
@@ -731,7 +759,8 @@ __global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
 
 template <bool M32>
 __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, int j, int wb, int lane,
-                                                   int32_t *RLn, long long *RLx, long long *RLxx)
+                                                   int32_t *RLn, long long *RLx, long long *RLxx,
+                                                   long long *stage)
 {
     const TileGrid &g = ps.g;
     const ChanDev &ch = ps.chan[ps.wch];
@@ -847,12 +876,30 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                                 make_uint4((uint32_t)acc[k][0], (uint32_t)acc[k][1], (uint32_t)acc[k][2],
                                            (uint32_t)acc[k][3]);
                     } else {
+                        // through the warp's stage: pair 2*lane+h holds columns
+                        // 4*lane+2h, +1; the two halves are written in an order
+                        // that alternates every 4 lanes (no bank conflicts), and
+                        // each store below writes 512 contiguous bytes
+                        const int h = (lane >> 2) & 1;
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            longlong2 *dst = reinterpret_cast<longlong2 *>(mo + k * plane + o);
-                            dst[0] = make_longlong2(acc[k][0], acc[k][1]);
-                            dst[1] = make_longlong2(acc[k][2], acc[k][3]);
+                            longlong2 *s2 = reinterpret_cast<longlong2 *>(stage + k * kChunk);
+                            const longlong2 lo = make_longlong2(acc[k][0], acc[k][1]);
+                            const longlong2 hi = make_longlong2(acc[k][2], acc[k][3]);
+                            s2[2 * lane + h] = h ? hi : lo;
+                            s2[2 * lane + 1 - h] = h ? lo : hi;
                         }
+                    }
+                }
+                if (!M32) {
+                    __syncwarp();
+                    const int64_t orow = (int64_t)(R0 + rr) * g.P + cc;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const longlong2 *s2 = reinterpret_cast<const longlong2 *>(stage + k * kChunk);
+                        longlong2 *dst = reinterpret_cast<longlong2 *>(mo + k * plane + orow);
+                        if (cc + 2 * lane < g.P) dst[lane] = s2[lane];
+                        if (cc + 64 + 2 * lane < g.P) dst[32 + lane] = s2[32 + lane];
                     }
                 }
                 __syncwarp();
@@ -872,6 +919,7 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant_
 {
     __shared__ int32_t sRLn[4][kMaxBandRows];
     __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
+    __shared__ __align__(16) long long sStage[4][4 * kChunk];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
     const int Bw = ps.chan[ps.wch].bins;
@@ -879,15 +927,16 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant_
     if (unit >= (int64_t)g.nb * g.ns * Bw) return;
     const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
     if (ps.mom32)
-        tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+        tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
     else
-        tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+        tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
 }
 
 __global__ void __launch_bounds__(128, 4) k_tiles_moments_b(const BatchDev bd)
 {
     __shared__ int32_t sRLn[4][kMaxBandRows];
     __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
+    __shared__ __align__(16) long long sStage[4][4 * kChunk];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
     if (unit >= bd.pre_mom[bd.n]) return;
@@ -897,9 +946,9 @@ __global__ void __launch_bounds__(128, 4) k_tiles_moments_b(const BatchDev bd)
     const int64_t local = unit - bd.pre_mom[f];
     const int tile = (int)(local / Bw), wb = (int)(local % Bw);
     if (ps.mom32)
-        tiles_moments_unit<true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+        tiles_moments_unit<true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
     else
-        tiles_moments_unit<false>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid]);
+        tiles_moments_unit<false>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
 }
 
 template <typename F>
@@ -965,10 +1014,10 @@ void prepare_kernels()
 {
     static bool attrs = false;
     if (!attrs) {
-        set_max_smem(k_tile_sums<false>, SumsSmem::count_bytes);
-        set_max_smem(k_tile_sums<true>, SumsSmem::weighted_bytes);
-        set_max_smem(k_tile_sums_b<false>, SumsSmem::count_bytes);
-        set_max_smem(k_tile_sums_b<true>, SumsSmem::weighted_bytes);
+        set_max_smem(k_tile_sums<false>, sums_smem_bytes(kMaxBandRows, false));
+        set_max_smem(k_tile_sums<true>, sums_smem_bytes(kMaxBandRows, true));
+        set_max_smem(k_tile_sums_b<false>, sums_smem_bytes(kMaxBandRows, false));
+        set_max_smem(k_tile_sums_b<true>, sums_smem_bytes(kMaxBandRows, true));
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -982,13 +1031,13 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
     int n = 0;
     if (totals[0]) {
         prof_mark(prof, KID_SUMS_COUNT, 0, st);
-        k_tile_sums_b<false><<<(unsigned)totals[0], kSumThreads, SumsSmem::count_bytes, st>>>(bd);
+        k_tile_sums_b<false><<<(unsigned)totals[0], kSumThreads, sums_smem_bytes(kMaxBandRows, false), st>>>(bd);
         prof_mark(prof, KID_SUMS_COUNT, 1, st);
         ++n;
     }
     if (totals[1]) {
         prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-        k_tile_sums_b<true><<<(unsigned)totals[1], kSumThreads, SumsSmem::weighted_bytes, st>>>(bd);
+        k_tile_sums_b<true><<<(unsigned)totals[1], kSumThreads, sums_smem_bytes(kMaxBandRows, true), st>>>(bd);
         prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
         ++n;
     }
@@ -1034,13 +1083,13 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         const int nw_count = ps.nwin_count, nw_weighted = ps.nwin - ps.nwin_count;
         if (nw_count) {
             prof_mark(prof, KID_SUMS_COUNT, 0, st);
-            k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), kSumThreads, SumsSmem::count_bytes, st>>>(ps, 0);
+            k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), kSumThreads, sums_smem_bytes(g.R, false), st>>>(ps, 0);
             prof_mark(prof, KID_SUMS_COUNT, 1, st);
             ++n;
         }
         if (nw_weighted) {
             prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-            k_tile_sums<true><<<dim3(g.ns, g.nb, nw_weighted), kSumThreads, SumsSmem::weighted_bytes, st>>>(ps, nw_count);
+            k_tile_sums<true><<<dim3(g.ns, g.nb, nw_weighted), kSumThreads, sums_smem_bytes(g.R, true), st>>>(ps, nw_count);
             prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
             ++n;
         }
