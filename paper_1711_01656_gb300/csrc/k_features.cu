@@ -9,6 +9,12 @@
 // gradient into the upper half plane, theta >= 20j degrees iff the cross
 // product of the unit vector at 20j degrees with (gx, gy) is >= 0, so the bin
 // is the number of the 8 inner boundaries the gradient lies at or beyond.
+// Only the four boundaries of the first quadrant are tested: with
+// theta' = atan2(gy, |gx|) in [0, 90] and n the number of j = 1..4 with
+// theta' >= 20j, the bin is n for gx >= 0 and 8 - n for gx < 0 (theta =
+// 180 - theta' lies at or beyond 20j for all j <= 4 and for j = 9 - m,
+// m = 1..4, exactly when theta' <= 20m; no integer gradient other than 0
+// lies on a boundary, so "<=" and "<" agree).
 // The unit vectors are scaled by 2^22 and rounded; for integer gradients in
 // [-255,255]^2 the angle to the nearest boundary is > 1e-5 rad, so the sign
 // of the cross product is exact: the rounding of the constants moves it by
@@ -34,9 +40,9 @@ constexpr int kSR = kTR + 2 * kHalo;  // staged rows
 constexpr int kSW = kTC / 4 + 2;      // staged words per row (one halo word each side)
 constexpr int kThreads = 256;
 
-// round(2^22 cos(20j deg)), round(2^22 sin(20j deg)), j = 1..8
-__constant__ int kUx[8] = {3941357, 3213023, 2097152, 728333, -728333, -2097152, -3213023, -3941357};
-__constant__ int kUy[8] = {1434536, 2696047, 3632374, 4130583, 4130583, 3632374, 2696047, 1434536};
+// round(2^22 cos(20j deg)), round(2^22 sin(20j deg)), j = 1..4
+__constant__ int kUx[4] = {3941357, 3213023, 2097152, 728333};
+__constant__ int kUy[4] = {1434536, 2696047, 3632374, 4130583};
 
 __device__ __forceinline__ int orientation_bin9(int gx, int gy)
 {
@@ -45,10 +51,11 @@ __device__ __forceinline__ int orientation_bin9(int gx, int gy)
         gy = -gy;
     }
     if ((gx | gy) == 0) return 0;
-    int b = 0;
+    const int ax = gx < 0 ? -gx : gx;
+    int n = 0;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) b += (kUx[k] * gy - kUy[k] * gx >= 0) ? 1 : 0;
-    return b;
+    for (int k = 0; k < 4; ++k) n += (kUx[k] * gy - kUy[k] * ax >= 0) ? 1 : 0;
+    return gx < 0 ? 8 - n : n;
 }
 
 __device__ __forceinline__ int byte_of(uint32_t w, int j) { return (int)((w >> (8 * j)) & 0xff); }
