@@ -34,6 +34,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "integral-hist cells/s & % HBM peak; batched/served vs per-frame, same GB300"
 UNIT = "cells/s"
+# --layout: (ih_layout value, description for the JSON line)
+LAYOUTS = {
+    "record": (2, "record (bins innermost; per-pixel records of up to 16 words in planes)"),
+    "slab": (1, "slab (bins innermost, groups of <= 8 bins of one channel)"),
+    "bin-major": (0, "bin-major (b x h x pitch, Fig. 5.1)"),
+}
 H, W = 1080, 1920
 N_RECTS = 100_000
 N_WINDOWS = 4096
@@ -305,7 +311,7 @@ def run_engine(args):
 
     def step(pix):
         h, = ih.ih_build(ctx, ih.Frame(pix, chans, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
-                                       layout=ih.IH_LAYOUT_SLAB))
+                                       layout=LAYOUTS[args.layout][0]))
         ih.ih_query_rects(ctx, h, d_rects, out_r)
         ih.ih_query_weighted(ctx, h, d_wins, out_w)
         ih.ih_release(ctx, h)
@@ -391,9 +397,9 @@ def run_engine(args):
 
     batched = served = None
     if not args.no_batched:
-        batched = batched_section(ih, dev)
+        batched = batched_section(ih, dev, LAYOUTS[args.layout][0])
     if not args.no_served:
-        served = served_section(ih, dev)
+        served = served_section(ih, dev, LAYOUTS[args.layout][0])
 
     line = None
     if rank == 0:
@@ -408,7 +414,7 @@ def run_engine(args):
             "config": {"workload": WORKLOAD, "global_batch": world, "frames_per_gpu": 1,
                        "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": "replicas: one frame per GPU, no collective",
-                       "layout": "slab (bins innermost, groups of <= 8 bins)"},
+                       "layout": LAYOUTS[args.layout][1]},
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(h_rgb.numel() + h_rects.numel() * 4 + h_wins.numel() * 4),
@@ -428,7 +434,7 @@ def run_engine(args):
 
 # ----------------------------------------------------------------- batched / served
 
-def batched_section(ih, dev, n_frames=64, runs=5):
+def batched_section(ih, dev, layout, n_frames=64, runs=5):
     """64 uneven FMV frames (sizes drawn from {640x480, 1280x720, 1920x1080,
     4096x2160}) with intensity moments and 4,096 weighted windows each: one
     batched launch per kernel replayed from a CUDA graph with autotuned tile
@@ -448,7 +454,7 @@ def batched_section(ih, dev, n_frames=64, runs=5):
     base = {s: synth.blob_rgb(s[0], s[1], 1000 + s[0]) for s in set(sizes)}
     pix = [torch.from_numpy(np.roll(base[s], 37 * k, axis=2)).to(dev) for k, s in enumerate(sizes)]
     frames = [ih.Frame(p, synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
-                       layout=ih.IH_LAYOUT_SLAB) for p in pix]
+                       layout=layout) for p in pix]
     nw = 4096
     wins = torch.from_numpy(np.concatenate([synth.rects_side_range(h, w, nw, 32, 256, 77 + k)
                                             for k, (h, w) in enumerate(sizes)])).to(dev)
@@ -500,7 +506,7 @@ def batched_section(ih, dev, n_frames=64, runs=5):
             "launches_per_batch": int(launches_b), "launches_per_frame_loop": int(launches_p)}
 
 
-def served_section(ih, dev, seconds=2.0, trackers=16, fps=30.0, budget_gb=60):
+def served_section(ih, dev, layout, seconds=2.0, trackers=16, fps=30.0, budget_gb=60):
     """16 tracker streams with Poisson frame arrivals (30 fps each); frames
     drawn from the batched workload's sizes (FMV, 91 bins + intensity int64
     moments) and, with probability 1/16, 8192x8192 WAMI frames (32 bins,
@@ -528,11 +534,11 @@ def served_section(ih, dev, seconds=2.0, trackers=16, fps=30.0, budget_gb=60):
 
     def frame_of(i):
         if kind[i] == 4:
-            return ih.Frame(wami, [(32, 0)], weighted_channel=0, layout=ih.IH_LAYOUT_SLAB, moment_bits=32), 32, 32, \
+            return ih.Frame(wami, [(32, 0)], weighted_channel=0, layout=layout, moment_bits=32), 32, 32, \
                 8192 * 8192
         s = sizes[kind[i]]
         return ih.Frame(fmv[s][i % 2], synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
-                        layout=ih.IH_LAYOUT_SLAB), 91, 16, s[0] * s[1]
+                        layout=layout), 91, 16, s[0] * s[1]
 
     def serve(streams, inflight, batch):
         ctx = ih.ih_create(dev.index or 0, hbm_budget_bytes=int(budget_gb * 1e9))
@@ -584,6 +590,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-frame batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the serving-loop comparison")
+    ap.add_argument("--layout", choices=sorted(LAYOUTS), default="slab", help="count-tensor layout")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
         ap.error("--warmup must be >= 3")

@@ -87,7 +87,15 @@ typedef enum {
      * ceil(B_c/8) groups of near-equal size (floor/ceil of B_c/groups), and
      * each group g of nb_g bins is stored as h x pitch x nb_g; a rectangle
      * query then reads each corner's bins from a few contiguous words */
-    IH_LAYOUT_SLAB = 1
+    IH_LAYOUT_SLAB = 1,
+    /* per-pixel records: the bin order (channel after channel) is cut into
+     * groups of up to 8 consecutive bins drawn from at most two channels
+     * (a new group starts where a third channel would begin); each group
+     * takes 8 words (one 32-byte sector), its padding words holding 0, and
+     * pairs of consecutive groups share a plane (the last group may be
+     * alone).  Plane p is stored as h x pitch x w_p, w_p = 16 or 8.  A
+     * rectangle query reads each corner from one 64-byte record per plane. */
+    IH_LAYOUT_RECORD = 2
 } ih_layout;
 
 typedef struct {

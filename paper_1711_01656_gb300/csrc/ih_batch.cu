@@ -316,7 +316,7 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
         rout += nr * fr.B;
         woff += nw;
         wout += nw * fr.Bw;
-        pre_r[k + 1] = pre_r[k] + nr * sets[k].ngroups;
+        pre_r[k + 1] = pre_r[k] + nr * rect_items(fr.view);
         pre_w[k + 1] = pre_w[k] + nw * fr.Bw;
     }
     b->q_rects = pre_r[n];

@@ -94,7 +94,8 @@ ih_status validate(ih_ctx *ctx, const ih_frame &f)
         return fail(ctx, IH_EINVAL, "input kind %d", f.input);
     if (f.input == IH_INPUT_RGB_FEATURES && f.channels != 7)
         return fail(ctx, IH_EINVAL, "IH_INPUT_RGB_FEATURES needs 7 channels");
-    if (f.layout != IH_LAYOUT_BIN_MAJOR && f.layout != IH_LAYOUT_SLAB) return fail(ctx, IH_EINVAL, "layout %d", f.layout);
+    if (f.layout != IH_LAYOUT_BIN_MAJOR && f.layout != IH_LAYOUT_SLAB && f.layout != IH_LAYOUT_RECORD)
+        return fail(ctx, IH_EINVAL, "layout %d", f.layout);
     for (int c = 0; c < f.channels; ++c) {
         if (f.chan[c].bins < 1 || f.chan[c].bins > 256)
             return fail(ctx, IH_EINVAL, "channel %d bins = %d (1..256)", c, f.chan[c].bins);
@@ -104,6 +105,14 @@ ih_status validate(ih_ctx *ctx, const ih_frame &f)
     int total = 0;
     for (int c = 0; c < f.channels; ++c) total += f.chan[c].bins;
     if (total > kMaxBins) return fail(ctx, IH_EINVAL, "%d bins in one frame (at most %d)", total, kMaxBins);
+    if (f.layout == IH_LAYOUT_RECORD) {
+        int bins[kMaxChannels], np = 0, words = 0;
+        GroupDev sp[kMaxGroups];
+        int16_t rw[kMaxGroups];
+        for (int c = 0; c < f.channels; ++c) bins[c] = f.chan[c].bins;
+        if (record_plan(bins, f.channels, sp, kMaxGroups, rw, &np, &words) < 0 || words > kMaxBins)
+            return fail(ctx, IH_EINVAL, "IH_LAYOUT_RECORD: the channels need more than %d bin groups", kMaxGroups);
+    }
     if (f.moment_bits != 0 && f.moment_bits != 32 && f.moment_bits != 64)
         return fail(ctx, IH_EINVAL, "moment_bits = %d (0, 32 or 64)", f.moment_bits);
     if (f.weighted_channel < -1 || f.weighted_channel >= f.channels)
@@ -120,29 +129,96 @@ int make_groups(const int *bins, int nchan, int cap, GroupDev *out, int max_out)
         for (int g = 0; g < ng; ++g) {
             if (n >= max_out) return -1;
             const int lo = bins[c] * g / ng, hi = bins[c] * (g + 1) / ng;
+            out[n] = GroupDev{};
             out[n].chan = (int16_t)c;
             out[n].b_lo = (int16_t)lo;
             out[n].nb = (int16_t)(hi - lo);
-            out[n].pad = 0;
             ++n;
         }
     }
     return n;
 }
 
-// Count groups ordered by size (one tiles launch per size); tile-sums
-// windows with the weighted channel's windows last.
+// LAYOUT_RECORD: the bin order (channel after channel) is cut into groups
+// of up to 8 consecutive bins drawn from at most two channels; each group
+// takes 8 words (one 32-byte sector) of the pixel record, its padding words
+// holding 0, and consecutive groups share a plane while the plane's record
+// stays within 16 words.  sp[] receives the groups with their plane and word
+// offset, rec_w[] the record width of each plane.  Returns the number of
+// groups, or -1 if there are more than max_sp.
+int record_plan(const int *bins, int nchan, GroupDev *sp, int max_sp, int16_t *rec_w, int *nplanes, int *words)
+{
+    int n = 0;
+    GroupDev *cur = nullptr;
+    for (int c = 0; c < nchan; ++c) {
+        int b = 0;
+        while (b < bins[c]) {
+            const int used = cur ? cur->nb + cur->nb1 : kGroupBins;
+            const bool two = cur && cur->nb1 > 0;
+            if (!cur || used == kGroupBins || two) {
+                if (n >= max_sp) return -1;
+                cur = &sp[n++];
+                *cur = GroupDev{};
+                cur->chan = (int16_t)c;
+                cur->b_lo = (int16_t)b;
+            } else if (cur->chan != c) {
+                cur->chan1 = (int16_t)c;  // the group continues with channel c
+                cur->b_lo1 = (int16_t)b;
+            }
+            const int take = std::min(kGroupBins - (cur->nb + cur->nb1), bins[c] - b);
+            if (cur->chan == c)
+                cur->nb = (int16_t)(cur->nb + take);
+            else
+                cur->nb1 = (int16_t)(cur->nb1 + take);
+            b += take;
+        }
+    }
+    int p = 0, w = 0, total = 0;
+    for (int k = 0; k < n; ++k) {
+        const int wk = kGroupBins;
+        if (w + wk > 2 * kGroupBins) {
+            rec_w[p++] = (int16_t)w;
+            total += w;
+            w = 0;
+        }
+        sp[k].plane = (int16_t)p;
+        sp[k].off = (int16_t)w;
+        w += wk;
+    }
+    rec_w[p] = (int16_t)w;
+    *nplanes = n ? p + 1 : 0;
+    *words = total + w;
+    return n;
+}
+
+// Count groups ordered by size (one tiles launch per size), except in
+// LAYOUT_RECORD (record_plan's order); tile-sums windows with the weighted
+// channel's windows last.
 bool plan_groups(PlaneSet &ps)
 {
     int bins[kMaxChannels];
     for (int c = 0; c < ps.nchan; ++c) bins[c] = ps.chan[c].bins;
     GroupDev tmp[kMaxGroups];
-    const int ng = make_groups(bins, ps.nchan, kGroupBins, tmp, kMaxGroups);
-    if (ng < 0) return false;
     int n = 0;
-    for (int size = kGroupBins; size >= 1; --size)
-        for (int k = 0; k < ng; ++k)
-            if (tmp[k].nb == size) ps.grp[n++] = tmp[k];
+    if (ps.layout == LAYOUT_RECORD) {
+        int words = 0;
+        n = record_plan(bins, ps.nchan, ps.grp, kMaxGroups, ps.rec_w, &ps.nplanes, &words);
+        if (n < 0) return false;
+        ps.seg2 = 0;
+        for (int k = 0; k < n; ++k) ps.seg2 |= ps.grp[k].nb1 > 0;
+    } else {
+        const int ng = make_groups(bins, ps.nchan, kGroupBins, tmp, kMaxGroups);
+        if (ng < 0) return false;
+        for (int size = kGroupBins; size >= 1; --size)
+            for (int k = 0; k < ng; ++k)
+                if (tmp[k].nb == size) {
+                    ps.grp[n] = tmp[k];
+                    ps.grp[n].plane = (int16_t)n;
+                    ps.rec_w[n] = tmp[k].nb;
+                    ++n;
+                }
+        ps.nplanes = n;
+    }
     ps.ngroups = n;
     const int nw = make_groups(bins, ps.nchan, kWindowBins, tmp, kMaxGroups);
     if (nw < 0) return false;
@@ -166,16 +242,29 @@ void make_view(const PlaneSet &ps, const int32_t *d, CountView &v)
     v.W = ps.g.W;
     v.P = ps.g.P;
     v.layout = ps.layout;
-    v.ngroups = ps.ngroups;
+    v.ngroups = ps.nplanes;
+    for (int p = 0; p < ps.nplanes; ++p) {
+        v.group_nb[p] = ps.rec_w[p];
+        v.slab_off[p] = ps.slab_off[p];
+        v.plane_w0[p] = (int16_t)(p ? v.plane_w0[p - 1] + ps.rec_w[p - 1] : 0);
+    }
+    int words = 0;
+    for (int p = 0; p < ps.nplanes; ++p) words += ps.rec_w[p];
+    for (int w = 0; w < words && w < kMaxBins; ++w) v.word_bin[w] = -1;
+    v.nquarters = words / 4;
+    for (int k = 0; k < v.nquarters && k < kMaxBins / 4; ++k) {
+        int p = 0;
+        while (p + 1 < ps.nplanes && v.plane_w0[p + 1] <= 4 * k) ++p;
+        v.quarter_plane[k] = (int16_t)p;
+    }
     for (int k = 0; k < ps.ngroups; ++k) {
         const GroupDev &gr = ps.grp[k];
-        v.group_nb[k] = gr.nb;
-        v.group_bin0[k] = (int16_t)(ps.chan[gr.chan].bin_off + gr.b_lo);
-        v.slab_off[k] = ps.slab_off[k];
-        for (int b = 0; b < gr.nb; ++b) {
-            const int gb = ps.chan[gr.chan].bin_off + gr.b_lo + b;
-            v.bin_group[gb] = (int16_t)k;
-            v.bin_local[gb] = (int16_t)b;
+        const int gb0 = ps.chan[gr.chan].bin_off + gr.b_lo;
+        if (ps.layout != LAYOUT_RECORD) v.group_bin0[gr.plane] = (int16_t)gb0;
+        for (int b = 0; b < gr.nb + gr.nb1; ++b) {
+            v.bin_group[gb0 + b] = gr.plane;
+            v.bin_local[gb0 + b] = (int16_t)(gr.off + b);
+            v.word_bin[v.plane_w0[gr.plane] + gr.off + b] = (int16_t)(gb0 + b);
         }
     }
 }
@@ -196,7 +285,14 @@ void frame_record(const ih_frame &f, FrameRec &fr)
     fr.wch = f.weighted_channel;
     fr.Bw = fr.wch >= 0 ? fr.bins[fr.wch] : 0;
     fr.mbits = f.moment_bits == 32 ? 32 : 64;
-    fr.count_bytes = (int64_t)fr.B * fr.H * fr.P * 4;
+    int words = fr.B;
+    if (f.layout == IH_LAYOUT_RECORD) {
+        GroupDev sp[kMaxGroups];
+        int16_t rw[kMaxGroups];
+        int np = 0;
+        if (record_plan(fr.bins, fr.nchan, sp, kMaxGroups, rw, &np, &words) < 0) words = fr.B;
+    }
+    fr.count_bytes = (int64_t)words * fr.H * fr.P * 4;
     fr.moment_bytes = (int64_t)4 * fr.Bw * fr.H * fr.P * (fr.mbits / 8);
 }
 
@@ -229,9 +325,9 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
                                   : choose_grid(fr.H, fr.W, ps.ngroups, ctx->nsm);
     ps.g.P = fr.P;
     int64_t off = 0;
-    for (int kg = 0; kg < ps.ngroups; ++kg) {
-        ps.slab_off[kg] = off;
-        off += (int64_t)fr.H * fr.P * ps.grp[kg].nb;
+    for (int p = 0; p < ps.nplanes; ++p) {
+        ps.slab_off[p] = off;
+        off += (int64_t)fr.H * fr.P * ps.rec_w[p];
     }
     ps.out = fr.d_ih;
     ps.mom = fr.d_mom;

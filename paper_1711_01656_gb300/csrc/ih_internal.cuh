@@ -38,7 +38,9 @@ constexpr int kSumCols = 128;     // columns per pass of the tile-sums kernel
 // Count-tensor layouts.
 enum Layout {
     LAYOUT_BIN_MAJOR = 0,  // [B][H][P]                (Fig. 5.1)
-    LAYOUT_SLAB = 1        // per bin group g: [H][P][nb_g], bins innermost
+    LAYOUT_SLAB = 1,       // per bin group g: [H][P][nb_g], bins innermost
+    LAYOUT_RECORD = 2      // per plane p: [H][P][rec_w_p]; a plane's record
+                           // holds up to two 8-bin spans of the bin order
 };
 
 // Weight kinds, used by the kernel-id table and the moment planes.
@@ -78,8 +80,17 @@ struct ChanDev {
     int32_t pad;
 };
 
-struct GroupDev {  // bins [b_lo, b_lo + nb) of channel `chan` (channel-local)
+// A bin group: bins [b_lo, b_lo + nb) of channel `chan` (channel-local) and,
+// in LAYOUT_RECORD only, the first nb1 bins [b_lo1, b_lo1 + nb1) of the next
+// channel chan1.  Either way the group's bins are consecutive in the
+// tensor's bin order; bin k of the group (0 <= k < nb + nb1) is field k of
+// the packed one-hot words of the count tiles kernel.  plane / off: the
+// plane holding the group and the word offset of its bins inside the
+// plane's per-pixel record (LAYOUT_SLAB: the group's own plane, offset 0).
+struct GroupDev {
     int16_t chan, b_lo, nb, pad;
+    int16_t chan1, b_lo1, nb1, pad1;
+    int16_t plane, off, pad2, pad3;
 };
 
 struct TileGrid {
@@ -102,7 +113,10 @@ struct PlaneSet {
     int32_t nwin_count;   // the first nwin_count windows are not of channel wch
     GroupDev grp[kMaxGroups];
     GroupDev win[kMaxGroups];
-    int64_t slab_off[kMaxGroups];  // LAYOUT_SLAB: element offset of group g's slab
+    int32_t nplanes;      // LAYOUT_SLAB / LAYOUT_RECORD planes
+    int32_t seg2;         // LAYOUT_RECORD: some group draws on two channels
+    int16_t rec_w[kMaxGroups];     // words per pixel record of each plane
+    int64_t slab_off[kMaxGroups];  // element offset of each plane
     int32_t *out;         // count tensor
     int64_t *mom;         // moment planes [4][Bw][H][P] (w = c, r, c^2, r^2), or null;
                           // uint32 (values mod 2^32) when mom32
@@ -176,12 +190,19 @@ struct CountView {
     const int32_t *d;
     int32_t B, H, W, layout;
     int64_t P;
-    int32_t ngroups;
-    int16_t bin_group[kMaxBins];  // global bin -> group (LAYOUT_SLAB)
-    int16_t bin_local[kMaxBins];  // global bin -> bin inside its group
-    int16_t group_nb[kMaxGroups];
-    int16_t group_bin0[kMaxGroups];  // first global bin of each group
-    int64_t slab_off[kMaxGroups];
+    int32_t ngroups;              // planes (LAYOUT_SLAB, LAYOUT_RECORD)
+    int16_t bin_group[kMaxBins];  // global bin -> plane
+    int16_t bin_local[kMaxBins];  // global bin -> word inside the plane's record
+    int16_t group_nb[kMaxGroups]; // words per record of each plane
+    int16_t group_bin0[kMaxGroups];  // LAYOUT_SLAB: first global bin of each plane
+    int64_t slab_off[kMaxGroups];    // element offset of each plane
+    // LAYOUT_RECORD: the concatenated records of all planes as nquarters
+    // 4-word quarters; quarter k lies in plane quarter_plane[k] at word
+    // 4k - plane_w0[plane]; word w holds global bin word_bin[w] (-1: padding)
+    int32_t nquarters;
+    int16_t plane_w0[kMaxGroups];
+    int16_t quarter_plane[kMaxBins / 4];
+    int16_t word_bin[kMaxBins];
 };
 struct MomentView {
     int32_t bin0;        // first bin of the weighted channel in the count tensor
@@ -191,6 +212,8 @@ struct MomentView {
 };
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out,
                        int *err, cudaStream_t st, const Prof *prof);
+// Work items of one rectangle query (threads per rectangle).
+inline int64_t rect_items(const CountView &v) { return v.layout == LAYOUT_RECORD ? v.nquarters : v.ngroups; }
 // Queries of one frame of a batch (device table).
 struct QueryJob {
     const CountView *v;   // device copy of the frame's view

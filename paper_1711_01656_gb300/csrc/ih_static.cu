@@ -54,10 +54,9 @@ int split_groups(int bins, int cap, GroupDev *out)
 {
     const int ng = (bins + cap - 1) / cap;
     for (int g = 0; g < ng; ++g) {
-        out[g].chan = 0;
+        out[g] = GroupDev{};
         out[g].b_lo = (int16_t)(bins * g / ng);
         out[g].nb = (int16_t)(bins * (g + 1) / ng - bins * g / ng);
-        out[g].pad = 0;
     }
     return ng;
 }

@@ -64,15 +64,20 @@ __device__ __forceinline__ T warp_incl_scan(T x, int lane)
 
 // The 4 pixels (r, c..c+3) of a channel as packed bytes (pixel j in byte j);
 // bytes at or beyond `cend` are 0 and must be masked by the caller.
-__device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int cend, bool vec_ok)
+__device__ __forceinline__ uint32_t load4(const uint8_t *plane, int64_t pitch, int r, int c, int cend, bool vec_ok)
 {
-    const uint8_t *row = ch.plane + (int64_t)r * ch.pitch;
+    const uint8_t *row = plane + (int64_t)r * pitch;
     if (vec_ok && c + 3 < cend) return __ldg(reinterpret_cast<const unsigned int *>(row + c));
     uint32_t v = 0;
 #pragma unroll
     for (int jj = 0; jj < 4; ++jj)
         if (c + jj < cend) v |= (uint32_t)__ldg(row + c + jj) << (8 * jj);
     return v;
+}
+
+__device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int cend, bool vec_ok)
+{
+    return load4(ch.plane, ch.pitch, r, c, cend, vec_ok);
 }
 
 // ------------------------------------------------------------- tile sums
@@ -547,32 +552,79 @@ __device__ __forceinline__ void store_slab_staged(int32_t *seg, int npx, const i
     }
 }
 
+// Record-layout row store through the same per-warp buffer.  Each of the
+// segment's npx pixels owns an NB-word chunk (NB = 8: one whole 32-byte
+// sector, so no sector is shared with another warp) at a stride of rec_w
+// words; unit u = 32m + L of the row is quarter u % (NB/4) of pixel
+// u / (NB/4), so consecutive lanes write consecutive 16-byte pieces of
+// consecutive chunks.
+template <int NB>
+__device__ __forceinline__ void store_record_staged(int32_t *row, int rec_w, int npx, const int (&acc)[NB][4],
+                                                    int4 *stage, int lane)
+{
+    static_assert(NB == 4 || NB == 8, "record chunks are 4 or 8 words");
+    constexpr int S = SlabStage<NB>::S, Q = NB / 4;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        int v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int f = 4 * k + e;  // flat index: pixel f / NB, bin f % NB
+            v[e] = acc[f % NB][f / NB];
+        }
+        stage[lane * S + k] = make_int4(v[0], v[1], v[2], v[3]);
+    }
+    __syncwarp();
+    const int nunits = npx * Q;
+#pragma unroll
+    for (int m = 0; m < NB; ++m) {
+        const int u = 32 * m + lane;
+        if (u < nunits) {
+            const int L = u / NB, k = u % NB;
+            const int px = 4 * L + k / Q, q = k % Q;
+            *reinterpret_cast<int4 *>(row + (int64_t)px * rec_w + 4 * q) = stage[L * S + k];
+        }
+    }
+}
+
 // One warp-unit of the count tiles: tile (i, j), group gi of exactly NB bins.
-template <int LAYOUT, int NB>
+// LAYOUT_RECORD: NB = 8 is the group's width in the record and its
+// nb + nb1 <= NB real bins may come from two channels (SEG2); the padding
+// fields are never hit and hold 0.
+template <int LAYOUT, int NB, bool SEG2>
 __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int j, int gi, int lane,
                                                  int32_t (*RL)[kGroupBins], int4 *stage)
 {
     const TileGrid &g = ps.g;
     const GroupDev gr = ps.grp[gi];
     const ChanDev &ch = ps.chan[gr.chan];
+    const ChanDev &ch1 = ps.chan[SEG2 ? gr.chan1 : gr.chan];
     const int64_t bg0 = ch.bin_off + gr.b_lo;
+    const int nbr = gr.nb + (SEG2 ? gr.nb1 : 0);  // real bins
     const int R0 = i * g.R, nr = min(g.R, g.H - R0);
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
 
     __syncwarp();
     for (int k = lane; k < nr * kGroupBins; k += 32) {
         const int rr = k / kGroupBins, b = k % kGroupBins;
-        RL[rr][b] = (ps.rowsum && b < NB) ? ps.rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] : 0;
+        RL[rr][b] = (ps.rowsum && b < nbr) ? ps.rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] : 0;
     }
     int TR[NB];  // H(R0-1, chunk start - 1) per bin: the tile corner to begin with
 #pragma unroll
     for (int b = 0; b < NB; ++b)
-        TR[b] = ps.corner ? sum_bands_above<int>(i, lane, [&](int ib) {
+        TR[b] = (ps.corner && b < nbr) ? sum_bands_above<int>(i, lane, [&](int ib) {
             return ps.corner[((int64_t)ib * g.ns + j) * ps.B + bg0 + b];
         }) : 0;
     __syncwarp();
 
-    const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
+    // the channels' descriptors in registers for the row loop
+    const uint8_t *const pl0 = ch.plane, *const pl1 = ch1.plane;
+    const int64_t pt0 = ch.pitch, pt1 = ch1.pitch;
+    const int bins0 = ch.bins, mode0 = ch.mode, bins1 = ch1.bins, mode1 = ch1.mode;
+    const int blo0 = gr.b_lo, nb0 = gr.nb, blo1 = gr.b_lo1, nbs1 = gr.nb1;
+    const bool vec_ok = ((pt0 & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl0) & 3) == 0);
+    const bool vec_ok1 = ((pt1 & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl1) & 3) == 0);
     for (int cc = C0; cc < C1; cc += kChunk) {
         const int c = cc + lane * 4;
         const int nvalid = max(0, min(4, C1 - c));
@@ -581,7 +633,7 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
             int p[4] = {0, 0, 0, 0};
-            if (ps.colsum) {
+            if (ps.colsum && b < nbr) {
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj)
                     if (jj < nvalid) p[jj] = ps.colsum[((int64_t)i * ps.B + bg0 + b) * g.W + c + jj];
@@ -595,9 +647,12 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
             for (int jj = 0; jj < 4; ++jj) acc[b][jj] = p[jj] + base;
             TR[b] += __shfl_sync(kFull, incl, 31);
         }
-        uint32_t pf[4];
+        uint32_t pf[4], pg[4];  // pixel words 4 rows ahead (pg: the second segment's channel)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) pf[k] = (k < nr) ? load4(ch, R0 + k, c, C1, vec_ok) : 0u;
+        for (int k = 0; k < 4; ++k) {
+            pf[k] = (k < nr) ? load4(pl0, pt0, R0 + k, c, C1, vec_ok) : 0u;
+            pg[k] = (SEG2 && k < nr) ? load4(pl1, pt1, R0 + k, c, C1, vec_ok1) : 0u;
+        }
         for (int rr0 = 0; rr0 < nr; rr0 += 4) {
             // two rows at a time: their shuffle scans are independent
 #pragma unroll
@@ -606,20 +661,40 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                 if (ra >= nr) break;  // warp-uniform
                 const bool hasb = rb < nr;
                 const uint32_t pxa = pf[2 * h], pxb = pf[2 * h + 1];
-                if (ra + 4 < nr) pf[2 * h] = load4(ch, R0 + ra + 4, c, C1, vec_ok);
-                if (rb + 4 < nr) pf[2 * h + 1] = load4(ch, R0 + rb + 4, c, C1, vec_ok);
+                const uint32_t pya = pg[2 * h], pyb = pg[2 * h + 1];
+                if (ra + 4 < nr) pf[2 * h] = load4(pl0, pt0, R0 + ra + 4, c, C1, vec_ok);
+                if (rb + 4 < nr) pf[2 * h + 1] = load4(pl0, pt0, R0 + rb + 4, c, C1, vec_ok);
+                if (SEG2 && ra + 4 < nr) pg[2 * h] = load4(pl1, pt1, R0 + ra + 4, c, C1, vec_ok1);
+                if (SEG2 && rb + 4 < nr) pg[2 * h + 1] = load4(pl1, pt1, R0 + rb + 4, c, C1, vec_ok1);
                 // packed one-hot of each row's 4 pixels and its in-lane prefix
                 uint32_t Pa0[4], Pa1[4], Pb0[4], Pb1[4];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const int qa = bin_of((pxa >> (8 * jj)) & 0xff, ch.bins, ch.mode);
-                    const int qb = bin_of((pxb >> (8 * jj)) & 0xff, ch.bins, ch.mode);
-                    const unsigned da = (jj < nvalid && qa >= 0) ? (unsigned)(qa - gr.b_lo) : 0xFFFFFFFFu;
-                    const unsigned db = (jj < nvalid && qb >= 0 && hasb) ? (unsigned)(qb - gr.b_lo) : 0xFFFFFFFFu;
-                    Pa0[jj] = (jj ? Pa0[jj - 1] : 0u) + (da < 4u ? (1u << (da << 3)) : 0u);
-                    Pa1[jj] = (jj ? Pa1[jj - 1] : 0u) + ((da - 4u) < 4u ? (1u << ((da - 4u) << 3)) : 0u);
-                    Pb0[jj] = (jj ? Pb0[jj - 1] : 0u) + (db < 4u ? (1u << (db << 3)) : 0u);
-                    Pb1[jj] = (jj ? Pb1[jj - 1] : 0u) + ((db - 4u) < 4u ? (1u << ((db - 4u) << 3)) : 0u);
+                    const int qa = bin_of((pxa >> (8 * jj)) & 0xff, bins0, mode0);
+                    const int qb = bin_of((pxb >> (8 * jj)) & 0xff, bins0, mode0);
+                    unsigned da = (jj < nvalid && qa >= 0) ? (unsigned)(qa - blo0) : 0xFFFFFFFFu;
+                    unsigned db = (jj < nvalid && qb >= 0 && hasb) ? (unsigned)(qb - blo0) : 0xFFFFFFFFu;
+                    uint32_t ea0 = 0u, ea1 = 0u, eb0 = 0u, eb1 = 0u;
+                    if (SEG2) {
+                        // a bin of the first channel beyond the group is
+                        // dropped; the second channel's bins follow at field nb
+                        if (da >= (unsigned)nb0) da = 0xFFFFFFFFu;
+                        if (db >= (unsigned)nb0) db = 0xFFFFFFFFu;
+                        const int ya = bin_of((pya >> (8 * jj)) & 0xff, bins1, mode1);
+                        const int yb = bin_of((pyb >> (8 * jj)) & 0xff, bins1, mode1);
+                        unsigned fa = (jj < nvalid && ya >= 0) ? (unsigned)(ya - blo1) : 0xFFFFFFFFu;
+                        unsigned fb = (jj < nvalid && yb >= 0 && hasb) ? (unsigned)(yb - blo1) : 0xFFFFFFFFu;
+                        fa = fa < (unsigned)nbs1 ? fa + nb0 : 0xFFFFFFFFu;
+                        fb = fb < (unsigned)nbs1 ? fb + nb0 : 0xFFFFFFFFu;
+                        ea0 = fa < 4u ? (1u << (fa << 3)) : 0u;
+                        ea1 = (fa - 4u) < 4u ? (1u << ((fa - 4u) << 3)) : 0u;
+                        eb0 = fb < 4u ? (1u << (fb << 3)) : 0u;
+                        eb1 = (fb - 4u) < 4u ? (1u << ((fb - 4u) << 3)) : 0u;
+                    }
+                    Pa0[jj] = (jj ? Pa0[jj - 1] : 0u) + (da < 4u ? (1u << (da << 3)) : 0u) + ea0;
+                    Pa1[jj] = (jj ? Pa1[jj - 1] : 0u) + ((da - 4u) < 4u ? (1u << ((da - 4u) << 3)) : 0u) + ea1;
+                    Pb0[jj] = (jj ? Pb0[jj - 1] : 0u) + (db < 4u ? (1u << (db << 3)) : 0u) + eb0;
+                    Pb1[jj] = (jj ? Pb1[jj - 1] : 0u) + ((db - 4u) < 4u ? (1u << ((db - 4u) << 3)) : 0u) + eb1;
                 }
                 const uint32_t ia0 = warp_incl_scan(Pa0[3], lane);
                 const uint32_t ib0 = warp_incl_scan(Pb0[3], lane);
@@ -641,16 +716,20 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                     for (int b = 0; b < NB; ++b)
                         acc[b][jj] += rla[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
                 }
-                if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                if constexpr (LAYOUT == LAYOUT_BIN_MAJOR) {
                     if (c < g.P) {
 #pragma unroll
                         for (int b = 0; b < NB; ++b)
                             *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + ra) * g.P + c) =
                                 make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
                     }
-                } else {
-                    store_slab_staged<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + ra) * g.P + cc) * NB,
+                } else if constexpr (LAYOUT == LAYOUT_SLAB) {
+                    store_slab_staged<NB>(ps.out + ps.slab_off[gr.plane] + ((int64_t)(R0 + ra) * g.P + cc) * NB,
                                           (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
+                } else {
+                    const int rw = ps.rec_w[gr.plane];
+                    store_record_staged<NB>(ps.out + ps.slab_off[gr.plane] + ((int64_t)(R0 + ra) * g.P + cc) * rw + gr.off,
+                                            rw, (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
                 }
                 // row b
                 if (hasb) {
@@ -661,16 +740,20 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                         for (int b = 0; b < NB; ++b)
                             acc[b][jj] += rlb[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
                     }
-                    if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                    if constexpr (LAYOUT == LAYOUT_BIN_MAJOR) {
                         if (c < g.P) {
 #pragma unroll
                             for (int b = 0; b < NB; ++b)
                                 *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + rb) * g.P + c) =
                                     make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
                         }
-                    } else {
-                        store_slab_staged<NB>(ps.out + ps.slab_off[gi] + ((int64_t)(R0 + rb) * g.P + cc) * NB,
+                    } else if constexpr (LAYOUT == LAYOUT_SLAB) {
+                        store_slab_staged<NB>(ps.out + ps.slab_off[gr.plane] + ((int64_t)(R0 + rb) * g.P + cc) * NB,
                                               (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
+                    } else {
+                        const int rw = ps.rec_w[gr.plane];
+                        store_record_staged<NB>(ps.out + ps.slab_off[gr.plane] + ((int64_t)(R0 + rb) * g.P + cc) * rw + gr.off,
+                                                rw, (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
                     }
                 }
                 // the last lane's inclusive sums are the chunk's row totals
@@ -706,33 +789,47 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
     }
 }
 
-// Unit = group * tiles + tile with the groups sorted by size, so the CTAs
-// dispatched first carry the largest groups and the tail of the grid is made
-// of the cheapest units.
+// LAYOUT_BIN_MAJOR / LAYOUT_SLAB: unit = group * tiles + tile with the
+// groups sorted by size, so the CTAs dispatched first carry the largest
+// groups and the tail of the grid is made of the cheapest units.
+// LAYOUT_RECORD: unit = tile * groups + group, so the groups sharing a
+// plane's records write them at about the same time.
 template <int LAYOUT>
 __device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t unit, int lane,
                                                      int32_t (*RL)[kGroupBins], int4 *stage)
 {
     const int64_t ntiles = (int64_t)ps.g.nb * ps.g.ns;
+    if constexpr (LAYOUT == LAYOUT_RECORD) {
+        const int tile = (int)(unit / ps.ngroups), gi = (int)(unit % ps.ngroups);
+        const int i = tile / ps.g.ns, j = tile % ps.g.ns;
+        // one code path per frame: when some group draws on two channels,
+        // every group runs the two-channel path (an empty second segment
+        // never hits), so an SM never interleaves two large loop bodies
+        if (ps.seg2)
+            tiles_count_unit<LAYOUT_RECORD, kGroupBins, true>(ps, i, j, gi, lane, RL, stage);
+        else
+            tiles_count_unit<LAYOUT_RECORD, kGroupBins, false>(ps, i, j, gi, lane, RL, stage);
+    } else {
     const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
     const int i = tile / ps.g.ns, j = tile % ps.g.ns;
     switch (ps.grp[gi].nb) {
-    case 1: tiles_count_unit<LAYOUT, 1>(ps, i, j, gi, lane, RL, stage); break;
-    case 2: tiles_count_unit<LAYOUT, 2>(ps, i, j, gi, lane, RL, stage); break;
-    case 3: tiles_count_unit<LAYOUT, 3>(ps, i, j, gi, lane, RL, stage); break;
-    case 4: tiles_count_unit<LAYOUT, 4>(ps, i, j, gi, lane, RL, stage); break;
-    case 5: tiles_count_unit<LAYOUT, 5>(ps, i, j, gi, lane, RL, stage); break;
-    case 6: tiles_count_unit<LAYOUT, 6>(ps, i, j, gi, lane, RL, stage); break;
-    case 7: tiles_count_unit<LAYOUT, 7>(ps, i, j, gi, lane, RL, stage); break;
-    default: tiles_count_unit<LAYOUT, 8>(ps, i, j, gi, lane, RL, stage); break;
+    case 1: tiles_count_unit<LAYOUT, 1, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 2: tiles_count_unit<LAYOUT, 2, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 3: tiles_count_unit<LAYOUT, 3, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 4: tiles_count_unit<LAYOUT, 4, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 5: tiles_count_unit<LAYOUT, 5, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 6: tiles_count_unit<LAYOUT, 6, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 7: tiles_count_unit<LAYOUT, 7, false>(ps, i, j, gi, lane, RL, stage); break;
+    default: tiles_count_unit<LAYOUT, 8, false>(ps, i, j, gi, lane, RL, stage); break;
+    }
     }
 }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 3 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
+__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_BIN_MAJOR ? 4 : 3) k_tiles_count(const __grid_constant__ PlaneSet ps)
 {
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
-    __shared__ int4 stages[4][LAYOUT == LAYOUT_SLAB ? 32 * SlabStage<kGroupBins>::S : 1];
+    __shared__ int4 stages[4][LAYOUT == LAYOUT_BIN_MAJOR ? 1 : 32 * SlabStage<kGroupBins>::S];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t units = (int64_t)ps.g.nb * ps.g.ns * ps.ngroups;
     const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
@@ -751,6 +848,8 @@ __global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
     const PlaneSet &ps = bd.sets[f];
     if (ps.layout == LAYOUT_SLAB)
         tiles_count_dispatch<LAYOUT_SLAB>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
+    else if (ps.layout == LAYOUT_RECORD)
+        tiles_count_dispatch<LAYOUT_RECORD>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
     else
         tiles_count_dispatch<LAYOUT_BIN_MAJOR>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
 }
@@ -1105,6 +1204,8 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     prof_mark(prof, KID_TILES_COUNT, 0, st);
     if (ps.layout == LAYOUT_SLAB)
         k_tiles_count<LAYOUT_SLAB><<<blocks, 128, 0, st>>>(ps);
+    else if (ps.layout == LAYOUT_RECORD)
+        k_tiles_count<LAYOUT_RECORD><<<blocks, 128, 0, st>>>(ps);
     else
         k_tiles_count<LAYOUT_BIN_MAJOR><<<blocks, 128, 0, st>>>(ps);
     prof_mark(prof, KID_TILES_COUNT, 1, st);

@@ -130,7 +130,48 @@ __device__ __forceinline__ void rect_item(const CountView &v, const int64_t *g_o
     }
 }
 
-// The group table is copied to shared memory so that threads of different
+// LAYOUT_RECORD: one thread per (rectangle, 4-word quarter of the pixel
+// record).  Quarter k lies in plane qp[k] at word 4k - w0[plane]; the four
+// corners are four aligned int4 loads, and consecutive threads read
+// consecutive quarters of the same records.  wb[] maps record words to
+// output bins (-1: padding).
+__device__ __forceinline__ void rect_item_record(const CountView &v, const int64_t *off, const int16_t *rw,
+                                                 const int16_t *w0, const int16_t *qp, const int16_t *wb,
+                                                 const int32_t *__restrict__ rects, int32_t *__restrict__ out,
+                                                 int64_t t, int *err)
+{
+    const int nq = v.nquarters;
+    const int64_t qi = t / nq;
+    const int k = (int)(t - qi * nq);
+    int32_t *o = out + qi * v.B;
+    const int r0 = __ldg(rects + 4 * qi), c0 = __ldg(rects + 4 * qi + 1);
+    const int r1 = __ldg(rects + 4 * qi + 2), c1 = __ldg(rects + 4 * qi + 3);
+    int sum[4] = {-1, -1, -1, -1};
+    if (!box_ok(r0, c0, r1, c1, v.H, v.W)) {
+        if (k == 0) atomicOr(err, 1);
+    } else {
+        const int p = qp[k];
+        const int64_t w = rw[p];
+        const int32_t *base = v.d + off[p] + (4 * k - w0[p]);
+        const bool top = r0 > 0, left = c0 > 0;
+        const int4 A = __ldg(reinterpret_cast<const int4 *>(base + ((int64_t)r1 * v.P + c1) * w));
+        int4 B = make_int4(0, 0, 0, 0), C = B, D = B;
+        if (top) B = __ldg(reinterpret_cast<const int4 *>(base + ((int64_t)(r0 - 1) * v.P + c1) * w));
+        if (left) C = __ldg(reinterpret_cast<const int4 *>(base + ((int64_t)r1 * v.P + (c0 - 1)) * w));
+        if (top && left) D = __ldg(reinterpret_cast<const int4 *>(base + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * w));
+        sum[0] = A.x - B.x - C.x + D.x;
+        sum[1] = A.y - B.y - C.y + D.y;
+        sum[2] = A.z - B.z - C.z + D.z;
+        sum[3] = A.w - B.w - C.w + D.w;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int b = wb[4 * k + e];
+        if (b >= 0) o[b] = sum[e];
+    }
+}
+
+// The group tables are copied to shared memory so that threads of different
 // groups do not serialise on the kernel-parameter bank.
 __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ CountView v,
                                                      const int32_t *__restrict__ rects, int64_t n,
@@ -138,12 +179,26 @@ __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ Cou
 {
     __shared__ int64_t s_off[kMaxGroups];
     __shared__ int s_nb[kMaxGroups], s_b0[kMaxGroups];
+    __shared__ int16_t s_rw[kMaxGroups], s_w0[kMaxGroups], s_qp[kMaxBins / 4], s_wb[kMaxBins];
     for (int k = threadIdx.x; k < v.ngroups; k += blockDim.x) {
         s_off[k] = v.slab_off[k];
         s_nb[k] = v.group_nb[k];
         s_b0[k] = v.group_bin0[k];
+        s_rw[k] = v.group_nb[k];
+        s_w0[k] = v.plane_w0[k];
+    }
+    if (v.layout == LAYOUT_RECORD) {
+        for (int k = threadIdx.x; k < v.nquarters; k += blockDim.x) s_qp[k] = v.quarter_plane[k];
+        for (int k = threadIdx.x; k < 4 * v.nquarters; k += blockDim.x) s_wb[k] = v.word_bin[k];
     }
     __syncthreads();
+    if (v.layout == LAYOUT_RECORD) {
+        const int64_t total = n * v.nquarters;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)gridDim.x * blockDim.x)
+            rect_item_record(v, s_off, s_rw, s_w0, s_qp, s_wb, rects, out, t, err);
+        return;
+    }
     const int64_t total = n * v.ngroups;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x)
@@ -174,14 +229,18 @@ __global__ void __launch_bounds__(256) k_query_rects_b(const QueryJob *__restric
         const int f = find_job(pre, n, t);
         const QueryJob &jb = jobs[f];
         const CountView &v = *jb.v;
-        rect_item(v, v.slab_off, v.group_nb, v.group_bin0, jb.rects, jb.rect_out, t - pre[f], err);
+        if (v.layout == LAYOUT_RECORD)
+            rect_item_record(v, v.slab_off, v.group_nb, v.plane_w0, v.quarter_plane, v.word_bin, jb.rects,
+                             jb.rect_out, t - pre[f], err);
+        else
+            rect_item(v, v.slab_off, v.group_nb, v.group_bin0, jb.rects, jb.rect_out, t - pre[f], err);
     }
 }
 
 // Element offset of bin gb's count at (0, 0) and its per-pixel stride.
 __device__ __forceinline__ void count_base(const CountView &v, int gb, int64_t &base, int64_t &px)
 {
-    if (v.layout == LAYOUT_SLAB) {
+    if (v.layout != LAYOUT_BIN_MAJOR) {
         const int g = v.bin_group[gb];
         base = v.slab_off[g] + v.bin_local[gb];
         px = v.group_nb[g];
@@ -321,7 +380,7 @@ int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int3
 {
     if (n == 0) return 0;
     prof_mark(prof, KID_QUERY_RECTS, 0, st);
-    k_query_rects<<<grid_for(n * v.ngroups), 256, 0, st>>>(v, rects, n, out, err);
+    k_query_rects<<<grid_for(n * rect_items(v)), 256, 0, st>>>(v, rects, n, out, err);
     prof_mark(prof, KID_QUERY_RECTS, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

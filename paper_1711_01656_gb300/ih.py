@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(PKG, "libih.so")
 IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT, IH_ETOOBIG = range(8)
 IH_BIN_UNIFORM8, IH_BIN_INDEX = 0, 1
 IH_INPUT_PLANES, IH_INPUT_RGB_FEATURES = 0, 1
-IH_LAYOUT_BIN_MAJOR, IH_LAYOUT_SLAB = 0, 1
+IH_LAYOUT_BIN_MAJOR, IH_LAYOUT_SLAB, IH_LAYOUT_RECORD = 0, 1, 2
 IH_K_EPANECHNIKOV = 0
 IH_NORMALIZE = 1
 

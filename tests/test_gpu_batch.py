@@ -19,7 +19,7 @@ def _frames(ih, seed):
     specs = []
     sizes = [(48, 64), (130, 300), (77, 1030), (257, 129), (1, 9), (200, 200)]
     for k, (h, w) in enumerate(sizes):
-        layout = k % 2
+        layout = k % 3
         if k % 3 == 0:
             rgb = synth.blob_rgb(h, w, seed + k)
             pix = torch.from_numpy(rgb).to(DEV)

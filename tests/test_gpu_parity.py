@@ -56,7 +56,7 @@ SHAPES = [(1, 1), (1, 7), (7, 1), (2, 3), (37, 53), (33, 129), (64, 128), (65, 2
           (200, 611), (257, 1030)]
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 @pytest.mark.parametrize("h,w", SHAPES)
 @pytest.mark.parametrize("bins", [1, 3, 16, 32])
 def test_counts_exact(ihlib, ctx, h, w, bins, layout):
@@ -68,7 +68,7 @@ def test_counts_exact(ihlib, ctx, h, w, bins, layout):
     ihlib.ih_release(ctx, hdl)
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 @pytest.mark.parametrize("bins", [2, 7, 9, 40, 64, 200, 256])
 def test_counts_exact_bin_counts(ihlib, ctx, bins, layout):
     img = synth.blob_plane(150, 260, bins)
@@ -93,7 +93,7 @@ def test_counts_pitched_input(ihlib, ctx, pitch):
     ihlib.ih_release(ctx, hdl)
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_counts_multichannel(ihlib, ctx, layout):
     h, w = 123, 517
     planes = np.stack([synth.uniform_plane(h, w, 10 + k) for k in range(4)])
@@ -181,7 +181,7 @@ def _rects_gpu(ihlib, ctx, hdl, rects, B):
     return out
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_rects_all_of_small_frame(ihlib, ctx, layout):
     h, w, bins = 14, 19, 5
     img = synth.uniform_plane(h, w, 4)
@@ -232,7 +232,7 @@ def test_plain_frame_640x480_all_rects(ihlib, ctx):
     ihlib.ih_release(ctx, hdl)
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_fmv_frame_1920x1080_features(ihlib, ctx, layout):
     """One 1920x1080 RGB frame, 7 feature channels (91 bins): the full
     tensor vs Algorithm 5 and 100,000 rectangles (a seeded 2,000 by
@@ -283,7 +283,7 @@ def _weighted_gpu(ihlib, ctx, hdl, wins, Bw, normalize=False):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 @pytest.mark.parametrize("normalize", [False, True])
 def test_weighted_vs_direct_sum(ihlib, ctx, normalize, layout):
     h, w = 300, 400
@@ -306,7 +306,7 @@ def test_weighted_hand_example(ihlib, ctx):
     ihlib.ih_release(ctx, hdl)
 
 
-@pytest.mark.parametrize("layout", [0, 1])
+@pytest.mark.parametrize("layout", [0, 1, 2])
 def test_weighted_on_feature_channel(ihlib, ctx, layout):
     h, w = 200, 330
     rgb = synth.blob_rgb(h, w, 8)
@@ -403,4 +403,62 @@ def test_moment_planes_u32_and_weighted(ihlib, ctx):
     # a window wider than 256 is refused on the device
     with pytest.raises(ihlib.IHError):
         _weighted_gpu(ihlib, ctx, hdl, [[0, 0, 10, 256]], bins)
+    ihlib.ih_release(ctx, hdl)
+
+
+# ---------------------------------------------------------------- record layout
+
+
+def _record_words(bins):
+    """Words per pixel of IH_LAYOUT_RECORD, from the rules stated in ih.h:
+    groups of up to 8 consecutive bins from at most two channels, each taking
+    8 words, packed into planes of at most 16 words."""
+    groups = []  # [bins, channels] per group
+    for nb in bins:
+        left, first = nb, True
+        while left:
+            if not groups or groups[-1][0] == 8 or (first and groups[-1][1] == 2):
+                groups.append([0, 0])
+            g = groups[-1]
+            if first or g[0] == 0:
+                g[1] += 1
+            take = min(8 - g[0], left)
+            g[0] += take
+            left -= take
+            first = False
+    planes, w = [], 0
+    for n, _ in groups:
+        wk = 8
+        if w + wk > 16:
+            planes.append(w)
+            w = 0
+        w += wk
+    planes.append(w)
+    return sum(planes), len(groups)
+
+
+@pytest.mark.parametrize("bins", [[1], [3], [8], [9], [16, 9, 9, 9], [1, 1, 1, 1, 1], [5, 2, 1, 7, 20, 3],
+                                  [13, 14, 15], [7, 1], [2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2, 2]])
+def test_record_layout_exact(ihlib, ctx, bins):
+    """Record layout with groups that span two channels, cuts where a third
+    channel would start, and zero padding: the tensor, its size, rectangle
+    queries and the moment planes of a channel inside a shared group."""
+    h, w = 75, 300
+    chans = [(b, 0) for b in bins]
+    planes = np.stack([synth.blob_plane(h, w, 70 + k) for k in range(len(bins))])
+    wch = len(bins) // 2
+    hdl, _ = _build(ihlib, ctx, planes, chans, weighted=wch, layout=2)
+    info = ihlib.ih_info(ctx, hdl)
+    words, _ = _record_words(bins)
+    assert info["count_bytes"] == words * h * ((w + 3) // 4 * 4) * 4
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.frame_integral_histogram(planes, chans))
+    rects = synth.rects_uniform_corners(h, w, 500, 91)
+    d_r = torch.from_numpy(rects).to(DEV)
+    out = torch.full((len(rects), sum(bins)), -5, dtype=torch.int32, device=DEV)
+    ihlib.ih_query_rects(ctx, hdl, d_r, out)
+    ihlib.ih_sync(ctx)
+    assert np.array_equal(out.cpu().numpy(), oracle.frame_rect_hist(planes, chans, rects))
+    bw = bins[wch]
+    wins = synth.rects_side_range(h, w, 200, 1, 60, 92)
+    _assert_weighted(_weighted_gpu(ihlib, ctx, hdl, wins, bw), oracle.weighted_hist(planes[wch], bw, wins))
     ihlib.ih_release(ctx, hdl)

@@ -28,7 +28,7 @@ def _requests(ih, seed, n=14):
         else:
             rgb = synth.blob_rgb(h, w, seed + k)
             frame = ih.Frame(torch.from_numpy(rgb).to(DEV), synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES,
-                             weighted_channel=3, layout=k % 2)
+                             weighted_channel=3, layout=k % 3)
             B, Bw = 91, 16
         rects = torch.from_numpy(synth.rects_uniform_corners(h, w, 200, seed * 7 + k)).to(DEV)
         wins = torch.from_numpy(synth.rects_side_range(h, w, 150, 1, 64, seed * 11 + k)).to(DEV)
