@@ -42,6 +42,13 @@ namespace ih {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// count tiles: two rows in flight per step (more ILP) or one (fewer
+// registers, so that 4 CTAs fit an SM); the record layout's units, whose
+// group may draw on two channels, take the second
+template <int LAYOUT>
+constexpr bool pair_rows() { return LAYOUT != LAYOUT_RECORD; }
+// (the batched kernel, which serves every layout with one register budget,
+// always takes the first)
 constexpr int kQStride = kSumCols + 4;  // padded row of the staged byte tile
 
 // Eq. 2.15's Q: the channel-local bin of value v, or -1 for none.
@@ -592,7 +599,7 @@ __device__ __forceinline__ void store_record_staged(int32_t *row, int rec_w, int
 // LAYOUT_RECORD: NB = 8 is the group's width in the record and its
 // nb + nb1 <= NB real bins may come from two channels (SEG2); the padding
 // fields are never hit and hold 0.
-template <int LAYOUT, int NB, bool SEG2>
+template <int LAYOUT, int NB, bool SEG2, bool PAIR>
 __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int j, int gi, int lane,
                                                  int32_t (*RL)[kGroupBins], int4 *stage)
 {
@@ -653,6 +660,7 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
             pf[k] = (k < nr) ? load4(pl0, pt0, R0 + k, c, C1, vec_ok) : 0u;
             pg[k] = (SEG2 && k < nr) ? load4(pl1, pt1, R0 + k, c, C1, vec_ok1) : 0u;
         }
+        if constexpr (PAIR) {
         for (int rr0 = 0; rr0 < nr; rr0 += 4) {
             // two rows at a time: their shuffle scans are independent
 #pragma unroll
@@ -785,6 +793,82 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                 }
             }
         }
+        } else {
+        // one row per step, pixel words 4 rows ahead in a register ring
+#pragma unroll 1
+        for (int ra = 0; ra < nr; ++ra) {
+            const uint32_t pxa = pf[0], pya = pg[0];
+            pf[0] = pf[1];
+            pf[1] = pf[2];
+            pf[2] = pf[3];
+            pf[3] = (ra + 4 < nr) ? load4(pl0, pt0, R0 + ra + 4, c, C1, vec_ok) : 0u;
+            if (SEG2) {
+                pg[0] = pg[1];
+                pg[1] = pg[2];
+                pg[2] = pg[3];
+                pg[3] = (ra + 4 < nr) ? load4(pl1, pt1, R0 + ra + 4, c, C1, vec_ok1) : 0u;
+            }
+            uint32_t Pa0[4], Pa1[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int qa = bin_of((pxa >> (8 * jj)) & 0xff, bins0, mode0);
+                unsigned da = (jj < nvalid && qa >= 0) ? (unsigned)(qa - blo0) : 0xFFFFFFFFu;
+                uint32_t ea0 = 0u, ea1 = 0u;
+                if (SEG2) {
+                    if (da >= (unsigned)nb0) da = 0xFFFFFFFFu;
+                    const int ya = bin_of((pya >> (8 * jj)) & 0xff, bins1, mode1);
+                    unsigned fa = (jj < nvalid && ya >= 0) ? (unsigned)(ya - blo1) : 0xFFFFFFFFu;
+                    fa = fa < (unsigned)nbs1 ? fa + nb0 : 0xFFFFFFFFu;
+                    ea0 = fa < 4u ? (1u << (fa << 3)) : 0u;
+                    ea1 = (fa - 4u) < 4u ? (1u << ((fa - 4u) << 3)) : 0u;
+                }
+                Pa0[jj] = (jj ? Pa0[jj - 1] : 0u) + (da < 4u ? (1u << (da << 3)) : 0u) + ea0;
+                Pa1[jj] = (jj ? Pa1[jj - 1] : 0u) + ((da - 4u) < 4u ? (1u << ((da - 4u) << 3)) : 0u) + ea1;
+            }
+            const uint32_t ia0 = warp_incl_scan(Pa0[3], lane);
+            const uint32_t ia1 = NB > 4 ? warp_incl_scan(Pa1[3], lane) : 0u;
+            const uint32_t xa0 = ia0 - Pa0[3], xa1 = ia1 - Pa1[3];
+            const int4 la0 = *reinterpret_cast<const int4 *>(&RL[ra][0]);
+            const int4 la1 = *reinterpret_cast<const int4 *>(&RL[ra][4]);
+            const int rla[8] = {la0.x, la0.y, la0.z, la0.w, la1.x, la1.y, la1.z, la1.w};
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const uint32_t y0 = xa0 + Pa0[jj], y1 = xa1 + Pa1[jj];
+#pragma unroll
+                for (int b = 0; b < NB; ++b)
+                    acc[b][jj] += rla[b] + (int)__byte_perm(b < 4 ? y0 : y1, 0, 0x4440 + (b & 3));
+            }
+            if constexpr (LAYOUT == LAYOUT_BIN_MAJOR) {
+                if (c < g.P) {
+#pragma unroll
+                    for (int b = 0; b < NB; ++b)
+                        *reinterpret_cast<int4 *>(ps.out + ((bg0 + b) * g.H + R0 + ra) * g.P + c) =
+                            make_int4(acc[b][0], acc[b][1], acc[b][2], acc[b][3]);
+                }
+            } else if constexpr (LAYOUT == LAYOUT_SLAB) {
+                store_slab_staged<NB>(ps.out + ps.slab_off[gr.plane] + ((int64_t)(R0 + ra) * g.P + cc) * NB,
+                                      (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
+            } else {
+                const int rw = ps.rec_w[gr.plane];
+                store_record_staged<NB>(ps.out + ps.slab_off[gr.plane] + ((int64_t)(R0 + ra) * g.P + cc) * rw + gr.off,
+                                        rw, (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
+            }
+            __syncwarp();
+            if (lane == 31) {
+                int4 a, b4;
+                a.x = rla[0] + (int)__byte_perm(ia0, 0, 0x4440);
+                a.y = rla[1] + (int)__byte_perm(ia0, 0, 0x4441);
+                a.z = rla[2] + (int)__byte_perm(ia0, 0, 0x4442);
+                a.w = rla[3] + (int)__byte_perm(ia0, 0, 0x4443);
+                b4.x = rla[4] + (int)__byte_perm(ia1, 0, 0x4440);
+                b4.y = rla[5] + (int)__byte_perm(ia1, 0, 0x4441);
+                b4.z = rla[6] + (int)__byte_perm(ia1, 0, 0x4442);
+                b4.w = rla[7] + (int)__byte_perm(ia1, 0, 0x4443);
+                *reinterpret_cast<int4 *>(&RL[ra][0]) = a;
+                *reinterpret_cast<int4 *>(&RL[ra][4]) = b4;
+            }
+        }
+        }
         __syncwarp();
     }
 }
@@ -794,7 +878,7 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
 // groups and the tail of the grid is made of the cheapest units.
 // LAYOUT_RECORD: unit = tile * groups + group, so the groups sharing a
 // plane's records write them at about the same time.
-template <int LAYOUT>
+template <int LAYOUT, bool PAIR>
 __device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t unit, int lane,
                                                      int32_t (*RL)[kGroupBins], int4 *stage)
 {
@@ -806,34 +890,34 @@ __device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t
         // every group runs the two-channel path (an empty second segment
         // never hits), so an SM never interleaves two large loop bodies
         if (ps.seg2)
-            tiles_count_unit<LAYOUT_RECORD, kGroupBins, true>(ps, i, j, gi, lane, RL, stage);
+            tiles_count_unit<LAYOUT_RECORD, kGroupBins, true, PAIR>(ps, i, j, gi, lane, RL, stage);
         else
-            tiles_count_unit<LAYOUT_RECORD, kGroupBins, false>(ps, i, j, gi, lane, RL, stage);
+            tiles_count_unit<LAYOUT_RECORD, kGroupBins, false, PAIR>(ps, i, j, gi, lane, RL, stage);
     } else {
     const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
     const int i = tile / ps.g.ns, j = tile % ps.g.ns;
     switch (ps.grp[gi].nb) {
-    case 1: tiles_count_unit<LAYOUT, 1, false>(ps, i, j, gi, lane, RL, stage); break;
-    case 2: tiles_count_unit<LAYOUT, 2, false>(ps, i, j, gi, lane, RL, stage); break;
-    case 3: tiles_count_unit<LAYOUT, 3, false>(ps, i, j, gi, lane, RL, stage); break;
-    case 4: tiles_count_unit<LAYOUT, 4, false>(ps, i, j, gi, lane, RL, stage); break;
-    case 5: tiles_count_unit<LAYOUT, 5, false>(ps, i, j, gi, lane, RL, stage); break;
-    case 6: tiles_count_unit<LAYOUT, 6, false>(ps, i, j, gi, lane, RL, stage); break;
-    case 7: tiles_count_unit<LAYOUT, 7, false>(ps, i, j, gi, lane, RL, stage); break;
-    default: tiles_count_unit<LAYOUT, 8, false>(ps, i, j, gi, lane, RL, stage); break;
+    case 1: tiles_count_unit<LAYOUT, 1, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    case 2: tiles_count_unit<LAYOUT, 2, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    case 3: tiles_count_unit<LAYOUT, 3, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    case 4: tiles_count_unit<LAYOUT, 4, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    case 5: tiles_count_unit<LAYOUT, 5, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    case 6: tiles_count_unit<LAYOUT, 6, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    case 7: tiles_count_unit<LAYOUT, 7, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
+    default: tiles_count_unit<LAYOUT, 8, false, PAIR>(ps, i, j, gi, lane, RL, stage); break;
     }
     }
 }
 
 template <int LAYOUT>
-__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_BIN_MAJOR ? 4 : 3) k_tiles_count(const __grid_constant__ PlaneSet ps)
+__global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 3 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
 {
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
     __shared__ int4 stages[4][LAYOUT == LAYOUT_BIN_MAJOR ? 1 : 32 * SlabStage<kGroupBins>::S];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t units = (int64_t)ps.g.nb * ps.g.ns * ps.ngroups;
     const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
-    if (unit < units) tiles_count_dispatch<LAYOUT>(ps, unit, lane, RLs[wid], stages[wid]);
+    if (unit < units) tiles_count_dispatch<LAYOUT, pair_rows<LAYOUT>()>(ps, unit, lane, RLs[wid], stages[wid]);
 }
 
 // Batched: warps over the concatenated units of all frames (any layout).
@@ -847,11 +931,11 @@ __global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
     const int f = find_frame(bd.pre_tiles, bd.n, unit);
     const PlaneSet &ps = bd.sets[f];
     if (ps.layout == LAYOUT_SLAB)
-        tiles_count_dispatch<LAYOUT_SLAB>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
+        tiles_count_dispatch<LAYOUT_SLAB, true>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
     else if (ps.layout == LAYOUT_RECORD)
-        tiles_count_dispatch<LAYOUT_RECORD>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
+        tiles_count_dispatch<LAYOUT_RECORD, true>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
     else
-        tiles_count_dispatch<LAYOUT_BIN_MAJOR>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
+        tiles_count_dispatch<LAYOUT_BIN_MAJOR, true>(ps, unit - bd.pre_tiles[f], lane, RLs[wid], stages[wid]);
 }
 
 // ------------------------------------------------------------- moment tiles
