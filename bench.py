@@ -167,6 +167,9 @@ def algorithmic_bytes(kernel: str, B: int, Bw: int, n_rects: int, n_wins: int) -
         return 7 * hw + 4.0 * B * hw          # 7 channel planes in, B int32 planes out
     if kernel == "tiles/moments":
         return hw + 4 * 8.0 * Bw * hw        # intensity in, 4 x Bw int64 planes out
+    if kernel == "tiles/count+moments":      # both kinds of tiles in one launch
+        return (algorithmic_bytes("tiles/count", B, Bw, n_rects, n_wins) +
+                algorithmic_bytes("tiles/moments", B, Bw, n_rects, n_wins))
     if kernel == "features":
         return 3 * hw + 4 * hw
     if kernel == "query_rects":
@@ -397,9 +400,11 @@ def run_engine(args):
 
     batched = served = None
     if not args.no_batched:
-        batched = batched_section(ih, dev, LAYOUTS[args.layout][0])
+        # the batch and the serving loop have no rectangle queries: the slab
+        # layout (no padding, one channel per group) suits them better
+        batched = batched_section(ih, dev, LAYOUTS["slab"][0])
     if not args.no_served:
-        served = served_section(ih, dev, LAYOUTS[args.layout][0])
+        served = served_section(ih, dev, LAYOUTS["slab"][0])
 
     line = None
     if rank == 0:
@@ -499,6 +504,7 @@ def batched_section(ih, dev, layout, n_frames=64, runs=5):
     gbytes = px * (91 * 4 + 16 * 32) / 1e9
     return {"workload": "%d uneven FMV frames (%s), 91 bins + intensity moments, %d weighted windows each"
                         % (n_frames, ", ".join("%dx%d:%d" % (w, h, sizes.count((h, w))) for h, w in sorted(set(sizes))), nw),
+            "layout": [k for k, v in LAYOUTS.items() if v[0] == layout][0],
             "frames": n_frames, "pixels": px, "output_GB": round(gbytes, 2),
             "batched_graph_ms": round(ms_b, 3), "per_frame_ms": round(ms_p, 3),
             "batched_cells_per_s": cells / (ms_b / 1e3), "per_frame_cells_per_s": cells / (ms_p / 1e3),
@@ -578,6 +584,7 @@ def served_section(ih, dev, layout, seconds=2.0, trackers=16, fps=30.0, budget_g
     return {"workload": "%d trackers x %.0f fps Poisson for %.1f s (%d frames, %d WAMI 8192^2), 2,000 rect + "
                         "2,000 weighted queries per frame, %d GB budget" % (trackers, fps, seconds, n,
                                                                             int((kind == 4).sum()), budget_gb),
+            "layout": [k for k, v in LAYOUTS.items() if v[0] == layout][0],
             "continuous_batching": cont, "one_request_at_a_time": single}
 
 
@@ -590,7 +597,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-frame batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the serving-loop comparison")
-    ap.add_argument("--layout", choices=sorted(LAYOUTS), default="slab", help="count-tensor layout")
+    ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
         ap.error("--warmup must be >= 3")

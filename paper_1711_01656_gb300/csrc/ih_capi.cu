@@ -76,7 +76,8 @@ const char *kernel_name(int kid)
 {
     static const char *names[KID_COUNT] = {"features",      "tile_sums/count", "tile_sums/weighted",
                                            "carry_scan",    "tiles/count",     "tiles/moments",
-                                           "query_rects",   "query_weighted",  "export"};
+                                           "query_rects",   "query_weighted",  "export",
+                                           "tiles/count+moments"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 

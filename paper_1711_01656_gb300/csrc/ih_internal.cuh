@@ -57,7 +57,8 @@ enum KernelId {
     KID_QUERY_RECTS = 6,
     KID_QUERY_WEIGHTED = 7,
     KID_EXPORT = 8,
-    KID_COUNT = 9
+    KID_TILES_BOTH = 9,  // count and moment tiles of one frame in one launch
+    KID_COUNT = 10
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on

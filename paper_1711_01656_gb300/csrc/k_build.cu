@@ -15,14 +15,14 @@
 //   moment carries from them.
 // k_carry_scan  exclusive prefixes over bands (G), strips (L) and both
 //   (corners), int32 for counts and int64 for the moments.
-// k_tiles_count  one warp per (tile, group of <= 8 bins).  A lane owns 4
+// count tiles  one warp per (tile, group of <= 8 bins).  A lane owns 4
 //   adjacent columns of a 128-column chunk; per row each pixel's bin becomes
 //   a one-hot packed as 8-bit fields (4 bins per 32-bit word), so one
 //   in-lane prefix and one warp shuffle scan of two words give the row
 //   prefix of all 8 bins (a field never exceeds 128, the chunk width).  Each
 //   column's running sum down the band lives in registers; each cell is
 //   stored once with 16-byte stores.  Pixel rows are prefetched 4 rows ahead.
-// k_tiles_moments  one warp per (tile, bin of the weighted channel); the same
+// moment tiles  one warp per (tile, bin of the weighted channel); the same
 //   walk produces the four moment planes.  With u the column offset inside
 //   the chunk, the row prefixes of Q, u Q and u^2 Q are packed into two words
 //   (count: 8 bits, sum of u: 24 bits; sum of u^2: 32 bits), scanned once,
@@ -30,6 +30,10 @@
 //   c = C + u gives Sum c Q = C n + Sum u Q, Sum c^2 Q = C^2 n + 2C Sum u Q +
 //   Sum u^2 Q.  The row-weighted planes accumulate r * (row prefix of Q) and
 //   r^2 * (row prefix of Q).  All moment arithmetic is exact in int64.
+//
+// k_tiles runs the moment units and then the count units of a frame in one
+// launch (k_tiles_count when the frame has no moment planes); k_tiles_b does
+// the same over the frames of a batch.
 //
 // No kernel waits on another CTA; the only inter-CTA data flow is through the
 // carry arrays between launches on one stream.
@@ -1098,40 +1102,84 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
     }
 }
 
-__global__ void __launch_bounds__(128, 4) k_tiles_moments(const __grid_constant__ PlaneSet ps)
+// Count and moment tiles of one frame in a single launch: the first
+// mom_blocks CTAs take the moment units (the longer ones), the rest the
+// count units, so the two unit kinds share one tail instead of two.  The
+// shared memory is the union of the two kinds' buffers.
+struct CountSmem {
+    int32_t RL[4][kMaxBandRows][kGroupBins];
+    int4 stage[4][32 * SlabStage<kGroupBins>::S];
+};
+struct MomentSmem {
+    int32_t RLn[4][kMaxBandRows];
+    long long RLx[4][kMaxBandRows], RLxx[4][kMaxBandRows];
+    long long stage[4][4 * kChunk];
+};
+constexpr size_t kTilesSmem = sizeof(CountSmem) > sizeof(MomentSmem) ? sizeof(CountSmem) : sizeof(MomentSmem);
+
+// The count units step one row at a time here, so that 4 CTAs fit an SM
+// and the moment units keep the occupancy they have on their own.
+template <int LAYOUT>
+__global__ void __launch_bounds__(128, 4) k_tiles(const __grid_constant__ PlaneSet ps, unsigned mom_blocks)
 {
-    __shared__ int32_t sRLn[4][kMaxBandRows];
-    __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
-    __shared__ __align__(16) long long sStage[4][4 * kChunk];
+    __shared__ __align__(16) unsigned char smem[kTilesSmem];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
-    const int Bw = ps.chan[ps.wch].bins;
-    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
-    if (unit >= (int64_t)g.nb * g.ns * Bw) return;
-    const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
-    if (ps.mom32)
-        tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
-    else
-        tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
+    if (blockIdx.x < mom_blocks) {
+        MomentSmem &m = *reinterpret_cast<MomentSmem *>(smem);
+        const int Bw = ps.chan[ps.wch].bins;
+        const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+        if (unit >= (int64_t)g.nb * g.ns * Bw) return;
+        const int tile = (int)(unit / Bw), wb = (int)(unit % Bw);
+        if (ps.mom32)
+            tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, m.RLn[wid], m.RLx[wid], m.RLxx[wid],
+                                     m.stage[wid]);
+        else
+            tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, m.RLn[wid], m.RLx[wid], m.RLxx[wid],
+                                      m.stage[wid]);
+    } else {
+        CountSmem &cs = *reinterpret_cast<CountSmem *>(smem);
+        const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
+        const int64_t unit = (int64_t)(blockIdx.x - mom_blocks) * 4 + wid;
+        if (unit < units) tiles_count_dispatch<LAYOUT, false>(ps, unit, lane, cs.RL[wid], cs.stage[wid]);
+    }
 }
 
-__global__ void __launch_bounds__(128, 4) k_tiles_moments_b(const BatchDev bd)
+// Batched: the moment units of all frames, then the count units of all
+// frames, in one launch (count units as in k_tiles_count_b).
+__global__ void __launch_bounds__(128, 4) k_tiles_b(const BatchDev bd, unsigned mom_blocks)
 {
-    __shared__ int32_t sRLn[4][kMaxBandRows];
-    __shared__ long long sRLx[4][kMaxBandRows], sRLxx[4][kMaxBandRows];
-    __shared__ __align__(16) long long sStage[4][4 * kChunk];
+    __shared__ __align__(16) unsigned char smem[kTilesSmem];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
-    if (unit >= bd.pre_mom[bd.n]) return;
-    const int f = find_frame(bd.pre_mom, bd.n, unit);
-    const PlaneSet &ps = bd.sets[f];
-    const int Bw = ps.chan[ps.wch].bins;
-    const int64_t local = unit - bd.pre_mom[f];
-    const int tile = (int)(local / Bw), wb = (int)(local % Bw);
-    if (ps.mom32)
-        tiles_moments_unit<true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
-    else
-        tiles_moments_unit<false>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, sRLn[wid], sRLx[wid], sRLxx[wid], sStage[wid]);
+    if (blockIdx.x < mom_blocks) {
+        MomentSmem &m = *reinterpret_cast<MomentSmem *>(smem);
+        const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+        if (unit >= bd.pre_mom[bd.n]) return;
+        const int f = find_frame(bd.pre_mom, bd.n, unit);
+        const PlaneSet &ps = bd.sets[f];
+        const int Bw = ps.chan[ps.wch].bins;
+        const int64_t local = unit - bd.pre_mom[f];
+        const int tile = (int)(local / Bw), wb = (int)(local % Bw);
+        if (ps.mom32)
+            tiles_moments_unit<true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, m.RLn[wid], m.RLx[wid],
+                                     m.RLxx[wid], m.stage[wid]);
+        else
+            tiles_moments_unit<false>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, m.RLn[wid], m.RLx[wid],
+                                      m.RLxx[wid], m.stage[wid]);
+    } else {
+        CountSmem &cs = *reinterpret_cast<CountSmem *>(smem);
+        const int64_t unit = (int64_t)(blockIdx.x - mom_blocks) * 4 + wid;
+        if (unit >= bd.pre_tiles[bd.n]) return;
+        const int f = find_frame(bd.pre_tiles, bd.n, unit);
+        const PlaneSet &ps = bd.sets[f];
+        const int64_t local = unit - bd.pre_tiles[f];
+        if (ps.layout == LAYOUT_SLAB)
+            tiles_count_dispatch<LAYOUT_SLAB, false>(ps, local, lane, cs.RL[wid], cs.stage[wid]);
+        else if (ps.layout == LAYOUT_RECORD)
+            tiles_count_dispatch<LAYOUT_RECORD, false>(ps, local, lane, cs.RL[wid], cs.stage[wid]);
+        else
+            tiles_count_dispatch<LAYOUT_BIN_MAJOR, false>(ps, local, lane, cs.RL[wid], cs.stage[wid]);
+    }
 }
 
 template <typename F>
@@ -1231,16 +1279,17 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
         prof_mark(prof, KID_SCAN, 1, st);
         ++n;
     }
-    if (totals[3]) {
+    if (totals[3] && totals[4]) {
+        // count and moment tiles of all frames in one launch
+        const unsigned mblocks = (unsigned)((totals[4] + 3) / 4);
+        prof_mark(prof, KID_TILES_BOTH, 0, st);
+        k_tiles_b<<<mblocks + (unsigned)((totals[3] + 3) / 4), 128, 0, st>>>(bd, mblocks);
+        prof_mark(prof, KID_TILES_BOTH, 1, st);
+        ++n;
+    } else if (totals[3]) {
         prof_mark(prof, KID_TILES_COUNT, 0, st);
         k_tiles_count_b<<<(unsigned)((totals[3] + 3) / 4), 128, 0, st>>>(bd);
         prof_mark(prof, KID_TILES_COUNT, 1, st);
-        ++n;
-    }
-    if (totals[4]) {
-        prof_mark(prof, KID_TILES_MOMENTS, 0, st);
-        k_tiles_moments_b<<<(unsigned)((totals[4] + 3) / 4), 128, 0, st>>>(bd);
-        prof_mark(prof, KID_TILES_MOMENTS, 1, st);
         ++n;
     }
     return cudaPeekAtLastError() == cudaSuccess ? n : -1;
@@ -1285,6 +1334,21 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     }
     const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
     const unsigned blocks = (unsigned)((units + 3) / 4);
+    if (ps.mom) {
+        // count and moment tiles in one launch
+        const int64_t mu = (int64_t)g.nb * g.ns * ps.chan[ps.wch].bins;
+        const unsigned mblocks = (unsigned)((mu + 3) / 4);
+        prof_mark(prof, KID_TILES_BOTH, 0, st);
+        if (ps.layout == LAYOUT_SLAB)
+            k_tiles<LAYOUT_SLAB><<<mblocks + blocks, 128, 0, st>>>(ps, mblocks);
+        else if (ps.layout == LAYOUT_RECORD)
+            k_tiles<LAYOUT_RECORD><<<mblocks + blocks, 128, 0, st>>>(ps, mblocks);
+        else
+            k_tiles<LAYOUT_BIN_MAJOR><<<mblocks + blocks, 128, 0, st>>>(ps, mblocks);
+        prof_mark(prof, KID_TILES_BOTH, 1, st);
+        ++n;
+        return cudaPeekAtLastError() == cudaSuccess ? n : -1;
+    }
     prof_mark(prof, KID_TILES_COUNT, 0, st);
     if (ps.layout == LAYOUT_SLAB)
         k_tiles_count<LAYOUT_SLAB><<<blocks, 128, 0, st>>>(ps);
@@ -1294,14 +1358,6 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         k_tiles_count<LAYOUT_BIN_MAJOR><<<blocks, 128, 0, st>>>(ps);
     prof_mark(prof, KID_TILES_COUNT, 1, st);
     ++n;
-    if (ps.mom) {
-        const int64_t mu = (int64_t)g.nb * g.ns * ps.chan[ps.wch].bins;
-        const unsigned mblocks = (unsigned)((mu + 3) / 4);
-        prof_mark(prof, KID_TILES_MOMENTS, 0, st);
-        k_tiles_moments<<<mblocks, 128, 0, st>>>(ps);
-        prof_mark(prof, KID_TILES_MOMENTS, 1, st);
-        ++n;
-    }
     return cudaPeekAtLastError() == cudaSuccess ? n : -1;
 }
 
