@@ -398,12 +398,17 @@ def run_engine(args):
                    "gbs": round(algorithmic_bytes(k, B, Bw, N_RECTS, N_WINDOWS) / (v[1] / v[0] / 1e3) / 1e9, 1)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    batched = served = None
-    if not args.no_batched:
+    batched = served = wami = plain = None
+    sections = world == 1  # the side workloads run once, on a single GPU
+    if sections and not args.no_wami:
+        wami = wami_section(ih, dev, LAYOUTS[args.layout][0])
+    if sections and not args.no_plain:
+        plain = plain_section(ih, dev)
+    if sections and not args.no_batched:
         # the batch and the serving loop have no rectangle queries: the slab
         # layout (no padding, one channel per group) suits them better
         batched = batched_section(ih, dev, LAYOUTS["slab"][0])
-    if not args.no_served:
+    if sections and not args.no_served:
         served = served_section(ih, dev, LAYOUTS["slab"][0])
 
     line = None
@@ -429,6 +434,8 @@ def run_engine(args):
             "kernels": kernels,
             "batched": batched,
             "served": served,
+            "wami": wami,
+            "plain": plain,
         }
         print(json.dumps(line))
     ih.ih_destroy(ctx)
@@ -438,6 +445,126 @@ def run_engine(args):
 
 
 # ----------------------------------------------------------------- batched / served
+
+def wami_section(ih, dev, layout, reps=3):
+    """One 8192 x 8192 wide-area frame: 32-bin integral histogram (2.15 G int32
+    cells) with the four int64 moment planes of its single channel (68.7 GB),
+    1,000,000 rectangle queries of side 16..256 and 100,000 Epanechnikov
+    windows of side 32..256.  Each phase is timed with events after one
+    warm-up, L2 flushed before each repetition."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    hh = ww = 8192
+    B = 32
+    p = (ww + 3) // 4 * 4
+    need = hh * p * (B * 4 + 4 * B * 8) + 64e6 * 4 + 2e9
+    free, _ = torch.cuda.mem_get_info(dev)
+    if need > free * 0.9:
+        return {"skipped": "needs %.1f GB of HBM, %.1f GB free" % (need / 1e9, free / 1e9)}
+    img = synth.blob_plane(hh, ww, synth.config_seed(3))
+    pix = torch.from_numpy(img).to(dev)[None]
+    rects = torch.from_numpy(synth.rects_side_range(hh, ww, 1_000_000, 16, 256, synth.config_seed(3) + 100)).to(dev)
+    wins = torch.from_numpy(synth.rects_side_range(hh, ww, 100_000, 32, 256, synth.config_seed(3) + 200)).to(dev)
+    r_out = torch.empty((rects.shape[0], B), dtype=torch.int32, device=dev)
+    w_out = torch.empty((wins.shape[0], B), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    ctx = ih.ih_create(dev.index or 0, flags=ih.IH_CFG_PROFILE)
+    frame = ih.Frame(pix, [(B, 0)], weighted_channel=0, layout=layout)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t = {"build": [], "rects": [], "weighted": []}
+    for rep in range(reps + 1):
+        flush.fill_(rep & 0xFF)
+        ev[0].record()
+        h, = ih.ih_build(ctx, frame)
+        ev[1].record()
+        ih.ih_query_rects(ctx, h, rects, r_out)
+        ev[2].record()
+        ih.ih_query_weighted(ctx, h, wins, w_out)
+        ev[3].record()
+        torch.cuda.synchronize()
+        ih.ih_release(ctx, h)
+        if rep == 0:
+            ih.ih_profile_read(ctx, reset=True)
+            continue
+        t["build"].append(ev[0].elapsed_time(ev[1]))
+        t["rects"].append(ev[1].elapsed_time(ev[2]))
+        t["weighted"].append(ev[2].elapsed_time(ev[3]))
+    torch.cuda.synchronize()
+    prof = ih.ih_profile_read(ctx, reset=True)
+    ih.ih_destroy(ctx)
+    del pix, r_out, w_out, flush
+    torch.cuda.empty_cache()
+    ms = {k: float(np.median(v)) for k, v in t.items()}
+    cells = B * hh * ww
+    count_bytes = hh * ww + 4.0 * cells
+    moment_bytes = hh * ww + 4 * 8.0 * B * hh * ww
+    peak = measured_peak()[0]
+    kern = {}
+    for name, (n, tot) in prof.items():
+        kern[name] = round(tot / n, 3)
+    tiles_ms = kern.get("tiles/count+moments")
+    out = {"workload": "WAMI 8192x8192 blobs+noise, 32 bins, int64 moment planes, 1,000,000 rects (side 16..256), "
+                       "100,000 weighted windows (side 32..256)",
+           "layout": [k for k, v in LAYOUTS.items() if v[0] == layout][0],
+           "build_ms": round(ms["build"], 3), "rect_queries_ms": round(ms["rects"], 3),
+           "weighted_queries_ms": round(ms["weighted"], 3),
+           "build_cells_per_s": cells / (ms["build"] / 1e3),
+           "build_GBs": round((count_bytes + moment_bytes) / (ms["build"] / 1e3) / 1e9, 1),
+           "rects_per_s": 1e6 / (ms["rects"] / 1e3), "windows_per_s": 1e5 / (ms["weighted"] / 1e3),
+           "kernel_ms": kern}
+    if tiles_ms:
+        gbs = (count_bytes + moment_bytes) / (tiles_ms / 1e3) / 1e9
+        out["tiles_roofline"] = {"bound": "hbm", "kernel": "tiles/count+moments", "achieved": round(gbs, 1),
+                                 "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
+    return out
+
+
+def plain_section(ih, dev, runs=50):
+    """The plain frame: 640 x 480 uniform grayscale, 16 bins, 10,000 random
+    rectangles.  Launch latency dominates, so the build + queries are timed
+    both as plain per-frame calls and as one replayed CUDA graph (a one-frame
+    batch)."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    hh, ww, B = 480, 640, 16
+    img = synth.uniform_plane(hh, ww, synth.config_seed(0))
+    pix = torch.from_numpy(img).to(dev)[None]
+    rects = torch.from_numpy(synth.rects_uniform_corners(hh, ww, 10_000, synth.config_seed(0) + 1)).to(dev)
+    r_out = torch.empty((rects.shape[0], B), dtype=torch.int32, device=dev)
+    ctx = ih.ih_create(dev.index or 0)
+    frame = ih.Frame(pix, [(B, 0)])
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(k):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / k * 1e3
+
+    def per_frame():
+        h, = ih.ih_build(ctx, frame)
+        ih.ih_query_rects(ctx, h, rects, r_out)
+        ih.ih_release(ctx, h)
+
+    us_plain = timed(per_frame, runs)
+    batch, handles = ih.ih_batch_create(ctx, [frame], rects=rects, rect_counts=[rects.shape[0]],
+                                        rect_out=r_out.view(-1), batch_flags=ih.IH_BATCH_GRAPH)
+    us_graph = timed(lambda: ih.ih_batch_run(ctx, batch), runs)
+    ih.ih_batch_destroy(batch)
+    for h in handles:
+        ih.ih_release(ctx, h)
+    ih.ih_destroy(ctx)
+    cells = B * hh * ww
+    return {"workload": "plain 640x480 uniform gray, 16 bins, 10,000 rects", "per_frame_us": round(us_plain, 2),
+            "graph_us": round(us_graph, 2), "cells_per_s_per_frame": cells / (us_plain / 1e6),
+            "cells_per_s_graph": cells / (us_graph / 1e6)}
+
 
 def batched_section(ih, dev, layout, n_frames=64, runs=5):
     """64 uneven FMV frames (sizes drawn from {640x480, 1280x720, 1920x1080,
@@ -597,6 +724,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-frame batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the serving-loop comparison")
+    ap.add_argument("--no-wami", action="store_true", help="skip the 8192x8192 wide-area frame")
+    ap.add_argument("--no-plain", action="store_true", help="skip the 640x480 plain frame")
     ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
