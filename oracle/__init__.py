@@ -64,6 +64,12 @@ def _bind(path: str):
     lib.oracle_weighted_hist.restype = i64
     lib.oracle_kernel_weight.argtypes = [p, i32, i32]
     lib.oracle_kernel_weight.restype = ctypes.c_double
+    lib.oracle_weighted_hist_k.argtypes = [p, i64, i32, i32, i32, i32, p, i64, i32, i32, i32, p]
+    lib.oracle_weighted_hist_k.restype = i64
+    lib.oracle_manhattan_weight.argtypes = [p, i32, i32]
+    lib.oracle_manhattan_weight.restype = ctypes.c_double
+    lib.oracle_wedding_weight.argtypes = [p, i32, i32, i32]
+    lib.oracle_wedding_weight.restype = ctypes.c_double
     lib.oracle_orientation_bin.argtypes = [i32, i32, i32]
     lib.oracle_orientation_bin.restype = i32
     lib.oracle_features.argtypes = [p, i32, i32, p]
@@ -132,15 +138,36 @@ def rect_hist(img, bins: int, rects, mode: int = BIN_UNIFORM8) -> np.ndarray:
     return out
 
 
+# spatial kernels of weighted_hist
+K_EPANECHNIKOV, K_MANHATTAN, K_WEDDING_CAKE = 0, 1, 2
+
+
 def weighted_hist(img, bins: int, windows, mode: int = BIN_UNIFORM8,
-                  normalize: bool = False) -> np.ndarray:
-    """Eq. 3.1 by direct FP64 summation with the Epanechnikov window kernel."""
+                  normalize: bool = False, kernel: int = K_EPANECHNIKOV, layers: int = 4) -> np.ndarray:
+    """Eq. 3.1 by direct FP64 summation with the Epanechnikov window kernel,
+    the Manhattan kernel (Eq. 3.3) or the wedding-cake rings (Eq. 3.2)."""
     a, q = _plane(img), _boxes(windows)
     h, w = a.shape
     out = np.empty((q.shape[0], bins), dtype=np.float64)
-    _load().oracle_weighted_hist(a.ctypes.data, w, h, w, bins, mode, q.ctypes.data,
-                                 q.shape[0], int(bool(normalize)), out.ctypes.data)
+    if kernel == K_EPANECHNIKOV:
+        _load().oracle_weighted_hist(a.ctypes.data, w, h, w, bins, mode, q.ctypes.data,
+                                     q.shape[0], int(bool(normalize)), out.ctypes.data)
+    else:
+        _load().oracle_weighted_hist_k(a.ctypes.data, w, h, w, bins, mode, q.ctypes.data, q.shape[0],
+                                       int(kernel), int(layers), int(bool(normalize)), out.ctypes.data)
     return out
+
+
+def manhattan_weight(window, r: int, c: int) -> float:
+    """The Manhattan-kernel weight of one pixel inside `window`."""
+    q = np.ascontiguousarray(window, dtype=np.int32).reshape(4)
+    return _load().oracle_manhattan_weight(q.ctypes.data, int(r), int(c))
+
+
+def wedding_weight(window, layers: int, r: int, c: int) -> float:
+    """The wedding-cake weight of one pixel inside `window` (`layers` rings)."""
+    q = np.ascontiguousarray(window, dtype=np.int32).reshape(4)
+    return _load().oracle_wedding_weight(q.ctypes.data, int(layers), int(r), int(c))
 
 
 def kernel_weight(window, r: int, c: int) -> float:

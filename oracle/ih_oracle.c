@@ -19,6 +19,8 @@
  *     region's pixels                             Eq. 2.15 + Eq. 2.16 (definition)
  *   - spatially weighted local histogram by
  *     direct summation (the brute force)          Eq. 3.1, Sec. 3.1.1
+ *     with the Manhattan kernel                   Eq. 3.3, Sec. 3.1.3
+ *     or the wedding-cake rings                   Eq. 3.2, Sec. 3.1.2
  *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
  *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
  *
@@ -34,6 +36,11 @@
  *     ellipse passes through the window's outer corners:
  *       k(r,c) = 1 - (2c-(c0+c1))^2/(2w^2) - (2r-(r0+r1))^2/(2h^2),
  *     w = c1-c0+1, h = r1-r0+1 (every pixel centre has k > 0);
+ *   - the Manhattan kernel is h + w minus the city-block distance from the
+ *     window centre in doubled coordinates (the thesis leaves the scale and
+ *     the normalisation open); the wedding-cake windows shrink by
+ *     floor(j*h/(2L)), floor(j*w/(2L)) per side and ring j weighs
+ *     (h + w)(j + 1)/L (the thesis leaves the ring sizes and weights open);
  *   - intensity rounds down; gradient orientation is unsigned, in
  *     [0,180) degrees, 9 bins of 20 degrees, central differences at step
  *     s with replicated borders, (0,0) -> bin 0.
@@ -206,14 +213,44 @@ double oracle_kernel_weight(const int32_t *q, int r, int c)
     return 1.0 - dc * dc / (2.0 * wdt * wdt) - dr * dr / (2.0 * hgt * hgt);
 }
 
+/* The Manhattan (city-block) kernel of Sec. 3.1.3: Eq. 3.3's distance
+ * |x_i - x_c| + |y_i - y_c| from the window centre, taken in doubled
+ * coordinates so that the centre of an even side is exact, subtracted from
+ * h + w (more than the largest doubled distance, h - 1 + w - 1), so weights
+ * fall linearly from the centre to the border and stay >= 2. */
+double oracle_manhattan_weight(const int32_t *q, int r, int c)
+{
+    int wdt = q[3] - q[1] + 1, hgt = q[2] - q[0] + 1;
+    int dr = 2 * r - (q[0] + q[2]), dc = 2 * c - (q[1] + q[3]);
+    return (double)(hgt + wdt - abs(dr) - abs(dc));
+}
+
+/* The wedding-cake approximation of Sec. 3.1.2 (Eq. 3.2): `layers` nested
+ * windows R_0 = T, R_j = T shrunk by floor(j*h/(2*layers)) rows and
+ * floor(j*w/(2*layers)) columns on each side; a pixel of the ring
+ * R_j \ R_{j+1} (R_layers empty) gets w_j = (h + w)(j + 1)/layers, a
+ * staircase under the Manhattan pyramid above. */
+double oracle_wedding_weight(const int32_t *q, int layers, int r, int c)
+{
+    int wdt = q[3] - q[1] + 1, hgt = q[2] - q[0] + 1;
+    int ring = -1;
+    for (int j = 0; j < layers; j++) {
+        int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);
+        if (r >= q[0] + dr && r <= q[2] - dr && c >= q[1] + dc && c <= q[3] - dc) ring = j;
+    }
+    return ring < 0 ? 0.0 : (double)(hgt + wdt) * (ring + 1) / layers;
+}
+
 /* Eq. 3.1 by direct summation (the brute force of Sec. 3.1.1):
  *   H(T, b_i) = sum_{(x,y) in T} delta(Q(f(x,y)) - b_i) * w(x,y)
- * in FP64.  normalize != 0 divides every bin by sum_{T} w(x,y), the
- * normalisation step of the SWIH flow (Ch. 3 introduction).  out: n x b
- * double; an invalid window yields a row of -1.  Returns #invalid. */
-int64_t oracle_weighted_hist(const uint8_t *img, int64_t pitch, int h, int w,
-                             int b, int mode, const int32_t *wins, int64_t n,
-                             int normalize, double *out)
+ * in FP64, with w the Epanechnikov kernel (kernel 0), the Manhattan kernel
+ * (1) or the wedding-cake rings (2, `layers` nested windows).  normalize != 0
+ * divides every bin by sum_{T} w(x,y), the normalisation step of the SWIH
+ * flow (Ch. 3 introduction).  out: n x b double; an invalid window yields a
+ * row of -1.  Returns #invalid. */
+int64_t oracle_weighted_hist_k(const uint8_t *img, int64_t pitch, int h, int w,
+                               int b, int mode, const int32_t *wins, int64_t n,
+                               int kernel, int layers, int normalize, double *out)
 {
     int64_t bad = 0;
     for (int64_t i = 0; i < n; i++) {
@@ -228,7 +265,9 @@ int64_t oracle_weighted_hist(const uint8_t *img, int64_t pitch, int h, int w,
         for (int k = 0; k < b; k++) o[k] = 0.0;
         for (int r = q[0]; r <= q[2]; r++)
             for (int c = q[1]; c <= q[3]; c++) {
-                double wt = oracle_kernel_weight(q, r, c);
+                double wt = kernel == 1 ? oracle_manhattan_weight(q, r, c)
+                          : kernel == 2 ? oracle_wedding_weight(q, layers, r, c)
+                                        : oracle_kernel_weight(q, r, c);
                 int k = oracle_bin_of(img[(int64_t)r * pitch + c], b, mode);
                 if (k >= 0) o[k] += wt;
                 wsum += wt;
@@ -237,6 +276,13 @@ int64_t oracle_weighted_hist(const uint8_t *img, int64_t pitch, int h, int w,
             for (int k = 0; k < b; k++) o[k] /= wsum;
     }
     return bad;
+}
+
+int64_t oracle_weighted_hist(const uint8_t *img, int64_t pitch, int h, int w,
+                             int b, int mode, const int32_t *wins, int64_t n,
+                             int normalize, double *out)
+{
+    return oracle_weighted_hist_k(img, pitch, h, w, b, mode, wins, n, 0, 0, normalize, out);
 }
 
 /* Gradient orientation bin (Fig. 2.3, Algorithm 2): unsigned

@@ -39,6 +39,15 @@ MUTANTS = [
      [pins.test_intensity_is_floor_mean]),
     ("hog_stencil_step", "clampi(c + s, 0, w - 1)", "clampi(c + 1, 0, w - 1)",
      [pins.test_hog_stencil_replicated_borders]),
+    ("manhattan_centre", "int dr = 2 * r - (q[0] + q[2]), dc = 2 * c - (q[1] + q[3]);",
+     "int dr = 2 * r - (q[0] + q[2]), dc = 2 * c - (q[1] + q[3] + 1);",
+     [pins.test_manhattan_equals_quadrant_decomposition]),
+    ("manhattan_scale", "return (double)(hgt + wdt - abs(dr) - abs(dc));",
+     "return (double)(hgt + wdt - abs(dr) - 2 * abs(dc));",
+     [lambda: pins.test_manhattan_constant_image_closed_form((8, 8))]),
+    ("wedding_shrink_axes", "int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);",
+     "int dr = j * wdt / (2 * layers), dc = j * hgt / (2 * layers);",
+     [lambda: pins.test_wedding_cake_is_sum_of_nested_windows(3)]),
 ]
 
 

@@ -255,6 +255,148 @@ def test_weighted_equals_exact_rational_sum():
     assert out[0].tolist() == pytest.approx([float(x) for x in exact], rel=1e-14)
 
 
+# ---------------------------------------------------------------- Eq. 3.3 Manhattan kernel, Eq. 3.2 wedding cake
+
+def test_manhattan_and_wedding_hand_example(golden_dir):
+    g = json.load(open(os.path.join(golden_dir, "hand_2x3.json")))
+    img = np.array(g["image"], np.uint8)
+    m = g["manhattan"]
+    for r in range(2):
+        for c in range(3):
+            assert oracle.manhattan_weight(m["window"], r, c) == m["k_rows"][r][c]
+    assert oracle.weighted_hist(img, 2, [m["window"]], kernel=oracle.K_MANHATTAN)[0].tolist() == m["hist"]
+    assert oracle.weighted_hist(img, 2, [m["window"]], kernel=oracle.K_MANHATTAN, normalize=True)[0].tolist() == \
+        [x / m["K"] for x in m["hist"]]
+    wc = g["wedding_cake"]
+    assert oracle.weighted_hist(img, 2, [wc["window"]], kernel=oracle.K_WEDDING_CAKE,
+                                layers=wc["layers"])[0].tolist() == wc["hist"]
+
+
+def _manhattan_K(w, h):
+    """sum over a w x h window of (h + w) - |2r - (r0+r1)| - |2c - (c0+c1)|:
+    the |2i - (n-1)| over i = 0..n-1 sum to floor(n^2/2)."""
+    return (h + w) * h * w - w * (h * h // 2) - h * (w * w // 2)
+
+
+@pytest.mark.parametrize("wh", [(1, 1), (1, 5), (4, 1), (3, 2), (8, 8), (33, 17), (64, 100)])
+def test_manhattan_constant_image_closed_form(wh):
+    w, h = wh
+    img = np.full((h + 3, w + 2), 200, np.uint8)
+    out = oracle.weighted_hist(img, 8, [[1, 2, h, w + 1]], kernel=oracle.K_MANHATTAN)
+    assert out[0, 200 * 8 // 256] == _manhattan_K(w, h)
+    assert np.count_nonzero(out[0]) == 1
+
+
+def test_manhattan_equals_quadrant_decomposition():
+    """Sec. 3.1.3 / Fig. 3.4: split the window at its centre into four
+    quadrants; inside each, the weight is linear in (r, c), so each quadrant's
+    weighted histogram is a combination of plain, r-weighted and c-weighted
+    region sums -- here taken from numpy cumulative sums, not from the
+    oracle."""
+    img = synth.blob_plane(50, 61, 12)
+    B = 16
+    q = (img.astype(np.int64) * B) >> 8
+    onehot = (q[None] == np.arange(B)[:, None, None]).astype(np.int64)
+    rr, cc = np.meshgrid(np.arange(50), np.arange(61), indexing="ij")
+    planes = {k: np.cumsum(np.cumsum(onehot * wgt[None], axis=1), axis=2)
+              for k, wgt in (("n", np.ones_like(rr)), ("r", rr), ("c", cc))}
+
+    def box(plane, r0, c0, r1, c1):
+        if r1 < r0 or c1 < c0:
+            return np.zeros(B, np.int64)
+        P = planes[plane]
+        s = P[:, r1, c1].copy()
+        if r0 > 0:
+            s -= P[:, r0 - 1, c1]
+        if c0 > 0:
+            s -= P[:, r1, c0 - 1]
+        if r0 > 0 and c0 > 0:
+            s += P[:, r0 - 1, c0 - 1]
+        return s
+
+    wins = synth.rects_side_range(50, 61, 60, 1, 40, 13)
+    ref = oracle.weighted_hist(img, B, wins, kernel=oracle.K_MANHATTAN)
+    for (r0, c0, r1, c1), row in zip(wins, ref):
+        h, w, sr, sc = r1 - r0 + 1, c1 - c0 + 1, r0 + r1, c0 + c1
+        rs, cs = sr // 2, sc // 2
+        tot = np.zeros(B, np.int64)
+        for (a, b, er) in ((r0, rs, -1), (rs + 1, r1, 1)):       # rows: |2r - sr| = er * (2r - sr)
+            for (c, d, ec) in ((c0, cs, -1), (cs + 1, c1, 1)):
+                n, sr_, sc_ = box("n", a, c, b, d), box("r", a, c, b, d), box("c", a, c, b, d)
+                tot += (h + w + er * sr + ec * sc) * n - 2 * er * sr_ - 2 * ec * sc_
+        assert np.array_equal(row, tot.astype(np.float64))
+
+
+def test_manhattan_translation_and_mirror():
+    patch = synth.uniform_plane(9, 14, 8)
+    a = synth.uniform_plane(30, 40, 1)
+    b = synth.uniform_plane(30, 40, 2)
+    a[3:12, 5:19] = patch
+    b[20:29, 22:36] = patch
+    oa = oracle.weighted_hist(a, 8, [[3, 5, 11, 18]], kernel=oracle.K_MANHATTAN)
+    ob = oracle.weighted_hist(b, 8, [[20, 22, 28, 35]], kernel=oracle.K_MANHATTAN)
+    assert np.array_equal(oa, ob)
+    img = synth.uniform_plane(11, 16, 5)
+    base = oracle.weighted_hist(img, 8, [[0, 0, 10, 15]], kernel=oracle.K_MANHATTAN)
+    assert np.array_equal(oracle.weighted_hist(img[:, ::-1].copy(), 8, [[0, 0, 10, 15]], kernel=oracle.K_MANHATTAN),
+                          base)
+
+
+@pytest.mark.parametrize("layers", [1, 2, 3, 5, 8])
+def test_wedding_cake_is_sum_of_nested_windows(layers):
+    """Eq. 3.2 telescopes: sum_j w_j (H(R_j) - H(R_{j+1})) with equal steps
+    w_j - w_{j-1} = (h+w)/L is (h+w)/L times the sum of the nested windows'
+    plain histograms (np.bincount of each sub-rectangle)."""
+    img = synth.blob_plane(40, 52, 21)
+    B = 8
+    wins = synth.rects_side_range(40, 52, 40, 1, 40, 22)
+    ref = oracle.weighted_hist(img, B, wins, kernel=oracle.K_WEDDING_CAKE, layers=layers)
+    for (r0, c0, r1, c1), row in zip(wins, ref):
+        h, w = r1 - r0 + 1, c1 - c0 + 1
+        tot = np.zeros(B, np.int64)
+        for j in range(layers):
+            dr, dc = j * h // (2 * layers), j * w // (2 * layers)
+            sub = img[r0 + dr: r1 - dr + 1, c0 + dc: c1 - dc + 1].astype(np.int64)
+            tot += np.bincount(((sub * B) >> 8).ravel(), minlength=B)
+        assert row == pytest.approx(tot * (h + w) / layers, rel=1e-14)
+
+
+def test_wedding_cake_one_layer_is_plain_histogram():
+    img = synth.uniform_plane(20, 30, 4)
+    wins = synth.rects_side_range(20, 30, 30, 1, 20, 5)
+    plain = oracle.rect_hist(img, 8, wins).astype(np.float64)
+    wc = oracle.weighted_hist(img, 8, wins, kernel=oracle.K_WEDDING_CAKE, layers=1)
+    sides = (wins[:, 2] - wins[:, 0] + 1) + (wins[:, 3] - wins[:, 1] + 1)
+    assert np.array_equal(wc, plain * sides[:, None])
+
+
+def test_wedding_cake_rings_are_a_staircase():
+    """Sec. 3.1.2 / Fig. 3.3: nested windows around the centre; each pixel's
+    weight is (h+w)/L times the number of nested windows holding it, so the
+    weights never decrease towards the centre and reach h+w there; with a
+    few layers the rings approximate the Manhattan pyramid better than one
+    flat window does (normalised histograms' L1 distance)."""
+    win = [3, 4, 20, 30]
+    r0, c0, r1, c1 = win
+    h, w = r1 - r0 + 1, c1 - c0 + 1
+    for L in (1, 3, 6):
+        wt = np.array([[oracle.wedding_weight(win, L, r, c) for c in range(c0, c1 + 1)] for r in range(r0, r1 + 1)])
+        nest = np.zeros_like(wt)
+        for j in range(L):
+            dr, dc = j * h // (2 * L), j * w // (2 * L)
+            nest[dr: h - dr, dc: w - dc] += 1
+        assert np.array_equal(wt, nest * (h + w) / L)
+        mid_r, mid_c = h // 2, w // 2
+        assert np.all(np.diff(wt[mid_r, : mid_c + 1]) >= 0) and np.all(np.diff(wt[: mid_r + 1, mid_c]) >= 0)
+        assert wt[mid_r, mid_c] == h + w
+    img = synth.blob_plane(64, 64, 30)
+    wins = np.array([[0, 0, 63, 63], [5, 9, 60, 50], [10, 3, 41, 62]], np.int32)
+    man = oracle.weighted_hist(img, 16, wins, kernel=oracle.K_MANHATTAN, normalize=True)
+    err = {L: np.abs(oracle.weighted_hist(img, 16, wins, kernel=oracle.K_WEDDING_CAKE, layers=L, normalize=True)
+                     - man).sum() for L in (1, 4)}
+    assert err[4] < err[1]
+
+
 # ---------------------------------------------------------------- Eq. 3.4 moment planes
 
 @pytest.mark.parametrize("weight", [oracle.W_ONE] + list(oracle.MOMENT_WEIGHTS))
