@@ -155,15 +155,27 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
 ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, int64_t n,
                          int32_t *d_out, void *stream);
 
-/* Spatial kernels for ih_query_weighted. */
+/* Spatial kernels for ih_query_weighted (w = c1-c0+1, h = r1-r0+1). */
 typedef enum {
     /* Epanechnikov profile whose ellipse passes through the window's outer
-     * corners: k(r,c) = 1 - (2c-c0-c1)^2/(2w^2) - (2r-r0-r1)^2/(2h^2),
-     * w = c1-c0+1, h = r1-r0+1 (every pixel of the window has k > 0) */
-    IH_K_EPANECHNIKOV = 0
+     * corners: k(r,c) = 1 - (2c-c0-c1)^2/(2w^2) - (2r-r0-r1)^2/(2h^2)
+     * (every pixel of the window has k > 0) */
+    IH_K_EPANECHNIKOV = 0,
+    /* Manhattan (city-block) kernel, Eq. 3.3: k(r,c) = (h + w) -
+     * |2r-r0-r1| - |2c-c0-c1| (>= 2 inside the window), evaluated exactly
+     * from four quadrants (Sec. 3.1.3, Fig. 3.4) of the count plane and the
+     * c- and r-weighted moment planes */
+    IH_K_MANHATTAN = 1,
+    /* wedding-cake approximation, Eq. 3.2 (Sec. 3.1.2): L nested windows,
+     * window j shrunk by floor(j*h/(2L)) rows and floor(j*w/(2L)) columns
+     * per side; the ring between windows j and j+1 weighs (h + w)(j + 1)/L.
+     * Only the count plane is read; L = IH_LAYERS field of `flags`. */
+    IH_K_WEDDING_CAKE = 2
 } ih_kernel;
 
 enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
+/* flags field: wedding-cake layers L (1..64; 0 means 4) */
+#define IH_LAYERS(n) ((((uint32_t)(n)) & 0xffu) << 8)
 
 /* Spatially weighted local histograms (Eq. 3.1) of n windows on the frame's
  * weighted channel, in O(1) each from the moment planes (Sec. 3.1.3):
@@ -171,10 +183,11 @@ enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
  * remainder computed exactly in int64/uint64) converted to float with a
  * relative error below 4e-7; no step uses FP64.  d_windows: device,
  * n x 4 int32; d_out: device, n x B_w float (B_w = bins of the weighted
- * channel).  Windows must have sides <= 32768 (<= 256 when the frame's
- * moment planes are 32-bit).  Invalid windows give a row of -1 and
- * IH_EINVAL at the next ih_sync().  IH_EINVAL (host) if the frame has no
- * moment planes. */
+ * channel).  Windows must have sides <= 32768 (<= 256 for the Epanechnikov
+ * and Manhattan kernels when the frame's moment planes are 32-bit).  Invalid
+ * windows give a row of -1 and IH_EINVAL at the next ih_sync().  IH_EINVAL
+ * (host) if the frame has no moment planes, for an unknown kernel or flag,
+ * or for more than 64 layers. */
 ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_windows, int64_t n,
                             uint32_t kernel, uint32_t flags, float *d_out, void *stream);
 

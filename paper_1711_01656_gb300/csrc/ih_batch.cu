@@ -196,7 +196,8 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
     if (!frames || n < 1 || !out || !out_handles) return fail(ctx, IH_EINVAL, "ih_batch_create: bad arguments");
     if (flags & ~(uint32_t)(IH_BATCH_GRAPH | IH_BATCH_AUTOTUNE)) return fail(ctx, IH_EINVAL, "batch flags %u", flags);
     if (q && ((q->d_rects && (!q->rects || !q->d_rect_out)) || (q->d_windows && (!q->windows || !q->d_weighted_out)) ||
-              q->kernel != IH_K_EPANECHNIKOV || (q->flags & ~(uint32_t)IH_NORMALIZE)))
+              q->kernel > IH_K_WEDDING_CAKE || (q->flags & ~((uint32_t)IH_NORMALIZE | IH_LAYERS(0xff))) ||
+              weighted_layers(q->flags) > 64))
         return fail(ctx, IH_EINVAL, "ih_batch_create: bad query description");
     DevGuard dg(ctx->device);
     std::vector<FrameRec> recs(n);
@@ -311,6 +312,8 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
             j.wins = q->d_windows + 4 * woff;
             j.wout = q->d_weighted_out + wout;
             j.normalize = (q->flags & IH_NORMALIZE) ? 1 : 0;
+            j.kernel = (int32_t)q->kernel;
+            j.layers = weighted_layers(q->flags);
         }
         roff += nr;
         rout += nr * fr.B;

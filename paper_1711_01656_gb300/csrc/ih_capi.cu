@@ -511,13 +511,15 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
     FrameRec *fr = get_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (!fr->Bw) return fail(ctx, IH_EINVAL, "frame %d has no moment planes", handle);
-    if (kernel != IH_K_EPANECHNIKOV || (flags & ~(uint32_t)IH_NORMALIZE))
+    const int layers = weighted_layers(flags);
+    if (kernel > IH_K_WEDDING_CAKE || (flags & ~((uint32_t)IH_NORMALIZE | IH_LAYERS(0xff))) || layers > 64)
         return fail(ctx, IH_EINVAL, "kernel %u / flags %u", kernel, flags);
     if (n < 0 || (n > 0 && (!d_windows || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_weighted: bad arguments");
     DevGuard dg(ctx->device);
     const MomentView m{fr->bin_off[fr->wch], fr->d_mom, fr->Bw, fr->mbits == 32};
-    const int k = launch_query_weighted(fr->view, m, d_windows, n, (flags & IH_NORMALIZE) ? 1 : 0, d_out,
-                                        ctx->d_err, static_cast<cudaStream_t>(stream), prof_of(ctx));
+    const int k = launch_query_weighted(fr->view, m, d_windows, n, (int)kernel, layers,
+                                        (flags & IH_NORMALIZE) ? 1 : 0, d_out, ctx->d_err,
+                                        static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
     ctx->launches += k;
     return IH_OK;

@@ -83,6 +83,12 @@ ih_status fail(ih_ctx *ctx, ih_status s, const char *fmt, ...);
 ih_status cuda_fail(ih_ctx *ctx, cudaError_t e, const char *what);
 const Prof *prof_of(ih_ctx *ctx);
 ih_status validate(ih_ctx *ctx, const ih_frame &f);
+// Wedding-cake layers from ih_query_weighted's flags (IH_LAYERS field, 0 -> 4).
+inline int weighted_layers(uint32_t flags)
+{
+    const int l = (int)((flags >> 8) & 0xffu);
+    return l ? l : 4;
+}
 // LAYOUT_RECORD groups and planes of a frame's channels (ih_capi.cu).
 int record_plan(const int *bins, int nchan, GroupDev *sp, int max_sp, int16_t *rec_w, int *nplanes, int *words);
 // Geometry, byte sizes and bin offsets of a valid frame descriptor.

@@ -43,6 +43,9 @@ enum Layout {
                            // holds up to two 8-bin spans of the bin order
 };
 
+// Spatial kernels of the weighted queries (the values of ih_kernel).
+enum WeightKernel { IH_KERNEL_EPANECHNIKOV = 0, IH_KERNEL_MANHATTAN = 1, IH_KERNEL_WEDDING_CAKE = 2 };
+
 // Weight kinds, used by the kernel-id table and the moment planes.
 enum WeightKind { WK_ONE = 0, WK_COL = 1, WK_ROW = 2, WK_COL2 = 3, WK_ROW2 = 4 };
 
@@ -224,12 +227,13 @@ struct QueryJob {
     const int32_t *wins;
     float *wout;
     int32_t normalize;
+    int32_t kernel, layers;  // spatial kernel (WeightKernel) and wedding-cake layers
 };
 // pre_rects: rect work items (rects x groups), pre_wins: windows x Bw, per frame.
 int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const int64_t *pre_wins, int n,
                          int64_t total_rects, int64_t total_wins, int *err, cudaStream_t st, const Prof *prof);
-int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n,
-                          int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
+int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n, int kernel,
+                          int layers, int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
 // Moment plane k of [4][Bw][H][P] (int64, or uint32 when m32) -> packed Bw x H x W int64.

@@ -234,6 +234,8 @@ bool launch_tick(ih_server *s, Slot &sl, std::vector<Req *> &reqs)
         jb.wins = q->r.d_windows;
         jb.wout = q->r.d_weighted_out;
         jb.normalize = (q->r.weighted_flags & IH_NORMALIZE) ? 1 : 0;
+        jb.kernel = IH_KERNEL_EPANECHNIKOV;
+        jb.layers = 0;
         pre_r[k + 1] = pre_r[k] + nr * rect_items(q->fr.view);
         pre_w[k + 1] = pre_w[k] + nw * q->fr.Bw;
         memcpy(h + oS + sizeof(PlaneSet) * k, &sets[k], sizeof(PlaneSet));

@@ -320,14 +320,135 @@ __device__ __forceinline__ void weighted_item(const CountView &v, const MomentVi
     out[t] = s;
 }
 
+// Sums over a box on the 3 x 3 grid of corner points: P[i][j] holds the
+// plane's prefix at (y[i], x[j]) (0 outside the frame), and the box between
+// grid lines i..i+1 and j..j+1 is the four-corner difference.
+template <typename T>
+__device__ __forceinline__ T grid_box(const T (&P)[3][3], int i, int j)
+{
+    return P[i + 1][j + 1] - P[i][j + 1] - P[i + 1][j] + P[i][j];
+}
+
+template <typename T, typename L>
+__device__ __forceinline__ void grid_load(T (&P)[3][3], const int (&y)[3], const int (&x)[3], L at)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[i][j] = (y[i] >= 0 && x[j] >= 0) ? at(y[i], x[j]) : T(0);
+}
+
+// The Manhattan kernel of Sec. 3.1.3 (Eq. 3.3) and the wedding-cake rings of
+// Sec. 3.1.2 (Eq. 3.2), one thread per (window, bin).
+//
+// Manhattan: k(r,c) = (h + w) - |2r - Sr| - |2c - Sc|, Sr = r0 + r1,
+// Sc = c0 + c1.  Split at rs = floor(Sr/2), cs = floor(Sc/2) into four
+// quadrants (Fig. 3.4); in the quadrant with row sign er and column sign ec
+// (-1: top/left, where |2r - Sr| = Sr - 2r) the weight is linear,
+//   k = (h + w + er Sr + ec Sc) - 2 er r - 2 ec c,
+// so its weighted sum is (h + w + er Sr + ec Sc) N - 2 er Sum r - 2 ec Sum c
+// with N, Sum r, Sum c the quadrant's four-corner sums of the count plane and
+// the r- and c-weighted moment planes (Eq. 3.4).  The 4 quadrants share a
+// 3 x 3 grid of corner points (27 loads).  The sum is an exact integer
+// (int64; modulo 2^32 with 32-bit planes, exact as it stays below 2^32 for
+// sides <= 256); IH_NORMALIZE divides by
+//   K = (h + w) h w - w floor(h^2/2) - h floor(w^2/2).
+//
+// Wedding cake, L layers: R_j = the window shrunk by floor(j h/(2L)) rows and
+// floor(j w/(2L)) columns per side, ring j = R_j minus R_{j+1} weighs
+// (h + w)(j + 1)/L, which telescopes to (h + w)/L times the sum of the L
+// nested windows' plain counts.  IH_NORMALIZE divides by the same sum over a
+// constant image, (h + w)/L times the sum of the windows' areas.
+__device__ __forceinline__ void weighted_item_alt(const CountView &v, const MomentView &m,
+                                                  const int32_t *__restrict__ wins, int kernel, int layers,
+                                                  int normalize, float *__restrict__ out, int64_t t, int *err)
+{
+    const int64_t plane = (int64_t)v.H * v.P;
+    const int64_t mplane = (int64_t)m.Bw * plane;
+    const int64_t qi = t / m.Bw;
+    const int b = (int)(t - qi * m.Bw);
+    const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
+    const int r1 = __ldg(wins + 4 * qi + 2), c1 = __ldg(wins + 4 * qi + 3);
+    const int smax = (kernel == IH_KERNEL_MANHATTAN && m.m32) ? 256 : 32768;
+    if (!box_ok(r0, c0, r1, c1, v.H, v.W) || r1 - r0 >= smax || c1 - c0 >= smax) {
+        out[t] = -1.0f;
+        if (b == 0) atomicOr(err, 1);
+        return;
+    }
+    int64_t cbase, px;
+    count_base(v, m.bin0 + b, cbase, px);
+    const int32_t *cp = v.d + cbase;
+    const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
+    auto count_at = [&](int r, int c) -> long long { return __ldg(cp + ((int64_t)r * v.P + c) * px); };
+    if (kernel == IH_KERNEL_MANHATTAN) {
+        const long long Sr = r0 + r1, Sc = c0 + c1;
+        const int y[3] = {r0 - 1, (r0 + r1) >> 1, r1}, x[3] = {c0 - 1, (c0 + c1) >> 1, c1};
+        const int64_t mo = b * plane;
+        long long S;
+        if (m.m32) {
+            const uint32_t *m32 = reinterpret_cast<const uint32_t *>(m.m);
+            uint32_t N[3][3], C[3][3], R[3][3];
+            grid_load(N, y, x, [&](int r, int c) { return (uint32_t)count_at(r, c); });
+            grid_load(C, y, x, [&](int r, int c) { return __ldg(m32 + 0 * mplane + mo + (int64_t)r * v.P + c); });
+            grid_load(R, y, x, [&](int r, int c) { return __ldg(m32 + 1 * mplane + mo + (int64_t)r * v.P + c); });
+            uint32_t s = 0;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int er = i ? 1 : -1, ec = j ? 1 : -1;
+                    s += (uint32_t)(h + w + er * Sr + ec * Sc) * grid_box(N, i, j) -
+                         (uint32_t)(2 * er) * grid_box(R, i, j) - (uint32_t)(2 * ec) * grid_box(C, i, j);
+                }
+            S = (long long)s;
+        } else {
+            long long N[3][3], C[3][3], R[3][3];
+            grid_load(N, y, x, count_at);
+            grid_load(C, y, x, [&](int r, int c) { return (long long)__ldg(m.m + 0 * mplane + mo + (int64_t)r * v.P + c); });
+            grid_load(R, y, x, [&](int r, int c) { return (long long)__ldg(m.m + 1 * mplane + mo + (int64_t)r * v.P + c); });
+            S = 0;
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const long long er = i ? 1 : -1, ec = j ? 1 : -1;
+                    S += (h + w + er * Sr + ec * Sc) * grid_box(N, i, j) - 2 * er * grid_box(R, i, j) -
+                         2 * ec * grid_box(C, i, j);
+                }
+        }
+        if (normalize) {
+            const long long K = (h + w) * h * w - w * (h * h / 2) - h * (w * w / 2);
+            out[t] = (float)S / (float)K;
+        } else {
+            out[t] = (float)S;
+        }
+        return;
+    }
+    // wedding cake
+    long long S = 0, area = 0;
+    for (int j = 0; j < layers; ++j) {
+        const int dr = (int)(j * h / (2 * layers)), dc = (int)(j * w / (2 * layers));
+        const int a0 = r0 + dr, b0 = c0 + dc, a1 = r1 - dr, b1 = c1 - dc;
+        S += count_at(a1, b1) - (a0 > 0 ? count_at(a0 - 1, b1) : 0) - (b0 > 0 ? count_at(a1, b0 - 1) : 0) +
+             ((a0 > 0 && b0 > 0) ? count_at(a0 - 1, b0 - 1) : 0);
+        area += (long long)(a1 - a0 + 1) * (b1 - b0 + 1);
+    }
+    out[t] = normalize ? (float)S / (float)area : (float)((h + w) * S) / (float)layers;
+}
+
+template <int KERNEL>
 __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ CountView v, const MomentView m,
-                                                        const int32_t *__restrict__ wins, int64_t n,
+                                                        const int32_t *__restrict__ wins, int64_t n, int layers,
                                                         int normalize, float *__restrict__ out, int *err)
 {
     const int64_t total = n * m.Bw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x)
-        weighted_item(v, m, wins, normalize, out, t, err);
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (KERNEL == IH_KERNEL_EPANECHNIKOV)
+            weighted_item(v, m, wins, normalize, out, t, err);
+        else
+            weighted_item_alt(v, m, wins, KERNEL, layers, normalize, out, t, err);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__restrict__ jobs,
@@ -338,7 +459,10 @@ __global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__rest
          t += (int64_t)gridDim.x * blockDim.x) {
         const int f = find_job(pre, n, t);
         const QueryJob &jb = jobs[f];
-        weighted_item(*jb.v, jb.m, jb.wins, jb.normalize, jb.wout, t - pre[f], err);
+        if (jb.kernel == IH_KERNEL_EPANECHNIKOV)
+            weighted_item(*jb.v, jb.m, jb.wins, jb.normalize, jb.wout, t - pre[f], err);
+        else
+            weighted_item_alt(*jb.v, jb.m, jb.wins, jb.kernel, jb.layers, jb.normalize, jb.wout, t - pre[f], err);
     }
 }
 
@@ -385,12 +509,18 @@ int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int3
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
-int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n, int normalize,
-                          float *out, int *err, cudaStream_t st, const Prof *prof)
+int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n, int kernel,
+                          int layers, int normalize, float *out, int *err, cudaStream_t st, const Prof *prof)
 {
     if (n == 0) return 0;
     prof_mark(prof, KID_QUERY_WEIGHTED, 0, st);
-    k_query_weighted<<<grid_for(n * m.Bw), 256, 0, st>>>(v, m, wins, n, normalize, out, err);
+    const unsigned blocks = grid_for(n * m.Bw);
+    if (kernel == IH_KERNEL_MANHATTAN)
+        k_query_weighted<IH_KERNEL_MANHATTAN><<<blocks, 256, 0, st>>>(v, m, wins, n, layers, normalize, out, err);
+    else if (kernel == IH_KERNEL_WEDDING_CAKE)
+        k_query_weighted<IH_KERNEL_WEDDING_CAKE><<<blocks, 256, 0, st>>>(v, m, wins, n, layers, normalize, out, err);
+    else
+        k_query_weighted<IH_KERNEL_EPANECHNIKOV><<<blocks, 256, 0, st>>>(v, m, wins, n, layers, normalize, out, err);
     prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -19,8 +19,13 @@ IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT, IH
 IH_BIN_UNIFORM8, IH_BIN_INDEX = 0, 1
 IH_INPUT_PLANES, IH_INPUT_RGB_FEATURES = 0, 1
 IH_LAYOUT_BIN_MAJOR, IH_LAYOUT_SLAB, IH_LAYOUT_RECORD = 0, 1, 2
-IH_K_EPANECHNIKOV = 0
+IH_K_EPANECHNIKOV, IH_K_MANHATTAN, IH_K_WEDDING_CAKE = 0, 1, 2
 IH_NORMALIZE = 1
+
+
+def IH_LAYERS(n):
+    """flags field of ih_query_weighted: wedding-cake layers (1..64; 0 means 4)."""
+    return (int(n) & 0xFF) << 8
 
 STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: "IH_ECUDA",
                 5: "IH_ETIMEOUT", 6: "IH_ENOTBUILT", 7: "IH_ETOOBIG"}

@@ -156,3 +156,40 @@ def test_batch_autotune_flag(ihlib, ctx):
         ih.ih_batch_destroy(batch)
         for hdl in handles:
             ih.ih_release(ctx, hdl)
+
+
+@pytest.mark.parametrize("kernel,layers", [(1, 0), (2, 5)])
+def test_batch_other_kernels_equal_single(ihlib, ctx, kernel, layers):
+    """Batched weighted queries with the Manhattan kernel or the wedding cake
+    give exactly the single-frame queries, which match the oracle."""
+    ih = ihlib
+    sizes = [(90, 130), (33, 517), (200, 200)]
+    imgs = [synth.blob_plane(h, w, 60 + k) for k, (h, w) in enumerate(sizes)]
+    frames = [ih.Frame(torch.from_numpy(im).to(DEV)[None], [(16, 0)], weighted_channel=0, layout=k % 3)
+              for k, im in enumerate(imgs)]
+    wins = [synth.rects_side_range(h, w, 50, 1, 80, 70 + k) for k, (h, w) in enumerate(sizes)]
+    d_w = torch.from_numpy(np.concatenate(wins)).to(DEV)
+    w_out = torch.full((sum(len(x) for x in wins) * 16,), -9.0, dtype=torch.float32, device=DEV)
+    flags = ih.IH_LAYERS(layers)
+    batch, handles = ih.ih_batch_create(ctx, frames, windows=d_w, window_counts=[len(x) for x in wins],
+                                        weighted_out=w_out, kernel=kernel, flags=flags)
+    try:
+        ih.ih_batch_run(ctx, batch)
+        ih.ih_sync(ctx)
+        off = 0
+        for k, (im, hdl) in enumerate(zip(imgs, handles)):
+            n = len(wins[k])
+            single = torch.empty((n, 16), dtype=torch.float32, device=DEV)
+            ih.ih_query_weighted(ctx, hdl, torch.from_numpy(wins[k]).to(DEV), single, kernel=kernel, flags=flags)
+            ih.ih_sync(ctx)
+            assert torch.equal(w_out[off:off + n * 16].view(n, 16), single)
+            off += n * 16
+            ref = oracle.weighted_hist(im, 16, wins[k], kernel=kernel, layers=layers or 4)
+            got = single.cpu().numpy().astype(np.float64)
+            nz = ref != 0
+            assert np.array_equal(got[~nz], ref[~nz])
+            assert (np.abs(got[nz] - ref[nz]) <= 1e-5 * np.abs(ref[nz])).all()
+    finally:
+        ih.ih_batch_destroy(batch)
+        for hdl in handles:
+            ih.ih_release(ctx, hdl)

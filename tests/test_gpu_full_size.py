@@ -51,6 +51,13 @@ def test_wami_8192_full_size(ihlib):
         assert np.array_equal(r_out[torch.from_numpy(sr).to(DEV)].cpu().numpy(), oracle.rect_hist(img, B, rects[sr]))
         sw = g.choice(len(wins), 1000, replace=False)
         _assert_weighted(w_out[torch.from_numpy(sw).to(DEV)].cpu().numpy(), oracle.weighted_hist(img, B, wins[sw]))
+        # the Manhattan kernel (Eq. 3.3) and the wedding cake (Eq. 3.2) on the same windows
+        for kernel in (ih.IH_K_MANHATTAN, ih.IH_K_WEDDING_CAKE):
+            ih.ih_query_weighted(c, h, d_w, w_out, kernel=kernel)
+            ih.ih_sync(c)
+            s2 = sw[:300]
+            _assert_weighted(w_out[torch.from_numpy(s2).to(DEV)].cpu().numpy(),
+                             oracle.weighted_hist(img, B, wins[s2], kernel=kernel, layers=4))
         del r_out, w_out
         # the tensor: exact on a top-left crop (the integral histogram of a
         # top-left crop is the crop of the integral histogram), invariants on

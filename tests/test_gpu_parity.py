@@ -275,10 +275,11 @@ def test_moment_planes_exact(ihlib, ctx, h, w, bins):
     ihlib.ih_release(ctx, hdl)
 
 
-def _weighted_gpu(ihlib, ctx, hdl, wins, Bw, normalize=False):
+def _weighted_gpu(ihlib, ctx, hdl, wins, Bw, normalize=False, kernel=0, layers=0):
     d = torch.from_numpy(np.ascontiguousarray(wins, dtype=np.int32)).to(DEV)
     out = torch.empty((len(wins), Bw), dtype=torch.float32, device=DEV)
-    ihlib.ih_query_weighted(ctx, hdl, d, out, flags=ihlib.IH_NORMALIZE if normalize else 0)
+    flags = (ihlib.IH_NORMALIZE if normalize else 0) | ihlib.IH_LAYERS(layers)
+    ihlib.ih_query_weighted(ctx, hdl, d, out, kernel=kernel, flags=flags)
     ihlib.ih_sync(ctx)
     return out.cpu().numpy()
 
@@ -403,6 +404,72 @@ def test_moment_planes_u32_and_weighted(ihlib, ctx):
     # a window wider than 256 is refused on the device
     with pytest.raises(ihlib.IHError):
         _weighted_gpu(ihlib, ctx, hdl, [[0, 0, 10, 256]], bins)
+    ihlib.ih_release(ctx, hdl)
+
+
+# ---------------------------------------------------------------- Manhattan kernel (Eq. 3.3), wedding cake (Eq. 3.2)
+
+def _edge_windows(h, w):
+    return np.array([[0, 0, h - 1, w - 1], [0, 0, 0, 0], [h - 1, w - 1, h - 1, w - 1], [0, 5, 0, 60],
+                     [3, 0, 90, 0], [1, 2, 2, 3]], np.int32)
+
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_manhattan_vs_direct_sum(ihlib, ctx, normalize, layout):
+    h, w = 300, 400
+    img = synth.blob_plane(h, w, 14)
+    hdl, _ = _build(ihlib, ctx, img, [(16, 0)], weighted=0, layout=layout)
+    wins = np.concatenate([synth.rects_side_range(h, w, 1500, 1, 64, 5),
+                           synth.rects_side_range(h, w, 100, 32, 256, 6), _edge_windows(h, w)])
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, 16, normalize, kernel=ihlib.IH_K_MANHATTAN)
+    ref = oracle.weighted_hist(img, 16, wins, normalize=normalize, kernel=oracle.K_MANHATTAN)
+    _assert_weighted(got, ref)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_manhattan_32bit_moment_planes(ihlib, ctx):
+    h, w = 600, 700
+    img = synth.blob_plane(h, w, 15)
+    pix = torch.from_numpy(img).to(DEV)[None]
+    hdl, = ihlib.ih_build(ctx, ihlib.Frame(pix, [(16, 0)], weighted_channel=0, layout=1, moment_bits=32))
+    wins = np.concatenate([synth.rects_side_range(h, w, 800, 1, 256, 16),
+                           np.array([[0, 0, 255, 255], [h - 256, w - 256, h - 1, w - 1]], np.int32)])
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, 16, kernel=ihlib.IH_K_MANHATTAN)
+    _assert_weighted(got, oracle.weighted_hist(img, 16, wins, kernel=oracle.K_MANHATTAN))
+    # a side above 256 is refused with 32-bit planes
+    bad = torch.empty((1, 16), dtype=torch.float32, device=DEV)
+    ihlib.ih_query_weighted(ctx, hdl, torch.tensor([[0, 0, 300, 10]], dtype=torch.int32, device=DEV), bad,
+                            kernel=ihlib.IH_K_MANHATTAN)
+    with pytest.raises(ihlib.IHError):
+        ihlib.ih_sync(ctx)
+    assert (bad == -1).all().item()
+    ihlib.ih_release(ctx, hdl)
+
+
+@pytest.mark.parametrize("layers", [0, 1, 3, 9])
+@pytest.mark.parametrize("normalize", [False, True])
+def test_wedding_cake_vs_direct_sum(ihlib, ctx, layers, normalize):
+    h, w = 257, 333
+    planes = np.stack([synth.blob_plane(h, w, 40 + k) for k in range(2)])
+    hdl, _ = _build(ihlib, ctx, planes, [(5, 0), (12, 0)], weighted=1, layout=2)
+    wins = np.concatenate([synth.rects_side_range(h, w, 600, 1, 64, 7),
+                           synth.rects_side_range(h, w, 60, 32, 256, 8), _edge_windows(h, w)])
+    got = _weighted_gpu(ihlib, ctx, hdl, wins, 12, normalize, kernel=ihlib.IH_K_WEDDING_CAKE, layers=layers)
+    ref = oracle.weighted_hist(planes[1], 12, wins, normalize=normalize, kernel=oracle.K_WEDDING_CAKE,
+                               layers=layers or 4)
+    _assert_weighted(got, ref)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_weighted_kernel_arguments_refused(ihlib, ctx):
+    img = synth.blob_plane(20, 30, 1)
+    hdl, _ = _build(ihlib, ctx, img, [(8, 0)], weighted=0)
+    d = torch.zeros((1, 4), dtype=torch.int32, device=DEV)
+    out = torch.empty((1, 8), device=DEV)
+    for kernel, flags in [(3, 0), (0, 2), (2, ihlib.IH_LAYERS(65))]:
+        with pytest.raises(ihlib.IHError):
+            ihlib.ih_query_weighted(ctx, hdl, d, out, kernel=kernel, flags=flags)
     ihlib.ih_release(ctx, hdl)
 
 
