@@ -472,7 +472,8 @@ def wami_section(ih, dev, layout, reps=3):
     ctx = ih.ih_create(dev.index or 0, flags=ih.IH_CFG_PROFILE)
     frame = ih.Frame(pix, [(B, 0)], weighted_channel=0, layout=layout)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    t = {"build": [], "rects": [], "weighted": []}
+    t = {"build": [], "rects": [], "weighted": [], "manhattan": [], "wedding_cake": []}
+    ev += [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     for rep in range(reps + 1):
         flush.fill_(rep & 0xFF)
         ev[0].record()
@@ -482,6 +483,10 @@ def wami_section(ih, dev, layout, reps=3):
         ev[2].record()
         ih.ih_query_weighted(ctx, h, wins, w_out)
         ev[3].record()
+        ih.ih_query_weighted(ctx, h, wins, w_out, kernel=ih.IH_K_MANHATTAN)
+        ev[4].record()
+        ih.ih_query_weighted(ctx, h, wins, w_out, kernel=ih.IH_K_WEDDING_CAKE, flags=ih.IH_LAYERS(4))
+        ev[5].record()
         torch.cuda.synchronize()
         ih.ih_release(ctx, h)
         if rep == 0:
@@ -490,6 +495,8 @@ def wami_section(ih, dev, layout, reps=3):
         t["build"].append(ev[0].elapsed_time(ev[1]))
         t["rects"].append(ev[1].elapsed_time(ev[2]))
         t["weighted"].append(ev[2].elapsed_time(ev[3]))
+        t["manhattan"].append(ev[3].elapsed_time(ev[4]))
+        t["wedding_cake"].append(ev[4].elapsed_time(ev[5]))
     torch.cuda.synchronize()
     prof = ih.ih_profile_read(ctx, reset=True)
     ih.ih_destroy(ctx)
@@ -505,13 +512,17 @@ def wami_section(ih, dev, layout, reps=3):
         kern[name] = round(tot / n, 3)
     tiles_ms = kern.get("tiles/count+moments")
     out = {"workload": "WAMI 8192x8192 blobs+noise, 32 bins, int64 moment planes, 1,000,000 rects (side 16..256), "
-                       "100,000 weighted windows (side 32..256)",
+                       "100,000 weighted windows (side 32..256) with the Epanechnikov kernel, the Manhattan "
+                       "kernel (Eq. 3.3) and the 4-layer wedding cake (Eq. 3.2)",
            "layout": [k for k, v in LAYOUTS.items() if v[0] == layout][0],
            "build_ms": round(ms["build"], 3), "rect_queries_ms": round(ms["rects"], 3),
            "weighted_queries_ms": round(ms["weighted"], 3),
            "build_cells_per_s": cells / (ms["build"] / 1e3),
            "build_GBs": round((count_bytes + moment_bytes) / (ms["build"] / 1e3) / 1e9, 1),
+           "manhattan_queries_ms": round(ms["manhattan"], 3), "wedding_cake_queries_ms": round(ms["wedding_cake"], 3),
            "rects_per_s": 1e6 / (ms["rects"] / 1e3), "windows_per_s": 1e5 / (ms["weighted"] / 1e3),
+           "manhattan_windows_per_s": 1e5 / (ms["manhattan"] / 1e3),
+           "wedding_cake_windows_per_s": 1e5 / (ms["wedding_cake"] / 1e3),
            "kernel_ms": kern}
     if tiles_ms:
         gbs = (count_bytes + moment_bytes) / (tiles_ms / 1e3) / 1e9

@@ -70,6 +70,8 @@ def _bind(path: str):
     lib.oracle_manhattan_weight.restype = ctypes.c_double
     lib.oracle_wedding_weight.argtypes = [p, i32, i32, i32]
     lib.oracle_wedding_weight.restype = ctypes.c_double
+    lib.oracle_match_window.argtypes = [p, i64, i32, i32, i32, i32, p, i32, i32, i32, i32, i32, i32, p]
+    lib.oracle_match_window.restype = i64
     lib.oracle_orientation_bin.argtypes = [i32, i32, i32]
     lib.oracle_orientation_bin.restype = i32
     lib.oracle_features.argtypes = [p, i32, i32, p]
@@ -155,6 +157,21 @@ def weighted_hist(img, bins: int, windows, mode: int = BIN_UNIFORM8,
     else:
         _load().oracle_weighted_hist_k(a.ctypes.data, w, h, w, bins, mode, q.ctypes.data, q.shape[0],
                                        int(kernel), int(layers), int(bool(normalize)), out.ctypes.data)
+    return out
+
+
+def match_window(img, bins: int, target, win_h: int, win_w: int, search, mode: int = BIN_UNIFORM8) -> np.ndarray:
+    """City-block distance (Eq. 2.22, p = 1) between `target` (bins counts)
+    and the histogram of every win_h x win_w window whose top-left pixel lies
+    in search = (sr0, sc0, sr1, sc1); returns an int64 map of the placements."""
+    a = _plane(img)
+    h, w = a.shape
+    t = np.ascontiguousarray(target, dtype=np.int32).reshape(bins)
+    sr0, sc0, sr1, sc1 = (int(x) for x in search)
+    out = np.empty((sr1 - sr0 + 1, sc1 - sc0 + 1), dtype=np.int64)
+    if _load().oracle_match_window(a.ctypes.data, w, h, w, bins, mode, t.ctypes.data, int(win_h), int(win_w),
+                                   sr0, sc0, sr1, sc1, out.ctypes.data) < 0:
+        raise ValueError("a placement leaves the image")
     return out
 
 

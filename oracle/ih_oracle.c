@@ -21,6 +21,8 @@
  *     direct summation (the brute force)          Eq. 3.1, Sec. 3.1.1
  *     with the Manhattan kernel                   Eq. 3.3, Sec. 3.1.3
  *     or the wedding-cake rings                   Eq. 3.2, Sec. 3.1.2
+ *   - sliding-window histogram matching by the
+ *     city-block distance of every placement      Eq. 2.22 (p = 1), Sec. 2.4.3
  *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
  *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
  *
@@ -201,6 +203,37 @@ int64_t oracle_rect_hist(const uint8_t *img, int64_t pitch, int h, int w, int b,
             }
     }
     return bad;
+}
+
+/* Sliding-window histogram matching (Sec. 2.4.3): for every placement of a
+ * wh x ww window whose top-left pixel (r, c) lies in [sr0, sr1] x
+ * [sc0, sc1], the city-block distance of Eq. 2.22 (p = 1),
+ *   sum_i |H_window(i) - target(i)|,
+ * with the window histogram counted pixel by pixel.  out: row-major
+ * (sr1-sr0+1) x (sc1-sc0+1) int64.  Returns -1 if a placement leaves the
+ * image, else 0. */
+int64_t oracle_match_window(const uint8_t *img, int64_t pitch, int h, int w, int b, int mode,
+                            const int32_t *target, int wh, int ww, int sr0, int sc0, int sr1,
+                            int sc1, int64_t *out)
+{
+    if (sr0 < 0 || sc0 < 0 || sr1 < sr0 || sc1 < sc0 || sr1 + wh > h || sc1 + ww > w || wh < 1 || ww < 1)
+        return -1;
+    int64_t *hist = (int64_t *)malloc(sizeof(int64_t) * (size_t)b);
+    int64_t k = 0;
+    for (int r = sr0; r <= sr1; r++)
+        for (int c = sc0; c <= sc1; c++) {
+            for (int i = 0; i < b; i++) hist[i] = 0;
+            for (int y = r; y < r + wh; y++)
+                for (int x = c; x < c + ww; x++) {
+                    int i = oracle_bin_of(img[(int64_t)y * pitch + x], b, mode);
+                    if (i >= 0) hist[i]++;
+                }
+            int64_t d = 0;
+            for (int i = 0; i < b; i++) d += hist[i] > target[i] ? hist[i] - target[i] : target[i] - hist[i];
+            out[k++] = d;
+        }
+    free(hist);
+    return 0;
 }
 
 /* The spatial kernel of Eq. 3.1 for window [r0,r1] x [c0,c1] (Epanechnikov

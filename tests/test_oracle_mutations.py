@@ -45,6 +45,8 @@ MUTANTS = [
     ("manhattan_scale", "return (double)(hgt + wdt - abs(dr) - abs(dc));",
      "return (double)(hgt + wdt - abs(dr) - 2 * abs(dc));",
      [lambda: pins.test_manhattan_constant_image_closed_form((8, 8))]),
+    ("match_window_extent", "for (int x = c; x < c + ww; x++) {", "for (int x = c; x <= c + ww; x++) {",
+     [lambda: pins.test_match_window_equals_cumsum_boxes(3, 5)]),
     ("wedding_shrink_axes", "int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);",
      "int dr = j * wdt / (2 * layers), dc = j * hgt / (2 * layers);",
      [lambda: pins.test_wedding_cake_is_sum_of_nested_windows(3)]),

@@ -397,6 +397,45 @@ def test_wedding_cake_rings_are_a_staircase():
     assert err[4] < err[1]
 
 
+# ---------------------------------------------------------------- Eq. 2.22 sliding-window matching
+
+def _box_hist_numpy(img, bins, wh, ww):
+    """Every placement's window histogram from 2-D cumulative sums of the
+    one-hot (numpy, independent of the oracle): [bins, h-wh+1, w-ww+1]."""
+    q = (img.astype(np.int64) * bins) >> 8
+    onehot = (q[None] == np.arange(bins)[:, None, None]).astype(np.int64)
+    P = np.zeros((bins, img.shape[0] + 1, img.shape[1] + 1), np.int64)
+    P[:, 1:, 1:] = onehot.cumsum(1).cumsum(2)
+    return P[:, wh:, ww:] - P[:, :-wh, ww:] - P[:, wh:, :-ww] + P[:, :-wh, :-ww]
+
+
+@pytest.mark.parametrize("wh,ww", [(1, 1), (3, 5), (8, 8), (12, 4)])
+def test_match_window_equals_cumsum_boxes(wh, ww):
+    img = synth.blob_plane(30, 41, 50)
+    B = 8
+    target = np.array([5, 0, 3, 9, 1, 0, 2, 7], np.int32)
+    search = (2, 3, 30 - wh, 41 - ww)
+    got = oracle.match_window(img, B, target, wh, ww, search)
+    boxes = _box_hist_numpy(img, B, wh, ww)[:, search[0]:search[2] + 1, search[1]:search[3] + 1]
+    assert np.array_equal(got, np.abs(boxes - target[:, None, None]).sum(0))
+
+
+def test_match_window_zero_at_own_placement_and_constant_image():
+    img = synth.uniform_plane(25, 30, 51)
+    B = 16
+    r, c, wh, ww = 7, 11, 6, 9
+    target = np.bincount((img[r:r + wh, c:c + ww].astype(np.int64) * B >> 8).ravel(), minlength=B).astype(np.int32)
+    got = oracle.match_window(img, B, target, wh, ww, (0, 0, 25 - wh, 30 - ww))
+    assert got[r, c] == 0 and (got >= 0).all()
+    const = np.full((20, 20), 90, np.uint8)
+    t = np.arange(B, dtype=np.int32)
+    d = oracle.match_window(const, B, t, 4, 5, (0, 0, 16, 15))
+    k = 90 * B >> 8
+    assert (d == t.sum() - t[k] + abs(20 - t[k])).all()
+    with pytest.raises(ValueError):
+        oracle.match_window(const, B, t, 4, 5, (0, 0, 17, 15))
+
+
 # ---------------------------------------------------------------- Eq. 3.4 moment planes
 
 @pytest.mark.parametrize("weight", [oracle.W_ONE] + list(oracle.MOMENT_WEIGHTS))
