@@ -191,6 +191,19 @@ enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
 ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_windows, int64_t n,
                             uint32_t kernel, uint32_t flags, float *d_out, void *stream);
 
+/* Sliding-window histogram matching (Sec. 2.4.3): for every placement of a
+ * win_h x win_w window whose top-left pixel (r, c) lies in the search region
+ * search = (sr0, sc0, sr1, sc1) (host, 4 int32, inclusive), the city-block
+ * distance of Eq. 2.22 with p = 1 between the window's histogram over the
+ * tensor bins bin0 .. bin0 + nbins - 1 (four corners each, Eq. 2.16) and
+ * d_target (device, nbins int32):
+ *   d_out[(r - sr0) * (sc1 - sc0 + 1) + (c - sc0)] = sum_i |H(i) - target(i)|
+ * (device, int32).  IH_EINVAL (host) if a placement leaves the frame or the
+ * bin range is empty or leaves the frame's bins. */
+ih_status ih_match_window(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbins, const int32_t *d_target,
+                          int32_t win_h, int32_t win_w, const int32_t *search, int32_t *d_out,
+                          void *stream);
+
 /* Frees every tensor the context owns and the context.  NULL-safe.
  * Synchronises the device first. */
 ih_status ih_destroy(ih_ctx *ctx);

@@ -77,7 +77,7 @@ const char *kernel_name(int kid)
     static const char *names[KID_COUNT] = {"features",      "tile_sums/count", "tile_sums/weighted",
                                            "carry_scan",    "tiles/count",     "tiles/moments",
                                            "query_rects",   "query_weighted",  "export",
-                                           "tiles/count+moments"};
+                                           "tiles/count+moments", "match_window"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -521,6 +521,27 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
                                         (flags & IH_NORMALIZE) ? 1 : 0, d_out, ctx->d_err,
                                         static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_match_window(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbins, const int32_t *d_target,
+                          int32_t win_h, int32_t win_w, const int32_t *search, int32_t *d_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    if (!search || !d_target || !d_out) return fail(ctx, IH_EINVAL, "ih_match_window: NULL argument");
+    const int sr0 = search[0], sc0 = search[1], sr1 = search[2], sc1 = search[3];
+    if (nbins < 1 || bin0 < 0 || bin0 + nbins > fr->B || win_h < 1 || win_w < 1 || sr0 < 0 || sc0 < 0 ||
+        sr1 < sr0 || sc1 < sc0 || (int64_t)sr1 + win_h > fr->H || (int64_t)sc1 + win_w > fr->W)
+        return fail(ctx, IH_EINVAL, "ih_match_window: bins [%d, %d) / window %dx%d / search (%d,%d)-(%d,%d)",
+                    bin0, bin0 + nbins, win_h, win_w, sr0, sc0, sr1, sc1);
+    DevGuard dg(ctx->device);
+    const int k = launch_match_window(fr->view, bin0, nbins, d_target, win_h, win_w, sr0, sc0, sr1, sc1, d_out,
+                                      static_cast<cudaStream_t>(stream), prof_of(ctx));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "match launch");
     ctx->launches += k;
     return IH_OK;
 }

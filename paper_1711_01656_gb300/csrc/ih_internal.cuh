@@ -61,7 +61,8 @@ enum KernelId {
     KID_QUERY_WEIGHTED = 7,
     KID_EXPORT = 8,
     KID_TILES_BOTH = 9,  // count and moment tiles of one frame in one launch
-    KID_COUNT = 10
+    KID_MATCH = 10,
+    KID_COUNT = 11
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -234,6 +235,10 @@ int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const i
                          int64_t total_rects, int64_t total_wins, int *err, cudaStream_t st, const Prof *prof);
 int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n, int kernel,
                           int layers, int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
+// Sliding-window city-block distances (Eq. 2.22, p = 1) over bins
+// [bin0, bin0 + nbins) for placements [sr0, sr1] x [sc0, sc1] of a wh x ww window.
+int launch_match_window(const CountView &v, int bin0, int nbins, const int32_t *target, int wh, int ww, int sr0,
+                        int sc0, int sr1, int sc1, int32_t *out, cudaStream_t st, const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
 // Moment plane k of [4][Bw][H][P] (int64, or uint32 when m32) -> packed Bw x H x W int64.

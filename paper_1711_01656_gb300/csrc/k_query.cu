@@ -466,6 +466,48 @@ __global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__rest
     }
 }
 
+// Sliding-window matching (Sec. 2.4.3, Eq. 2.22 with p = 1): one thread per
+// placement; consecutive threads take consecutive columns, so each corner
+// load of a bin is coalesced across the warp.  The bin tables and the target
+// histogram sit in shared memory.
+__global__ void __launch_bounds__(256) k_match_window(const __grid_constant__ CountView v, int bin0, int nbins,
+                                                      const int32_t *__restrict__ target, int wh, int ww, int sr0,
+                                                      int sc0, int sr1, int sc1, int32_t *__restrict__ out)
+{
+    __shared__ int64_t s_base[kMaxBins];  // element offset of bin (bin0 + i) at pixel (0, 0)
+    __shared__ int s_px[kMaxBins], s_t[kMaxBins];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+        int64_t base, px;
+        count_base(v, bin0 + i, base, px);
+        s_base[i] = base;
+        s_px[i] = (int)px;
+        s_t[i] = __ldg(target + i);
+    }
+    __syncthreads();
+    const int nc = sc1 - sc0 + 1;
+    const int64_t total = (int64_t)(sr1 - sr0 + 1) * nc;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = sr0 + (int)(t / nc), c = sc0 + (int)(t % nc);
+        const int r1 = r + wh - 1, c1 = c + ww - 1;
+        const int64_t a = (int64_t)r1 * v.P + c1, bq = (int64_t)(r - 1) * v.P + c1;
+        const int64_t cq = (int64_t)r1 * v.P + (c - 1), dq = (int64_t)(r - 1) * v.P + (c - 1);
+        const bool top = r > 0, left = c > 0;
+        int32_t d = 0;
+        for (int i = 0; i < nbins; ++i) {
+            const int32_t *p = v.d + s_base[i];
+            const int64_t px = s_px[i];
+            int32_t n = __ldg(p + a * px);
+            if (top) n -= __ldg(p + bq * px);
+            if (left) n -= __ldg(p + cq * px);
+            if (top && left) n += __ldg(p + dq * px);
+            const int32_t e = n - s_t[i];
+            d += e < 0 ? -e : e;
+        }
+        out[t] = d;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_export(const __grid_constant__ CountView v, int32_t *__restrict__ dst)
 {
     const int64_t total = (int64_t)v.B * v.H * v.W;
@@ -550,6 +592,16 @@ int launch_export_moments(const void *m, int m32, int Bw, int H, int W, int64_t 
     prof_mark(prof, KID_EXPORT, 0, st);
     k_export_moments<<<grid_for((int64_t)Bw * H * W), 256, 0, st>>>(m, m32, Bw, H, W, P, k, dst);
     prof_mark(prof, KID_EXPORT, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_match_window(const CountView &v, int bin0, int nbins, const int32_t *target, int wh, int ww, int sr0,
+                        int sc0, int sr1, int sc1, int32_t *out, cudaStream_t st, const Prof *prof)
+{
+    const int64_t total = (int64_t)(sr1 - sr0 + 1) * (sc1 - sc0 + 1);
+    prof_mark(prof, KID_MATCH, 0, st);
+    k_match_window<<<grid_for(total), 256, 0, st>>>(v, bin0, nbins, target, wh, ww, sr0, sc0, sr1, sc1, out);
+    prof_mark(prof, KID_MATCH, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

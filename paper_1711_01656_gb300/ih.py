@@ -35,7 +35,8 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_release", "ih_sync", "ih_info", "ih_export", "ih_export_moments", "ih_features",
              "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_batch_create", "ih_batch_run",
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
-             "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static")
+             "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
+             "ih_match_window")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -118,6 +119,7 @@ def load_library(path: str = LIB_PATH):
             "ih_build": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(i32), p], i32),
             "ih_query_rects": ([p, i32, p, i64, p, p], i32),
             "ih_query_weighted": ([p, i32, p, i64, u32, u32, p, p], i32),
+            "ih_match_window": ([p, i32, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_destroy": ([p], i32),
             "ih_release": ([p, i32, p], i32),
             "ih_sync": ([p, p], i32),
@@ -230,6 +232,17 @@ def ih_query_rects(ctx, handle, rects, out, stream=None):
     """rects: (n, 4) int32 CUDA tensor; out: (n, B) int32 CUDA tensor."""
     n = 0 if rects is None else rects.shape[0]
     _check(ctx, load_library().ih_query_rects(ctx, int(handle), _ptr(rects), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_match_window(ctx, handle, bin0, nbins, target, win_h, win_w, search, out, stream=None):
+    """City-block distance map (Eq. 2.22, p = 1) of every win_h x win_w window
+    with its top-left pixel in search = (sr0, sc0, sr1, sc1) against `target`
+    (nbins int32 CUDA tensor) over bins bin0..bin0+nbins-1; out: int32 CUDA
+    tensor of (sr1-sr0+1) x (sc1-sc0+1)."""
+    s = (ctypes.c_int32 * 4)(*[int(x) for x in search])
+    _check(ctx, load_library().ih_match_window(ctx, int(handle), int(bin0), int(nbins), _ptr(target), int(win_h),
+                                               int(win_w), s, _ptr(out), _stream(stream)))
     return out
 
 

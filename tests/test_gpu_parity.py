@@ -473,6 +473,44 @@ def test_weighted_kernel_arguments_refused(ihlib, ctx):
     ihlib.ih_release(ctx, hdl)
 
 
+# ---------------------------------------------------------------- sliding-window matching (Eq. 2.22)
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_match_window_vs_oracle(ihlib, ctx, layout):
+    h, w = 120, 170
+    planes = np.stack([synth.blob_plane(h, w, 80), synth.blob_plane(h, w, 81)])
+    chans = [(16, 0), (9, 0)]
+    hdl, _ = _build(ihlib, ctx, planes, chans, layout=layout)
+    wh, ww = 17, 23
+    search = (5, 7, 5 + 60, 7 + 90)
+    g = np.random.Generator(np.random.PCG64(9))
+    t = g.integers(0, 30, size=25).astype(np.int32)
+    ref0 = oracle.match_window(planes[0], 16, t[:16], wh, ww, search)
+    ref1 = oracle.match_window(planes[1], 9, t[16:], wh, ww, search)
+    for bin0, nbins, ref in ((0, 16, ref0), (16, 9, ref1), (0, 25, ref0 + ref1)):
+        out = torch.full(ref.shape, -3, dtype=torch.int32, device=DEV)
+        ihlib.ih_match_window(ctx, hdl, bin0, nbins, torch.from_numpy(t[bin0:bin0 + nbins].copy()).to(DEV), wh, ww,
+                              search, out)
+        ihlib.ih_sync(ctx)
+        assert np.array_equal(out.cpu().numpy(), ref), (bin0, nbins)
+    # one placement covering the whole frame; a target equal to the window's
+    # own histogram gives 0
+    own = oracle.rect_hist(planes[0], 16, [[30, 40, 30 + wh - 1, 40 + ww - 1]])[0]
+    one = torch.empty((1, 1), dtype=torch.int32, device=DEV)
+    ihlib.ih_match_window(ctx, hdl, 0, 16, torch.from_numpy(own).to(DEV), wh, ww, (30, 40, 30, 40), one)
+    full = torch.empty((1, 1), dtype=torch.int32, device=DEV)
+    ihlib.ih_match_window(ctx, hdl, 0, 16, torch.from_numpy(t[:16].copy()).to(DEV), h, w, (0, 0, 0, 0), full)
+    ihlib.ih_sync(ctx)
+    assert one.item() == 0
+    assert full.item() == int(oracle.match_window(planes[0], 16, t[:16], h, w, (0, 0, 0, 0))[0, 0])
+    for bad in ((0, 0, h - wh + 1, 0), (0, -1, 0, 0)):
+        with pytest.raises(ihlib.IHError):
+            ihlib.ih_match_window(ctx, hdl, 0, 16, torch.from_numpy(t[:16].copy()).to(DEV), wh, ww, bad, out)
+    with pytest.raises(ihlib.IHError):
+        ihlib.ih_match_window(ctx, hdl, 20, 6, torch.from_numpy(t[:6].copy()).to(DEV), wh, ww, search, out)
+    ihlib.ih_release(ctx, hdl)
+
+
 # ---------------------------------------------------------------- record layout
 
 
