@@ -398,12 +398,14 @@ def run_engine(args):
                    "gbs": round(algorithmic_bytes(k, B, Bw, N_RECTS, N_WINDOWS) / (v[1] / v[0] / 1e3) / 1e9, 1)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    batched = served = wami = plain = None
+    batched = served = wami = plain = match = None
     sections = world == 1  # the side workloads run once, on a single GPU
     if sections and not args.no_wami:
         wami = wami_section(ih, dev, LAYOUTS[args.layout][0])
     if sections and not args.no_plain:
         plain = plain_section(ih, dev)
+    if sections and not args.no_match:
+        match = match_section(ih, dev, LAYOUTS[args.layout][0])
     if sections and not args.no_batched:
         # the batch and the serving loop have no rectangle queries: the slab
         # layout (no padding, one channel per group) suits them better
@@ -436,6 +438,7 @@ def run_engine(args):
             "served": served,
             "wami": wami,
             "plain": plain,
+            "match": match,
         }
         print(json.dumps(line))
     ih.ih_destroy(ctx)
@@ -529,6 +532,53 @@ def wami_section(ih, dev, layout, reps=3):
         out["tiles_roofline"] = {"bound": "hbm", "kernel": "tiles/count+moments", "achieved": round(gbs, 1),
                                  "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
     return out
+
+
+def match_section(ih, dev, layout, runs=20):
+    """Sliding-window histogram matching (Sec. 2.4.3, Eq. 2.22 with p = 1) on
+    the FMV frame: a 64 x 64 target window's 91-bin histogram against every
+    placement in a 256 x 256 search region (65,536 placements), and the same
+    over the whole frame (1017 x 1857 placements) on the intensity bins."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    rgb = torch.from_numpy(synth.blob_rgb(H, W, synth.config_seed(2))).to(dev)
+    ctx = ih.ih_create(dev.index or 0)
+    h, = ih.ih_build(ctx, ih.Frame(rgb, synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES, layout=layout))
+    B = total_bins()
+    wh = ww = 64
+    target = torch.empty((1, B), dtype=torch.int32, device=dev)
+    ih.ih_query_rects(ctx, h, torch.tensor([[500, 900, 500 + wh - 1, 900 + ww - 1]], dtype=torch.int32,
+                                           device=dev), target)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(runs):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / runs
+
+    local = (372, 772, 372 + 255, 772 + 255)
+    out_l = torch.empty((256, 256), dtype=torch.int32, device=dev)
+    ms_l = timed(lambda: ih.ih_match_window(ctx, h, 0, B, target.view(-1), wh, ww, local, out_l))
+    full = (0, 0, H - wh, W - ww)
+    out_f = torch.empty((H - wh + 1, W - ww + 1), dtype=torch.int32, device=dev)
+    t_int = target.view(-1)[48:64].contiguous()  # intensity: channel 3, bins 48..63
+    ms_f = timed(lambda: ih.ih_match_window(ctx, h, 48, 16, t_int, wh, ww, full, out_f))
+    best = int(out_l.view(-1).argmin().item())
+    ih.ih_release(ctx, h)
+    ih.ih_destroy(ctx)
+    n_l, n_f = 256 * 256, (H - wh + 1) * (W - ww + 1)
+    return {"workload": "FMV frame, 64x64 window: 91-bin match over 256x256 placements; 16-bin intensity match "
+                        "over all %d placements" % n_f,
+            "local_ms": round(ms_l, 4), "local_placements_per_s": n_l / (ms_l / 1e3),
+            "local_bin_windows_per_s": n_l * B / (ms_l / 1e3),
+            "full_frame_ms": round(ms_f, 4), "full_frame_placements_per_s": n_f / (ms_f / 1e3),
+            "best_placement_found": [local[0] + best // 256, local[1] + best % 256], "target_at": [500, 900]}
 
 
 def plain_section(ih, dev, runs=50):
@@ -737,6 +787,7 @@ def main(argv=None):
     ap.add_argument("--no-served", action="store_true", help="skip the serving-loop comparison")
     ap.add_argument("--no-wami", action="store_true", help="skip the 8192x8192 wide-area frame")
     ap.add_argument("--no-plain", action="store_true", help="skip the 640x480 plain frame")
+    ap.add_argument("--no-match", action="store_true", help="skip the sliding-window matching maps")
     ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":

@@ -72,6 +72,8 @@ def _bind(path: str):
     lib.oracle_wedding_weight.restype = ctypes.c_double
     lib.oracle_match_window.argtypes = [p, i64, i32, i32, i32, i32, p, i32, i32, i32, i32, i32, i32, p]
     lib.oracle_match_window.restype = i64
+    lib.oracle_local_median.argtypes = [p, i32, i32, i32, i32, i32, i32, i32, p]
+    lib.oracle_local_median.restype = None
     lib.oracle_orientation_bin.argtypes = [i32, i32, i32]
     lib.oracle_orientation_bin.restype = i32
     lib.oracle_features.argtypes = [p, i32, i32, p]
@@ -172,6 +174,18 @@ def match_window(img, bins: int, target, win_h: int, win_w: int, search, mode: i
     if _load().oracle_match_window(a.ctypes.data, w, h, w, bins, mode, t.ctypes.data, int(win_h), int(win_w),
                                    sr0, sc0, sr1, sc1, out.ctypes.data) < 0:
         raise ValueError("a placement leaves the image")
+    return out
+
+
+def local_median(frames, bins: int, m: int, n: int, mode: int = BIN_UNIFORM8) -> np.ndarray:
+    """Per-pixel lower-median bin of the m x n box (clipped at the border) over
+    all frames (Algorithm 4); frames: (nf, h, w) or (h, w) uint8; int32 map."""
+    a = np.ascontiguousarray(frames, dtype=np.uint8)
+    if a.ndim == 2:
+        a = a[None]
+    nf, h, w = a.shape
+    out = np.empty((h, w), dtype=np.int32)
+    _load().oracle_local_median(a.ctypes.data, nf, h, w, bins, mode, int(m), int(n), out.ctypes.data)
     return out
 
 

@@ -23,6 +23,8 @@
  *     or the wedding-cake rings                   Eq. 3.2, Sec. 3.1.2
  *   - sliding-window histogram matching by the
  *     city-block distance of every placement      Eq. 2.22 (p = 1), Sec. 2.4.3
+ *   - spatio-temporal median by sorting the box's
+ *     quantised values over the frames             Algorithm 4, Sec. 4.1.1
  *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
  *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
  *
@@ -43,6 +45,9 @@
  *     the normalisation open); the wedding-cake windows shrink by
  *     floor(j*h/(2L)), floor(j*w/(2L)) per side and ring j weighs
  *     (h + w)(j + 1)/L (the thesis leaves the ring sizes and weights open);
+ *   - the median of Algorithm 4 is the lower median bin of the box's
+ *     quantised values, the box clipped at the frame border (the thesis
+ *     leaves both open);
  *   - intensity rounds down; gradient orientation is unsigned, in
  *     [0,180) degrees, 9 bins of 20 degrees, central differences at step
  *     s with replicated borders, (0,0) -> bin 0.
@@ -234,6 +239,43 @@ int64_t oracle_match_window(const uint8_t *img, int64_t pitch, int h, int w, int
         }
     free(hist);
     return 0;
+}
+
+static int cmp_int(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+/* Spatio-temporal median (Sec. 4.1.1, Algorithm 4): for every pixel (r, c),
+ * the quantised values of the nf frames (`frames`: nf planes of h x w) over
+ * the m x n box of rows r - floor(m/2) .. r + ceil(m/2) - 1 and columns
+ * c - floor(n/2) .. c + ceil(n/2) - 1, clipped to the frame, are sorted and
+ * the element of rank ceil(N/2) (the lower median of the N values) is the
+ * pixel's median bin; a value that falls in no bin is left out.  out: h x w
+ * int32, -1 where the box holds no binned value. */
+void oracle_local_median(const uint8_t *frames, int nf, int h, int w, int b, int mode, int m, int n,
+                         int32_t *out)
+{
+    int *vals = (int *)malloc(sizeof(int) * (size_t)nf * m * n);
+    for (int r = 0; r < h; r++)
+        for (int c = 0; c < w; c++) {
+            int cnt = 0;
+            for (int f = 0; f < nf; f++)
+                for (int y = r - m / 2; y <= r + (m + 1) / 2 - 1; y++)
+                    for (int x = c - n / 2; x <= c + (n + 1) / 2 - 1; x++) {
+                        if (y < 0 || y >= h || x < 0 || x >= w) continue;
+                        int k = oracle_bin_of(frames[((int64_t)f * h + y) * w + x], b, mode);
+                        if (k >= 0) vals[cnt++] = k;
+                    }
+            if (cnt == 0) {
+                out[(int64_t)r * w + c] = -1;
+                continue;
+            }
+            qsort(vals, (size_t)cnt, sizeof(int), cmp_int);
+            out[(int64_t)r * w + c] = vals[(cnt + 1) / 2 - 1];
+        }
+    free(vals);
 }
 
 /* The spatial kernel of Eq. 3.1 for window [r0,r1] x [c0,c1] (Epanechnikov

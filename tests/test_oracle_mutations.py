@@ -47,6 +47,10 @@ MUTANTS = [
      [lambda: pins.test_manhattan_constant_image_closed_form((8, 8))]),
     ("match_window_extent", "for (int x = c; x < c + ww; x++) {", "for (int x = c; x <= c + ww; x++) {",
      [lambda: pins.test_match_window_equals_cumsum_boxes(3, 5)]),
+    ("median_rank", "vals[(cnt + 1) / 2 - 1]", "vals[cnt / 2]",
+     [lambda: pins.test_local_median_equals_counting(5, 4, 2)]),
+    ("median_box_rows", "y <= r + (m + 1) / 2 - 1", "y <= r + m / 2",
+     [lambda: pins.test_local_median_equals_counting(5, 4, 2)]),
     ("wedding_shrink_axes", "int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);",
      "int dr = j * wdt / (2 * layers), dc = j * hgt / (2 * layers);",
      [lambda: pins.test_wedding_cake_is_sum_of_nested_windows(3)]),

@@ -436,6 +436,42 @@ def test_match_window_zero_at_own_placement_and_constant_image():
         oracle.match_window(const, B, t, 4, 5, (0, 0, 17, 15))
 
 
+# ---------------------------------------------------------------- Algorithm 4 spatio-temporal median
+
+def _median_by_counting(frames, bins, m, n):
+    """Lower median bin per pixel from per-bin counts and their running sum
+    (the histogram route), not by sorting."""
+    nf, h, w = frames.shape
+    q = (frames.astype(np.int64) * bins) >> 8
+    out = np.empty((h, w), np.int32)
+    for r in range(h):
+        for c in range(w):
+            box = q[:, max(0, r - m // 2): r + (m + 1) // 2, max(0, c - n // 2): c + (n + 1) // 2]
+            cnt = np.bincount(box.ravel(), minlength=bins)
+            out[r, c] = int(np.searchsorted(np.cumsum(cnt), (box.size + 1) // 2))
+    return out
+
+
+@pytest.mark.parametrize("nf,m,n", [(1, 1, 1), (1, 3, 3), (3, 3, 5), (5, 4, 2), (4, 6, 6)])
+def test_local_median_equals_counting(nf, m, n):
+    frames = np.stack([synth.blob_plane(17, 23, 60 + k) for k in range(nf)])
+    assert np.array_equal(oracle.local_median(frames, 16, m, n), _median_by_counting(frames, 16, m, n))
+
+
+def test_local_median_special_cases():
+    img = synth.uniform_plane(12, 15, 61)
+    assert np.array_equal(oracle.local_median(img, 8, 1, 1), (img.astype(np.int32) * 8) >> 8)
+    const = np.full((3, 10, 10), 200, np.uint8)
+    assert (oracle.local_median(const, 4, 5, 3) == 200 * 4 // 256).all()
+    # nf identical frames: the 3-D median is the 2-D median of one frame
+    f = synth.blob_plane(14, 16, 62)
+    assert np.array_equal(oracle.local_median(np.stack([f] * 4), 16, 3, 5), oracle.local_median(f, 16, 3, 5))
+    # one salt pixel in a flat 3 x 3 neighbourhood does not move the median
+    g = np.full((9, 9), 10, np.uint8)
+    g[4, 4] = 250
+    assert (oracle.local_median(g, 16, 3, 3) == 0).all()
+
+
 # ---------------------------------------------------------------- Eq. 3.4 moment planes
 
 @pytest.mark.parametrize("weight", [oracle.W_ONE] + list(oracle.MOMENT_WEIGHTS))
