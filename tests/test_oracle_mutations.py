@@ -49,7 +49,7 @@ MUTANTS = [
      [lambda: pins.test_match_window_equals_cumsum_boxes(3, 5)]),
     ("median_rank", "vals[(cnt + 1) / 2 - 1]", "vals[cnt / 2]",
      [lambda: pins.test_local_median_equals_counting(5, 4, 2)]),
-    ("median_box_rows", "y <= r + (m + 1) / 2 - 1", "y <= r + m / 2",
+    ("median_box_rows", "for (int y = r - m / 2; y <=", "for (int y = r - m / 2 + 1; y <=",
      [lambda: pins.test_local_median_equals_counting(5, 4, 2)]),
     ("wedding_shrink_axes", "int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);",
      "int dr = j * wdt / (2 * layers), dc = j * hgt / (2 * layers);",
