@@ -204,6 +204,25 @@ ih_status ih_match_window(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
                           int32_t win_h, int32_t win_w, const int32_t *search, int32_t *d_out,
                           void *stream);
 
+/* Joint integral histogram update of Algorithm 4 (Sec. 4.1.1):
+ *   count tensor of dst += count tensor of add - count tensor of sub,
+ * element by element, in one stream-ordered pass; add or sub may be -1
+ * (none).  The frames must have the same size, channels' bins and layout and
+ * no moment planes; the counts must stay within int32 (a joint histogram of
+ * F frames holds at most F*H*W per cell).  IH_EINVAL (host) otherwise. */
+ih_status ih_accumulate(ih_ctx *ctx, int32_t dst, int32_t add, int32_t sub, void *stream);
+
+/* Local median of Algorithm 4 (ComputeLocalMedian): for every pixel (r, c)
+ * the box of rows r - floor(m/2) .. r + ceil(m/2) - 1 and columns
+ * c - floor(n/2) .. c + ceil(n/2) - 1, clipped to the frame, gives by four
+ * corners (Eq. 2.16) the histogram H over the bins bin0 .. bin0 + nbins - 1;
+ * the output is the smallest i with H(bin0) + ... + H(bin0 + i) >= ceil(N/2),
+ * N = H's total (the lower median bin), or -1 when N = 0.  On a joint
+ * histogram of F frames (ih_accumulate) this is the spatio-temporal median of
+ * the m x n x F neighbourhood.  d_out: device, h x w int32, row-major. */
+ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbins, int32_t m, int32_t n,
+                          int32_t *d_out, void *stream);
+
 /* Frees every tensor the context owns and the context.  NULL-safe.
  * Synchronises the device first. */
 ih_status ih_destroy(ih_ctx *ctx);

@@ -77,7 +77,8 @@ const char *kernel_name(int kid)
     static const char *names[KID_COUNT] = {"features",      "tile_sums/count", "tile_sums/weighted",
                                            "carry_scan",    "tiles/count",     "tiles/moments",
                                            "query_rects",   "query_weighted",  "export",
-                                           "tiles/count+moments", "match_window"};
+                                           "tiles/count+moments", "match_window", "accumulate",
+                                           "local_median"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -542,6 +543,48 @@ ih_status ih_match_window(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
     const int k = launch_match_window(fr->view, bin0, nbins, d_target, win_h, win_w, sr0, sc0, sr1, sc1, d_out,
                                       static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "match launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_accumulate(ih_ctx *ctx, int32_t dst, int32_t add, int32_t sub, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *d = get_frame(ctx, dst);
+    FrameRec *a = add >= 0 ? get_frame(ctx, add) : nullptr;
+    FrameRec *b = sub >= 0 ? get_frame(ctx, sub) : nullptr;
+    if (!d || (add >= 0 && !a) || (sub >= 0 && !b)) return fail(ctx, IH_ENOTBUILT, "ih_accumulate: no such frame");
+    for (const FrameRec *o : {a, b}) {
+        if (!o) continue;
+        bool same = o->H == d->H && o->W == d->W && o->nchan == d->nchan && o->P == d->P &&
+                    o->count_bytes == d->count_bytes && o->view.layout == d->view.layout;
+        for (int c = 0; same && c < d->nchan; ++c) same = o->bins[c] == d->bins[c];
+        if (!same) return fail(ctx, IH_EINVAL, "ih_accumulate: frames of different shape, bins or layout");
+    }
+    if (d->d_mom || (a && a->d_mom) || (b && b->d_mom))
+        return fail(ctx, IH_EINVAL, "ih_accumulate: frames with moment planes");
+    DevGuard dg(ctx->device);
+    const int k = launch_accumulate(d->d_ih, a ? a->d_ih : nullptr, b ? b->d_ih : nullptr, d->count_bytes / 4,
+                                    static_cast<cudaStream_t>(stream), prof_of(ctx));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "accumulate launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbins, int32_t m, int32_t n,
+                          int32_t *d_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    if (!d_out || nbins < 1 || bin0 < 0 || bin0 + nbins > fr->B || m < 1 || n < 1)
+        return fail(ctx, IH_EINVAL, "ih_local_median: bins [%d, %d) / box %d x %d", bin0, bin0 + nbins, m, n);
+    DevGuard dg(ctx->device);
+    const int k = launch_local_median(fr->view, bin0, nbins, m, n, d_out, static_cast<cudaStream_t>(stream),
+                                      prof_of(ctx));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "median launch");
     ctx->launches += k;
     return IH_OK;
 }

@@ -62,7 +62,9 @@ enum KernelId {
     KID_EXPORT = 8,
     KID_TILES_BOTH = 9,  // count and moment tiles of one frame in one launch
     KID_MATCH = 10,
-    KID_COUNT = 11
+    KID_ACCUMULATE = 11,
+    KID_MEDIAN = 12,
+    KID_COUNT = 13
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -239,6 +241,12 @@ int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t
 // [bin0, bin0 + nbins) for placements [sr0, sr1] x [sc0, sc1] of a wh x ww window.
 int launch_match_window(const CountView &v, int bin0, int nbins, const int32_t *target, int wh, int ww, int sr0,
                         int sc0, int sr1, int sc1, int32_t *out, cudaStream_t st, const Prof *prof);
+// dst[i] += add[i] - sub[i] over n int32 words (add / sub may be null).
+int launch_accumulate(int32_t *dst, const int32_t *add, const int32_t *sub, int64_t n, cudaStream_t st,
+                      const Prof *prof);
+// Lower-median bin of each pixel's m x n box over bins [bin0, bin0 + nbins).
+int launch_local_median(const CountView &v, int bin0, int nbins, int m, int n, int32_t *out, cudaStream_t st,
+                        const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
 // Moment plane k of [4][Bw][H][P] (int64, or uint32 when m32) -> packed Bw x H x W int64.

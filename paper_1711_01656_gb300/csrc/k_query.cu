@@ -508,6 +508,77 @@ __global__ void __launch_bounds__(256) k_match_window(const __grid_constant__ Co
     }
 }
 
+// Joint integral histogram update (Algorithm 4): dst += add - sub, 16 bytes
+// per thread and step (the tensors are 16-byte aligned and a multiple of 4
+// words long).
+__global__ void __launch_bounds__(256) k_accumulate(int4 *__restrict__ dst, const int4 *__restrict__ add,
+                                                    const int4 *__restrict__ sub, int64_t n4)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        int4 d = dst[i];
+        if (add) {
+            const int4 a = __ldg(add + i);
+            d.x += a.x, d.y += a.y, d.z += a.z, d.w += a.w;
+        }
+        if (sub) {
+            const int4 b = __ldg(sub + i);
+            d.x -= b.x, d.y -= b.y, d.z -= b.z, d.w -= b.w;
+        }
+        dst[i] = d;
+    }
+}
+
+// Local median (Algorithm 4): one thread per pixel, consecutive threads on
+// consecutive columns (coalesced corner loads).  A first pass over the bins
+// gives the box total N, a second accumulates until ceil(N/2).
+__global__ void __launch_bounds__(256) k_local_median(const __grid_constant__ CountView v, int bin0, int nbins,
+                                                      int m, int n, int32_t *__restrict__ out)
+{
+    __shared__ int64_t s_base[kMaxBins];
+    __shared__ int s_px[kMaxBins];
+    for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
+        int64_t base, px;
+        count_base(v, bin0 + i, base, px);
+        s_base[i] = base;
+        s_px[i] = (int)px;
+    }
+    __syncthreads();
+    const int64_t total = (int64_t)v.H * v.W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / v.W), c = (int)(t % v.W);
+        const int ra = max(r - m / 2, 0), rb = min(r + (m + 1) / 2 - 1, v.H - 1);
+        const int ca = max(c - n / 2, 0), cb = min(c + (n + 1) / 2 - 1, v.W - 1);
+        const int64_t a = (int64_t)rb * v.P + cb, bq = (int64_t)(ra - 1) * v.P + cb;
+        const int64_t cq = (int64_t)rb * v.P + (ca - 1), dq = (int64_t)(ra - 1) * v.P + (ca - 1);
+        const bool top = ra > 0, left = ca > 0;
+        auto box = [&](int i) -> int32_t {
+            const int32_t *p = v.d + s_base[i];
+            const int64_t px = s_px[i];
+            int32_t x = __ldg(p + a * px);
+            if (top) x -= __ldg(p + bq * px);
+            if (left) x -= __ldg(p + cq * px);
+            if (top && left) x += __ldg(p + dq * px);
+            return x;
+        };
+        int64_t N = 0;
+        for (int i = 0; i < nbins; ++i) N += box(i);
+        int med = -1;
+        if (N > 0) {
+            const int64_t half = (N + 1) / 2;
+            int64_t run = 0;
+            for (int i = 0; i < nbins; ++i) {
+                run += box(i);
+                if (run >= half) {
+                    med = i;
+                    break;
+                }
+            }
+        }
+        out[t] = med;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_export(const __grid_constant__ CountView v, int32_t *__restrict__ dst)
 {
     const int64_t total = (int64_t)v.B * v.H * v.W;
@@ -602,6 +673,26 @@ int launch_match_window(const CountView &v, int bin0, int nbins, const int32_t *
     prof_mark(prof, KID_MATCH, 0, st);
     k_match_window<<<grid_for(total), 256, 0, st>>>(v, bin0, nbins, target, wh, ww, sr0, sc0, sr1, sc1, out);
     prof_mark(prof, KID_MATCH, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_accumulate(int32_t *dst, const int32_t *add, const int32_t *sub, int64_t n, cudaStream_t st,
+                      const Prof *prof)
+{
+    const int64_t n4 = n / 4;
+    prof_mark(prof, KID_ACCUMULATE, 0, st);
+    k_accumulate<<<grid_for(n4), 256, 0, st>>>(reinterpret_cast<int4 *>(dst), reinterpret_cast<const int4 *>(add),
+                                               reinterpret_cast<const int4 *>(sub), n4);
+    prof_mark(prof, KID_ACCUMULATE, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_local_median(const CountView &v, int bin0, int nbins, int m, int n, int32_t *out, cudaStream_t st,
+                        const Prof *prof)
+{
+    prof_mark(prof, KID_MEDIAN, 0, st);
+    k_local_median<<<grid_for((int64_t)v.H * v.W), 256, 0, st>>>(v, bin0, nbins, m, n, out);
+    prof_mark(prof, KID_MEDIAN, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

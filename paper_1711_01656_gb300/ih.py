@@ -36,7 +36,7 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_batch_create", "ih_batch_run",
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
-             "ih_match_window")
+             "ih_match_window", "ih_accumulate", "ih_local_median")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -120,6 +120,8 @@ def load_library(path: str = LIB_PATH):
             "ih_query_rects": ([p, i32, p, i64, p, p], i32),
             "ih_query_weighted": ([p, i32, p, i64, u32, u32, p, p], i32),
             "ih_match_window": ([p, i32, i32, i32, p, i32, i32, p, p, p], i32),
+            "ih_accumulate": ([p, i32, i32, i32, p], i32),
+            "ih_local_median": ([p, i32, i32, i32, i32, i32, p, p], i32),
             "ih_destroy": ([p], i32),
             "ih_release": ([p, i32, p], i32),
             "ih_sync": ([p, p], i32),
@@ -243,6 +245,19 @@ def ih_match_window(ctx, handle, bin0, nbins, target, win_h, win_w, search, out,
     s = (ctypes.c_int32 * 4)(*[int(x) for x in search])
     _check(ctx, load_library().ih_match_window(ctx, int(handle), int(bin0), int(nbins), _ptr(target), int(win_h),
                                                int(win_w), s, _ptr(out), _stream(stream)))
+    return out
+
+
+def ih_accumulate(ctx, dst, add=-1, sub=-1, stream=None):
+    """Joint integral histogram update (Algorithm 4): counts of dst += add - sub."""
+    _check(ctx, load_library().ih_accumulate(ctx, int(dst), int(add), int(sub), _stream(stream)))
+
+
+def ih_local_median(ctx, handle, bin0, nbins, m, n, out, stream=None):
+    """Lower-median bin of every pixel's m x n box over bins bin0..bin0+nbins-1;
+    out: (H, W) int32 CUDA tensor (-1 where the box holds no count)."""
+    _check(ctx, load_library().ih_local_median(ctx, int(handle), int(bin0), int(nbins), int(m), int(n), _ptr(out),
+                                               _stream(stream)))
     return out
 
 

@@ -511,6 +511,58 @@ def test_match_window_vs_oracle(ihlib, ctx, layout):
     ihlib.ih_release(ctx, hdl)
 
 
+# ---------------------------------------------------------------- Algorithm 4: joint IH and local median
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+def test_joint_ih_sliding_median(ihlib, ctx, layout):
+    """Algorithm 4 over 9 frames with a temporal window of 5: the joint
+    histogram is built from the first 5 integral histograms, then slid by
+    adding the head frame and subtracting the tail; each step's local median
+    matches the oracle's sort-based spatio-temporal median."""
+    h, w, B, nf, T1 = 70, 90, 16, 9, 5
+    frames = np.stack([synth.blob_plane(h, w, 90 + k) for k in range(nf)])
+    pix = [torch.from_numpy(f).to(DEV)[None] for f in frames]
+    hs = [ihlib.ih_build(ctx, ihlib.Frame(p, [(B, 0)], layout=layout))[0] for p in pix]
+    jih, = ihlib.ih_build(ctx, ihlib.Frame(pix[0], [(B, 0)], layout=layout))
+    for k in range(1, T1):
+        ihlib.ih_accumulate(ctx, jih, add=hs[k])
+    out = torch.empty((h, w), dtype=torch.int32, device=DEV)
+    for start in range(0, nf - T1 + 1):
+        if start:
+            ihlib.ih_accumulate(ctx, jih, add=hs[start + T1 - 1], sub=hs[start - 1])
+        for (m, n) in ((3, 5), (4, 2)):
+            ihlib.ih_local_median(ctx, jih, 0, B, m, n, out)
+            ihlib.ih_sync(ctx)
+            ref = oracle.local_median(frames[start:start + T1], B, m, n)
+            assert np.array_equal(out.cpu().numpy(), ref), (start, m, n)
+    # the joint histogram's tensor is the sum of the window's tensors
+    full = _export(ihlib, ctx, jih)
+    ref = sum(oracle.integral_histogram(f, B).astype(np.int64) for f in frames[nf - T1:])
+    assert np.array_equal(full, ref)
+    # a single frame: the 2-D median filter; a bin range of another channel
+    ihlib.ih_local_median(ctx, hs[0], 0, B, 7, 7, out)
+    ihlib.ih_sync(ctx)
+    assert np.array_equal(out.cpu().numpy(), oracle.local_median(frames[0], B, 7, 7))
+    for hd in hs + [jih]:
+        ihlib.ih_release(ctx, hd)
+
+
+def test_accumulate_refuses_mismatched_frames(ihlib, ctx):
+    a = torch.from_numpy(synth.blob_plane(20, 30, 1)).to(DEV)[None]
+    b = torch.from_numpy(synth.blob_plane(20, 31, 2)).to(DEV)[None]
+    ha, = ihlib.ih_build(ctx, ihlib.Frame(a, [(8, 0)]))
+    hb, = ihlib.ih_build(ctx, ihlib.Frame(b, [(8, 0)]))
+    hc, = ihlib.ih_build(ctx, ihlib.Frame(a, [(8, 0)], layout=1))
+    hm, = ihlib.ih_build(ctx, ihlib.Frame(a, [(8, 0)], weighted_channel=0))
+    for add in (hb, hc, hm):
+        with pytest.raises(ihlib.IHError):
+            ihlib.ih_accumulate(ctx, ha, add=add)
+    with pytest.raises(ihlib.IHError):
+        ihlib.ih_local_median(ctx, ha, 4, 5, 3, 3, torch.empty((20, 30), dtype=torch.int32, device=DEV))
+    for hd in (ha, hb, hc, hm):
+        ihlib.ih_release(ctx, hd)
+
+
 # ---------------------------------------------------------------- record layout
 
 
