@@ -398,7 +398,7 @@ def run_engine(args):
                    "gbs": round(algorithmic_bytes(k, B, Bw, N_RECTS, N_WINDOWS) / (v[1] / v[0] / 1e3) / 1e9, 1)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    batched = served = wami = plain = match = None
+    batched = served = wami = plain = match = median = None
     sections = world == 1  # the side workloads run once, on a single GPU
     if sections and not args.no_wami:
         wami = wami_section(ih, dev, LAYOUTS[args.layout][0])
@@ -406,6 +406,8 @@ def run_engine(args):
         plain = plain_section(ih, dev)
     if sections and not args.no_match:
         match = match_section(ih, dev, LAYOUTS[args.layout][0])
+    if sections and not args.no_median:
+        median = median_section(ih, dev, LAYOUTS[args.layout][0])
     if sections and not args.no_batched:
         # the batch and the serving loop have no rectangle queries: the slab
         # layout (no padding, one channel per group) suits them better
@@ -439,6 +441,7 @@ def run_engine(args):
             "wami": wami,
             "plain": plain,
             "match": match,
+            "median": median,
         }
         print(json.dumps(line))
     ih.ih_destroy(ctx)
@@ -579,6 +582,45 @@ def match_section(ih, dev, layout, runs=20):
             "local_bin_windows_per_s": n_l * B / (ms_l / 1e3),
             "full_frame_ms": round(ms_f, 4), "full_frame_placements_per_s": n_f / (ms_f / 1e3),
             "best_placement_found": [local[0] + best // 256, local[1] + best % 256], "target_at": [500, 900]}
+
+
+def median_section(ih, dev, layout, n_frames=24, window=9, box=5):
+    """Algorithm 4 on a 1920 x 1080 grayscale video (16 bins): per frame, the
+    head frame's integral histogram, the joint-histogram update (head in,
+    tail out) and the 5 x 5 x 9 spatio-temporal median of the centre frame;
+    frames are built once the window is full, as in the algorithm's loop."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    B = 16
+    base = [synth.blob_plane(H, W, synth.config_seed(6) + k) for k in range(4)]
+    pix = [torch.from_numpy(np.roll(base[k % 4], 13 * k, axis=1)).to(dev)[None] for k in range(n_frames)]
+    ctx = ih.ih_create(dev.index or 0)
+    frame = lambda k: ih.Frame(pix[k], [(B, 0)], layout=layout)
+    hs = [ih.ih_build(ctx, frame(k))[0] for k in range(window)]
+    jih, = ih.ih_build(ctx, frame(0))
+    for k in range(1, window):
+        ih.ih_accumulate(ctx, jih, add=hs[k])
+    out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    steps = 0
+    for k in range(window, n_frames):
+        head, = ih.ih_build(ctx, frame(k))
+        ih.ih_accumulate(ctx, jih, add=head, sub=hs[0])
+        ih.ih_release(ctx, hs.pop(0))
+        hs.append(head)
+        ih.ih_local_median(ctx, jih, 0, B, box, box, out)
+        steps += 1
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    for hd in hs + [jih]:
+        ih.ih_release(ctx, hd)
+    ih.ih_destroy(ctx)
+    return {"workload": "1920x1080 gray video, 16 bins, median over 5x5 pixels x 9 frames (Algorithm 4)",
+            "ms_per_frame": round(ms, 4), "frames_per_s": round(1e3 / ms, 1), "frames_timed": steps}
 
 
 def plain_section(ih, dev, runs=50):
@@ -788,6 +830,7 @@ def main(argv=None):
     ap.add_argument("--no-wami", action="store_true", help="skip the 8192x8192 wide-area frame")
     ap.add_argument("--no-plain", action="store_true", help="skip the 640x480 plain frame")
     ap.add_argument("--no-match", action="store_true", help="skip the sliding-window matching maps")
+    ap.add_argument("--no-median", action="store_true", help="skip the spatio-temporal median video")
     ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
