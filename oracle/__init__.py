@@ -74,6 +74,16 @@ def _bind(path: str):
     lib.oracle_match_window.restype = i64
     lib.oracle_local_median.argtypes = [p, i32, i32, i32, i32, i32, i32, i32, p]
     lib.oracle_local_median.restype = None
+    lib.oracle_isqrt.argtypes = [i64]
+    lib.oracle_isqrt.restype = i64
+    lib.oracle_phog_planes.argtypes = [p, i32, i32, i32, p, p]
+    lib.oracle_phog_planes.restype = None
+    lib.oracle_phog_ih.argtypes = [p, p, i32, i32, i32, p]
+    lib.oracle_phog_ih.restype = None
+    lib.oracle_phog_descriptor.argtypes = [p, p, i32, i32, i32, i32, i32, i32, i32, i32, p]
+    lib.oracle_phog_descriptor.restype = None
+    lib.oracle_pyramid_match.argtypes = [p, p, i32, i32]
+    lib.oracle_pyramid_match.restype = ctypes.c_double
     lib.oracle_orientation_bin.argtypes = [i32, i32, i32]
     lib.oracle_orientation_bin.restype = i32
     lib.oracle_features.argtypes = [p, i32, i32, p]
@@ -187,6 +197,55 @@ def local_median(frames, bins: int, m: int, n: int, mode: int = BIN_UNIFORM8) ->
     out = np.empty((h, w), dtype=np.int32)
     _load().oracle_local_median(a.ctypes.data, nf, h, w, bins, mode, int(m), int(n), out.ctypes.data)
     return out
+
+
+PHOG_BINS = 9
+
+
+def isqrt(n: int) -> int:
+    return int(_load().oracle_isqrt(int(n)))
+
+
+def phog_planes(gray, tau: int):
+    """Algorithm 2 steps 1-3: (bins uint8 with 255 off edges, int32 weights)."""
+    a = _plane(gray)
+    h, w = a.shape
+    bins = np.empty((h, w), np.uint8)
+    wt = np.empty((h, w), np.int32)
+    _load().oracle_phog_planes(a.ctypes.data, h, w, int(tau), bins.ctypes.data, wt.ctypes.data)
+    return bins, wt
+
+
+def phog_ih(bins, weight, b: int = PHOG_BINS) -> np.ndarray:
+    """Algorithm 2 step 4: b x h x w int64 magnitude-weighted integral histogram."""
+    q = np.ascontiguousarray(bins, dtype=np.uint8)
+    wt = np.ascontiguousarray(weight, dtype=np.int32)
+    h, w = q.shape
+    out = np.empty((b, h, w), np.int64)
+    _load().oracle_phog_ih(q.ctypes.data, wt.ctypes.data, h, w, b, out.ctypes.data)
+    return out
+
+
+def phog_descriptor_len(levels: int, b: int = PHOG_BINS) -> int:
+    return b * sum(4 ** l for l in range(levels + 1))
+
+
+def phog_descriptor(bins, weight, levels: int, r0: int, c0: int, wh: int, ww: int, b: int = PHOG_BINS):
+    """Algorithm 2 steps 5-20 for one window: the concatenated cell histograms."""
+    q = np.ascontiguousarray(bins, dtype=np.uint8)
+    wt = np.ascontiguousarray(weight, dtype=np.int32)
+    h, w = q.shape
+    out = np.empty(phog_descriptor_len(levels, b), np.int64)
+    _load().oracle_phog_descriptor(q.ctypes.data, wt.ctypes.data, h, w, b, int(levels), int(r0), int(c0), int(wh),
+                                   int(ww), out.ctypes.data)
+    return out
+
+
+def pyramid_match(x, y, levels: int, b: int = PHOG_BINS) -> float:
+    """Eq. 2.24's pyramid match kernel of two descriptors."""
+    a = np.ascontiguousarray(x, dtype=np.int64)
+    c = np.ascontiguousarray(y, dtype=np.int64)
+    return float(_load().oracle_pyramid_match(a.ctypes.data, c.ctypes.data, b, int(levels)))
 
 
 def manhattan_weight(window, r: int, c: int) -> float:

@@ -25,6 +25,9 @@
  *     city-block distance of every placement      Eq. 2.22 (p = 1), Sec. 2.4.3
  *   - spatio-temporal median by sorting the box's
  *     quantised values over the frames             Algorithm 4, Sec. 4.1.1
+ *   - magnitude-weighted orientation planes, their
+ *     integral histogram, pyramid descriptors by
+ *     pixel sums and the pyramid match kernel      Algorithm 2, Eq. 2.23-2.24
  *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
  *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
  *
@@ -48,6 +51,11 @@
  *   - the median of Algorithm 4 is the lower median bin of the box's
  *     quantised values, the box clipped at the frame border (the thesis
  *     leaves both open);
+ *   - Algorithm 2's Canny step is read as a gradient-magnitude threshold
+ *     (no non-maximum suppression or hysteresis), the magnitude is kept in
+ *     fixed point (floor(16 |g|)), the pyramid cells are floor(h/2^l) x
+ *     floor(w/2^l) at multiples of that size, and its garbled index
+ *     updates are read as visiting the s x s cells once each;
  *   - intensity rounds down; gradient orientation is unsigned, in
  *     [0,180) degrees, 9 bins of 20 degrees, central differences at step
  *     s with replicated borders, (0,0) -> bin 0.
@@ -404,3 +412,102 @@ void oracle_features(const uint8_t *rgb, int h, int w, uint8_t *out)
             }
     }
 }
+
+/* ---- spatial pyramid of gradient orientations (Algorithm 2, Sec. 2.4.4) */
+
+/* floor(sqrt(n)) of a non-negative integer by bisection. */
+int64_t oracle_isqrt(int64_t n)
+{
+    int64_t lo = 0, hi = 1;
+    while (hi * hi <= n) hi *= 2;
+    while (hi - lo > 1) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (mid * mid <= n)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+/* Algorithm 2, steps 1-3 on a grayscale search window: central differences
+ * (step 1, replicated borders), gradient magnitude in fixed point with 4
+ * fractional bits, w = floor(16 sqrt(gx^2 + gy^2)), and the 9-bin unsigned
+ * orientation; a pixel is an edge pixel when w >= 16 * tau (the reading of
+ * the Canny step: a magnitude threshold).  bins: h x w uint8 (the bin, 255
+ * off edges); weight: h x w int32 (w on edges, 0 off them). */
+void oracle_phog_planes(const uint8_t *gray, int h, int w, int tau, uint8_t *bins, int32_t *weight)
+{
+    for (int r = 0; r < h; r++)
+        for (int c = 0; c < w; c++) {
+            int gx = (int)gray[(int64_t)r * w + clampi(c + 1, 0, w - 1)] -
+                     (int)gray[(int64_t)r * w + clampi(c - 1, 0, w - 1)];
+            int gy = (int)gray[(int64_t)clampi(r + 1, 0, h - 1) * w + c] -
+                     (int)gray[(int64_t)clampi(r - 1, 0, h - 1) * w + c];
+            int64_t m = oracle_isqrt(256 * ((int64_t)gx * gx + (int64_t)gy * gy));
+            int edge = m >= 16 * (int64_t)tau;
+            bins[(int64_t)r * w + c] = edge ? (uint8_t)oracle_orientation_bin(gx, gy, 9) : 255;
+            weight[(int64_t)r * w + c] = edge ? (int32_t)m : 0;
+        }
+}
+
+/* Algorithm 2, step 4: the magnitude-weighted integral histogram of the
+ * orientation bins (Eq. 3.4 with w = the magnitude plane), by Algorithm 5's
+ * recurrence.  out: b x h x w int64. */
+void oracle_phog_ih(const uint8_t *bins, const int32_t *weight, int h, int w, int b, int64_t *out)
+{
+    for (int k = 0; k < b; k++) {
+        int64_t *o = out + (int64_t)k * h * w;
+        for (int r = 0; r < h; r++)
+            for (int c = 0; c < w; c++) {
+                int64_t above = r > 0 ? o[(int64_t)(r - 1) * w + c] : 0;
+                int64_t before = c > 0 ? o[(int64_t)r * w + c - 1] : 0;
+                int64_t corner = (r > 0 && c > 0) ? o[(int64_t)(r - 1) * w + c - 1] : 0;
+                int64_t inc = bins[(int64_t)r * w + c] == k ? weight[(int64_t)r * w + c] : 0;
+                o[(int64_t)r * w + c] = above + before - corner + inc;
+            }
+    }
+}
+
+/* Algorithm 2, steps 5-20 for one window [r0, r0+wh) x [c0, c0+ww): level
+ * l = 0..L cuts the window into s x s cells (s = 2^l) of floor(wh/s) x
+ * floor(ww/s) pixels at offsets (i*floor(wh/s), j*floor(ww/s)); each cell's
+ * weighted histogram is summed pixel by pixel.  desc: b * sum_l 4^l int64,
+ * level after level, cells row-major, bins innermost. */
+void oracle_phog_descriptor(const uint8_t *bins, const int32_t *weight, int h, int w, int b, int L, int r0,
+                            int c0, int wh, int ww, int64_t *desc)
+{
+    int64_t k = 0;
+    for (int l = 0; l <= L; l++) {
+        int s = 1 << l, ch = wh / s, cw = ww / s;
+        for (int i = 0; i < s; i++)
+            for (int j = 0; j < s; j++) {
+                for (int q = 0; q < b; q++) desc[k + q] = 0;
+                for (int y = r0 + i * ch; y < r0 + (i + 1) * ch; y++)
+                    for (int x = c0 + j * cw; x < c0 + (j + 1) * cw; x++) {
+                        if (y >= h || x >= w) continue;
+                        int q = bins[(int64_t)y * w + x];
+                        if (q < b) desc[k + q] += weight[(int64_t)y * w + x];
+                    }
+                k += b;
+            }
+    }
+}
+
+/* The pyramid match kernel of Eq. 2.23-2.24 between two descriptors of L+1
+ * levels: I^l = sum of min over level l's entries, and
+ *   kappa = I^0 / 2^L + sum_{l=1..L} I^l / 2^(L-l+1). */
+double oracle_pyramid_match(const int64_t *x, const int64_t *y, int b, int L)
+{
+    double kappa = 0.0;
+    int64_t k = 0;
+    for (int l = 0; l <= L; l++) {
+        int64_t n = (int64_t)b << (2 * l);
+        double il = 0.0;
+        for (int64_t i = 0; i < n; i++) il += (double)(x[k + i] < y[k + i] ? x[k + i] : y[k + i]);
+        kappa += l == 0 ? il / (double)(1 << L) : il / (double)(1 << (L - l + 1));
+        k += n;
+    }
+    return kappa;
+}
+

@@ -51,6 +51,13 @@ MUTANTS = [
      [lambda: pins.test_local_median_equals_counting(5, 4, 2)]),
     ("median_box_rows", "for (int y = r - m / 2; y <=", "for (int y = r - m / 2 + 1; y <=",
      [lambda: pins.test_local_median_equals_counting(5, 4, 2)]),
+    ("isqrt_round_up", "    return lo;\n}", "    return hi;\n}",
+     [pins.test_isqrt_exhaustive_against_math_isqrt]),
+    ("phog_cell_offset", "for (int y = r0 + i * ch; y < r0 + (i + 1) * ch; y++)",
+     "for (int y = r0 + i * cw; y < r0 + (i + 1) * ch; y++)",
+     [lambda: pins.test_phog_descriptor_cells(2)]),
+    ("pyramid_level_weight", "il / (double)(1 << (L - l + 1))", "il / (double)(1 << (L - l))",
+     [pins.test_pyramid_match_kernel_forms_agree]),
     ("wedding_shrink_axes", "int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);",
      "int dr = j * wdt / (2 * layers), dc = j * hgt / (2 * layers);",
      [lambda: pins.test_wedding_cake_is_sum_of_nested_windows(3)]),

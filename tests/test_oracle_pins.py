@@ -472,6 +472,82 @@ def test_local_median_special_cases():
     assert (oracle.local_median(g, 16, 3, 3) == 0).all()
 
 
+# ---------------------------------------------------------------- Algorithm 2 PHoG, Eq. 2.23-2.24
+
+def test_isqrt_exhaustive_against_math_isqrt():
+    import math
+    vals = sorted({256 * (gx * gx + gy * gy) for gx in range(256) for gy in range(256)})
+    for n in vals[::7] + vals[-50:] + [0, 1, 2, 3, 4, 15, 16, 17]:
+        assert oracle.isqrt(n) == math.isqrt(n)
+
+
+def test_phog_planes_follow_the_stencil():
+    import math
+    g = synth.blob_plane(23, 31, 70)
+    tau = 6
+    bins, wt = oracle.phog_planes(g, tau)
+    p = np.pad(g.astype(np.int64), 1, mode="edge")
+    gx = p[1:-1, 2:] - p[1:-1, :-2]
+    gy = p[2:, 1:-1] - p[:-2, 1:-1]
+    for r in range(23):
+        for c in range(31):
+            m = math.isqrt(256 * int(gx[r, c] ** 2 + gy[r, c] ** 2))
+            if m >= 16 * tau:
+                assert wt[r, c] == m and bins[r, c] == oracle.orientation_bin(int(gx[r, c]), int(gy[r, c]))
+            else:
+                assert wt[r, c] == 0 and bins[r, c] == 255
+    assert (bins < 9).any() and (bins == 255).any()
+
+
+def test_phog_ih_equals_cumsum():
+    g = synth.blob_plane(30, 37, 71)
+    bins, wt = oracle.phog_planes(g, 4)
+    onehot = (bins[None] == np.arange(9)[:, None, None]) * wt[None].astype(np.int64)
+    assert np.array_equal(oracle.phog_ih(bins, wt), onehot.cumsum(1).cumsum(2))
+
+
+@pytest.mark.parametrize("L", [0, 1, 2, 3])
+def test_phog_descriptor_cells(L):
+    g = synth.blob_plane(70, 90, 72)
+    bins, wt = oracle.phog_planes(g, 5)
+    r0, c0, wh, ww = 6, 9, 48, 64
+    d = oracle.phog_descriptor(bins, wt, L, r0, c0, wh, ww)
+    assert d.shape == (9 * sum(4 ** l for l in range(L + 1)),)
+    k = 0
+    for l in range(L + 1):
+        s_ = 2 ** l
+        ch, cw = wh // s_, ww // s_
+        lev = d[k: k + 9 * s_ * s_].reshape(s_, s_, 9)
+        for i in range(s_):
+            for j in range(s_):
+                cb = bins[r0 + i * ch: r0 + (i + 1) * ch, c0 + j * cw: c0 + (j + 1) * cw]
+                cwt = wt[r0 + i * ch: r0 + (i + 1) * ch, c0 + j * cw: c0 + (j + 1) * cw]
+                assert np.array_equal(lev[i, j], [int(cwt[cb == q].sum()) for q in range(9)])
+        # 48 and 64 divide by 2^l up to l = 3: every level covers the window
+        assert np.array_equal(lev.sum((0, 1)), d[:9])
+        k += 9 * s_ * s_
+
+
+def test_pyramid_match_kernel_forms_agree():
+    """Eq. 2.24: I^L + sum_{l<L} (I^l - I^{l+1}) / 2^(L-l) equals
+    I^0 / 2^L + sum_{l>=1} I^l / 2^(L-l+1); the oracle computes the second
+    form, numpy the first; kappa(X, X) is X's total weight."""
+    g = synth.blob_plane(80, 80, 73)
+    bins, wt = oracle.phog_planes(g, 5)
+    L = 3
+    x = oracle.phog_descriptor(bins, wt, L, 4, 4, 64, 64)
+    y = oracle.phog_descriptor(bins, wt, L, 10, 7, 64, 64)
+    I, k = [], 0
+    for l in range(L + 1):
+        n = 9 * 4 ** l
+        I.append(float(np.minimum(x[k:k + n], y[k:k + n]).sum()))
+        k += n
+    first = I[L] + sum((I[l] - I[l + 1]) / 2 ** (L - l) for l in range(L))
+    assert oracle.pyramid_match(x, y, L) == pytest.approx(first, rel=1e-13)
+    assert oracle.pyramid_match(x, x, L) == pytest.approx(float(x[:9].sum()), rel=1e-13)
+    assert oracle.pyramid_match(x, np.zeros_like(x), L) == 0.0
+
+
 # ---------------------------------------------------------------- Eq. 3.4 moment planes
 
 @pytest.mark.parametrize("weight", [oracle.W_ONE] + list(oracle.MOMENT_WEIGHTS))
