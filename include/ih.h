@@ -223,6 +223,42 @@ ih_status ih_accumulate(ih_ctx *ctx, int32_t dst, int32_t add, int32_t sub, void
 ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbins, int32_t m, int32_t n,
                           int32_t *d_out, void *stream);
 
+/* Spatial pyramids of gradient orientations (Algorithm 2, Sec. 2.3).
+ * ih_phog_build runs steps 1-4 on a grayscale search window d_gray (device,
+ * height x width uint8, row pitch pitch_bytes): central differences (step 1,
+ * replicated borders); gradient magnitude in fixed point with 4 fractional
+ * bits, w = floor(16 sqrt(gx^2 + gy^2)) (exact integer square root); a pixel
+ * is an edge pixel when w >= 16 * tau (this reading of step 1's Canny
+ * detector keeps the magnitude threshold and leaves out non-maximum
+ * suppression and hysteresis); the unsigned orientation of edge pixels in 9
+ * bins of 20 degrees; and the w-weighted integral histogram of those bins
+ * (Eq. 3.4 with a pixel weight), int64 9 x height x pitch, owned by the
+ * context as frame *out_handle (ih_info reports it with 9 bins and its
+ * bytes as moment_bytes; count-tensor calls refuse it).  Errors as for
+ * ih_build. */
+ih_status ih_phog_build(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int32_t width, int64_t pitch_bytes,
+                        int32_t tau, int32_t *out_handle, void *stream);
+
+/* Steps 5-20: the descriptor of each of n windows (device n x 4 int32
+ * r0, c0, r1, c1): for l = 0 .. levels, the window's 2^l x 2^l cells of
+ * floor(h/2^l) x floor(w/2^l) pixels at multiples of that size, each cell's
+ * 9 weighted bins; d_out: device n x 9 * sum_l 4^l int64, level after level,
+ * cells row-major, bins innermost.  levels 0..4 (IH_EINVAL otherwise).  A
+ * window outside the frame gets a row of -1 and makes the next ih_sync()
+ * return IH_EINVAL. */
+ih_status ih_phog_descriptors(ih_ctx *ctx, int32_t handle, int32_t levels, const int32_t *d_windows, int64_t n,
+                              int64_t *d_out, void *stream);
+
+/* Sec. 2.4.4: the pyramid match kernel (Eq. 2.24) of d_target (device, a
+ * descriptor from ih_phog_descriptors with the same levels) against the
+ * descriptor of every win_h x win_w window whose top-left pixel lies in
+ * search = (sr0, sc0, sr1, sc1) (host): kappa = I^0/2^L + sum_{l>=1}
+ * I^l/2^(L-l+1), I^l = sum of min over level l's entries; d_out: device,
+ * (sr1-sr0+1) x (sc1-sc0+1) float.  IH_EINVAL (host) for a placement outside
+ * the frame. */
+ih_status ih_phog_match(ih_ctx *ctx, int32_t handle, int32_t levels, const int64_t *d_target, int32_t win_h,
+                        int32_t win_w, const int32_t *search, float *d_out, void *stream);
+
 /* Frees every tensor the context owns and the context.  NULL-safe.
  * Synchronises the device first. */
 ih_status ih_destroy(ih_ctx *ctx);

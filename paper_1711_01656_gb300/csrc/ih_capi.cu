@@ -78,7 +78,7 @@ const char *kernel_name(int kid)
                                            "carry_scan",    "tiles/count",     "tiles/moments",
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
-                                           "local_median"};
+                                           "local_median", "phog_build",     "phog_query"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -343,6 +343,12 @@ FrameRec *get_frame(ih_ctx *ctx, int32_t handle)
     return &ctx->frames[handle];
 }
 
+FrameRec *count_frame(ih_ctx *ctx, int32_t handle)
+{
+    FrameRec *fr = get_frame(ctx, handle);
+    return (fr && !fr->phog) ? fr : nullptr;
+}
+
 int publish_frame(ih_ctx *ctx, FrameRec &fr)
 {
     int h = -1;
@@ -493,7 +499,7 @@ ih_status ih_query_rects(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, in
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *fr = get_frame(ctx, handle);
+    FrameRec *fr = count_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (n < 0 || (n > 0 && (!d_rects || !d_out))) return fail(ctx, IH_EINVAL, "ih_query_rects: bad arguments");
     DevGuard dg(ctx->device);
@@ -509,7 +515,7 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *fr = get_frame(ctx, handle);
+    FrameRec *fr = count_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (!fr->Bw) return fail(ctx, IH_EINVAL, "frame %d has no moment planes", handle);
     const int layers = weighted_layers(flags);
@@ -531,7 +537,7 @@ ih_status ih_match_window(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *fr = get_frame(ctx, handle);
+    FrameRec *fr = count_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (!search || !d_target || !d_out) return fail(ctx, IH_EINVAL, "ih_match_window: NULL argument");
     const int sr0 = search[0], sc0 = search[1], sr1 = search[2], sc1 = search[3];
@@ -551,9 +557,9 @@ ih_status ih_accumulate(ih_ctx *ctx, int32_t dst, int32_t add, int32_t sub, void
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *d = get_frame(ctx, dst);
-    FrameRec *a = add >= 0 ? get_frame(ctx, add) : nullptr;
-    FrameRec *b = sub >= 0 ? get_frame(ctx, sub) : nullptr;
+    FrameRec *d = count_frame(ctx, dst);
+    FrameRec *a = add >= 0 ? count_frame(ctx, add) : nullptr;
+    FrameRec *b = sub >= 0 ? count_frame(ctx, sub) : nullptr;
     if (!d || (add >= 0 && !a) || (sub >= 0 && !b)) return fail(ctx, IH_ENOTBUILT, "ih_accumulate: no such frame");
     for (const FrameRec *o : {a, b}) {
         if (!o) continue;
@@ -577,7 +583,7 @@ ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *fr = get_frame(ctx, handle);
+    FrameRec *fr = count_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (!d_out || nbins < 1 || bin0 < 0 || bin0 + nbins > fr->B || m < 1 || n < 1)
         return fail(ctx, IH_EINVAL, "ih_local_median: bins [%d, %d) / box %d x %d", bin0, bin0 + nbins, m, n);
@@ -585,6 +591,89 @@ ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
     const int k = launch_local_median(fr->view, bin0, nbins, m, n, d_out, static_cast<cudaStream_t>(stream),
                                       prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "median launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_phog_build(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int32_t width, int64_t pitch_bytes,
+                        int32_t tau, int32_t *out_handle, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!d_gray || !out_handle || height < 1 || width < 1 || pitch_bytes < width || tau < 0 ||
+        (int64_t)height * width > ((int64_t)1 << 31))
+        return fail(ctx, IH_EINVAL, "ih_phog_build: bad arguments");
+    DevGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FrameRec fr;
+    fr.H = height;
+    fr.W = width;
+    fr.nchan = 1;
+    fr.B = kPhogBins;
+    fr.bins[0] = kPhogBins;
+    fr.P = (width + 3) & ~3;
+    fr.phog = true;
+    fr.moment_bytes = (int64_t)kPhogBins * height * fr.P * 8;
+    if (ctx->budget && ctx->used + (uint64_t)fr.moment_bytes > ctx->budget)
+        return fail(ctx, IH_EBUDGET, "pyramid planes of %lld bytes exceed the HBM budget", (long long)fr.moment_bytes);
+    const int64_t px = (int64_t)height * width;
+    uint8_t *scratch = nullptr;
+    cudaError_t e = pool_alloc(ctx, &fr.d_mom, fr.moment_bytes, st);
+    if (e == cudaSuccess) e = pool_alloc(ctx, &scratch, (size_t)px * 5 + 16, st);
+    if (e != cudaSuccess) {
+        if (fr.d_mom) cudaFreeAsync(fr.d_mom, st);
+        return cuda_fail(ctx, e, "pyramid allocation");
+    }
+    int32_t *wt = reinterpret_cast<int32_t *>(scratch);
+    uint8_t *bins = scratch + px * 4;
+    const int k = launch_phog_build(d_gray, pitch_bytes, height, width, tau, bins, wt, fr.P, fr.d_mom, st,
+                                    prof_of(ctx));
+    cudaFreeAsync(scratch, st);
+    if (k < 0) {
+        cudaFreeAsync(fr.d_mom, st);
+        return cuda_fail(ctx, cudaGetLastError(), "pyramid launch");
+    }
+    ctx->launches += k;
+    *out_handle = publish_frame(ctx, fr);
+    return IH_OK;
+}
+
+ih_status ih_phog_descriptors(ih_ctx *ctx, int32_t handle, int32_t levels, const int32_t *d_windows, int64_t n,
+                              int64_t *d_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr || !fr->phog) return fail(ctx, IH_ENOTBUILT, "no pyramid frame %d", handle);
+    if (levels < 0 || levels > kPhogMaxLevels || n < 0 || (n > 0 && (!d_windows || !d_out)))
+        return fail(ctx, IH_EINVAL, "ih_phog_descriptors: levels %d / n %lld", levels, (long long)n);
+    if (n == 0) return IH_OK;
+    DevGuard dg(ctx->device);
+    const int k = launch_phog_descriptors(fr->d_mom, fr->H, fr->W, fr->P, levels, d_windows, n, d_out, ctx->d_err,
+                                          static_cast<cudaStream_t>(stream), prof_of(ctx));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "descriptor launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_phog_match(ih_ctx *ctx, int32_t handle, int32_t levels, const int64_t *d_target, int32_t win_h,
+                        int32_t win_w, const int32_t *search, float *d_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = get_frame(ctx, handle);
+    if (!fr || !fr->phog) return fail(ctx, IH_ENOTBUILT, "no pyramid frame %d", handle);
+    if (!search || !d_target || !d_out || levels < 0 || levels > kPhogMaxLevels)
+        return fail(ctx, IH_EINVAL, "ih_phog_match: bad arguments");
+    const int sr0 = search[0], sc0 = search[1], sr1 = search[2], sc1 = search[3];
+    if (win_h < 1 || win_w < 1 || sr0 < 0 || sc0 < 0 || sr1 < sr0 || sc1 < sc0 || (int64_t)sr1 + win_h > fr->H ||
+        (int64_t)sc1 + win_w > fr->W)
+        return fail(ctx, IH_EINVAL, "ih_phog_match: window %dx%d / search (%d,%d)-(%d,%d)", win_h, win_w, sr0, sc0,
+                    sr1, sc1);
+    DevGuard dg(ctx->device);
+    const int k = launch_phog_match(fr->d_mom, fr->H, fr->P, levels, d_target, win_h, win_w, sr0, sc0, sr1, sc1,
+                                    d_out, static_cast<cudaStream_t>(stream), prof_of(ctx));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "pyramid match launch");
     ctx->launches += k;
     return IH_OK;
 }
@@ -646,7 +735,7 @@ ih_status ih_export(ih_ctx *ctx, int32_t handle, int32_t *d_dst, void *stream)
 {
     if (!ctx || !d_dst) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *fr = get_frame(ctx, handle);
+    FrameRec *fr = count_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     DevGuard dg(ctx->device);
     if (launch_export(fr->view, d_dst, static_cast<cudaStream_t>(stream), prof_of(ctx)) < 0)
@@ -659,7 +748,7 @@ ih_status ih_export_moments(ih_ctx *ctx, int32_t handle, int32_t plane, int64_t 
 {
     if (!ctx || !d_dst) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    FrameRec *fr = get_frame(ctx, handle);
+    FrameRec *fr = count_frame(ctx, handle);
     if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
     if (!fr->Bw || plane < 0 || plane > 3) return fail(ctx, IH_EINVAL, "no moment plane %d", plane);
     DevGuard dg(ctx->device);

@@ -22,6 +22,7 @@ struct FrameRec {
     int64_t *d_mom = nullptr;  // int64 or uint32 planes (mbits)
     int64_t count_bytes = 0, moment_bytes = 0;
     int R = 0, Wc = 0;  // tile grid used by the build
+    bool phog = false;  // d_mom holds Algorithm 2's 9 weighted planes; no count tensor
     CountView view{};
 };
 
@@ -101,6 +102,8 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
 std::string shape_key(const ih_frame &f);
 void make_view(const PlaneSet &ps, const int32_t *d, CountView &v);
 FrameRec *get_frame(ih_ctx *ctx, int32_t handle);
+// A live frame with a count tensor (not a pyramid frame), else null.
+FrameRec *count_frame(ih_ctx *ctx, int32_t handle);
 int publish_frame(ih_ctx *ctx, FrameRec &fr);  // registers a built frame, returns its handle
 
 }  // namespace ih

@@ -64,7 +64,9 @@ enum KernelId {
     KID_MATCH = 10,
     KID_ACCUMULATE = 11,
     KID_MEDIAN = 12,
-    KID_COUNT = 13
+    KID_PHOG_BUILD = 13,
+    KID_PHOG_QUERY = 14,
+    KID_COUNT = 15
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -247,6 +249,23 @@ int launch_accumulate(int32_t *dst, const int32_t *add, const int32_t *sub, int6
 // Lower-median bin of each pixel's m x n box over bins [bin0, bin0 + nbins).
 int launch_local_median(const CountView &v, int bin0, int nbins, int m, int n, int32_t *out, cudaStream_t st,
                         const Prof *prof);
+// Spatial pyramids of gradient orientations (k_phog.cu, Algorithm 2).
+constexpr int kPhogBins = 9;
+constexpr int kPhogMaxLevels = 4;  // descriptors of at most 9 * 341 entries
+inline int64_t phog_descriptor_len(int L)
+{
+    int64_t n = 0;
+    for (int l = 0; l <= L; ++l) n += (int64_t)kPhogBins << (2 * l);
+    return n;
+}
+// Orientation bins, magnitude weights (scratch, h x w each) and the weighted
+// integral histogram ih: kPhogBins x H x P int64.  Returns launches or -1.
+int launch_phog_build(const uint8_t *gray, int64_t pitch, int H, int W, int tau, uint8_t *bins, int32_t *wt,
+                      int64_t P, int64_t *ih, cudaStream_t st, const Prof *prof);
+int launch_phog_descriptors(const int64_t *ih, int H, int W, int64_t P, int L, const int32_t *wins, int64_t n,
+                            int64_t *out, int *err, cudaStream_t st, const Prof *prof);
+int launch_phog_match(const int64_t *ih, int H, int64_t P, int L, const int64_t *target, int wh, int ww, int sr0,
+                      int sc0, int sr1, int sc1, float *out, cudaStream_t st, const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
 // Moment plane k of [4][Bw][H][P] (int64, or uint32 when m32) -> packed Bw x H x W int64.

@@ -30,6 +30,7 @@
 // neighbours at horizontal distance s = 1, 2 are assembled from two staged
 // words with byte permutes; s = 4 is the adjacent word.
 #include "ih_internal.cuh"
+#include "ih_orient.cuh"
 
 namespace ih {
 
@@ -39,24 +40,6 @@ constexpr int kTR = 32, kTC = 128, kHalo = 4;
 constexpr int kSR = kTR + 2 * kHalo;  // staged rows
 constexpr int kSW = kTC / 4 + 2;      // staged words per row (one halo word each side)
 constexpr int kThreads = 256;
-
-// round(2^22 cos(20j deg)), round(2^22 sin(20j deg)), j = 1..4
-__constant__ int kUx[4] = {3941357, 3213023, 2097152, 728333};
-__constant__ int kUy[4] = {1434536, 2696047, 3632374, 4130583};
-
-__device__ __forceinline__ int orientation_bin9(int gx, int gy)
-{
-    if (gy < 0 || (gy == 0 && gx < 0)) {
-        gx = -gx;
-        gy = -gy;
-    }
-    if ((gx | gy) == 0) return 0;
-    const int ax = gx < 0 ? -gx : gx;
-    int n = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) n += (kUx[k] * gy - kUy[k] * ax >= 0) ? 1 : 0;
-    return gx < 0 ? 8 - n : n;
-}
 
 __device__ __forceinline__ int byte_of(uint32_t w, int j) { return (int)((w >> (8 * j)) & 0xff); }
 

@@ -36,7 +36,8 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_profile_read", "ih_launch_count", "ih_last_error", "ih_batch_create", "ih_batch_run",
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
-             "ih_match_window", "ih_accumulate", "ih_local_median")
+             "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
+             "ih_phog_match")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -121,6 +122,9 @@ def load_library(path: str = LIB_PATH):
             "ih_query_weighted": ([p, i32, p, i64, u32, u32, p, p], i32),
             "ih_match_window": ([p, i32, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_accumulate": ([p, i32, i32, i32, p], i32),
+            "ih_phog_build": ([p, p, i32, i32, i64, i32, ctypes.POINTER(i32), p], i32),
+            "ih_phog_descriptors": ([p, i32, i32, p, i64, p, p], i32),
+            "ih_phog_match": ([p, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_local_median": ([p, i32, i32, i32, i32, i32, p, p], i32),
             "ih_destroy": ([p], i32),
             "ih_release": ([p, i32, p], i32),
@@ -245,6 +249,45 @@ def ih_match_window(ctx, handle, bin0, nbins, target, win_h, win_w, search, out,
     s = (ctypes.c_int32 * 4)(*[int(x) for x in search])
     _check(ctx, load_library().ih_match_window(ctx, int(handle), int(bin0), int(nbins), _ptr(target), int(win_h),
                                                int(win_w), s, _ptr(out), _stream(stream)))
+    return out
+
+
+PHOG_BINS = 9
+
+
+def phog_descriptor_len(levels):
+    return PHOG_BINS * sum(4 ** l for l in range(int(levels) + 1))
+
+
+def ih_phog_build(ctx, gray, tau, stream=None):
+    """Algorithm 2 steps 1-4 on a (H, W) uint8 CUDA tensor (rows may be
+    strided): returns the handle of the 9-bin magnitude-weighted orientation
+    integral histogram."""
+    h, w = gray.shape
+    pitch = gray.stride(0) if gray.stride(1) == 1 else None
+    if pitch is None:
+        gray = gray.contiguous()
+        pitch = w
+    out = ctypes.c_int32(-1)
+    _check(ctx, load_library().ih_phog_build(ctx, _ptr(gray), int(h), int(w), int(pitch), int(tau),
+                                             ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def ih_phog_descriptors(ctx, handle, levels, windows, out, stream=None):
+    """windows: (n, 4) int32 CUDA tensor; out: (n, 9 * sum 4^l) int64 CUDA tensor."""
+    n = 0 if windows is None else windows.shape[0]
+    _check(ctx, load_library().ih_phog_descriptors(ctx, int(handle), int(levels), _ptr(windows), n, _ptr(out),
+                                                   _stream(stream)))
+    return out
+
+
+def ih_phog_match(ctx, handle, levels, target, win_h, win_w, search, out, stream=None):
+    """Pyramid match kernel map (Eq. 2.24) of `target` (int64 descriptor,
+    CUDA) against every win_h x win_w window with top-left pixel in search."""
+    sr = (ctypes.c_int32 * 4)(*[int(x) for x in search])
+    _check(ctx, load_library().ih_phog_match(ctx, int(handle), int(levels), _ptr(target), int(win_h), int(win_w),
+                                             sr, _ptr(out), _stream(stream)))
     return out
 
 

@@ -563,6 +563,59 @@ def test_accumulate_refuses_mismatched_frames(ihlib, ctx):
         ihlib.ih_release(ctx, hd)
 
 
+# ---------------------------------------------------------------- Algorithm 2: spatial pyramid of orientations
+
+@pytest.mark.parametrize("tau", [0, 6, 40])
+def test_phog_descriptors_vs_oracle(ihlib, ctx, tau):
+    h, w = 130, 171
+    g = synth.blob_plane(h, w, 120)
+    hdl = ihlib.ih_phog_build(ctx, torch.from_numpy(g).to(DEV), tau)
+    info = ihlib.ih_info(ctx, hdl)
+    assert info["total_bins"] == 9 and info["count_bytes"] == 0
+    assert info["moment_bytes"] == 9 * h * ((w + 3) // 4 * 4) * 8
+    bins, wt = oracle.phog_planes(g, tau)
+    wins = np.concatenate([synth.rects_side_range(h, w, 40, 1, 100, 121),
+                           np.array([[0, 0, h - 1, w - 1], [5, 6, 5, 6], [3, 4, 66, 131]], np.int32)])
+    for L in (0, 2, 3):
+        D = ihlib.phog_descriptor_len(L)
+        out = torch.full((len(wins), D), -7, dtype=torch.int64, device=DEV)
+        ihlib.ih_phog_descriptors(ctx, hdl, L, torch.from_numpy(wins).to(DEV), out)
+        ihlib.ih_sync(ctx)
+        got = out.cpu().numpy()
+        for k, (r0, c0, r1, c1) in enumerate(wins):
+            ref = oracle.phog_descriptor(bins, wt, L, r0, c0, r1 - r0 + 1, c1 - c0 + 1)
+            assert np.array_equal(got[k], ref), (L, k)
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_phog_match_map_vs_oracle(ihlib, ctx):
+    h, w = 96, 128
+    g = synth.blob_plane(h, w, 122)
+    hdl = ihlib.ih_phog_build(ctx, torch.from_numpy(g).to(DEV), 5)
+    bins, wt = oracle.phog_planes(g, 5)
+    L, wh, ww = 2, 32, 40
+    target = oracle.phog_descriptor(bins, wt, L, 30, 50, wh, ww)
+    search = (20, 40, 20 + 23, 40 + 30)
+    out = torch.empty((24, 31), dtype=torch.float32, device=DEV)
+    ihlib.ih_phog_match(ctx, hdl, L, torch.from_numpy(target).to(DEV), wh, ww, search, out)
+    ihlib.ih_sync(ctx)
+    got = out.cpu().numpy().astype(np.float64)
+    for i in range(24):
+        for j in range(31):
+            d = oracle.phog_descriptor(bins, wt, L, 20 + i, 40 + j, wh, ww)
+            ref = oracle.pyramid_match(d, target, L)
+            assert abs(got[i, j] - ref) <= 1e-6 * max(ref, 1.0), (i, j)
+    # the best match is the target window itself (kappa(X, X) = its total)
+    assert got[10, 10] == pytest.approx(float(target[:9].sum()), rel=1e-6)
+    assert got.max() == pytest.approx(got[10, 10], rel=1e-6)
+    with pytest.raises(ihlib.IHError):
+        ihlib.ih_phog_match(ctx, hdl, L, torch.from_numpy(target).to(DEV), wh, ww, (0, 0, h - wh + 1, 0), out)
+    with pytest.raises(ihlib.IHError):  # count-tensor calls refuse a pyramid frame
+        ihlib.ih_query_rects(ctx, hdl, torch.zeros((1, 4), dtype=torch.int32, device=DEV),
+                             torch.empty((1, 9), dtype=torch.int32, device=DEV))
+    ihlib.ih_release(ctx, hdl)
+
+
 # ---------------------------------------------------------------- record layout
 
 
