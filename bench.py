@@ -398,7 +398,7 @@ def run_engine(args):
                    "gbs": round(algorithmic_bytes(k, B, Bw, N_RECTS, N_WINDOWS) / (v[1] / v[0] / 1e3) / 1e9, 1)}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
 
-    batched = served = wami = plain = match = median = None
+    batched = served = wami = plain = match = median = phog = None
     sections = world == 1  # the side workloads run once, on a single GPU
     if sections and not args.no_wami:
         wami = wami_section(ih, dev, LAYOUTS[args.layout][0])
@@ -408,6 +408,8 @@ def run_engine(args):
         match = match_section(ih, dev, LAYOUTS[args.layout][0])
     if sections and not args.no_median:
         median = median_section(ih, dev, LAYOUTS[args.layout][0])
+    if sections and not args.no_phog:
+        phog = phog_section(ih, dev)
     if sections and not args.no_batched:
         # the batch and the serving loop have no rectangle queries: the slab
         # layout (no padding, one channel per group) suits them better
@@ -442,6 +444,7 @@ def run_engine(args):
             "plain": plain,
             "match": match,
             "median": median,
+            "phog": phog,
         }
         print(json.dumps(line))
     ih.ih_destroy(ctx)
@@ -621,6 +624,46 @@ def median_section(ih, dev, layout, n_frames=24, window=9, box=5):
     ih.ih_destroy(ctx)
     return {"workload": "1920x1080 gray video, 16 bins, median over 5x5 pixels x 9 frames (Algorithm 4)",
             "ms_per_frame": round(ms, 4), "frames_per_s": round(1e3 / ms, 1), "frames_timed": steps}
+
+
+def phog_section(ih, dev, runs=10):
+    """Algorithm 2 and Eq. 2.24 on a 512 x 512 grayscale search window: the
+    magnitude-weighted orientation integral histogram (tau = 8), a 64 x 64
+    target's 3-level pyramid descriptor, and the pyramid match kernel over
+    256 x 256 placements."""
+    import numpy as np
+    import torch
+    from paper_1711_01656_gb300 import synth
+    sw = torch.from_numpy(synth.blob_plane(512, 512, synth.config_seed(7))).to(dev)
+    ctx = ih.ih_create(dev.index or 0)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    L, wh, ww = 2, 64, 64
+    D = ih.phog_descriptor_len(L)
+    target = torch.empty((1, D), dtype=torch.int64, device=dev)
+    out = torch.empty((256, 256), dtype=torch.float32, device=dev)
+    tw = torch.tensor([[200, 210, 200 + wh - 1, 210 + ww - 1]], dtype=torch.int32, device=dev)
+    t_build, t_match = [], []
+    for rep in range(runs + 1):
+        ev[0].record()
+        h = ih.ih_phog_build(ctx, sw, 8)
+        ev[1].record()
+        ih.ih_phog_descriptors(ctx, h, L, tw, target)
+        ev[2].record()
+        ih.ih_phog_match(ctx, h, L, target.view(-1), wh, ww, (72, 82, 72 + 255, 82 + 255), out)
+        ev[3].record()
+        torch.cuda.synchronize()
+        ih.ih_release(ctx, h)
+        if rep:
+            t_build.append(ev[0].elapsed_time(ev[1]))
+            t_match.append(ev[2].elapsed_time(ev[3]))
+    best = int(out.view(-1).argmax().item())
+    ih.ih_destroy(ctx)
+    mb, mm = float(np.median(t_build)), float(np.median(t_match))
+    return {"workload": "512x512 gray search window, 9 orientation bins weighted by gradient magnitude, "
+                        "3-level pyramid (189 entries), 64x64 windows, 256x256 placements",
+            "build_ms": round(mb, 4), "match_ms": round(mm, 4),
+            "match_placements_per_s": 65536 / (mm / 1e3),
+            "best_placement_found": [72 + best // 256, 82 + best % 256], "target_at": [200, 210]}
 
 
 def plain_section(ih, dev, runs=50):
@@ -831,6 +874,7 @@ def main(argv=None):
     ap.add_argument("--no-plain", action="store_true", help="skip the 640x480 plain frame")
     ap.add_argument("--no-match", action="store_true", help="skip the sliding-window matching maps")
     ap.add_argument("--no-median", action="store_true", help="skip the spatio-temporal median video")
+    ap.add_argument("--no-phog", action="store_true", help="skip the pyramid-of-orientations matching")
     ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
