@@ -315,6 +315,13 @@ typedef struct {
 ih_status ih_profile_read(ih_ctx *ctx, ih_kernel_stat *out, int32_t max, int32_t *count,
                           int32_t reset);
 
+/* Restricts the event pairs of a context created with IH_CFG_PROFILE to the
+ * kernels named in `names` (host, n NUL-terminated strings as reported by
+ * ih_profile_read, e.g. "tiles/count+moments"); n = 0 restores all kernels.
+ * Fewer events perturb the timed work less.  IH_EINVAL without
+ * IH_CFG_PROFILE or for an unknown name. */
+ih_status ih_profile_select(ih_ctx *ctx, const char *const *names, int32_t n);
+
 /* Kernel launches issued by this context since it was created (all of them
  * are this library's own kernels). */
 int64_t ih_launch_count(ih_ctx *ctx);

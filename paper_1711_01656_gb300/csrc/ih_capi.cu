@@ -56,6 +56,7 @@ cudaEvent_t take_event(ih_ctx *ctx)
 void prof_mark_cb(void *p, int kid, int phase, cudaStream_t st)
 {
     ih_ctx *ctx = static_cast<ih_ctx *>(p);
+    if (!((ctx->prof_mask >> kid) & 1u)) return;
     cudaEvent_t e = take_event(ctx);
     cudaEventRecord(e, st);
     if (phase == 0) {
@@ -798,6 +799,24 @@ ih_status ih_destroy(ih_ctx *ctx)
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
     }
     delete ctx;
+    return IH_OK;
+}
+
+ih_status ih_profile_select(ih_ctx *ctx, const char *const *names, int32_t n)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!ctx->profiling) return fail(ctx, IH_EINVAL, "context was created without IH_CFG_PROFILE");
+    if (n < 0 || (n > 0 && !names)) return fail(ctx, IH_EINVAL, "ih_profile_select: bad arguments");
+    uint32_t mask = n ? 0u : ~0u;
+    for (int32_t i = 0; i < n; ++i) {
+        int kid = -1;
+        for (int k = 0; k < KID_COUNT; ++k)
+            if (names[i] && strcmp(names[i], kernel_name(k)) == 0) kid = k;
+        if (kid < 0) return fail(ctx, IH_EINVAL, "ih_profile_select: no kernel named %s", names[i] ? names[i] : "");
+        mask |= 1u << kid;
+    }
+    ctx->prof_mask = mask;
     return IH_OK;
 }
 

@@ -44,6 +44,7 @@ struct ih_ctx {
     int64_t prof_launches[ih::KID_COUNT] = {0};
     double prof_ms[ih::KID_COUNT] = {0};
     ih::Prof prof;
+    uint32_t prof_mask = ~0u;  // kernel ids (bits) that get event pairs
     uint64_t budget = 0;
     uint64_t used = 0;
     cudaMemPool_t pool = nullptr;

@@ -37,7 +37,7 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
              "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
-             "ih_phog_match")
+             "ih_phog_match", "ih_profile_select")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -122,6 +122,7 @@ def load_library(path: str = LIB_PATH):
             "ih_query_weighted": ([p, i32, p, i64, u32, u32, p, p], i32),
             "ih_match_window": ([p, i32, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_accumulate": ([p, i32, i32, i32, p], i32),
+            "ih_profile_select": ([p, p, i32], i32),
             "ih_phog_build": ([p, p, i32, i32, i64, i32, ctypes.POINTER(i32), p], i32),
             "ih_phog_descriptors": ([p, i32, i32, p, i64, p, p], i32),
             "ih_phog_match": ([p, i32, i32, p, i32, i32, p, p, p], i32),
@@ -352,6 +353,12 @@ def ih_profile_read(ctx, reset=True):
     n = ctypes.c_int32()
     _check(ctx, load_library().ih_profile_read(ctx, arr, 64, ctypes.byref(n), int(bool(reset))))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def ih_profile_select(ctx, names=()):
+    """Time only the named kernels (ih_profile_read names); () = all."""
+    arr = (ctypes.c_char_p * max(1, len(names)))(*[n.encode() for n in names])
+    _check(ctx, load_library().ih_profile_select(ctx, ctypes.cast(arr, ctypes.c_void_p), len(names)))
 
 
 def ih_batch_create(ctx, frames, rects=None, rect_counts=None, rect_out=None, windows=None, window_counts=None,
