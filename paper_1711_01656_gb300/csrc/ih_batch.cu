@@ -121,7 +121,7 @@ ih_status tune_frame(ih_ctx *ctx, const ih_frame &f, cudaStream_t st)
     }
     PlaneSet ps;
     if (!make_planeset(ctx, f, fr, planes, cpitch, ps)) return fail(ctx, IH_EINVAL, "too many bins for one build");
-    static const int kR[] = {32, 64, 128};
+    static const int kR[] = {8, 16, 32, 64, 128};
     static const int kWc[] = {128, 256, 512, 1024};
     std::vector<std::pair<int, int>> cands;
     size_t max_carry = 0;

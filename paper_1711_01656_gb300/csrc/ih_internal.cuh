@@ -80,6 +80,35 @@ inline void prof_mark(const Prof *p, int kid, int phase, cudaStream_t st)
     if (p && p->mark) p->mark(p->ctx, kid, phase, st);
 }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl is set up
+// while the previous kernel on its stream drains: its CTAs are dispatched as
+// soon as every CTA of the previous grid has exited, overlapping that grid's
+// completion and memory flush, and each calls pdl_wait() before it reads or
+// writes anything, which returns once the previous grid has completed and its
+// writes are visible.  No kernel triggers its dependents early (triggering at
+// a CTA's start filled the SMs with waiting CTAs and measured slower than the
+// implicit trigger at CTA exit).  Setting the environment variable IH_PDL=0
+// launches every kernel with plain stream order instead.
+bool pdl_enabled();
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 struct ChanDev {
     const uint8_t *plane;  // row r starts at plane + r * pitch
     int64_t pitch;

@@ -39,6 +39,8 @@
 // carry arrays between launches on one stream.
 #include <algorithm>
 
+#include <stdlib.h>
+
 #include "ih_internal.cuh"
 
 namespace ih {
@@ -333,6 +335,7 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
 template <bool WT>
 __global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
 {
+    pdl_wait();
     tile_sums_body<WT>(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
 }
 
@@ -354,6 +357,7 @@ __device__ __forceinline__ int find_frame(const int64_t *pre, int n, int64_t x)
 template <bool WT>
 __global__ void __launch_bounds__(kSumThreads) k_tile_sums_b(const BatchDev bd)
 {
+    pdl_wait();
     const int64_t *pre = WT ? bd.pre_sums1 : bd.pre_sums0;
     const int64_t flat = blockIdx.x;
     const int f = find_frame(pre, bd.n, flat);
@@ -497,6 +501,7 @@ __device__ __forceinline__ void carry_scan_item(const PlaneSet &ps, int64_t t)
 
 __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ PlaneSet ps)
 {
+    pdl_wait();
     const int64_t total = carry_scan_items(ps);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x)
         carry_scan_item(ps, t);
@@ -504,6 +509,7 @@ __global__ void __launch_bounds__(256) k_carry_scan(const __grid_constant__ Plan
 
 __global__ void __launch_bounds__(256) k_carry_scan_b(const BatchDev bd)
 {
+    pdl_wait();
     const int64_t total = bd.pre_scan[bd.n];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -916,6 +922,7 @@ __device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t
 template <int LAYOUT>
 __global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 3 : 4) k_tiles_count(const __grid_constant__ PlaneSet ps)
 {
+    pdl_wait();
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
     __shared__ int4 stages[4][LAYOUT == LAYOUT_BIN_MAJOR ? 1 : 32 * SlabStage<kGroupBins>::S];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -927,6 +934,7 @@ __global__ void __launch_bounds__(128, LAYOUT == LAYOUT_SLAB ? 3 : 4) k_tiles_co
 // Batched: warps over the concatenated units of all frames (any layout).
 __global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
 {
+    pdl_wait();
     __shared__ __align__(16) int32_t RLs[4][kMaxBandRows][kGroupBins];
     __shared__ int4 stages[4][32 * SlabStage<kGroupBins>::S];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1122,6 +1130,7 @@ constexpr size_t kTilesSmem = sizeof(CountSmem) > sizeof(MomentSmem) ? sizeof(Co
 template <int LAYOUT>
 __global__ void __launch_bounds__(128, 4) k_tiles(const __grid_constant__ PlaneSet ps, unsigned mom_blocks)
 {
+    pdl_wait();
     __shared__ __align__(16) unsigned char smem[kTilesSmem];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const TileGrid &g = ps.g;
@@ -1149,6 +1158,7 @@ __global__ void __launch_bounds__(128, 4) k_tiles(const __grid_constant__ PlaneS
 // frames, in one launch (count units as in k_tiles_count_b).
 __global__ void __launch_bounds__(128, 4) k_tiles_b(const BatchDev bd, unsigned mom_blocks)
 {
+    pdl_wait();
     __shared__ __align__(16) unsigned char smem[kTilesSmem];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (blockIdx.x < mom_blocks) {
@@ -1193,6 +1203,15 @@ size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
 int g_nsm = 148;
 
 }  // namespace
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("IH_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
+}
 
 size_t carry_bytes(const PlaneSet &ps)
 {
@@ -1262,20 +1281,20 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
     int n = 0;
     if (totals[0]) {
         prof_mark(prof, KID_SUMS_COUNT, 0, st);
-        k_tile_sums_b<false><<<(unsigned)totals[0], kSumThreads, sums_smem_bytes(kMaxBandRows, false), st>>>(bd);
+        launch_pdl(k_tile_sums_b<false>, (unsigned)totals[0], kSumThreads, sums_smem_bytes(kMaxBandRows, false), st, bd);
         prof_mark(prof, KID_SUMS_COUNT, 1, st);
         ++n;
     }
     if (totals[1]) {
         prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-        k_tile_sums_b<true><<<(unsigned)totals[1], kSumThreads, sums_smem_bytes(kMaxBandRows, true), st>>>(bd);
+        launch_pdl(k_tile_sums_b<true>, (unsigned)totals[1], kSumThreads, sums_smem_bytes(kMaxBandRows, true), st, bd);
         prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
         ++n;
     }
     if (totals[2]) {
         const int64_t blocks = (totals[2] + 255) / 256;
         prof_mark(prof, KID_SCAN, 0, st);
-        k_carry_scan_b<<<(unsigned)(blocks < 16384 ? blocks : 16384), 256, 0, st>>>(bd);
+        launch_pdl(k_carry_scan_b, (unsigned)(blocks < 16384 ? blocks : 16384), 256, 0, st, bd);
         prof_mark(prof, KID_SCAN, 1, st);
         ++n;
     }
@@ -1283,12 +1302,12 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
         // count and moment tiles of all frames in one launch
         const unsigned mblocks = (unsigned)((totals[4] + 3) / 4);
         prof_mark(prof, KID_TILES_BOTH, 0, st);
-        k_tiles_b<<<mblocks + (unsigned)((totals[3] + 3) / 4), 128, 0, st>>>(bd, mblocks);
+        launch_pdl(k_tiles_b, mblocks + (unsigned)((totals[3] + 3) / 4), 128, 0, st, bd, mblocks);
         prof_mark(prof, KID_TILES_BOTH, 1, st);
         ++n;
     } else if (totals[3]) {
         prof_mark(prof, KID_TILES_COUNT, 0, st);
-        k_tiles_count_b<<<(unsigned)((totals[3] + 3) / 4), 128, 0, st>>>(bd);
+        launch_pdl(k_tiles_count_b, (unsigned)((totals[3] + 3) / 4), 128, 0, st, bd);
         prof_mark(prof, KID_TILES_COUNT, 1, st);
         ++n;
     }
@@ -1315,20 +1334,20 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         const int nw_count = ps.nwin_count, nw_weighted = ps.nwin - ps.nwin_count;
         if (nw_count) {
             prof_mark(prof, KID_SUMS_COUNT, 0, st);
-            k_tile_sums<false><<<dim3(g.ns, g.nb, nw_count), kSumThreads, sums_smem_bytes(g.R, false), st>>>(ps, 0);
+            launch_pdl(k_tile_sums<false>, dim3(g.ns, g.nb, nw_count), kSumThreads, sums_smem_bytes(g.R, false), st, ps, 0);
             prof_mark(prof, KID_SUMS_COUNT, 1, st);
             ++n;
         }
         if (nw_weighted) {
             prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-            k_tile_sums<true><<<dim3(g.ns, g.nb, nw_weighted), kSumThreads, sums_smem_bytes(g.R, true), st>>>(ps, nw_count);
+            launch_pdl(k_tile_sums<true>, dim3(g.ns, g.nb, nw_weighted), kSumThreads, sums_smem_bytes(g.R, true), st, ps, nw_count);
             prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
             ++n;
         }
         const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.nb * ps.B;
         const int64_t blocks = (tot + 255) / 256;
         prof_mark(prof, KID_SCAN, 0, st);
-        k_carry_scan<<<(unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, st>>>(ps);
+        launch_pdl(k_carry_scan, (unsigned)(blocks < 8192 ? blocks : 8192), 256, 0, st, ps);
         prof_mark(prof, KID_SCAN, 1, st);
         ++n;
     }
@@ -1340,22 +1359,22 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         const unsigned mblocks = (unsigned)((mu + 3) / 4);
         prof_mark(prof, KID_TILES_BOTH, 0, st);
         if (ps.layout == LAYOUT_SLAB)
-            k_tiles<LAYOUT_SLAB><<<mblocks + blocks, 128, 0, st>>>(ps, mblocks);
+            launch_pdl(k_tiles<LAYOUT_SLAB>, mblocks + blocks, 128, 0, st, ps, mblocks);
         else if (ps.layout == LAYOUT_RECORD)
-            k_tiles<LAYOUT_RECORD><<<mblocks + blocks, 128, 0, st>>>(ps, mblocks);
+            launch_pdl(k_tiles<LAYOUT_RECORD>, mblocks + blocks, 128, 0, st, ps, mblocks);
         else
-            k_tiles<LAYOUT_BIN_MAJOR><<<mblocks + blocks, 128, 0, st>>>(ps, mblocks);
+            launch_pdl(k_tiles<LAYOUT_BIN_MAJOR>, mblocks + blocks, 128, 0, st, ps, mblocks);
         prof_mark(prof, KID_TILES_BOTH, 1, st);
         ++n;
         return cudaPeekAtLastError() == cudaSuccess ? n : -1;
     }
     prof_mark(prof, KID_TILES_COUNT, 0, st);
     if (ps.layout == LAYOUT_SLAB)
-        k_tiles_count<LAYOUT_SLAB><<<blocks, 128, 0, st>>>(ps);
+        launch_pdl(k_tiles_count<LAYOUT_SLAB>, blocks, 128, 0, st, ps);
     else if (ps.layout == LAYOUT_RECORD)
-        k_tiles_count<LAYOUT_RECORD><<<blocks, 128, 0, st>>>(ps);
+        launch_pdl(k_tiles_count<LAYOUT_RECORD>, blocks, 128, 0, st, ps);
     else
-        k_tiles_count<LAYOUT_BIN_MAJOR><<<blocks, 128, 0, st>>>(ps);
+        launch_pdl(k_tiles_count<LAYOUT_BIN_MAJOR>, blocks, 128, 0, st, ps);
     prof_mark(prof, KID_TILES_COUNT, 1, st);
     ++n;
     return cudaPeekAtLastError() == cudaSuccess ? n : -1;

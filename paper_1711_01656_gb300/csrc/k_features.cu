@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_features(const uint8_t *__restrict
                                                        uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog,
                                                        int64_t opitch)
 {
+    pdl_wait();
     features_tile(pr, pg, pb, pitch, H, W, out_rgb, out_i, out_hog, opitch, blockIdx.y, blockIdx.x);
 }
 
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_features(const uint8_t *__restrict
 __global__ void __launch_bounds__(kThreads) k_features_b(const FeatJob *__restrict__ jobs,
                                                          const int64_t *__restrict__ pre, int n)
 {
+    pdl_wait();
     const int64_t flat = blockIdx.x;
     int lo = 0, hi = n;
     while (hi - lo > 1) {
@@ -165,7 +167,7 @@ int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_
 {
     dim3 grid((W + kTC - 1) / kTC, (H + kTR - 1) / kTR);
     prof_mark(prof, KID_FEATURES, 0, st);
-    k_features<<<grid, kThreads, 0, st>>>(r, g, b, pitch, H, W, out_rgb, out_i, out_hog, out_pitch);
+    launch_pdl(k_features, grid, kThreads, 0, st, r, g, b, pitch, H, W, out_rgb, out_i, out_hog, out_pitch);
     prof_mark(prof, KID_FEATURES, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -180,7 +182,7 @@ int launch_features_batch(const FeatJob *jobs, const int64_t *pre, int n, int64_
 {
     if (!total) return 0;
     prof_mark(prof, KID_FEATURES, 0, st);
-    k_features_b<<<(unsigned)total, kThreads, 0, st>>>(jobs, pre, n);
+    launch_pdl(k_features_b, (unsigned)total, kThreads, 0, st, jobs, pre, n);
     prof_mark(prof, KID_FEATURES, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -40,6 +40,7 @@ __device__ __forceinline__ int64_t isqrt_exact(int64_t n)
 __global__ void __launch_bounds__(256) k_phog_planes(const uint8_t *__restrict__ gray, int64_t pitch, int H, int W,
                                                      int tau, uint8_t *__restrict__ bins, int32_t *__restrict__ wt)
 {
+    pdl_wait();
     const int64_t total = (int64_t)H * W;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -60,6 +61,7 @@ __global__ void __launch_bounds__(256) k_phog_planes(const uint8_t *__restrict__
 __global__ void __launch_bounds__(256) k_phog_rows(const uint8_t *__restrict__ bins, const int32_t *__restrict__ wt,
                                                    int H, int W, int64_t P, int64_t *__restrict__ out)
 {
+    pdl_wait();
     const int lane = threadIdx.x & 31;
     const int64_t unit = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (unit >= (int64_t)kPhogBins * H) return;
@@ -94,6 +96,7 @@ __global__ void __launch_bounds__(256) k_phog_rows(const uint8_t *__restrict__ b
 // column).
 __global__ void __launch_bounds__(256) k_phog_cols(int H, int64_t P, int64_t *__restrict__ out)
 {
+    pdl_wait();
     const int64_t total = (int64_t)kPhogBins * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -142,6 +145,7 @@ __global__ void __launch_bounds__(256) k_phog_desc(const int64_t *__restrict__ i
                                                    const int32_t *__restrict__ wins, int64_t n, int64_t D,
                                                    int64_t *__restrict__ out, int *err)
 {
+    pdl_wait();
     const int64_t total = n * D;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -167,6 +171,7 @@ __global__ void __launch_bounds__(256) k_phog_match(const int64_t *__restrict__ 
                                                     const int64_t *__restrict__ target, int64_t D, int wh, int ww,
                                                     int sr0, int sc0, int sr1, int sc1, float *__restrict__ out)
 {
+    pdl_wait();
     extern __shared__ int64_t s_t[];
     for (int64_t k = threadIdx.x; k < D; k += blockDim.x) s_t[k] = __ldg(target + k);
     __syncthreads();
@@ -204,10 +209,10 @@ int launch_phog_build(const uint8_t *gray, int64_t pitch, int H, int W, int tau,
                       int64_t P, int64_t *ih, cudaStream_t st, const Prof *prof)
 {
     prof_mark(prof, KID_PHOG_BUILD, 0, st);
-    k_phog_planes<<<grid_for((int64_t)H * W), 256, 0, st>>>(gray, pitch, H, W, tau, bins, wt);
+    launch_pdl(k_phog_planes, grid_for((int64_t)H * W), 256, 0, st, gray, pitch, H, W, tau, bins, wt);
     const int64_t warps = (int64_t)kPhogBins * H;
-    k_phog_rows<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(bins, wt, H, W, P, ih);
-    k_phog_cols<<<grid_for((int64_t)kPhogBins * P), 256, 0, st>>>(H, P, ih);
+    launch_pdl(k_phog_rows, (unsigned)((warps + 7) / 8), 256, 0, st, bins, wt, H, W, P, ih);
+    launch_pdl(k_phog_cols, grid_for((int64_t)kPhogBins * P), 256, 0, st, H, P, ih);
     prof_mark(prof, KID_PHOG_BUILD, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
 }
@@ -217,7 +222,7 @@ int launch_phog_descriptors(const int64_t *ih, int H, int W, int64_t P, int L, c
 {
     const int64_t D = phog_descriptor_len(L);
     prof_mark(prof, KID_PHOG_QUERY, 0, st);
-    k_phog_desc<<<grid_for(n * D), 256, 0, st>>>(ih, H, W, P, L, wins, n, D, out, err);
+    launch_pdl(k_phog_desc, grid_for(n * D), 256, 0, st, ih, H, W, P, L, wins, n, D, out, err);
     prof_mark(prof, KID_PHOG_QUERY, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -228,7 +233,7 @@ int launch_phog_match(const int64_t *ih, int H, int64_t P, int L, const int64_t 
     const int64_t D = phog_descriptor_len(L);
     const int64_t total = (int64_t)(sr1 - sr0 + 1) * (sc1 - sc0 + 1);
     prof_mark(prof, KID_PHOG_QUERY, 0, st);
-    k_phog_match<<<grid_for(total), 256, (size_t)D * 8, st>>>(ih, H, P, L, target, D, wh, ww, sr0, sc0, sr1, sc1,
+    launch_pdl(k_phog_match, grid_for(total), 256, (size_t)D * 8, st, ih, H, P, L, target, D, wh, ww, sr0, sc0, sr1, sc1,
                                                                out);
     prof_mark(prof, KID_PHOG_QUERY, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;

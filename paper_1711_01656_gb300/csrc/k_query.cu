@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ Cou
                                                      const int32_t *__restrict__ rects, int64_t n,
                                                      int32_t *__restrict__ out, int *err)
 {
+    pdl_wait();
     __shared__ int64_t s_off[kMaxGroups];
     __shared__ int s_nb[kMaxGroups], s_b0[kMaxGroups];
     __shared__ int16_t s_rw[kMaxGroups], s_w0[kMaxGroups], s_qp[kMaxBins / 4], s_wb[kMaxBins];
@@ -223,6 +224,7 @@ __device__ __forceinline__ int find_job(const int64_t *pre, int n, int64_t x)
 __global__ void __launch_bounds__(256) k_query_rects_b(const QueryJob *__restrict__ jobs,
                                                        const int64_t *__restrict__ pre, int n, int *err)
 {
+    pdl_wait();
     const int64_t total = pre[n];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -441,6 +443,7 @@ __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ 
                                                         const int32_t *__restrict__ wins, int64_t n, int layers,
                                                         int normalize, float *__restrict__ out, int *err)
 {
+    pdl_wait();
     const int64_t total = n * m.Bw;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -454,6 +457,7 @@ __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ 
 __global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__restrict__ jobs,
                                                           const int64_t *__restrict__ pre, int n, int *err)
 {
+    pdl_wait();
     const int64_t total = pre[n];
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -474,6 +478,7 @@ __global__ void __launch_bounds__(256) k_match_window(const __grid_constant__ Co
                                                       const int32_t *__restrict__ target, int wh, int ww, int sr0,
                                                       int sc0, int sr1, int sc1, int32_t *__restrict__ out)
 {
+    pdl_wait();
     __shared__ int64_t s_base[kMaxBins];  // element offset of bin (bin0 + i) at pixel (0, 0)
     __shared__ int s_px[kMaxBins], s_t[kMaxBins];
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
@@ -514,6 +519,7 @@ __global__ void __launch_bounds__(256) k_match_window(const __grid_constant__ Co
 __global__ void __launch_bounds__(256) k_accumulate(int4 *__restrict__ dst, const int4 *__restrict__ add,
                                                     const int4 *__restrict__ sub, int64_t n4)
 {
+    pdl_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
         int4 d = dst[i];
         if (add) {
@@ -534,6 +540,7 @@ __global__ void __launch_bounds__(256) k_accumulate(int4 *__restrict__ dst, cons
 __global__ void __launch_bounds__(256) k_local_median(const __grid_constant__ CountView v, int bin0, int nbins,
                                                       int m, int n, int32_t *__restrict__ out)
 {
+    pdl_wait();
     __shared__ int64_t s_base[kMaxBins];
     __shared__ int s_px[kMaxBins];
     for (int i = threadIdx.x; i < nbins; i += blockDim.x) {
@@ -581,6 +588,7 @@ __global__ void __launch_bounds__(256) k_local_median(const __grid_constant__ Co
 
 __global__ void __launch_bounds__(256) k_export(const __grid_constant__ CountView v, int32_t *__restrict__ dst)
 {
+    pdl_wait();
     const int64_t total = (int64_t)v.B * v.H * v.W;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -594,6 +602,7 @@ __global__ void __launch_bounds__(256) k_export(const __grid_constant__ CountVie
 __global__ void __launch_bounds__(256) k_export_moments(const void *__restrict__ m, int m32, int Bw, int H, int W,
                                                         int64_t P, int k, int64_t *__restrict__ dst)
 {
+    pdl_wait();
     const int64_t total = (int64_t)Bw * H * W;
     const int64_t plane = (int64_t)Bw * H * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -617,7 +626,7 @@ int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int3
 {
     if (n == 0) return 0;
     prof_mark(prof, KID_QUERY_RECTS, 0, st);
-    k_query_rects<<<grid_for(n * rect_items(v)), 256, 0, st>>>(v, rects, n, out, err);
+    launch_pdl(k_query_rects, grid_for(n * rect_items(v)), 256, 0, st, v, rects, n, out, err);
     prof_mark(prof, KID_QUERY_RECTS, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -629,11 +638,11 @@ int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t
     prof_mark(prof, KID_QUERY_WEIGHTED, 0, st);
     const unsigned blocks = grid_for(n * m.Bw);
     if (kernel == IH_KERNEL_MANHATTAN)
-        k_query_weighted<IH_KERNEL_MANHATTAN><<<blocks, 256, 0, st>>>(v, m, wins, n, layers, normalize, out, err);
+        launch_pdl(k_query_weighted<IH_KERNEL_MANHATTAN>, blocks, 256, 0, st, v, m, wins, n, layers, normalize, out, err);
     else if (kernel == IH_KERNEL_WEDDING_CAKE)
-        k_query_weighted<IH_KERNEL_WEDDING_CAKE><<<blocks, 256, 0, st>>>(v, m, wins, n, layers, normalize, out, err);
+        launch_pdl(k_query_weighted<IH_KERNEL_WEDDING_CAKE>, blocks, 256, 0, st, v, m, wins, n, layers, normalize, out, err);
     else
-        k_query_weighted<IH_KERNEL_EPANECHNIKOV><<<blocks, 256, 0, st>>>(v, m, wins, n, layers, normalize, out, err);
+        launch_pdl(k_query_weighted<IH_KERNEL_EPANECHNIKOV>, blocks, 256, 0, st, v, m, wins, n, layers, normalize, out, err);
     prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -644,13 +653,13 @@ int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const i
     int k = 0;
     if (total_rects) {
         prof_mark(prof, KID_QUERY_RECTS, 0, st);
-        k_query_rects_b<<<grid_for(total_rects), 256, 0, st>>>(jobs, pre_rects, n, err);
+        launch_pdl(k_query_rects_b, grid_for(total_rects), 256, 0, st, jobs, pre_rects, n, err);
         prof_mark(prof, KID_QUERY_RECTS, 1, st);
         ++k;
     }
     if (total_wins) {
         prof_mark(prof, KID_QUERY_WEIGHTED, 0, st);
-        k_query_weighted_b<<<grid_for(total_wins), 256, 0, st>>>(jobs, pre_wins, n, err);
+        launch_pdl(k_query_weighted_b, grid_for(total_wins), 256, 0, st, jobs, pre_wins, n, err);
         prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
         ++k;
     }
@@ -661,7 +670,7 @@ int launch_export_moments(const void *m, int m32, int Bw, int H, int W, int64_t 
                           cudaStream_t st, const Prof *prof)
 {
     prof_mark(prof, KID_EXPORT, 0, st);
-    k_export_moments<<<grid_for((int64_t)Bw * H * W), 256, 0, st>>>(m, m32, Bw, H, W, P, k, dst);
+    launch_pdl(k_export_moments, grid_for((int64_t)Bw * H * W), 256, 0, st, m, m32, Bw, H, W, P, k, dst);
     prof_mark(prof, KID_EXPORT, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -671,7 +680,7 @@ int launch_match_window(const CountView &v, int bin0, int nbins, const int32_t *
 {
     const int64_t total = (int64_t)(sr1 - sr0 + 1) * (sc1 - sc0 + 1);
     prof_mark(prof, KID_MATCH, 0, st);
-    k_match_window<<<grid_for(total), 256, 0, st>>>(v, bin0, nbins, target, wh, ww, sr0, sc0, sr1, sc1, out);
+    launch_pdl(k_match_window, grid_for(total), 256, 0, st, v, bin0, nbins, target, wh, ww, sr0, sc0, sr1, sc1, out);
     prof_mark(prof, KID_MATCH, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -681,7 +690,7 @@ int launch_accumulate(int32_t *dst, const int32_t *add, const int32_t *sub, int6
 {
     const int64_t n4 = n / 4;
     prof_mark(prof, KID_ACCUMULATE, 0, st);
-    k_accumulate<<<grid_for(n4), 256, 0, st>>>(reinterpret_cast<int4 *>(dst), reinterpret_cast<const int4 *>(add),
+    launch_pdl(k_accumulate, grid_for(n4), 256, 0, st, reinterpret_cast<int4 *>(dst), reinterpret_cast<const int4 *>(add),
                                                reinterpret_cast<const int4 *>(sub), n4);
     prof_mark(prof, KID_ACCUMULATE, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
@@ -691,7 +700,7 @@ int launch_local_median(const CountView &v, int bin0, int nbins, int m, int n, i
                         const Prof *prof)
 {
     prof_mark(prof, KID_MEDIAN, 0, st);
-    k_local_median<<<grid_for((int64_t)v.H * v.W), 256, 0, st>>>(v, bin0, nbins, m, n, out);
+    launch_pdl(k_local_median, grid_for((int64_t)v.H * v.W), 256, 0, st, v, bin0, nbins, m, n, out);
     prof_mark(prof, KID_MEDIAN, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
@@ -699,7 +708,7 @@ int launch_local_median(const CountView &v, int bin0, int nbins, int m, int n, i
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof)
 {
     prof_mark(prof, KID_EXPORT, 0, st);
-    k_export<<<grid_for((int64_t)v.B * v.H * v.W), 256, 0, st>>>(v, dst);
+    launch_pdl(k_export, grid_for((int64_t)v.B * v.H * v.W), 256, 0, st, v, dst);
     prof_mark(prof, KID_EXPORT, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
