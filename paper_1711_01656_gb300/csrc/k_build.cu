@@ -389,7 +389,9 @@ __device__ __forceinline__ void carry_scan_item(const PlaneSet &ps, int64_t t)
     const int wch = ps.wch;
     const int64_t bin0 = wch >= 0 ? ps.chan[wch].bin_off : 0;
     const int64_t Bw = wch >= 0 ? ps.chan[wch].bins : 0;
-    const int64_t nA = B * g.W, nB = B * g.H;
+    const int64_t nA = B * g.W, nB = B * g.H, nC = (int64_t)g.nb * B;
+    // the corner scans (the longest items) take the first indices
+    t = t < nC ? t + nA + nB : t - nC;
     {
         if (t < nA) {  // G(i, c, b): exclusive over bands
             const int64_t b = t / g.W, c = t % g.W, wb = b - bin0;
@@ -475,24 +477,34 @@ __device__ __forceinline__ void carry_scan_item(const PlaneSet &ps, int64_t t)
             const long long R0 = (long long)i * g.R;
             int32_t run = 0;
             long long rw[4] = {0, 0, 0, 0};  // w = c, r, c^2, r^2
-            for (int j = 0; j < g.ns; ++j) {
-                const int64_t ti = ((int64_t)i * g.ns + j) * B + b;
-                const int32_t n = ps.tilesum[ti];
-                ps.corner[ti] = run;
-                run += n;
+            for (int j0 = 0; j0 < g.ns; j0 += kScanBatch) {
+                const int nj = min(kScanBatch, g.ns - j0);
+                int32_t v[kScanBatch];
+#pragma unroll
+                for (int k = 0; k < kScanBatch; ++k)
+                    if (k < nj) v[k] = ps.tilesum[((int64_t)i * g.ns + j0 + k) * B + b];
+#pragma unroll
+                for (int k = 0; k < kScanBatch; ++k)
+                    if (k < nj) {
+                        ps.corner[((int64_t)i * g.ns + j0 + k) * B + b] = run;
+                        run += v[k];
+                    }
                 if (wt) {
-                    const int64_t wi = (((int64_t)i * g.ns + j) * Bw + wb) * 4;
-                    const int64_t *tw = ps.tile_w + wi;
-                    int64_t *cw = ps.corner_w + wi;
-                    cw[0] = rw[0];
-                    cw[1] = rw[1];
-                    cw[2] = rw[2];
-                    cw[3] = rw[3];
-                    const long long C0 = (long long)j * g.Wc;
-                    rw[0] += C0 * n + tw[2];
-                    rw[1] += R0 * n + tw[0];
-                    rw[2] += C0 * C0 * n + 2 * C0 * tw[2] + tw[3];
-                    rw[3] += R0 * R0 * n + 2 * R0 * tw[0] + tw[1];
+                    for (int k = 0; k < nj; ++k) {
+                        const int j = j0 + k;
+                        const int64_t wi = (((int64_t)i * g.ns + j) * Bw + wb) * 4;
+                        const int64_t *tw = ps.tile_w + wi;
+                        int64_t *cw = ps.corner_w + wi;
+                        cw[0] = rw[0];
+                        cw[1] = rw[1];
+                        cw[2] = rw[2];
+                        cw[3] = rw[3];
+                        const long long C0 = (long long)j * g.Wc, n = ps.tilesum[((int64_t)i * g.ns + j) * B + b];
+                        rw[0] += C0 * n + tw[2];
+                        rw[1] += R0 * n + tw[0];
+                        rw[2] += C0 * C0 * n + 2 * C0 * tw[2] + tw[3];
+                        rw[3] += R0 * R0 * n + 2 * R0 * tw[0] + tw[1];
+                    }
                 }
             }
         }

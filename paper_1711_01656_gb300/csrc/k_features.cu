@@ -22,7 +22,7 @@
 // 2^22 * 1e-5 * |g| > 41 |g|.  Every term stays below 2^31 (4.2e6 * 255 +
 // 4.2e6 * 255 < 2.1e9), so the test runs in int32.
 //
-// One CTA computes a 32 x 128 tile, 4 adjacent pixels per thread as one
+// One CTA computes a 16 x 128 tile, 4 adjacent pixels per thread as one
 // 32-bit word of bytes.  It stages I for the tile plus a 4-pixel halo in
 // shared memory as words, clamping coordinates when it loads, which gives the
 // replicated borders: the staged byte for column x is I at clamp(x), which is
@@ -36,7 +36,7 @@ namespace ih {
 
 namespace {
 
-constexpr int kTR = 32, kTC = 128, kHalo = 4;
+constexpr int kTR = 16, kTC = 128, kHalo = 4;
 constexpr int kSR = kTR + 2 * kHalo;  // staged rows
 constexpr int kSW = kTC / 4 + 2;      // staged words per row (one halo word each side)
 constexpr int kThreads = 256;
