@@ -332,11 +332,126 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
     }
 }
 
+// Tile sums of a window of an unweighted channel, 4 warps per (band, strip,
+// window).  Row rr of the band goes to warp rr % 4; a lane holds 4 adjacent
+// columns of the 128-column pass.  A pixel's window-local bin is one 8-bit
+// field of NW packed words (4 bins per word): a lane's per-column words add
+// up its rows (at most 32 per field), and a row's words over the warp are
+// one redux.sync.add each (at most 128 per field), so no field overflows.
+constexpr int kCntThreads = 128;
+
+template <int NW>
+__device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, int i, int widx,
+                                                     uint32_t (*colpk)[16][32], int32_t (*rows)[kMaxBandRows])
+{
+    const TileGrid &g = ps.g;
+    const GroupDev wd = ps.win[widx];
+    const ChanDev &ch = ps.chan[wd.chan];
+    const int R0 = i * g.R, nr = min(g.R, g.H - R0);
+    const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
+    const int nbw = wd.nb, blo = wd.b_lo;
+    const int64_t bglob = ch.bin_off + wd.b_lo;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const uint8_t *const pl = ch.plane;
+    const int64_t pt = ch.pitch;
+    const int bins = ch.bins, mode = ch.mode;
+    const bool vec_ok = ((pt & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl) & 3) == 0);
+
+    for (int k = tid; k < nbw * nr; k += kCntThreads) rows[k / nr][k % nr] = 0;
+    __syncthreads();
+    for (int cp = C0; cp < C1; cp += kChunk) {
+        const int c = cp + lane * 4;
+        const int nvalid = max(0, min(4, C1 - c));
+        uint32_t col[4][NW];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) col[jj][k] = 0u;
+        // two rows of this warp in flight
+        uint32_t pa = wid < nr ? load4(pl, pt, R0 + wid, c, C1, vec_ok) : 0u;
+        uint32_t pb = wid + 4 < nr ? load4(pl, pt, R0 + wid + 4, c, C1, vec_ok) : 0u;
+        for (int rr = wid; rr < nr; rr += 4) {
+            const uint32_t px = pa;
+            pa = pb;
+            if (rr + 8 < nr) pb = load4(pl, pt, R0 + rr + 8, c, C1, vec_ok);
+            uint32_t rw[NW];
+#pragma unroll
+            for (int k = 0; k < NW; ++k) rw[k] = 0u;
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const int q = bin_of((px >> (8 * jj)) & 0xff, bins, mode) - blo;
+                const unsigned d = (jj < nvalid && q >= 0 && q < nbw) ? (unsigned)q : 0xFFFFFFFFu;
+                const uint32_t e = 1u << ((d & 3u) << 3);
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    const uint32_t v = (d >> 2) == (unsigned)k ? e : 0u;
+                    col[jj][k] += v;
+                    rw[k] += v;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < NW; ++k) rw[k] = __reduce_add_sync(kFull, rw[k]);
+            if (lane < nbw) {
+                uint32_t w = rw[0];
+#pragma unroll
+                for (int k = 1; k < NW; ++k)
+                    if ((lane >> 2) == k) w = rw[k];
+                rows[lane][rr] += (int32_t)((w >> ((lane & 3) << 3)) & 0xFFu);
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) colpk[wid][jj * 4 + k][lane] = col[jj][k];
+        __syncthreads();
+        {
+            // column 4 l + jj of the pass: thread (warp jj, lane l)
+            const int l = lane, jj = wid, cc = 4 * l + jj;
+            if (cp + cc < C1) {
+                uint32_t sw[NW];
+#pragma unroll
+                for (int k = 0; k < NW; ++k)
+                    sw[k] = colpk[0][jj * 4 + k][l] + colpk[1][jj * 4 + k][l] + colpk[2][jj * 4 + k][l] +
+                            colpk[3][jj * 4 + k][l];
+                int32_t *dst = ps.colsum + ((int64_t)i * ps.B + bglob) * g.W + cp + cc;
+#pragma unroll
+                for (int b = 0; b < 4 * NW; ++b)
+                    if (b < nbw) dst[(int64_t)b * g.W] = (int32_t)((sw[b >> 2] >> ((b & 3) << 3)) & 0xFFu);
+            }
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < nbw * nr; k += kCntThreads) {
+        const int b = k / nr, rr = k % nr;
+        ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = rows[b][rr];
+    }
+    for (int b = wid; b < nbw; b += 4) {
+        int32_t t = 0;
+        for (int rr = lane; rr < nr; rr += 32) t += rows[b][rr];
+        t = (int32_t)__reduce_add_sync(kFull, (uint32_t)t);
+        if (lane == 0) ps.tilesum[((int64_t)i * g.ns + j) * ps.B + bglob + b] = t;
+    }
+}
+
+__device__ __forceinline__ void tile_sums_count(const PlaneSet &ps, int j, int i, int widx)
+{
+    __shared__ uint32_t colpk[4][16][32];
+    __shared__ int32_t rows[kWindowBins][kMaxBandRows];
+    if (ps.win[widx].nb <= 8)
+        tile_sums_count_body<2>(ps, j, i, widx, colpk, rows);
+    else
+        tile_sums_count_body<4>(ps, j, i, widx, colpk, rows);
+}
+
 template <bool WT>
-__global__ void __launch_bounds__(kSumThreads) k_tile_sums(const __grid_constant__ PlaneSet ps, int win0)
+__global__ void __launch_bounds__(WT ? kSumThreads : kCntThreads) k_tile_sums(const __grid_constant__ PlaneSet ps,
+                                                                              int win0)
 {
     pdl_wait();
-    tile_sums_body<WT>(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
+    if constexpr (WT)
+        tile_sums_body<true>(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
+    else
+        tile_sums_count(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
 }
 
 // Largest f in [0, n) with pre[f] <= x (pre is a prefix sum of n counts).
@@ -355,7 +470,7 @@ __device__ __forceinline__ int find_frame(const int64_t *pre, int n, int64_t x)
 
 // Batched: one CTA per (frame, window, band, strip), frames concatenated.
 template <bool WT>
-__global__ void __launch_bounds__(kSumThreads) k_tile_sums_b(const BatchDev bd)
+__global__ void __launch_bounds__(WT ? kSumThreads : kCntThreads) k_tile_sums_b(const BatchDev bd)
 {
     pdl_wait();
     const int64_t *pre = WT ? bd.pre_sums1 : bd.pre_sums0;
@@ -365,7 +480,10 @@ __global__ void __launch_bounds__(kSumThreads) k_tile_sums_b(const BatchDev bd)
     const int64_t local = flat - pre[f];
     const int64_t per = (int64_t)ps.g.ns * ps.g.nb;
     const int z = (int)(local / per), rem = (int)(local % per);
-    tile_sums_body<WT>(ps, rem % ps.g.ns, rem / ps.g.ns, (WT ? ps.nwin_count : 0) + z);
+    if constexpr (WT)
+        tile_sums_body<true>(ps, rem % ps.g.ns, rem / ps.g.ns, ps.nwin_count + z);
+    else
+        tile_sums_count(ps, rem % ps.g.ns, rem / ps.g.ns, z);
 }
 
 // ------------------------------------------------------------- carry scan
@@ -1276,9 +1394,7 @@ void prepare_kernels()
 {
     static bool attrs = false;
     if (!attrs) {
-        set_max_smem(k_tile_sums<false>, sums_smem_bytes(kMaxBandRows, false));
         set_max_smem(k_tile_sums<true>, sums_smem_bytes(kMaxBandRows, true));
-        set_max_smem(k_tile_sums_b<false>, sums_smem_bytes(kMaxBandRows, false));
         set_max_smem(k_tile_sums_b<true>, sums_smem_bytes(kMaxBandRows, true));
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1293,7 +1409,7 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
     int n = 0;
     if (totals[0]) {
         prof_mark(prof, KID_SUMS_COUNT, 0, st);
-        launch_pdl(k_tile_sums_b<false>, (unsigned)totals[0], kSumThreads, sums_smem_bytes(kMaxBandRows, false), st, bd);
+        launch_pdl(k_tile_sums_b<false>, (unsigned)totals[0], kCntThreads, 0, st, bd);
         prof_mark(prof, KID_SUMS_COUNT, 1, st);
         ++n;
     }
@@ -1346,7 +1462,7 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         const int nw_count = ps.nwin_count, nw_weighted = ps.nwin - ps.nwin_count;
         if (nw_count) {
             prof_mark(prof, KID_SUMS_COUNT, 0, st);
-            launch_pdl(k_tile_sums<false>, dim3(g.ns, g.nb, nw_count), kSumThreads, sums_smem_bytes(g.R, false), st, ps, 0);
+            launch_pdl(k_tile_sums<false>, dim3(g.ns, g.nb, nw_count), kCntThreads, 0, st, ps, 0);
             prof_mark(prof, KID_SUMS_COUNT, 1, st);
             ++n;
         }
