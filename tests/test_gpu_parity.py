@@ -382,10 +382,11 @@ def test_moments_on_multichannel_frame(ihlib, ctx, wch):
     ihlib.ih_release(ctx, hdl)
 
 
-def test_moment_planes_u32_and_weighted(ihlib, ctx):
+@pytest.mark.parametrize("bins", [16, 5])
+def test_moment_planes_u32_and_weighted(ihlib, ctx, bins):
     """32-bit moment planes hold the int64 planes modulo 2^32 and still give
     the exact weighted histograms of windows with sides up to 256."""
-    h, w, bins = 700, 900, 16
+    h, w = 700, 900
     img = synth.blob_plane(h, w, 44)
     pix = torch.from_numpy(img).to(DEV)[None]
     hdl, = ihlib.ih_build(ctx, ihlib.Frame(pix, [(bins, 0)], weighted_channel=0, layout=1, moment_bits=32))
