@@ -772,6 +772,9 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
     const int blo0 = gr.b_lo, nb0 = gr.nb, blo1 = gr.b_lo1, nbs1 = gr.nb1;
     const bool vec_ok = ((pt0 & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl0) & 3) == 0);
     const bool vec_ok1 = ((pt1 & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl1) & 3) == 0);
+    // the second segment's loads and bin tests only where the group has one
+    // (a warp-uniform branch inside the one loop body of the frame)
+    const bool two = SEG2 && nbs1 > 0;
     for (int cc = C0; cc < C1; cc += kChunk) {
         const int c = cc + lane * 4;
         const int nvalid = max(0, min(4, C1 - c));
@@ -798,7 +801,7 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             pf[k] = (k < nr) ? load4(pl0, pt0, R0 + k, c, C1, vec_ok) : 0u;
-            pg[k] = (SEG2 && k < nr) ? load4(pl1, pt1, R0 + k, c, C1, vec_ok1) : 0u;
+            pg[k] = (two && k < nr) ? load4(pl1, pt1, R0 + k, c, C1, vec_ok1) : 0u;
         }
         if constexpr (PAIR) {
         for (int rr0 = 0; rr0 < nr; rr0 += 4) {
@@ -942,28 +945,33 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
             pf[1] = pf[2];
             pf[2] = pf[3];
             pf[3] = (ra + 4 < nr) ? load4(pl0, pt0, R0 + ra + 4, c, C1, vec_ok) : 0u;
-            if (SEG2) {
+            if (two) {
                 pg[0] = pg[1];
                 pg[1] = pg[2];
                 pg[2] = pg[3];
                 pg[3] = (ra + 4 < nr) ? load4(pl1, pt1, R0 + ra + 4, c, C1, vec_ok1) : 0u;
+            }
+            uint32_t ea0[4] = {0u, 0u, 0u, 0u}, ea1[4] = {0u, 0u, 0u, 0u};
+            if (two) {
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int ya = bin_of((pya >> (8 * jj)) & 0xff, bins1, mode1);
+                    unsigned fa = (jj < nvalid && ya >= 0) ? (unsigned)(ya - blo1) : 0xFFFFFFFFu;
+                    fa = fa < (unsigned)nbs1 ? fa + nb0 : 0xFFFFFFFFu;
+                    ea0[jj] = fa < 4u ? (1u << (fa << 3)) : 0u;
+                    ea1[jj] = (fa - 4u) < 4u ? (1u << ((fa - 4u) << 3)) : 0u;
+                }
             }
             uint32_t Pa0[4], Pa1[4];
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
                 const int qa = bin_of((pxa >> (8 * jj)) & 0xff, bins0, mode0);
                 unsigned da = (jj < nvalid && qa >= 0) ? (unsigned)(qa - blo0) : 0xFFFFFFFFu;
-                uint32_t ea0 = 0u, ea1 = 0u;
-                if (SEG2) {
-                    if (da >= (unsigned)nb0) da = 0xFFFFFFFFu;
-                    const int ya = bin_of((pya >> (8 * jj)) & 0xff, bins1, mode1);
-                    unsigned fa = (jj < nvalid && ya >= 0) ? (unsigned)(ya - blo1) : 0xFFFFFFFFu;
-                    fa = fa < (unsigned)nbs1 ? fa + nb0 : 0xFFFFFFFFu;
-                    ea0 = fa < 4u ? (1u << (fa << 3)) : 0u;
-                    ea1 = (fa - 4u) < 4u ? (1u << ((fa - 4u) << 3)) : 0u;
-                }
-                Pa0[jj] = (jj ? Pa0[jj - 1] : 0u) + (da < 4u ? (1u << (da << 3)) : 0u) + ea0;
-                Pa1[jj] = (jj ? Pa1[jj - 1] : 0u) + ((da - 4u) < 4u ? (1u << ((da - 4u) << 3)) : 0u) + ea1;
+                // a bin of the first channel beyond the group is dropped; the
+                // second channel's bins follow at field nb
+                if (SEG2 && da >= (unsigned)nb0) da = 0xFFFFFFFFu;
+                Pa0[jj] = (jj ? Pa0[jj - 1] : 0u) + (da < 4u ? (1u << (da << 3)) : 0u) + ea0[jj];
+                Pa1[jj] = (jj ? Pa1[jj - 1] : 0u) + ((da - 4u) < 4u ? (1u << ((da - 4u) << 3)) : 0u) + ea1[jj];
             }
             const uint32_t ia0 = warp_incl_scan(Pa0[3], lane);
             const uint32_t ia1 = NB > 4 ? warp_incl_scan(Pa1[3], lane) : 0u;
