@@ -1158,6 +1158,8 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
             }
         }
         const long long Cb = cc;
+        const int Cb32 = cc;
+        const long long CbCb = Cb * Cb;
         uint32_t pf[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) pf[k] = (k < nr) ? load4(ch, R0 + k, c, C1, vec_ok) : 0u;
@@ -1187,17 +1189,20 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                 const int ex_n = (int)(x1 & 0xFF), ex_u = (int)(x1 >> 8), ex_uu = (int)x2;
                 const int rn = RLn[rr];
                 const long long rx = RLx[rr], rxx = RLxx[rr];
-                const long long r = R0 + rr;
+                // 32-bit operands where the values fit (one widening multiply
+                // each); the int64 sums are the same values as in full int64
+                const int r = R0 + rr;
+                const long long r2 = (long long)r * r;
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const long long n = ex_n + pn[jj];          // row prefix of Q inside the chunk
-                    const long long su = ex_u + pu[jj];         // ... of u Q
-                    const long long suu = ex_uu + puu[jj];      // ... of u^2 Q
-                    const long long N = rn + n;                 // row prefix of Q from column 0
-                    acc[0][jj] += rx + Cb * n + su;
-                    acc[1][jj] += r * N;
-                    acc[2][jj] += rxx + Cb * Cb * n + 2 * Cb * su + suu;
-                    acc[3][jj] += r * r * N;
+                    const int n = ex_n + pn[jj];          // row prefix of Q inside the chunk (<= 128)
+                    const int su = ex_u + pu[jj];         // ... of u Q (<= 8128)
+                    const int suu = ex_uu + puu[jj];      // ... of u^2 Q (<= 690880)
+                    const unsigned N = (unsigned)rn + (unsigned)n;  // row prefix of Q from column 0 (<= W)
+                    acc[0][jj] += rx + (long long)Cb32 * n + su;
+                    acc[1][jj] += (long long)r * (long long)N;
+                    acc[2][jj] += rxx + CbCb * n + 2 * ((long long)Cb32 * su) + suu;
+                    acc[3][jj] += r2 * (long long)N;
                 }
                 if (c < g.P) {
                     const int64_t o = (int64_t)(R0 + rr) * g.P + c;
