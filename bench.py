@@ -176,6 +176,8 @@ def algorithmic_bytes(kernel: str, B: int, Bw: int, n_rects: int, n_wins: int) -
         return n_rects * (16 + 4 * B * 4 + 4 * B)
     if kernel == "query_weighted":
         return n_wins * (16 + 4 * Bw * (4 + 4 * 8) + 4 * Bw)
+    if kernel == "tile_sums":                # all windows of the frame in one launch
+        return 7 * hw
     if kernel == "tile_sums/count":
         return 6 * hw
     if kernel == "tile_sums/weighted":

@@ -79,7 +79,8 @@ const char *kernel_name(int kid)
                                            "carry_scan",    "tiles/count",     "tiles/moments",
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
-                                           "local_median", "phog_build",     "phog_query"};
+                                           "local_median", "phog_build",     "phog_query",
+                                           "tile_sums"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 

@@ -66,7 +66,8 @@ enum KernelId {
     KID_MEDIAN = 12,
     KID_PHOG_BUILD = 13,
     KID_PHOG_QUERY = 14,
-    KID_COUNT = 15
+    KID_SUMS_ALL = 15,  // tile sums of all windows of one frame in one launch
+    KID_COUNT = 16
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on

@@ -5,14 +5,18 @@
 // and columns.  The frame is cut into bands of R rows and strips of Wc
 // columns and three kernels remove the serial dependence (ih_internal.cuh):
 //
-// k_tile_sums  one CTA per (tile, window of <= 16 bins of one channel).  It
-//   stages the tile's bins in shared memory as bytes, then each thread walks
-//   32-pixel pieces of columns (down the band) and of rows (along the strip),
-//   accumulating run lengths in registers and flushing each run to shared
-//   counters with one atomic add.  For the weighted channel it also sums the
-//   offsets (r-R0), (r-R0)^2 per column and (c-C0), (c-C0)^2 per row, which
-//   are small enough for int32; the carry scan rebuilds the global int64
-//   moment carries from them.
+// k_tile_sums_all  per (tile, window of <= 16 bins of one channel), the
+//   window's column sums down the band, row sums along the strip and tile
+//   sum, all windows of a frame in one launch.  A window of an unweighted
+//   channel takes 4 warps: each pixel's bin is an 8-bit field of packed
+//   words, column counts add up in registers and a row's totals are one
+//   warp reduction per word.  A window of the weighted channel takes a
+//   256-thread CTA that stages the tile's bins in shared memory as bytes and
+//   walks 32-pixel pieces of columns and rows, flushing each run of equal
+//   bins with one shared atomic add; it also sums the offsets (r-R0),
+//   (r-R0)^2 per column and (c-C0), (c-C0)^2 per row, which are small enough
+//   for int32; the carry scan rebuilds the global int64 moment carries from
+//   them.
 // k_carry_scan  exclusive prefixes over bands (G), strips (L) and both
 //   (corners), int32 for counts and int64 for the moments.
 // count tiles  one warp per (tile, group of <= 8 bins).  A lane owns 4
@@ -31,9 +35,9 @@
 //   Sum u^2 Q.  The row-weighted planes accumulate r * (row prefix of Q) and
 //   r^2 * (row prefix of Q).  All moment arithmetic is exact in int64.
 //
-// k_tiles runs the moment units and then the count units of a frame in one
+// k_tiles runs the count units and then the moment units of a frame in one
 // launch (k_tiles_count when the frame has no moment planes); k_tiles_b does
-// the same over the frames of a batch.
+// the same over the frames of a batch (moment units first).
 //
 // No kernel waits on another CTA; the only inter-CTA data flow is through the
 // carry arrays between launches on one stream.
@@ -340,9 +344,17 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
 // one redux.sync.add each (at most 128 per field), so no field overflows.
 constexpr int kCntThreads = 128;
 
+// The 128 threads of one group (a whole CTA, or half of a 256-thread CTA:
+// tid = thread index in the group, bar = the group's named barrier).
+__device__ __forceinline__ void group_sync(int bar)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(kCntThreads) : "memory");
+}
+
 template <int NW>
 __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, int i, int widx,
-                                                     uint32_t (*colpk)[16][32], int32_t (*rows)[kMaxBandRows])
+                                                     uint32_t (*colpk)[16][32], int32_t (*rows)[kMaxBandRows],
+                                                     int tid, int bar)
 {
     const TileGrid &g = ps.g;
     const GroupDev wd = ps.win[widx];
@@ -351,14 +363,14 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
     const int C0 = j * g.Wc, C1 = min(C0 + g.Wc, g.W);
     const int nbw = wd.nb, blo = wd.b_lo;
     const int64_t bglob = ch.bin_off + wd.b_lo;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int lane = tid & 31, wid = tid >> 5;
     const uint8_t *const pl = ch.plane;
     const int64_t pt = ch.pitch;
     const int bins = ch.bins, mode = ch.mode;
     const bool vec_ok = ((pt & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl) & 3) == 0);
 
     for (int k = tid; k < nbw * nr; k += kCntThreads) rows[k / nr][k % nr] = 0;
-    __syncthreads();
+    group_sync(bar);
     for (int cp = C0; cp < C1; cp += kChunk) {
         const int c = cp + lane * 4;
         const int nvalid = max(0, min(4, C1 - c));
@@ -403,7 +415,7 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
         for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
             for (int k = 0; k < NW; ++k) colpk[wid][jj * 4 + k][lane] = col[jj][k];
-        __syncthreads();
+        group_sync(bar);
         {
             // column 4 l + jj of the pass: thread (warp jj, lane l)
             const int l = lane, jj = wid, cc = 4 * l + jj;
@@ -419,7 +431,7 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
                     if (b < nbw) dst[(int64_t)b * g.W] = (int32_t)((sw[b >> 2] >> ((b & 3) << 3)) & 0xFFu);
             }
         }
-        __syncthreads();
+        group_sync(bar);
     }
     for (int k = tid; k < nbw * nr; k += kCntThreads) {
         const int b = k / nr, rr = k % nr;
@@ -433,25 +445,44 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
     }
 }
 
-__device__ __forceinline__ void tile_sums_count(const PlaneSet &ps, int j, int i, int widx)
+// Shared memory of one count group.
+struct CountSumsSmem {
+    uint32_t colpk[4][16][32];
+    int32_t rows[kWindowBins][kMaxBandRows];
+};
+
+__device__ __forceinline__ void tile_sums_count_group(const PlaneSet &ps, int j, int i, int widx, CountSumsSmem &sm,
+                                                      int tid, int bar)
 {
-    __shared__ uint32_t colpk[4][16][32];
-    __shared__ int32_t rows[kWindowBins][kMaxBandRows];
     if (ps.win[widx].nb <= 8)
-        tile_sums_count_body<2>(ps, j, i, widx, colpk, rows);
+        tile_sums_count_body<2>(ps, j, i, widx, sm.colpk, sm.rows, tid, bar);
     else
-        tile_sums_count_body<4>(ps, j, i, widx, colpk, rows);
+        tile_sums_count_body<4>(ps, j, i, widx, sm.colpk, sm.rows, tid, bar);
 }
 
-template <bool WT>
-__global__ void __launch_bounds__(WT ? kSumThreads : kCntThreads) k_tile_sums(const __grid_constant__ PlaneSet ps,
-                                                                              int win0)
+__device__ __forceinline__ void tile_sums_count(const PlaneSet &ps, int j, int i, int widx)
+{
+    __shared__ CountSumsSmem sm;
+    tile_sums_count_group(ps, j, i, widx, sm, threadIdx.x, 0);
+}
+
+// Tile sums of all windows of a frame in one launch of 256-thread CTAs:
+// z < nw_w: one window of the weighted channel per CTA (they take longest,
+// so they go first); then two windows of the other channels per CTA, one
+// per 128-thread half.
+__global__ void __launch_bounds__(kSumThreads) k_tile_sums_all(const __grid_constant__ PlaneSet ps, int nw_w)
 {
     pdl_wait();
-    if constexpr (WT)
-        tile_sums_body<true>(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
-    else
-        tile_sums_count(ps, blockIdx.x, blockIdx.y, win0 + blockIdx.z);
+    const int z = blockIdx.z;
+    if (z < nw_w) {
+        tile_sums_body<true>(ps, blockIdx.x, blockIdx.y, ps.nwin_count + z);
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int half = threadIdx.x >> 7, widx = 2 * (z - nw_w) + half;
+    if (widx >= ps.nwin_count) return;  // the odd window's CTA: a whole idle half
+    CountSumsSmem &sm = reinterpret_cast<CountSumsSmem *>(dsm)[half];
+    tile_sums_count_group(ps, blockIdx.x, blockIdx.y, widx, sm, threadIdx.x & 127, 1 + half);
 }
 
 // Largest f in [0, n) with pre[f] <= x (pre is a prefix sum of n counts).
@@ -1411,7 +1442,7 @@ void prepare_kernels()
 {
     static bool attrs = false;
     if (!attrs) {
-        set_max_smem(k_tile_sums<true>, sums_smem_bytes(kMaxBandRows, true));
+        set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
         set_max_smem(k_tile_sums_b<true>, sums_smem_bytes(kMaxBandRows, true));
         int dev = 0;
         cudaGetDevice(&dev);
@@ -1477,18 +1508,13 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     int n = 0;
     if (ps.colsum) {
         const int nw_count = ps.nwin_count, nw_weighted = ps.nwin - ps.nwin_count;
-        if (nw_count) {
-            prof_mark(prof, KID_SUMS_COUNT, 0, st);
-            launch_pdl(k_tile_sums<false>, dim3(g.ns, g.nb, nw_count), kCntThreads, 0, st, ps, 0);
-            prof_mark(prof, KID_SUMS_COUNT, 1, st);
-            ++n;
-        }
-        if (nw_weighted) {
-            prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-            launch_pdl(k_tile_sums<true>, dim3(g.ns, g.nb, nw_weighted), kSumThreads, sums_smem_bytes(g.R, true), st, ps, nw_count);
-            prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
-            ++n;
-        }
+        // both window kinds in one launch: the weighted CTAs overlap the count CTAs
+        const size_t smem = std::max(nw_weighted ? sums_smem_bytes(g.R, true) : 0, 2 * sizeof(CountSumsSmem));
+        prof_mark(prof, KID_SUMS_ALL, 0, st);
+        launch_pdl(k_tile_sums_all, dim3(g.ns, g.nb, nw_weighted + (nw_count + 1) / 2), kSumThreads, smem, st, ps,
+                   nw_weighted);
+        prof_mark(prof, KID_SUMS_ALL, 1, st);
+        ++n;
         const int64_t tot = (int64_t)ps.B * g.W + (int64_t)ps.B * g.H + (int64_t)g.nb * ps.B;
         const int64_t blocks = (tot + 255) / 256;
         prof_mark(prof, KID_SCAN, 0, st);
