@@ -176,6 +176,9 @@ def algorithmic_bytes(kernel: str, B: int, Bw: int, n_rects: int, n_wins: int) -
         return n_rects * (16 + 4 * B * 4 + 4 * B)
     if kernel == "query_weighted":
         return n_wins * (16 + 4 * Bw * (4 + 4 * 8) + 4 * Bw)
+    if kernel == "queries":                  # both query kinds in one launch
+        return (algorithmic_bytes("query_rects", B, Bw, n_rects, n_wins) +
+                algorithmic_bytes("query_weighted", B, Bw, n_rects, n_wins))
     if kernel == "tile_sums":                # all windows of the frame in one launch
         return 7 * hw
     if kernel == "tile_sums/count":
@@ -317,8 +320,7 @@ def run_engine(args):
     def step(pix):
         h, = ih.ih_build(ctx, ih.Frame(pix, chans, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=WEIGHTED_CH,
                                        layout=LAYOUTS[args.layout][0]))
-        ih.ih_query_rects(ctx, h, d_rects, out_r)
-        ih.ih_query_weighted(ctx, h, d_wins, out_w)
+        ih.ih_query(ctx, h, d_rects, out_r, d_wins, out_w)
         ih.ih_release(ctx, h)
 
     def timed(fn, k):
@@ -388,8 +390,7 @@ def run_engine(args):
             b["wins"].copy_(h_wins, non_blocking=True)
             h, = ih.ih_build(ctx, ih.Frame(b["x_rgb"], chans, input=ih.IH_INPUT_RGB_FEATURES,
                                            weighted_channel=WEIGHTED_CH, layout=LAYOUTS[args.layout][0]), stream=st)
-            ih.ih_query_rects(ctx, h, b["rects"], b["out_r"], stream=st)
-            ih.ih_query_weighted(ctx, h, b["wins"], b["out_w"], stream=st)
+            ih.ih_query(ctx, h, b["rects"], b["out_r"], b["wins"], b["out_w"], stream=st)
             ih.ih_release(ctx, h, stream=st)
             b["h_out_r"].copy_(b["out_r"], non_blocking=True)
             b["h_out_w"].copy_(b["out_w"], non_blocking=True)

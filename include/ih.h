@@ -191,6 +191,17 @@ enum { IH_NORMALIZE = 1 }; /* divide each histogram by sum_T k(r,c) */
 ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_windows, int64_t n,
                             uint32_t kernel, uint32_t flags, float *d_out, void *stream);
 
+/* Both query kinds of one frame in one call and one launch: the rectangles
+ * of ih_query_rects (Eq. 2.16) and the weighted windows of
+ * ih_query_weighted (Sec. 3.1.3), with the same arguments, layouts, results
+ * and errors as those two calls; either count may be 0 (then its pointers
+ * may be NULL, and a frame without moment planes is accepted when
+ * n_windows = 0).  The weighted work runs in its own CTAs beside the
+ * rectangle CTAs, so its latency overlaps the rectangles' loads. */
+ih_status ih_query(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, int64_t n_rects, int32_t *d_rect_out,
+                   const int32_t *d_windows, int64_t n_windows, uint32_t kernel, uint32_t flags,
+                   float *d_weighted_out, void *stream);
+
 /* Sliding-window histogram matching (Sec. 2.4.3): for every placement of a
  * win_h x win_w window whose top-left pixel (r, c) lies in the search region
  * search = (sr0, sc0, sr1, sc1) (host, 4 int32, inclusive), the city-block

@@ -80,7 +80,7 @@ const char *kernel_name(int kid)
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
                                            "local_median", "phog_build",     "phog_query",
-                                           "tile_sums"};
+                                           "tile_sums", "queries"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -529,6 +529,33 @@ ih_status ih_query_weighted(ih_ctx *ctx, int32_t handle, const int32_t *d_window
     const int k = launch_query_weighted(fr->view, m, d_windows, n, (int)kernel, layers,
                                         (flags & IH_NORMALIZE) ? 1 : 0, d_out, ctx->d_err,
                                         static_cast<cudaStream_t>(stream), prof_of(ctx));
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
+ih_status ih_query(ih_ctx *ctx, int32_t handle, const int32_t *d_rects, int64_t n_rects, int32_t *d_rect_out,
+                   const int32_t *d_windows, int64_t n_windows, uint32_t kernel, uint32_t flags,
+                   float *d_weighted_out, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    FrameRec *fr = count_frame(ctx, handle);
+    if (!fr) return fail(ctx, IH_ENOTBUILT, "no live frame %d", handle);
+    if (n_rects < 0 || (n_rects > 0 && (!d_rects || !d_rect_out)) || n_windows < 0 ||
+        (n_windows > 0 && (!d_windows || !d_weighted_out)))
+        return fail(ctx, IH_EINVAL, "ih_query: bad arguments");
+    const int layers = weighted_layers(flags);
+    if (n_windows > 0) {
+        if (!fr->Bw) return fail(ctx, IH_EINVAL, "frame %d has no moment planes", handle);
+        if (kernel > IH_K_WEDDING_CAKE || (flags & ~((uint32_t)IH_NORMALIZE | IH_LAYERS(0xff))) || layers > 64)
+            return fail(ctx, IH_EINVAL, "kernel %u / flags %u", kernel, flags);
+    }
+    DevGuard dg(ctx->device);
+    const MomentView m{fr->Bw ? fr->bin_off[fr->wch] : 0, fr->d_mom, fr->Bw, fr->mbits == 32};
+    const int k = launch_query_both(fr->view, m, d_rects, n_rects, d_rect_out, d_windows, n_windows, (int)kernel,
+                                    layers, (flags & IH_NORMALIZE) ? 1 : 0, d_weighted_out, ctx->d_err,
+                                    static_cast<cudaStream_t>(stream), prof_of(ctx));
     if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "query launch");
     ctx->launches += k;
     return IH_OK;

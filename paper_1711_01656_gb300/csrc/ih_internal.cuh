@@ -67,7 +67,8 @@ enum KernelId {
     KID_PHOG_BUILD = 13,
     KID_PHOG_QUERY = 14,
     KID_SUMS_ALL = 15,  // tile sums of all windows of one frame in one launch
-    KID_COUNT = 16
+    KID_QUERY_BOTH = 16,  // rectangle and weighted queries of one frame in one launch
+    KID_COUNT = 17
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -269,6 +270,10 @@ int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const i
                          int64_t total_rects, int64_t total_wins, int *err, cudaStream_t st, const Prof *prof);
 int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t *wins, int64_t n, int kernel,
                           int layers, int normalize, float *out, int *err, cudaStream_t st, const Prof *prof);
+// Rectangle and weighted queries of one frame in one launch (either count may be 0).
+int launch_query_both(const CountView &v, const MomentView &m, const int32_t *rects, int64_t nr, int32_t *rout,
+                      const int32_t *wins, int64_t nw, int kernel, int layers, int normalize, float *wout, int *err,
+                      cudaStream_t st, const Prof *prof);
 // Sliding-window city-block distances (Eq. 2.22, p = 1) over bins
 // [bin0, bin0 + nbins) for placements [sr0, sr1] x [sc0, sc1] of a wh x ww window.
 int launch_match_window(const CountView &v, int bin0, int nbins, const int32_t *target, int wh, int ww, int sr0,

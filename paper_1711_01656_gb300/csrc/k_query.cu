@@ -171,13 +171,12 @@ __device__ __forceinline__ void rect_item_record(const CountView &v, const int64
     }
 }
 
+// The rectangle items of CTA bx of nbx (a grid-stride loop over the items).
 // The group tables are copied to shared memory so that threads of different
 // groups do not serialise on the kernel-parameter bank.
-__global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ CountView v,
-                                                     const int32_t *__restrict__ rects, int64_t n,
-                                                     int32_t *__restrict__ out, int *err)
+__device__ __forceinline__ void query_rects_cta(const CountView &v, const int32_t *__restrict__ rects, int64_t n,
+                                                int32_t *__restrict__ out, int *err, unsigned bx, unsigned nbx)
 {
-    pdl_wait();
     __shared__ int64_t s_off[kMaxGroups];
     __shared__ int s_nb[kMaxGroups], s_b0[kMaxGroups];
     __shared__ int16_t s_rw[kMaxGroups], s_w0[kMaxGroups], s_qp[kMaxBins / 4], s_wb[kMaxBins];
@@ -195,15 +194,21 @@ __global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ Cou
     __syncthreads();
     if (v.layout == LAYOUT_RECORD) {
         const int64_t total = n * v.nquarters;
-        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-             t += (int64_t)gridDim.x * blockDim.x)
+        for (int64_t t = bx * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nbx * blockDim.x)
             rect_item_record(v, s_off, s_rw, s_w0, s_qp, s_wb, rects, out, t, err);
         return;
     }
     const int64_t total = n * v.ngroups;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t t = bx * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nbx * blockDim.x)
         rect_item(v, s_off, s_nb, s_b0, rects, out, t, err);
+}
+
+__global__ void __launch_bounds__(256) k_query_rects(const __grid_constant__ CountView v,
+                                                     const int32_t *__restrict__ rects, int64_t n,
+                                                     int32_t *__restrict__ out, int *err)
+{
+    pdl_wait();
+    query_rects_cta(v, rects, n, out, err, blockIdx.x, gridDim.x);
 }
 
 // Largest f in [0, n) with pre[f] <= x.
@@ -454,6 +459,33 @@ __global__ void __launch_bounds__(256) k_query_weighted(const __grid_constant__ 
     }
 }
 
+// Both query kinds of one frame in one launch: the first wblocks CTAs run
+// the weighted items (few CTAs, each bound by the latency of its scattered
+// corner loads), the rest the rectangle items, so that the weighted CTAs
+// overlap the rectangles' loads instead of running alone on a mostly idle
+// GPU.
+template <int KERNEL>
+__global__ void __launch_bounds__(256) k_query_both(const __grid_constant__ CountView v, const MomentView m,
+                                                    const int32_t *__restrict__ rects, int64_t nr,
+                                                    int32_t *__restrict__ rout, const int32_t *__restrict__ wins,
+                                                    int64_t nw, int layers, int normalize,
+                                                    float *__restrict__ wout, unsigned wblocks, int *err)
+{
+    pdl_wait();
+    if (blockIdx.x < wblocks) {
+        const int64_t total = nw * m.Bw;
+        for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+             t += (int64_t)wblocks * blockDim.x) {
+            if (KERNEL == IH_KERNEL_EPANECHNIKOV)
+                weighted_item(v, m, wins, normalize, wout, t, err);
+            else
+                weighted_item_alt(v, m, wins, KERNEL, layers, normalize, wout, t, err);
+        }
+        return;
+    }
+    query_rects_cta(v, rects, nr, rout, err, blockIdx.x - wblocks, gridDim.x - wblocks);
+}
+
 __global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__restrict__ jobs,
                                                           const int64_t *__restrict__ pre, int n, int *err)
 {
@@ -644,6 +676,28 @@ int launch_query_weighted(const CountView &v, const MomentView &m, const int32_t
     else
         launch_pdl(k_query_weighted<IH_KERNEL_EPANECHNIKOV>, blocks, 256, 0, st, v, m, wins, n, layers, normalize, out, err);
     prof_mark(prof, KID_QUERY_WEIGHTED, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+}
+
+int launch_query_both(const CountView &v, const MomentView &m, const int32_t *rects, int64_t nr, int32_t *rout,
+                      const int32_t *wins, int64_t nw, int kernel, int layers, int normalize, float *wout, int *err,
+                      cudaStream_t st, const Prof *prof)
+{
+    if (nw == 0) return launch_query_rects(v, rects, nr, rout, err, st, prof);
+    if (nr == 0)
+        return launch_query_weighted(v, m, wins, nw, kernel, layers, normalize, wout, err, st, prof);
+    const unsigned wb = grid_for(nw * m.Bw), rb = grid_for(nr * rect_items(v));
+    prof_mark(prof, KID_QUERY_BOTH, 0, st);
+    if (kernel == IH_KERNEL_MANHATTAN)
+        launch_pdl(k_query_both<IH_KERNEL_MANHATTAN>, wb + rb, 256, 0, st, v, m, rects, nr, rout, wins, nw, layers,
+                   normalize, wout, wb, err);
+    else if (kernel == IH_KERNEL_WEDDING_CAKE)
+        launch_pdl(k_query_both<IH_KERNEL_WEDDING_CAKE>, wb + rb, 256, 0, st, v, m, rects, nr, rout, wins, nw, layers,
+                   normalize, wout, wb, err);
+    else
+        launch_pdl(k_query_both<IH_KERNEL_EPANECHNIKOV>, wb + rb, 256, 0, st, v, m, rects, nr, rout, wins, nw, layers,
+                   normalize, wout, wb, err);
+    prof_mark(prof, KID_QUERY_BOTH, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 

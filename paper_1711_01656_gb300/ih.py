@@ -37,7 +37,7 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
              "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
-             "ih_phog_match", "ih_profile_select")
+             "ih_phog_match", "ih_profile_select", "ih_query")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
             "ih_build": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(i32), p], i32),
             "ih_query_rects": ([p, i32, p, i64, p, p], i32),
             "ih_query_weighted": ([p, i32, p, i64, u32, u32, p, p], i32),
+            "ih_query": ([p, i32, p, i64, p, p, i64, u32, u32, p, p], i32),
             "ih_match_window": ([p, i32, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_accumulate": ([p, i32, i32, i32, p], i32),
             "ih_profile_select": ([p, p, i32], i32),
@@ -311,6 +312,17 @@ def ih_query_weighted(ctx, handle, windows, out, kernel=IH_K_EPANECHNIKOV, flags
     _check(ctx, load_library().ih_query_weighted(ctx, int(handle), _ptr(windows), n, int(kernel),
                                                  int(flags), _ptr(out), _stream(stream)))
     return out
+
+
+def ih_query(ctx, handle, rects=None, rect_out=None, windows=None, weighted_out=None, kernel=IH_K_EPANECHNIKOV,
+             flags=0, stream=None):
+    """ih_query_rects and ih_query_weighted of one frame in one call and one
+    launch; either part may be None."""
+    nr = 0 if rects is None else rects.shape[0]
+    nw = 0 if windows is None else windows.shape[0]
+    _check(ctx, load_library().ih_query(ctx, int(handle), _ptr(rects), nr, _ptr(rect_out), _ptr(windows), nw,
+                                        int(kernel), int(flags), _ptr(weighted_out), _stream(stream)))
+    return rect_out, weighted_out
 
 
 def ih_release(ctx, handle, stream=None):

@@ -673,3 +673,57 @@ def test_record_layout_exact(ihlib, ctx, bins):
     wins = synth.rects_side_range(h, w, 200, 1, 60, 92)
     _assert_weighted(_weighted_gpu(ihlib, ctx, hdl, wins, bw), oracle.weighted_hist(planes[wch], bw, wins))
     ihlib.ih_release(ctx, hdl)
+
+
+# ---------------------------------------------------------------- both query kinds in one launch
+
+@pytest.mark.parametrize("layout", [0, 1, 2])
+@pytest.mark.parametrize("kernel", [0, 1, 2])
+def test_query_both_equals_separate_calls(ihlib, ctx, layout, kernel):
+    """ih_query (one launch) returns exactly what ih_query_rects and
+    ih_query_weighted return, and the rectangles match the oracle."""
+    ih = ihlib
+    h, w = 200, 611
+    planes = np.stack([synth.blob_plane(h, w, 70 + k) for k in range(3)])
+    chans = [(16, 0), (9, 0), (12, 0)]
+    hdl, _ = _build(ih, ctx, planes, chans, weighted=0, layout=layout)
+    rects = synth.rects_uniform_corners(h, w, 3000, 81)
+    wins = synth.rects_side_range(h, w, 700, 1, 120, 82)
+    d_r, d_w = (torch.from_numpy(x).to(DEV) for x in (rects, wins))
+    r1 = torch.full((len(rects), 37), -7, dtype=torch.int32, device=DEV)
+    w1 = torch.full((len(wins), 16), -7.0, dtype=torch.float32, device=DEV)
+    r2, w2 = torch.full_like(r1, -9), torch.full_like(w1, -9.0)
+    flags = ih.IH_NORMALIZE | ih.IH_LAYERS(3)
+    ih.ih_query_rects(ctx, hdl, d_r, r1)
+    ih.ih_query_weighted(ctx, hdl, d_w, w1, kernel=kernel, flags=flags)
+    ih.ih_query(ctx, hdl, d_r, r2, d_w, w2, kernel=kernel, flags=flags)
+    ih.ih_sync(ctx)
+    assert torch.equal(r1, r2) and torch.equal(w1, w2)
+    assert np.array_equal(r2.cpu().numpy(), oracle.frame_rect_hist(planes, chans, rects))
+    ih.ih_release(ctx, hdl)
+
+
+def test_query_both_partial_and_refusals(ihlib, ctx):
+    ih = ihlib
+    h, w = 90, 130
+    img = synth.blob_plane(h, w, 5)
+    hdl, _ = _build(ih, ctx, img, [(8, 0)])  # no moment planes
+    rects = torch.from_numpy(synth.rects_uniform_corners(h, w, 50, 6)).to(DEV)
+    out = torch.empty((50, 8), dtype=torch.int32, device=DEV)
+    ih.ih_query(ctx, hdl, rects, out)  # rectangles only: accepted without moment planes
+    ih.ih_sync(ctx)
+    assert np.array_equal(out.cpu().numpy(), oracle.rect_hist(img, 8, rects.cpu().numpy()))
+    wins = torch.zeros((3, 4), dtype=torch.int32, device=DEV)
+    with pytest.raises(ih.IHError):  # windows need moment planes
+        ih.ih_query(ctx, hdl, rects, out, wins, torch.empty((3, 8), device=DEV))
+    ih.ih_release(ctx, hdl)
+    # a rectangle outside the frame: its row is -1 and the call's sync fails
+    hdl, _ = _build(ih, ctx, img, [(8, 0)], weighted=0)
+    bad = torch.tensor([[0, 0, 5, 5], [0, 0, h, 3]], dtype=torch.int32, device=DEV)
+    o = torch.zeros((2, 8), dtype=torch.int32, device=DEV)
+    wo = torch.zeros((1, 8), dtype=torch.float32, device=DEV)
+    ih.ih_query(ctx, hdl, bad, o, bad[:1], wo)
+    with pytest.raises(ih.IHError):
+        ih.ih_sync(ctx)
+    assert (o[1] == -1).all().item() and np.array_equal(o[0].cpu().numpy(), oracle.rect_hist(img, 8, bad[:1].cpu().numpy())[0])
+    ih.ih_release(ctx, hdl)
