@@ -226,13 +226,12 @@ __device__ __forceinline__ int find_job(const int64_t *pre, int n, int64_t x)
 }
 
 // Batched: work items of all frames concatenated; tables read from global.
-__global__ void __launch_bounds__(256) k_query_rects_b(const QueryJob *__restrict__ jobs,
-                                                       const int64_t *__restrict__ pre, int n, int *err)
+// CTA bx of nbx runs a grid-stride loop over the items.
+__device__ __forceinline__ void query_rects_b_cta(const QueryJob *__restrict__ jobs, const int64_t *__restrict__ pre,
+                                                  int n, int *err, unsigned bx, unsigned nbx)
 {
-    pdl_wait();
     const int64_t total = pre[n];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = bx * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nbx * blockDim.x) {
         const int f = find_job(pre, n, t);
         const QueryJob &jb = jobs[f];
         const CountView &v = *jb.v;
@@ -242,6 +241,13 @@ __global__ void __launch_bounds__(256) k_query_rects_b(const QueryJob *__restric
         else
             rect_item(v, v.slab_off, v.group_nb, v.group_bin0, jb.rects, jb.rect_out, t - pre[f], err);
     }
+}
+
+__global__ void __launch_bounds__(256) k_query_rects_b(const QueryJob *__restrict__ jobs,
+                                                       const int64_t *__restrict__ pre, int n, int *err)
+{
+    pdl_wait();
+    query_rects_b_cta(jobs, pre, n, err, blockIdx.x, gridDim.x);
 }
 
 // Element offset of bin gb's count at (0, 0) and its per-pixel stride.
@@ -486,13 +492,12 @@ __global__ void __launch_bounds__(256) k_query_both(const __grid_constant__ Coun
     query_rects_cta(v, rects, nr, rout, err, blockIdx.x - wblocks, gridDim.x - wblocks);
 }
 
-__global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__restrict__ jobs,
-                                                          const int64_t *__restrict__ pre, int n, int *err)
+__device__ __forceinline__ void query_weighted_b_cta(const QueryJob *__restrict__ jobs,
+                                                     const int64_t *__restrict__ pre, int n, int *err, unsigned bx,
+                                                     unsigned nbx)
 {
-    pdl_wait();
     const int64_t total = pre[n];
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = bx * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nbx * blockDim.x) {
         const int f = find_job(pre, n, t);
         const QueryJob &jb = jobs[f];
         if (jb.kernel == IH_KERNEL_EPANECHNIKOV)
@@ -500,6 +505,27 @@ __global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__rest
         else
             weighted_item_alt(*jb.v, jb.m, jb.wins, jb.kernel, jb.layers, jb.normalize, jb.wout, t - pre[f], err);
     }
+}
+
+__global__ void __launch_bounds__(256) k_query_weighted_b(const QueryJob *__restrict__ jobs,
+                                                          const int64_t *__restrict__ pre, int n, int *err)
+{
+    pdl_wait();
+    query_weighted_b_cta(jobs, pre, n, err, blockIdx.x, gridDim.x);
+}
+
+// Batched, both kinds in one launch: the first wblocks CTAs run the weighted
+// items (as in k_query_both).
+__global__ void __launch_bounds__(256) k_query_both_b(const QueryJob *__restrict__ jobs,
+                                                      const int64_t *__restrict__ pre_rects,
+                                                      const int64_t *__restrict__ pre_wins, int n, unsigned wblocks,
+                                                      int *err)
+{
+    pdl_wait();
+    if (blockIdx.x < wblocks)
+        query_weighted_b_cta(jobs, pre_wins, n, err, blockIdx.x, wblocks);
+    else
+        query_rects_b_cta(jobs, pre_rects, n, err, blockIdx.x - wblocks, gridDim.x - wblocks);
 }
 
 // Sliding-window matching (Sec. 2.4.3, Eq. 2.22 with p = 1): one thread per
@@ -705,6 +731,13 @@ int launch_queries_batch(const QueryJob *jobs, const int64_t *pre_rects, const i
                          int64_t total_rects, int64_t total_wins, int *err, cudaStream_t st, const Prof *prof)
 {
     int k = 0;
+    if (total_rects && total_wins) {
+        const unsigned wb = grid_for(total_wins);
+        prof_mark(prof, KID_QUERY_BOTH, 0, st);
+        launch_pdl(k_query_both_b, wb + grid_for(total_rects), 256, 0, st, jobs, pre_rects, pre_wins, n, wb, err);
+        prof_mark(prof, KID_QUERY_BOTH, 1, st);
+        return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+    }
     if (total_rects) {
         prof_mark(prof, KID_QUERY_RECTS, 0, st);
         launch_pdl(k_query_rects_b, grid_for(total_rects), 256, 0, st, jobs, pre_rects, n, err);
