@@ -351,6 +351,8 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
     b->bd.pre_scan = d_pre + 2 * (n + 1);
     b->bd.pre_tiles = d_pre + 3 * (n + 1);
     b->bd.pre_mom = d_pre + 4 * (n + 1);
+    b->bd.max_R = 1;
+    for (int k = 0; k < n; ++k) b->bd.max_R = std::max(b->bd.max_R, sets[k].g.R);
     b->d_pre_r = d_pre + 5 * (n + 1);
     b->d_pre_w = d_pre + 6 * (n + 1);
     b->d_feat_pre = d_pre + 7 * (n + 1);

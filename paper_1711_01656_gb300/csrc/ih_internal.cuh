@@ -200,6 +200,7 @@ struct BatchDev {
     const int64_t *pre_scan;  // carry-scan work items
     const int64_t *pre_tiles; // count-tile warp units
     const int64_t *pre_mom;   // moment-tile warp units
+    int32_t max_R = kMaxBandRows;  // the frames' largest band (sizes the tile sums' shared memory)
 };
 // Work counts of one frame for the five batched kernels (host).
 void batch_counts(const PlaneSet &ps, int64_t *counts5);

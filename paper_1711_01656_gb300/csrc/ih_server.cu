@@ -258,6 +258,8 @@ bool launch_tick(ih_server *s, Slot &sl, std::vector<Req *> &reqs)
     bd.pre_scan = d_pre + 2 * (n + 1);
     bd.pre_tiles = d_pre + 3 * (n + 1);
     bd.pre_mom = d_pre + 4 * (n + 1);
+    bd.max_R = 1;
+    for (int k = 0; k < n; ++k) bd.max_R = std::max(bd.max_R, sets[k].g.R);
     int64_t totals[5];
     for (int j = 0; j < 5; ++j) totals[j] = pre[j * (n + 1) + n];
     const Prof *prof = prof_of(ctx);

@@ -37,7 +37,7 @@
 //
 // k_tiles runs the count units and then the moment units of a frame in one
 // launch (k_tiles_count when the frame has no moment planes); k_tiles_b does
-// the same over the frames of a batch (moment units first).
+// the same over the frames of a batch.
 //
 // No kernel waits on another CTA; the only inter-CTA data flow is through the
 // carry arrays between launches on one stream.
@@ -460,11 +460,6 @@ __device__ __forceinline__ void tile_sums_count_group(const PlaneSet &ps, int j,
         tile_sums_count_body<4>(ps, j, i, widx, sm.colpk, sm.rows, tid, bar);
 }
 
-__device__ __forceinline__ void tile_sums_count(const PlaneSet &ps, int j, int i, int widx)
-{
-    __shared__ CountSumsSmem sm;
-    tile_sums_count_group(ps, j, i, widx, sm, threadIdx.x, 0);
-}
 
 // Tile sums of all windows of a frame in one launch of 256-thread CTAs:
 // z < nw_w: one window of the weighted channel per CTA (they take longest,
@@ -499,22 +494,33 @@ __device__ __forceinline__ int find_frame(const int64_t *pre, int n, int64_t x)
     return lo;
 }
 
-// Batched: one CTA per (frame, window, band, strip), frames concatenated.
-template <bool WT>
-__global__ void __launch_bounds__(WT ? kSumThreads : kCntThreads) k_tile_sums_b(const BatchDev bd)
+// Batched, all windows of all frames in one launch of 256-thread CTAs: the
+// first nw CTAs each take one (frame, weighted-channel window, tile); then
+// each CTA takes two (frame, window, tile) units
+// of the other windows, one per 128-thread half (the halves may belong to
+// different frames).
+__global__ void __launch_bounds__(kSumThreads) k_tile_sums_all_b(const BatchDev bd, unsigned nw)
 {
     pdl_wait();
-    const int64_t *pre = WT ? bd.pre_sums1 : bd.pre_sums0;
-    const int64_t flat = blockIdx.x;
-    const int f = find_frame(pre, bd.n, flat);
-    const PlaneSet &ps = bd.sets[f];
-    const int64_t local = flat - pre[f];
-    const int64_t per = (int64_t)ps.g.ns * ps.g.nb;
-    const int z = (int)(local / per), rem = (int)(local % per);
-    if constexpr (WT)
+    if (blockIdx.x < nw) {
+        const int64_t flat = blockIdx.x;
+        const int f = find_frame(bd.pre_sums1, bd.n, flat);
+        const PlaneSet &ps = bd.sets[f];
+        const int64_t local = flat - bd.pre_sums1[f], per = (int64_t)ps.g.ns * ps.g.nb;
+        const int z = (int)(local / per), rem = (int)(local % per);
         tile_sums_body<true>(ps, rem % ps.g.ns, rem / ps.g.ns, ps.nwin_count + z);
-    else
-        tile_sums_count(ps, rem % ps.g.ns, rem / ps.g.ns, z);
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const int half = threadIdx.x >> 7;
+    const int64_t flat = 2 * (int64_t)(blockIdx.x - nw) + half;
+    if (flat >= bd.pre_sums0[bd.n]) return;  // an idle half at the end
+    const int f = find_frame(bd.pre_sums0, bd.n, flat);
+    const PlaneSet &ps = bd.sets[f];
+    const int64_t local = flat - bd.pre_sums0[f], per = (int64_t)ps.g.ns * ps.g.nb;
+    const int z = (int)(local / per), rem = (int)(local % per);
+    CountSumsSmem &sm = reinterpret_cast<CountSumsSmem *>(dsm)[half];
+    tile_sums_count_group(ps, rem % ps.g.ns, rem / ps.g.ns, z, sm, threadIdx.x & 127, 1 + half);
 }
 
 // ------------------------------------------------------------- carry scan
@@ -1332,16 +1338,17 @@ __global__ void __launch_bounds__(128, 4) k_tiles(const __grid_constant__ PlaneS
     }
 }
 
-// Batched: the moment units of all frames, then the count units of all
+// Batched: the count units of all frames, then the moment units of all
 // frames, in one launch (count units as in k_tiles_count_b).
 __global__ void __launch_bounds__(128, 4) k_tiles_b(const BatchDev bd, unsigned mom_blocks)
 {
     pdl_wait();
     __shared__ __align__(16) unsigned char smem[kTilesSmem];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (blockIdx.x < mom_blocks) {
+    const unsigned cnt_blocks = gridDim.x - mom_blocks;
+    if (blockIdx.x >= cnt_blocks) {
         MomentSmem &m = *reinterpret_cast<MomentSmem *>(smem);
-        const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
+        const int64_t unit = (int64_t)(blockIdx.x - cnt_blocks) * 4 + wid;
         if (unit >= bd.pre_mom[bd.n]) return;
         const int f = find_frame(bd.pre_mom, bd.n, unit);
         const PlaneSet &ps = bd.sets[f];
@@ -1356,7 +1363,7 @@ __global__ void __launch_bounds__(128, 4) k_tiles_b(const BatchDev bd, unsigned 
                                       m.RLxx[wid], m.stage[wid]);
     } else {
         CountSmem &cs = *reinterpret_cast<CountSmem *>(smem);
-        const int64_t unit = (int64_t)(blockIdx.x - mom_blocks) * 4 + wid;
+        const int64_t unit = (int64_t)blockIdx.x * 4 + wid;
         if (unit >= bd.pre_tiles[bd.n]) return;
         const int f = find_frame(bd.pre_tiles, bd.n, unit);
         const PlaneSet &ps = bd.sets[f];
@@ -1443,7 +1450,7 @@ void prepare_kernels()
     static bool attrs = false;
     if (!attrs) {
         set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
-        set_max_smem(k_tile_sums_b<true>, sums_smem_bytes(kMaxBandRows, true));
+        set_max_smem(k_tile_sums_all_b, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -1455,16 +1462,13 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
 {
     prepare_kernels();
     int n = 0;
-    if (totals[0]) {
-        prof_mark(prof, KID_SUMS_COUNT, 0, st);
-        launch_pdl(k_tile_sums_b<false>, (unsigned)totals[0], kCntThreads, 0, st, bd);
-        prof_mark(prof, KID_SUMS_COUNT, 1, st);
-        ++n;
-    }
-    if (totals[1]) {
-        prof_mark(prof, KID_SUMS_WEIGHTED, 0, st);
-        launch_pdl(k_tile_sums_b<true>, (unsigned)totals[1], kSumThreads, sums_smem_bytes(kMaxBandRows, true), st, bd);
-        prof_mark(prof, KID_SUMS_WEIGHTED, 1, st);
+    if (totals[0] || totals[1]) {
+        // both window kinds in one launch, the weighted CTAs first
+        const size_t smem = std::max(totals[1] ? sums_smem_bytes(bd.max_R, true) : 0, 2 * sizeof(CountSumsSmem));
+        prof_mark(prof, KID_SUMS_ALL, 0, st);
+        launch_pdl(k_tile_sums_all_b, (unsigned)(totals[1] + (totals[0] + 1) / 2), kSumThreads, smem, st, bd,
+                   (unsigned)totals[1]);
+        prof_mark(prof, KID_SUMS_ALL, 1, st);
         ++n;
     }
     if (totals[2]) {
