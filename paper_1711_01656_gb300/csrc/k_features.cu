@@ -129,7 +129,7 @@ __device__ __forceinline__ void features_tile(const uint8_t *__restrict__ pr, co
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_features(const uint8_t *__restrict__ pr, const uint8_t *__restrict__ pg,
+__global__ void __launch_bounds__(kThreads, 8) k_features(const uint8_t *__restrict__ pr, const uint8_t *__restrict__ pg,
                                                        const uint8_t *__restrict__ pb, int64_t pitch, int H, int W,
                                                        uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog,
                                                        int64_t opitch)
