@@ -181,10 +181,6 @@ def algorithmic_bytes(kernel: str, B: int, Bw: int, n_rects: int, n_wins: int) -
                 algorithmic_bytes("query_weighted", B, Bw, n_rects, n_wins))
     if kernel == "tile_sums":                # all windows of the frame in one launch
         return 7 * hw
-    if kernel == "tile_sums/count":
-        return 6 * hw
-    if kernel == "tile_sums/weighted":
-        return hw
     return float("nan")
 
 

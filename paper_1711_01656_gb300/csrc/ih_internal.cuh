@@ -49,7 +49,9 @@ enum WeightKernel { IH_KERNEL_EPANECHNIKOV = 0, IH_KERNEL_MANHATTAN = 1, IH_KERN
 // Weight kinds, used by the kernel-id table and the moment planes.
 enum WeightKind { WK_ONE = 0, WK_COL = 1, WK_ROW = 2, WK_COL2 = 3, WK_ROW2 = 4 };
 
-// Kernel ids for the optional per-launch event timing.
+// Kernel ids for the optional per-launch event timing (ids 1, 2 and 5 name
+// no kernel any more: the tile sums of both window kinds and the moment
+// tiles run inside KID_SUMS_ALL and KID_TILES_BOTH; the ids stay fixed).
 enum KernelId {
     KID_FEATURES = 0,
     KID_SUMS_COUNT = 1,
