@@ -398,6 +398,10 @@ ih_status ih_create(const ih_config *cfg, ih_ctx **out)
         e = cudaMalloc(&ctx->d_err, sizeof(int));
     }
     if (e == cudaSuccess) e = cudaMemset(ctx->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        prepare_kernels();  // one-time tables and kernel attributes, before any launch or capture
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) {
         if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
         delete ctx;

@@ -216,6 +216,10 @@ int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_
                     uint8_t *out_hog /* 3 planes */, int64_t out_pitch, cudaStream_t st,
                     const Prof *prof);
 
+// The feature pre-pass's orientation table on the current device (once per
+// device; synchronises the device, so call it outside stream capture).
+void prepare_features();
+
 // One frame of a batched feature pre-pass.
 struct FeatJob {
     const uint8_t *r, *g, *b;

@@ -1447,6 +1447,7 @@ void carve_carries(PlaneSet &ps, void *base)
 
 void prepare_kernels()
 {
+    prepare_features();
     static bool attrs = false;
     if (!attrs) {
         set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));

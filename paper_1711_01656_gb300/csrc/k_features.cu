@@ -29,6 +29,8 @@
 // exactly the neighbour a central difference at the frame edge needs.  The
 // neighbours at horizontal distance s = 1, 2 are assembled from two staged
 // words with byte permutes; s = 4 is the adjacent word.
+#include <mutex>
+
 #include "ih_internal.cuh"
 #include "ih_orient.cuh"
 
@@ -42,6 +44,33 @@ constexpr int kSW = kTC / 4 + 2;      // staged words per row (one halo word eac
 constexpr int kThreads = 256;
 
 __device__ __forceinline__ int byte_of(uint32_t w, int j) { return (int)((w >> (8 * j)) & 0xff); }
+
+// The count n of orientation_bin9 for every folded gradient: entry
+// ax * 256 + gy (0 <= ax, gy <= 255) holds the number of the four
+// first-quadrant boundaries at or below the angle of (ax, gy), computed by
+// the same int32 test (0 for the zero gradient).  Filled once per device by
+// prepare_features; 64 KB, so it stays in L1 while the pre-pass runs.
+__device__ uint8_t g_orient_n[256 * 256];
+
+__global__ void k_orient_table()
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 256 * 256) return;
+    const int ax = t >> 8, gy = t & 255;
+    g_orient_n[t] = (uint8_t)((ax | gy) ? orientation_bin9(ax, gy) : 0);
+}
+
+// orientation_bin9 through the table: fold into the upper half plane, look
+// up n for (|gx|, gy), and mirror for gx < 0.
+__device__ __forceinline__ int orientation_bin9_table(int gx, int gy)
+{
+    if (gy < 0 || (gy == 0 && gx < 0)) {
+        gx = -gx;
+        gy = -gy;
+    }
+    const int n = __ldg(g_orient_n + ((gx < 0 ? -gx : gx) << 8) + gy);
+    return gx < 0 ? 8 - n : n;
+}
 
 // floor((R+G+B)/3) of 4 packed pixels.
 __device__ __forceinline__ uint32_t intensity4(uint32_t r, uint32_t g, uint32_t b)
@@ -116,7 +145,7 @@ __device__ __forceinline__ void features_tile(const uint8_t *__restrict__ pr, co
             for (int j = 0; j < 4; ++j) {
                 const int gx = byte_of(right, j) - byte_of(left, j);
                 const int gy = byte_of(down, j) - byte_of(up, j);
-                bins |= (uint32_t)orientation_bin9(gx, gy) << (8 * j);
+                bins |= (uint32_t)orientation_bin9_table(gx, gy) << (8 * j);
             }
             store4(out_hog + l * plane + o, bins, nv, vout);
         }
@@ -160,6 +189,18 @@ __global__ void __launch_bounds__(kThreads) k_features_b(const FeatJob *__restri
 }
 
 }  // namespace
+
+void prepare_features()
+{
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    k_orient_table<<<256, 256>>>();
+    if (cudaDeviceSynchronize() == cudaSuccess) done[dev] = true;
+}
 
 int launch_features(const uint8_t *r, const uint8_t *g, const uint8_t *b, int64_t pitch, int H,
                     int W, uint8_t *out_rgb, uint8_t *out_i, uint8_t *out_hog, int64_t out_pitch,
