@@ -20,7 +20,9 @@
 // of the cross product is exact: the rounding of the constants moves it by
 // at most |gx|/2 + |gy|/2 <= |g|, while its true magnitude exceeds
 // 2^22 * 1e-5 * |g| > 41 |g|.  Every term stays below 2^31 (4.2e6 * 255 +
-// 4.2e6 * 255 < 2.1e9), so the test runs in int32.
+// 4.2e6 * 255 < 2.1e9), so the test runs in int32.  The pre-pass reads n
+// for the folded gradient from a table that this same test fills once per
+// device (256 x 256 entries, one per (|gx|, gy)).
 //
 // One CTA computes a 16 x 128 tile, 4 adjacent pixels per thread as one
 // 32-bit word of bytes.  It stages I for the tile plus a 4-pixel halo in
