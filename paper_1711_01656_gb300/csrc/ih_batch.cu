@@ -268,8 +268,9 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
         int64_t cpitch[kMaxChannels];
         frame_planes(f, feat, fp, planes, cpitch);
         if (!make_planeset(ctx, f, fr, planes, cpitch, sets[k])) return bail(fail(ctx, IH_EINVAL, "too many bins"));
-        carry_total += (carry_bytes(sets[k]) + 255) & ~size_t(255);
     }
+    batch_grids(sets.data(), n, ctx->nsm);
+    for (int k = 0; k < n; ++k) carry_total += (carry_bytes(sets[k]) + 255) & ~size_t(255);
     char *carries = nullptr;
     if (carry_total) {
         cudaError_t e = batch_alloc(b, &carries, carry_total, st);

@@ -16,4 +16,9 @@ TileGrid choose_grid(int H, int W, int groups, int nsm);
 // Tile grid with explicit band rows and strip width (clamped to the frame).
 TileGrid make_grid(int H, int W, int R, int Wc);
 
+// The grids of the n plane sets of one batch: when the batch fills the GPU
+// even with the largest tiles, every frame takes them (else the sets keep
+// their grids).  Call before the carries are sized.
+void batch_grids(PlaneSet *sets, int n, int nsm);
+
 }  // namespace ih
