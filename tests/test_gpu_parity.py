@@ -727,3 +727,47 @@ def test_query_both_partial_and_refusals(ihlib, ctx):
         ih.ih_sync(ctx)
     assert (o[1] == -1).all().item() and np.array_equal(o[0].cpu().numpy(), oracle.rect_hist(img, 8, bad[:1].cpu().numpy())[0])
     ih.ih_release(ctx, hdl)
+
+
+def test_plain_stream_order_gives_the_same_results(ihlib, ctx, tmp_path):
+    """IH_PDL=0 (every launch in plain stream order, read once per process)
+    builds and queries the same bits as the default programmatic launches."""
+    import os
+    import subprocess
+    import sys
+    h, w = 300, 700
+    rgb = synth.blob_rgb(h, w, 91)
+    rects = synth.rects_uniform_corners(h, w, 500, 92)
+    wins = synth.rects_side_range(h, w, 200, 1, 100, 93)
+    np.save(tmp_path / "rgb.npy", rgb)
+    np.save(tmp_path / "rects.npy", rects)
+    np.save(tmp_path / "wins.npy", wins)
+    script = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_01656_gb300 import ih, synth
+d = sys.argv[2]
+rgb, rects, wins = (np.load(d + "/" + n + ".npy") for n in ("rgb", "rects", "wins"))
+dev = torch.device("cuda:0")
+c = ih.ih_create(0)
+f = ih.Frame(torch.from_numpy(rgb).to(dev), synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES,
+             weighted_channel=3, layout=ih.IH_LAYOUT_RECORD)
+hd, = ih.ih_build(c, f)
+full = torch.empty((91,) + rgb.shape[1:], dtype=torch.int32, device=dev)
+ih.ih_export(c, hd, full)
+r = torch.empty((len(rects), 91), dtype=torch.int32, device=dev)
+wo = torch.empty((len(wins), 16), dtype=torch.float32, device=dev)
+ih.ih_query(c, hd, torch.from_numpy(rects).to(dev), r, torch.from_numpy(wins).to(dev), wo)
+ih.ih_sync(c)
+np.save(d + "/out_" + sys.argv[3] + ".npy", np.concatenate([full.cpu().numpy().ravel().view(np.uint32),
+        r.cpu().numpy().ravel().view(np.uint32), wo.cpu().numpy().ravel().view(np.uint32)]))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for tag, pdl in (("pdl", "1"), ("plain", "0")):
+        env = dict(os.environ, IH_PDL=pdl)
+        subprocess.run([sys.executable, "-c", script, root, str(tmp_path), tag], env=env, check=True, timeout=600)
+    a, b = np.load(tmp_path / "out_pdl.npy"), np.load(tmp_path / "out_plain.npy")
+    assert np.array_equal(a, b)
+    feats = oracle.features(rgb)
+    full = a[:91 * h * w].view(np.int32).reshape(91, h, w)
+    assert np.array_equal(full, oracle.frame_integral_histogram(feats, synth.FMV_CHANNELS))
