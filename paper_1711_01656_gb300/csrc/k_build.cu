@@ -102,9 +102,11 @@ __device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int c
 constexpr int kSumThreads = 256;
 constexpr int kWalk = 32;  // pixels one thread walks per item
 
-// Dynamic shared memory of k_tile_sums for bands of up to R rows: the staged
-// byte tile, the column counters of one pass and the row counters of the
-// strip (and the offset sums of both for the weighted channel).
+// Dynamic shared memory of a run-length tile-sums CTA (tile_sums_body) for
+// bands of up to R rows: the staged byte tile, the column counters of one
+// pass and the row counters of the strip (and, with WT, the offset sums of
+// both).  The engine runs this CTA for windows of the weighted channel; the
+// other windows take the packed-field groups of tile_sums_count_body.
 __host__ __device__ constexpr size_t sums_q_bytes(int R) { return ((size_t)R * kQStride + 15) & ~size_t(15); }
 __host__ __device__ constexpr size_t sums_smem_bytes(int R, bool weighted)
 {
@@ -199,6 +201,8 @@ __device__ __forceinline__ void walk_row(const uint8_t *qt, int t, int clo, int 
     }
 }
 
+// Tile sums of window widx over tile (band i, strip j) by one 256-thread CTA
+// (WT: also the offset sums of the weighted channel).
 template <bool WT>
 __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i, int widx)
 {
