@@ -38,6 +38,14 @@ struct ih_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches_per_run = 0;
+    // a batch of one frame runs the single-frame kernels (no per-item frame
+    // search, tables in kernel parameters) with these host copies
+    bool single = false;
+    bool single_feat = false;
+    FeatJob feat0{};
+    PlaneSet set0{};
+    CountView view0{};
+    QueryJob q0{};
 };
 
 namespace {
@@ -54,6 +62,26 @@ cudaError_t batch_alloc(ih_batch *b, T **p, size_t bytes, cudaStream_t st)
 int enqueue_run(ih_batch *b, cudaStream_t st, const Prof *prof)
 {
     int n = 0, k = 0;
+    if (b->single) {
+        if (b->single_feat) {
+            const FeatJob &f = b->feat0;
+            k = launch_features(f.r, f.g, f.b, f.pitch, f.H, f.W, nullptr, f.out_i, f.out_hog, f.opitch, st, prof);
+            if (k < 0) return -1;
+            n += k;
+        }
+        k = launch_build(b->set0, st, prof);
+        if (k < 0) return -1;
+        n += k;
+        const QueryJob &q = b->q0;
+        const int64_t nr = q.rects ? b->q_rects / rect_items(b->view0) : 0, nw = q.wins ? b->q_wins / q.m.Bw : 0;
+        if (nr || nw) {
+            k = launch_query_both(b->view0, q.m, q.rects, nr, q.rect_out, q.wins, nw, q.kernel, q.layers, q.normalize,
+                                  q.wout, b->ctx->d_err, st, prof);
+            if (k < 0) return -1;
+            n += k;
+        }
+        return n;
+    }
     if (b->feat_total) {
         k = launch_features_batch(b->d_feat, b->d_feat_pre, b->nfeat, b->feat_total, st, prof);
         if (k < 0) return -1;
@@ -359,6 +387,14 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
     b->d_feat_pre = d_pre + 7 * (n + 1);
     b->nfeat = (int)feats.size();
     b->feat_total = feat_pre.back();
+    if (n == 1) {
+        b->single = true;
+        b->single_feat = !feats.empty();
+        if (b->single_feat) b->feat0 = feats[0];
+        b->set0 = sets[0];
+        b->view0 = recs[0].view;
+        b->q0 = qj[0];
+    }
     // graph
     if (flags & IH_BATCH_GRAPH) {
         prepare_kernels();
