@@ -336,6 +336,9 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
     ps.out = fr.d_ih;
     ps.mom = fr.d_mom;
     ps.mom32 = fr.mbits == 32;
+    ps.uni = 1;
+    for (int c = 0; c < fr.nchan; ++c)
+        if (f.chan[c].mode != 0) ps.uni = 0;
     return true;
 }
 

@@ -149,6 +149,8 @@ struct PlaneSet {
     int32_t layout;       // Layout of the count tensor
     int32_t wch;          // weighted channel, or -1
     int32_t mom32;        // moment planes stored as uint32
+    int32_t uni;          // every channel bins uniformly (mode 0): the tiles kernels take a
+                          // code path with the bin rule folded in
     ChanDev chan[kMaxChannels];
     int32_t ngroups;      // count bin groups (<= kGroupBins bins each)
     int32_t nwin;         // tile-sums windows (<= kWindowBins bins each)

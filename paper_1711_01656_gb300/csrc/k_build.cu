@@ -780,7 +780,7 @@ __device__ __forceinline__ void store_record_staged(int32_t *row, int rec_w, int
 // LAYOUT_RECORD: NB = 8 is the group's width in the record and its
 // nb + nb1 <= NB real bins may come from two channels (SEG2); the padding
 // fields are never hit and hold 0.
-template <int LAYOUT, int NB, bool SEG2, bool PAIR>
+template <int LAYOUT, int NB, bool SEG2, bool PAIR, bool UNI = false>
 __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int j, int gi, int lane,
                                                  int32_t (*RL)[kGroupBins], int4 *stage)
 {
@@ -809,7 +809,7 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
     // the channels' descriptors in registers for the row loop
     const uint8_t *const pl0 = ch.plane, *const pl1 = ch1.plane;
     const int64_t pt0 = ch.pitch, pt1 = ch1.pitch;
-    const int bins0 = ch.bins, mode0 = ch.mode, bins1 = ch1.bins, mode1 = ch1.mode;
+    const int bins0 = ch.bins, mode0 = UNI ? 0 : ch.mode, bins1 = ch1.bins, mode1 = UNI ? 0 : ch1.mode;
     const int blo0 = gr.b_lo, nb0 = gr.nb, blo1 = gr.b_lo1, nbs1 = gr.nb1;
     const bool vec_ok = ((pt0 & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl0) & 3) == 0);
     const bool vec_ok1 = ((pt1 & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl1) & 3) == 0);
@@ -1078,10 +1078,18 @@ __device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t
         // one code path per frame: when some group draws on two channels,
         // every group runs the two-channel path (an empty second segment
         // never hits), so an SM never interleaves two large loop bodies
-        if (ps.seg2)
-            tiles_count_unit<LAYOUT_RECORD, kGroupBins, true, PAIR>(ps, i, j, gi, lane, RL, stage);
-        else
-            tiles_count_unit<LAYOUT_RECORD, kGroupBins, false, PAIR>(ps, i, j, gi, lane, RL, stage);
+        // (likewise one bin rule per frame)
+        if (ps.seg2) {
+            if (ps.uni)
+                tiles_count_unit<LAYOUT_RECORD, kGroupBins, true, PAIR, true>(ps, i, j, gi, lane, RL, stage);
+            else
+                tiles_count_unit<LAYOUT_RECORD, kGroupBins, true, PAIR>(ps, i, j, gi, lane, RL, stage);
+        } else {
+            if (ps.uni)
+                tiles_count_unit<LAYOUT_RECORD, kGroupBins, false, PAIR, true>(ps, i, j, gi, lane, RL, stage);
+            else
+                tiles_count_unit<LAYOUT_RECORD, kGroupBins, false, PAIR>(ps, i, j, gi, lane, RL, stage);
+        }
     } else {
     const int gi = (int)(unit / ntiles), tile = (int)(unit % ntiles);
     const int i = tile / ps.g.ns, j = tile % ps.g.ns;
@@ -1131,7 +1139,7 @@ __global__ void __launch_bounds__(128, 3) k_tiles_count_b(const BatchDev bd)
 
 // ------------------------------------------------------------- moment tiles
 
-template <bool M32>
+template <bool M32, bool UNI = false>
 __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, int j, int wb, int lane,
                                                    int32_t *RLn, long long *RLx, long long *RLxx,
                                                    long long *stage)
@@ -1214,7 +1222,7 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                 int pn[4], pu[4], puu[4];
 #pragma unroll
                 for (int jj = 0; jj < 4; ++jj) {
-                    const int q = bin_of((px >> (8 * jj)) & 0xff, ch.bins, ch.mode);
+                    const int q = bin_of((px >> (8 * jj)) & 0xff, ch.bins, UNI ? 0 : ch.mode);
                     const int e = (jj < nvalid && q == wb) ? 1 : 0;
                     const int u = lane * 4 + jj;
                     pn[jj] = (jj ? pn[jj - 1] : 0) + e;
@@ -1331,6 +1339,9 @@ __global__ void __launch_bounds__(128, 4) k_tiles(const __grid_constant__ PlaneS
         if (ps.mom32)
             tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, m.RLn[wid], m.RLx[wid], m.RLxx[wid],
                                      m.stage[wid]);
+        else if (ps.uni)
+            tiles_moments_unit<false, true>(ps, tile / g.ns, tile % g.ns, wb, lane, m.RLn[wid], m.RLx[wid],
+                                            m.RLxx[wid], m.stage[wid]);
         else
             tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, m.RLn[wid], m.RLx[wid], m.RLxx[wid],
                                       m.stage[wid]);
@@ -1362,6 +1373,9 @@ __global__ void __launch_bounds__(128, 4) k_tiles_b(const BatchDev bd, unsigned 
         if (ps.mom32)
             tiles_moments_unit<true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, m.RLn[wid], m.RLx[wid],
                                      m.RLxx[wid], m.stage[wid]);
+        else if (ps.uni)
+            tiles_moments_unit<false, true>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, m.RLn[wid], m.RLx[wid],
+                                            m.RLxx[wid], m.stage[wid]);
         else
             tiles_moments_unit<false>(ps, tile / ps.g.ns, tile % ps.g.ns, wb, lane, m.RLn[wid], m.RLx[wid],
                                       m.RLxx[wid], m.stage[wid]);
