@@ -703,7 +703,7 @@ def phog_section(ih, dev, runs=10):
             "best_placement_found": [72 + best // 256, 82 + best % 256], "target_at": [200, 210]}
 
 
-def plain_section(ih, dev, runs=50):
+def plain_section(ih, dev, runs=400):
     """The plain frame: 640 x 480 uniform grayscale, 16 bins, 10,000 random
     rectangles.  Launch latency dominates, so the build + queries are timed
     both as plain per-frame calls and as one replayed CUDA graph (a one-frame
