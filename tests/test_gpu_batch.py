@@ -193,3 +193,38 @@ def test_batch_other_kernels_equal_single(ihlib, ctx, kernel, layers):
         ih.ih_batch_destroy(batch)
         for hdl in handles:
             ih.ih_release(ctx, hdl)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+@pytest.mark.parametrize("layout", [0, 2])
+def test_one_frame_batch(ihlib, ctx, graph, layout):
+    """A batch of one frame (run with the single-frame kernels) gives the
+    same tensor, rectangles and weighted windows as ih_build + ih_query."""
+    ih = ihlib
+    h, w = 333, 517
+    rgb = torch.from_numpy(synth.blob_rgb(h, w, 61)).to(DEV)
+    f = ih.Frame(rgb, synth.FMV_CHANNELS, input=ih.IH_INPUT_RGB_FEATURES, weighted_channel=3, layout=layout)
+    rects = torch.from_numpy(synth.rects_uniform_corners(h, w, 300, 62)).to(DEV)
+    wins = torch.from_numpy(synth.rects_side_range(h, w, 120, 1, 90, 63)).to(DEV)
+    r_out = torch.full((300 * 91,), -7, dtype=torch.int32, device=DEV)
+    w_out = torch.full((120 * 16,), -7.0, dtype=torch.float32, device=DEV)
+    batch, handles = ih.ih_batch_create(ctx, [f], rects=rects, rect_counts=[300], rect_out=r_out, windows=wins,
+                                        window_counts=[120], weighted_out=w_out,
+                                        batch_flags=ih.IH_BATCH_GRAPH if graph else 0)
+    try:
+        ih.ih_batch_run(ctx, batch)
+        ih.ih_sync(ctx)
+        single, = ih.ih_build(ctx, f)
+        sr = torch.empty((300, 91), dtype=torch.int32, device=DEV)
+        sw = torch.empty((120, 16), dtype=torch.float32, device=DEV)
+        ih.ih_query(ctx, single, rects, sr, wins, sw)
+        ih.ih_sync(ctx)
+        assert torch.equal(_export(ih, ctx, handles[0]), _export(ih, ctx, single))
+        assert torch.equal(r_out.view(300, 91), sr) and torch.equal(w_out.view(120, 16), sw)
+        feats = oracle.features(rgb.cpu().numpy())
+        assert np.array_equal(sr.cpu().numpy(), oracle.frame_rect_hist(feats, synth.FMV_CHANNELS, rects.cpu().numpy()))
+        ih.ih_release(ctx, single)
+    finally:
+        ih.ih_batch_destroy(batch)
+        for hd in handles:
+            ih.ih_release(ctx, hd)
