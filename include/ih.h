@@ -454,7 +454,7 @@ ih_status ih_server_destroy(ih_server *srv);
  * would synchronise the device, or an application whose allocator owns all
  * device memory).
  *
- * Builds the count integral histogram (Eq. 2.15) of ONE uint8 channel on the
+ * Builds the count integral histogram of ONE uint8 channel on the
  * CURRENT device, enqueued on `stream`, without allocating anything:
  *   d_pixels  device, H rows of pitch_bytes (>= W) bytes;
  *   bins      1..256, mode an ih_binmode;
@@ -463,8 +463,11 @@ ih_status ih_server_destroy(ih_server *srv);
  *             columns W..out_pitch-1 receive unspecified values.
  * Tile carries live in one device array of IH_STATIC_SCRATCH_BYTES that the
  * library holds on every GPU that loads it until the process exits.  The
- * array's device address is looked up on the first call made on each device;
- * make that first call before any stream capture begins.  All calls share the
+ * first call made on each device does a one-time set-up: it looks up the
+ * array's device address and prepares the build kernels for that device,
+ * which SYNCHRONISES THE DEVICE once; make that first call before any stream
+ * capture begins and before the loop that must not stall.  Later calls only
+ * enqueue kernels, on the same kernel path as ih_build.  All calls share the
  * array: calls whose work overlaps on the GPU race on it and must be ordered
  * by the caller (one stream, or events).  Returns IH_EINVAL for bad arguments,
  * IH_ETOOBIG when even the largest tiles need more than the array holds

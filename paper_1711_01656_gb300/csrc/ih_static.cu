@@ -11,9 +11,14 @@
 // statically sized device array of this library.
 //
 // The array lives in every GPU that loads the library until the process
-// exits.  Its device address is looked up with cudaGetSymbolAddress on the
-// first call made on each device (with that device current) and cached; that
-// first call should be made before any stream capture begins.  Every call
+// exits.  The first call made on each device (with that device current) does
+// the set-up: it looks up the array's device address with
+// cudaGetSymbolAddress and caches it, and it prepares the build kernels once
+// for the device (shared-memory limits, and the feature pre-pass's table,
+// whose fill synchronises the device).  Make that first call before any
+// stream capture begins and outside a loop that must not stall; later calls
+// only enqueue kernels.  This call takes the same kernel path as ih_build
+// on the same frame (a uniform channel takes the folded bin rule).  Every call
 // shares the array: calls whose work overlaps on the GPU (on different
 // streams, or on one device from several threads) race on it.  Every carry
 // cell a call reads is written earlier by the same call, so nothing needs
@@ -44,6 +49,9 @@ cudaError_t static_scratch_address(int dev, void **out)
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
         if (e != cudaSuccess) return e;
+        prepare_kernels();
+        const cudaError_t e2 = cudaGetLastError();
+        if (e2 != cudaSuccess) return e2;
         g_static_addr[dev] = p;
     }
     *out = g_static_addr[dev];
@@ -85,6 +93,7 @@ extern "C" ih_status ih_build_counts_static(const uint8_t *d_pixels, int32_t hei
     ps.chan[0].bins = bins;
     ps.chan[0].mode = mode;
     ps.chan[0].bin_off = 0;
+    ps.uni = (mode == IH_BIN_UNIFORM8) ? 1 : 0;
     // groups by size, largest first (one tiles launch per size)
     GroupDev tmp[kMaxGroups];
     const int ng = split_groups(bins, kGroupBins, tmp);
@@ -100,7 +109,8 @@ extern "C" ih_status ih_build_counts_static(const uint8_t *d_pixels, int32_t hei
     ps.g.P = out_pitch;
     ps.out = d_out;
     void *base = nullptr;
-    if (carry_bytes(ps) && static_scratch_address(dev, &base) != cudaSuccess) return IH_ECUDA;
+    if (static_scratch_address(dev, &base) != cudaSuccess) return IH_ECUDA;
+    if (!carry_bytes(ps)) base = nullptr;
     carve_carries(ps, base);
     if (launch_build(ps, static_cast<cudaStream_t>(stream), nullptr) < 0) return IH_ECUDA;
     return IH_OK;

@@ -42,6 +42,7 @@
 // No kernel waits on another CTA; the only inter-CTA data flow is through the
 // carry arrays between launches on one stream.
 #include <algorithm>
+#include <mutex>
 
 #include <stdlib.h>
 
@@ -1403,8 +1404,6 @@ void set_max_smem(F *f, size_t bytes)
 
 size_t r256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int g_nsm = 148;
-
 }  // namespace
 
 bool pdl_enabled()
@@ -1466,15 +1465,17 @@ void carve_carries(PlaneSet &ps, void *base)
 void prepare_kernels()
 {
     prepare_features();
-    static bool attrs = false;
-    if (!attrs) {
-        set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
-        set_max_smem(k_tile_sums_all_b, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev);
-        attrs = true;
-    }
+    // Shared-memory limits are function attributes of the current device:
+    // set them once per device, under a lock (callers may be on any thread).
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev < 0 || dev >= 64 || done[dev]) return;
+    set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
+    set_max_smem(k_tile_sums_all_b, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
+    done[dev] = true;
 }
 
 int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t st, const Prof *prof)
