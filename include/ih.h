@@ -235,20 +235,41 @@ ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
                           int32_t *d_out, void *stream);
 
 /* Spatial pyramids of gradient orientations (Algorithm 2, Sec. 2.3).
- * ih_phog_build runs steps 1-4 on a grayscale search window d_gray (device,
- * height x width uint8, row pitch pitch_bytes): central differences (step 1,
- * replicated borders); gradient magnitude in fixed point with 4 fractional
- * bits, w = floor(16 sqrt(gx^2 + gy^2)) (exact integer square root); a pixel
- * is an edge pixel when w >= 16 * tau (this reading of step 1's Canny
- * detector keeps the magnitude threshold and leaves out non-maximum
- * suppression and hysteresis); the unsigned orientation of edge pixels in 9
- * bins of 20 degrees; and the w-weighted integral histogram of those bins
- * (Eq. 3.4 with a pixel weight), int64 9 x height x pitch, owned by the
- * context as frame *out_handle (ih_info reports it with 9 bins and its
- * bytes as moment_bytes; count-tensor calls refuse it).  Errors as for
- * ih_build. */
+ *
+ * ih_canny_edges runs step 1 alone, Canny's edge detector (J. Canny 1986),
+ * on a grayscale window d_gray (device, height x width uint8, row pitch
+ * pitch_bytes; height * width <= 2^30), in integers: 5 x 5 binomial
+ * smoothing (1 4 6 4 1 x 1 4 6 4 1, replicated borders, left unnormalised:
+ * S = 256 x the smoothed image); the gradient G of S by central differences
+ * (replicated borders); non-maximum suppression across the edge in four
+ * direction sectors (a pixel survives when |G|^2 is above its neighbour's on
+ * the lower-column side of the sector's line -- the upper-row side for the
+ * vertical sector -- and not below the opposite neighbour's; neighbours
+ * outside the window count as 0); the double threshold: strong when
+ * |G| >= 256 tau_high, weak when |G| >= 256 tau_low (0 <= tau_low <=
+ * tau_high <= IH_CANNY_MAX_THRESHOLD, in units of a central difference of
+ * the normalised smoothed image); and hysteresis: a weak survivor is an edge
+ * pixel when 8-connected survivors join it to a strong one.  d_edges
+ * (device, caller-owned, height rows of edges_pitch >= width bytes) receives
+ * 1 on edge pixels and 0 elsewhere.  Hysteresis is a union-find whose
+ * pointer walks are bounded: one that gives up makes the next ih_sync()
+ * return IH_ETIMEOUT.  Scratch of 6 bytes per pixel comes from the
+ * context's pool.
+ *
+ * ih_phog_build runs steps 1-4 on the window: Canny's edge pixels (as
+ * above); the window's own gradient by central differences (replicated
+ * borders) and its magnitude in fixed point with 4 fractional bits,
+ * w = floor(16 sqrt(gx^2 + gy^2)) (exact integer square root); the
+ * unsigned orientation of edge pixels in 9 bins of 20 degrees; and the
+ * w-weighted integral histogram of those bins (Eq. 3.4 with a pixel
+ * weight), int64 9 x height x pitch, owned by the context as frame
+ * *out_handle (ih_info reports it with 9 bins and its bytes as
+ * moment_bytes; count-tensor calls refuse it).  Errors as for ih_build. */
+#define IH_CANNY_MAX_THRESHOLD 1024
+ih_status ih_canny_edges(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int32_t width, int64_t pitch_bytes,
+                         int32_t tau_low, int32_t tau_high, uint8_t *d_edges, int64_t edges_pitch, void *stream);
 ih_status ih_phog_build(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int32_t width, int64_t pitch_bytes,
-                        int32_t tau, int32_t *out_handle, void *stream);
+                        int32_t tau_low, int32_t tau_high, int32_t *out_handle, void *stream);
 
 /* Steps 5-20: the descriptor of each of n windows (device n x 4 int32
  * r0, c0, r1, c1): for l = 0 .. levels, the window's 2^l x 2^l cells of

@@ -76,7 +76,9 @@ def _bind(path: str):
     lib.oracle_local_median.restype = None
     lib.oracle_isqrt.argtypes = [i64]
     lib.oracle_isqrt.restype = i64
-    lib.oracle_phog_planes.argtypes = [p, i32, i32, i32, p, p]
+    lib.oracle_canny.argtypes = [p, i32, i32, i32, i32, p, p, p, p]
+    lib.oracle_canny.restype = None
+    lib.oracle_phog_planes.argtypes = [p, i32, i32, i32, i32, p, p]
     lib.oracle_phog_planes.restype = None
     lib.oracle_phog_ih.argtypes = [p, p, i32, i32, i32, p]
     lib.oracle_phog_ih.restype = None
@@ -206,13 +208,29 @@ def isqrt(n: int) -> int:
     return int(_load().oracle_isqrt(int(n)))
 
 
-def phog_planes(gray, tau: int):
-    """Algorithm 2 steps 1-3: (bins uint8 with 255 off edges, int32 weights)."""
+def canny(gray, lo: int, hi: int):
+    """Algorithm 2 step 1, Canny's detector: (edges uint8 0/1, smoothed S
+    int32 = 256 x the binomial-smoothed image, squared gradient magnitude of
+    S int64, survivor class uint8: 0 none, 1 weak, 2 strong)."""
+    a = _plane(gray)
+    h, w = a.shape
+    edges = np.empty((h, w), np.uint8)
+    smooth = np.empty((h, w), np.int32)
+    mag2 = np.empty((h, w), np.int64)
+    cls = np.empty((h, w), np.uint8)
+    _load().oracle_canny(a.ctypes.data, h, w, int(lo), int(hi), edges.ctypes.data, smooth.ctypes.data,
+                         mag2.ctypes.data, cls.ctypes.data)
+    return edges, smooth, mag2, cls
+
+
+def phog_planes(gray, lo: int, hi: int):
+    """Algorithm 2 steps 1-3: (bins uint8 with 255 off the Canny edges,
+    int32 magnitude weights)."""
     a = _plane(gray)
     h, w = a.shape
     bins = np.empty((h, w), np.uint8)
     wt = np.empty((h, w), np.int32)
-    _load().oracle_phog_planes(a.ctypes.data, h, w, int(tau), bins.ctypes.data, wt.ctypes.data)
+    _load().oracle_phog_planes(a.ctypes.data, h, w, int(lo), int(hi), bins.ctypes.data, wt.ctypes.data)
     return bins, wt
 
 

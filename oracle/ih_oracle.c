@@ -25,9 +25,11 @@
  *     city-block distance of every placement      Eq. 2.22 (p = 1), Sec. 2.4.3
  *   - spatio-temporal median by sorting the box's
  *     quantised values over the frames             Algorithm 4, Sec. 4.1.1
- *   - magnitude-weighted orientation planes, their
- *     integral histogram, pyramid descriptors by
- *     pixel sums and the pyramid match kernel      Algorithm 2, Eq. 2.23-2.24
+ *   - Canny edges (smoothing, non-maximum
+ *     suppression, hysteresis), magnitude-weighted
+ *     orientation planes, their integral histogram,
+ *     pyramid descriptors by pixel sums and the
+ *     pyramid match kernel                         Algorithm 2, Eq. 2.23-2.24
  *   - feature channels: intensity I=(R+G+B)/3     Eq. 2.33
  *     and gradient orientation tan^-1(Iy/Ix)      Fig. 2.3, Algorithm 2
  *
@@ -51,9 +53,13 @@
  *   - the median of Algorithm 4 is the lower median bin of the box's
  *     quantised values, the box clipped at the frame border (the thesis
  *     leaves both open);
- *   - Algorithm 2's Canny step is read as a gradient-magnitude threshold
- *     (no non-maximum suppression or hysteresis), the magnitude is kept in
- *     fixed point (floor(16 |g|)), the pyramid cells are floor(h/2^l) x
+ *   - Algorithm 2's Canny step follows Canny (1986) in integers: 5 x 5
+ *     binomial smoothing, central-difference gradient, non-maximum
+ *     suppression in four exact direction sectors (ties broken towards the
+ *     lower column / upper row), double threshold on |G| (lo, hi) and
+ *     hysteresis over 8-connected survivors; step 2's gradient is the
+ *     window's own (unsmoothed) central difference, its magnitude kept in
+ *     fixed point (floor(16 |g|)); the pyramid cells are floor(h/2^l) x
  *     floor(w/2^l) at multiples of that size, and its garbled index
  *     updates are read as visiting the s x s cells once each;
  *   - intensity rounds down; gradient orientation is unsigned, in
@@ -430,14 +436,123 @@ int64_t oracle_isqrt(int64_t n)
     return lo;
 }
 
-/* Algorithm 2, steps 1-3 on a grayscale search window: central differences
- * (step 1, replicated borders), gradient magnitude in fixed point with 4
- * fractional bits, w = floor(16 sqrt(gx^2 + gy^2)), and the 9-bin unsigned
- * orientation; a pixel is an edge pixel when w >= 16 * tau (the reading of
- * the Canny step: a magnitude threshold).  bins: h x w uint8 (the bin, 255
- * off edges); weight: h x w int32 (w on edges, 0 off them). */
-void oracle_phog_planes(const uint8_t *gray, int h, int w, int tau, uint8_t *bins, int32_t *weight)
+/* Algorithm 2, step 1: Canny's edge detector (J. Canny, "A computational
+ * approach to edge detection", IEEE TPAMI 8(6), 1986), in integers:
+ *   (a) smoothing by the 5 x 5 binomial kernel (1 4 6 4 1) x (1 4 6 4 1),
+ *       replicated borders, left unnormalised: S = 256 x the smoothed image;
+ *   (b) the gradient of S by central differences (replicated borders),
+ *       Gx = S(r, c+1) - S(r, c-1), Gy = S(r+1, c) - S(r-1, c), and its
+ *       squared magnitude M2 = Gx^2 + Gy^2;
+ *   (c) non-maximum suppression across the edge: the gradient direction is
+ *       put in one of four sectors (horizontal, vertical, and the two
+ *       diagonals) by the exact tests |Gy| < tan(22.5 deg) |Gx|, i.e.
+ *       (|Gx| + |Gy|)^2 < 2 Gx^2, and its mirror with the axes swapped; the
+ *       pixel survives when M2 > M2 of the neighbour on the lower-column
+ *       side of the sector's line (the upper-row side for the vertical
+ *       sector) and M2 >= M2 of the opposite neighbour (neighbours outside
+ *       the window count as 0), so a two-pixel plateau yields one pixel;
+ *   (d) double threshold: a survivor is strong when M2 >= (256 hi)^2 and
+ *       weak when (256 lo)^2 <= M2 < (256 hi)^2;
+ *   (e) hysteresis: a weak survivor is an edge pixel when a chain of
+ *       8-connected survivors (weak or strong) joins it to a strong one;
+ *       strong survivors are edge pixels.  Breadth-first search from every
+ *       strong survivor.
+ * lo and hi are in the units of a central difference of the normalised
+ * smoothed image (|G| / 256).  edges: h x w uint8 (1 = edge).  Optional
+ * outputs (NULL to skip): smooth (S, int32), mag2 (M2, int64), cls (0 none,
+ * 1 weak, 2 strong survivor). */
+static const int or_binom5[5] = {1, 4, 6, 4, 1};
+
+void oracle_canny(const uint8_t *gray, int h, int w, int lo, int hi, uint8_t *edges, int32_t *smooth,
+                  int64_t *mag2, uint8_t *cls)
 {
+    const int64_t n = (int64_t)h * w;
+    int32_t *S = (int32_t *)malloc(sizeof(int32_t) * (n ? n : 1));
+    int64_t *M = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+    uint8_t *K = (uint8_t *)malloc(n ? n : 1);
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (n ? n : 1));
+    /* (a) */
+    for (int r = 0; r < h; r++)
+        for (int c = 0; c < w; c++) {
+            int32_t acc = 0;
+            for (int i = 0; i < 5; i++)
+                for (int j = 0; j < 5; j++)
+                    acc += or_binom5[i] * or_binom5[j] *
+                           (int32_t)gray[(int64_t)clampi(r + i - 2, 0, h - 1) * w + clampi(c + j - 2, 0, w - 1)];
+            S[(int64_t)r * w + c] = acc;
+        }
+    /* (b) */
+    for (int r = 0; r < h; r++)
+        for (int c = 0; c < w; c++) {
+            int64_t gx = (int64_t)S[(int64_t)r * w + clampi(c + 1, 0, w - 1)] - S[(int64_t)r * w + clampi(c - 1, 0, w - 1)];
+            int64_t gy = (int64_t)S[(int64_t)clampi(r + 1, 0, h - 1) * w + c] - S[(int64_t)clampi(r - 1, 0, h - 1) * w + c];
+            M[(int64_t)r * w + c] = gx * gx + gy * gy;
+        }
+    /* (c) + (d) */
+    const int64_t thi = (int64_t)256 * hi * (int64_t)256 * hi, tlo = (int64_t)256 * lo * (int64_t)256 * lo;
+    for (int r = 0; r < h; r++)
+        for (int c = 0; c < w; c++) {
+            int64_t gx = (int64_t)S[(int64_t)r * w + clampi(c + 1, 0, w - 1)] - S[(int64_t)r * w + clampi(c - 1, 0, w - 1)];
+            int64_t gy = (int64_t)S[(int64_t)clampi(r + 1, 0, h - 1) * w + c] - S[(int64_t)clampi(r - 1, 0, h - 1) * w + c];
+            int64_t ax = gx < 0 ? -gx : gx, ay = gy < 0 ? -gy : gy, s2 = (ax + ay) * (ax + ay);
+            int dr, dc; /* the neighbour on the "minus" side is (r - dr, c - dc) */
+            if (s2 < 2 * ax * ax) {
+                dr = 0; dc = 1;            /* gradient near 0 deg: compare left / right */
+            } else if (s2 < 2 * ay * ay) {
+                dr = 1; dc = 0;            /* near 90 deg: compare up / down */
+            } else if ((gx > 0) == (gy > 0)) {
+                dr = 1; dc = 1;            /* near 45 deg (rows grow downwards): (r-1,c-1) / (r+1,c+1) */
+            } else {
+                dr = -1; dc = 1;           /* near 135 deg: (r+1,c-1) / (r-1,c+1) */
+            }
+            int64_t m = M[(int64_t)r * w + c];
+            int rm = r - dr, cm = c - dc, rp = r + dr, cp = c + dc;
+            int64_t mm = (rm >= 0 && rm < h && cm >= 0 && cm < w) ? M[(int64_t)rm * w + cm] : 0;
+            int64_t mp = (rp >= 0 && rp < h && cp >= 0 && cp < w) ? M[(int64_t)rp * w + cp] : 0;
+            uint8_t k = 0;
+            if (m > mm && m >= mp) k = m >= thi ? 2 : (m >= tlo ? 1 : 0);
+            K[(int64_t)r * w + c] = k;
+        }
+    /* (e) */
+    int64_t head = 0, tail = 0;
+    for (int64_t i = 0; i < n; i++) {
+        edges[i] = K[i] == 2;
+        if (K[i] == 2) queue[tail++] = i;
+    }
+    while (head < tail) {
+        int64_t i = queue[head++];
+        int r = (int)(i / w), c = (int)(i % w);
+        for (int a = -1; a <= 1; a++)
+            for (int b = -1; b <= 1; b++) {
+                int y = r + a, x = c + b;
+                if ((a == 0 && b == 0) || y < 0 || y >= h || x < 0 || x >= w) continue;
+                int64_t j = (int64_t)y * w + x;
+                if (K[j] != 0 && !edges[j]) {
+                    edges[j] = 1;
+                    queue[tail++] = j;
+                }
+            }
+    }
+    if (smooth) memcpy(smooth, S, sizeof(int32_t) * n);
+    if (mag2) memcpy(mag2, M, sizeof(int64_t) * n);
+    if (cls) memcpy(cls, K, n);
+    free(S);
+    free(M);
+    free(K);
+    free(queue);
+}
+
+/* Algorithm 2, steps 1-3 on a grayscale search window: the Canny edge
+ * pixels of step 1 (oracle_canny, thresholds lo and hi); step 2's gradient
+ * of the window by central differences (replicated borders) and its
+ * magnitude in fixed point with 4 fractional bits,
+ * w = floor(16 sqrt(gx^2 + gy^2)); step 3's 9-bin unsigned orientation of
+ * the edge pixels.  bins: h x w uint8 (the bin, 255 off edges); weight:
+ * h x w int32 (w on edges, 0 off them). */
+void oracle_phog_planes(const uint8_t *gray, int h, int w, int lo, int hi, uint8_t *bins, int32_t *weight)
+{
+    uint8_t *edge = (uint8_t *)malloc((size_t)h * w ? (size_t)h * w : 1);
+    oracle_canny(gray, h, w, lo, hi, edge, NULL, NULL, NULL);
     for (int r = 0; r < h; r++)
         for (int c = 0; c < w; c++) {
             int gx = (int)gray[(int64_t)r * w + clampi(c + 1, 0, w - 1)] -
@@ -445,10 +560,11 @@ void oracle_phog_planes(const uint8_t *gray, int h, int w, int tau, uint8_t *bin
             int gy = (int)gray[(int64_t)clampi(r + 1, 0, h - 1) * w + c] -
                      (int)gray[(int64_t)clampi(r - 1, 0, h - 1) * w + c];
             int64_t m = oracle_isqrt(256 * ((int64_t)gx * gx + (int64_t)gy * gy));
-            int edge = m >= 16 * (int64_t)tau;
-            bins[(int64_t)r * w + c] = edge ? (uint8_t)oracle_orientation_bin(gx, gy, 9) : 255;
-            weight[(int64_t)r * w + c] = edge ? (int32_t)m : 0;
+            int e = edge[(int64_t)r * w + c];
+            bins[(int64_t)r * w + c] = e ? (uint8_t)oracle_orientation_bin(gx, gy, 9) : 255;
+            weight[(int64_t)r * w + c] = e ? (int32_t)m : 0;
         }
+    free(edge);
 }
 
 /* Algorithm 2, step 4: the magnitude-weighted integral histogram of the

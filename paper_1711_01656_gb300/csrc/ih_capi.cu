@@ -632,12 +632,12 @@ ih_status ih_local_median(ih_ctx *ctx, int32_t handle, int32_t bin0, int32_t nbi
 }
 
 ih_status ih_phog_build(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int32_t width, int64_t pitch_bytes,
-                        int32_t tau, int32_t *out_handle, void *stream)
+                        int32_t tau_low, int32_t tau_high, int32_t *out_handle, void *stream)
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
-    if (!d_gray || !out_handle || height < 1 || width < 1 || pitch_bytes < width || tau < 0 ||
-        (int64_t)height * width > ((int64_t)1 << 31))
+    if (!d_gray || !out_handle || height < 1 || width < 1 || pitch_bytes < width || tau_low < 0 ||
+        tau_high < tau_low || tau_high > IH_CANNY_MAX_THRESHOLD || (int64_t)height * width > ((int64_t)1 << 30))
         return fail(ctx, IH_EINVAL, "ih_phog_build: bad arguments");
     DevGuard dg(ctx->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -653,17 +653,19 @@ ih_status ih_phog_build(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int3
     if (ctx->budget && ctx->used + (uint64_t)fr.moment_bytes > ctx->budget)
         return fail(ctx, IH_EBUDGET, "pyramid planes of %lld bytes exceed the HBM budget", (long long)fr.moment_bytes);
     const int64_t px = (int64_t)height * width;
+    const size_t cbytes = (canny_scratch_bytes(height, width) + 255) & ~size_t(255);
     uint8_t *scratch = nullptr;
     cudaError_t e = pool_alloc(ctx, &fr.d_mom, fr.moment_bytes, st);
-    if (e == cudaSuccess) e = pool_alloc(ctx, &scratch, (size_t)px * 5 + 16, st);
+    if (e == cudaSuccess) e = pool_alloc(ctx, &scratch, cbytes + (size_t)px * 5 + 16, st);
     if (e != cudaSuccess) {
         if (fr.d_mom) cudaFreeAsync(fr.d_mom, st);
         return cuda_fail(ctx, e, "pyramid allocation");
     }
-    int32_t *wt = reinterpret_cast<int32_t *>(scratch);
-    uint8_t *bins = scratch + px * 4;
-    const int k = launch_phog_build(d_gray, pitch_bytes, height, width, tau, bins, wt, fr.P, fr.d_mom, st,
-                                    prof_of(ctx));
+    const CannyScratch cs = carve_canny(scratch, height, width);
+    int32_t *wt = reinterpret_cast<int32_t *>(scratch + cbytes);
+    uint8_t *bins = scratch + cbytes + px * 4;
+    const int k = launch_phog_build(d_gray, pitch_bytes, height, width, tau_low, tau_high, cs, bins, wt, fr.P,
+                                    fr.d_mom, ctx->d_err, st, prof_of(ctx));
     cudaFreeAsync(scratch, st);
     if (k < 0) {
         cudaFreeAsync(fr.d_mom, st);
@@ -671,6 +673,29 @@ ih_status ih_phog_build(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int3
     }
     ctx->launches += k;
     *out_handle = publish_frame(ctx, fr);
+    return IH_OK;
+}
+
+ih_status ih_canny_edges(ih_ctx *ctx, const uint8_t *d_gray, int32_t height, int32_t width, int64_t pitch_bytes,
+                         int32_t tau_low, int32_t tau_high, uint8_t *d_edges, int64_t edges_pitch, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!d_gray || !d_edges || height < 1 || width < 1 || pitch_bytes < width || edges_pitch < width ||
+        tau_low < 0 || tau_high < tau_low || tau_high > IH_CANNY_MAX_THRESHOLD ||
+        (int64_t)height * width > ((int64_t)1 << 30))
+        return fail(ctx, IH_EINVAL, "ih_canny_edges: bad arguments");
+    DevGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *scratch = nullptr;
+    cudaError_t e = pool_alloc(ctx, &scratch, canny_scratch_bytes(height, width), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "edge-detector scratch");
+    const int k = launch_canny_edges(d_gray, pitch_bytes, height, width, tau_low, tau_high,
+                                     carve_canny(scratch, height, width), d_edges, edges_pitch, ctx->d_err, st,
+                                     prof_of(ctx));
+    cudaFreeAsync(scratch, st);
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "edge-detector launch");
+    ctx->launches += k;
     return IH_OK;
 }
 
@@ -742,7 +767,7 @@ ih_status ih_sync(ih_ctx *ctx, void *stream)
     if (h) {
         cudaMemset(ctx->d_err, 0, sizeof(int));
         if (h & 1) return fail(ctx, IH_EINVAL, "a query named a rectangle outside the frame or empty");
-        return fail(ctx, IH_ETIMEOUT, "a device-side wait gave up");
+        return fail(ctx, IH_ETIMEOUT, "a device-side wait or pointer walk gave up");
     }
     return IH_OK;
 }

@@ -302,10 +302,26 @@ inline int64_t phog_descriptor_len(int L)
     for (int l = 0; l <= L; ++l) n += (int64_t)kPhogBins << (2 * l);
     return n;
 }
-// Orientation bins, magnitude weights (scratch, h x w each) and the weighted
-// integral histogram ih: kPhogBins x H x P int64.  Returns launches or -1.
-int launch_phog_build(const uint8_t *gray, int64_t pitch, int H, int W, int tau, uint8_t *bins, int32_t *wt,
-                      int64_t P, int64_t *ih, cudaStream_t st, const Prof *prof);
+// Scratch of Canny's detector on an H x W window: union-find parents
+// (int32), survivor classes and root marks (uint8), H x W each.
+struct CannyScratch {
+    int32_t *parent;
+    uint8_t *cls;
+    uint8_t *mark;
+};
+size_t canny_scratch_bytes(int H, int W);
+CannyScratch carve_canny(void *base, int H, int W);
+// Algorithm 2 step 1 alone: Canny edge pixels (1) of the window into edges
+// (row pitch epitch bytes), thresholds lo <= hi on |G| / 256.  A pointer
+// walk that gives up sets bit 2 of *err.  Returns launches or -1.
+int launch_canny_edges(const uint8_t *gray, int64_t pitch, int H, int W, int lo, int hi, const CannyScratch &cs,
+                       uint8_t *edges, int64_t epitch, int *err, cudaStream_t st, const Prof *prof);
+// Steps 1-4: Canny edges, orientation bins and magnitude weights of the edge
+// pixels (scratch, h x w each) and the weighted integral histogram ih:
+// kPhogBins x H x P int64.  Returns launches or -1.
+int launch_phog_build(const uint8_t *gray, int64_t pitch, int H, int W, int lo, int hi, const CannyScratch &cs,
+                      uint8_t *bins, int32_t *wt, int64_t P, int64_t *ih, int *err, cudaStream_t st,
+                      const Prof *prof);
 int launch_phog_descriptors(const int64_t *ih, int H, int W, int64_t P, int L, const int32_t *wins, int64_t n,
                             int64_t *out, int *err, cudaStream_t st, const Prof *prof);
 int launch_phog_match(const int64_t *ih, int H, int64_t P, int L, const int64_t *target, int wh, int ww, int sr0,

@@ -1,12 +1,12 @@
 // k_phog.cu -- spatial pyramids of gradient orientations (Algorithm 2) and
 // their pyramid match kernel (Sec. 2.4.4, Eq. 2.23-2.24).
 //
-// Steps 1-3: per pixel of a grayscale search window, central differences
-// (step 1, replicated borders), the gradient magnitude in fixed point with 4
+// Step 1: Canny's edge detector (below, k_canny_*).  Steps 2-3: per edge
+// pixel of a grayscale search window, the window's central differences
+// (replicated borders), the gradient magnitude in fixed point with 4
 // fractional bits, w = floor(16 sqrt(gx^2 + gy^2)) (exact integer square
 // root: a rounded sqrt corrected by integer comparisons), and the 9-bin
-// unsigned orientation (ih_orient.cuh); a pixel is an edge pixel when
-// w >= 16 tau.  Step 4: the w-weighted integral histogram of the orientation
+// unsigned orientation (ih_orient.cuh).  Step 4: the w-weighted integral histogram of the orientation
 // bins over edge pixels (Eq. 3.4 with a pixel weight), int64, by a row pass
 // (one warp per (bin, row): chunked warp scans) and a column pass (one thread
 // per (bin, column), running sums down the rows).  Steps 5-20: the L+1-level
@@ -37,20 +37,214 @@ __device__ __forceinline__ int64_t isqrt_exact(int64_t n)
     return s;
 }
 
-__global__ void __launch_bounds__(256) k_phog_planes(const uint8_t *__restrict__ gray, int64_t pitch, int H, int W,
-                                                     int tau, uint8_t *__restrict__ bins, int32_t *__restrict__ wt)
+// ---- step 1: Canny's detector (J. Canny 1986), integer-exact ------------
+//
+// k_canny_nms, one CTA per 32 x 32 tile: the 5 x 5 binomial smoothing
+// S = sum b_i b_j I (b = 1 4 6 4 1, replicated borders, unnormalised), the
+// central-difference gradient of S (replicated borders), its squared
+// magnitude M2 = Gx^2 + Gy^2 (int64), non-maximum suppression in four
+// direction sectors decided exactly by (|Gx| + |Gy|)^2 < 2 Gx^2 (within
+// 22.5 degrees of the column axis) or < 2 Gy^2 (of the row axis), else the
+// diagonal given by the signs: a pixel survives when its M2 is above the
+// neighbour's on the lower-column side of the line (upper-row side for the
+// vertical sector) and not below the opposite one (neighbours outside the
+// window count as 0), then the double threshold: class 2 (strong) when
+// M2 >= (256 hi)^2, class 1 (weak) when M2 >= (256 lo)^2.  The tile stages
+// I (halo 4), the horizontal sums, S (halo 2) and M2 (halo 1) in shared
+// memory; a staged position outside the window holds the value of its
+// clamped position, which is what the replicated borders give.
+//
+// Hysteresis (8-connected survivors joined to a strong one) is a union-find
+// over the survivors: k_canny_union links each survivor to its survivor
+// neighbours W, NW, N and NE (roots always point to smaller indices;
+// atomicMin hooks a root, and a hook that lost a race re-links the tree it
+// displaced); k_canny_mark then flattens every survivor's parent to its root
+// and marks roots of strong survivors; a survivor is an edge pixel when its
+// root is marked.  Every pointer walk is bounded (parents strictly decrease,
+// and a walk gives up after kUfMaxSteps steps, setting bit 2 of the error
+// word, which ih_sync reports as IH_ETIMEOUT).
+constexpr int kCT = 32;           // output tile side
+constexpr int kCI = kCT + 8;      // staged input side (halo 4)
+constexpr int kCS = kCT + 4;      // staged smoothed side (halo 2)
+constexpr int kCM = kCT + 2;      // staged magnitude side (halo 1)
+constexpr int kUfMaxSteps = 1 << 26;
+
+struct CannySmem {
+    int32_t hs[kCI][kCS];         // horizontal binomial sums, rows R0-4.., columns C0-2..
+    int32_t s[kCS][kCS];          // S at rows R0-2.., columns C0-2.. (clamped positions)
+    long long m2[kCM][kCM];       // M2 at rows R0-1.., columns C0-1.. (0 outside the window)
+    uint8_t in[kCI][kCI];         // I at rows R0-4.., columns C0-4.. (clamped)
+};
+
+__device__ __forceinline__ int clampi_d(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__global__ void __launch_bounds__(256) k_canny_nms(const uint8_t *__restrict__ gray, int64_t pitch, int H, int W,
+                                                   long long tlo, long long thi, uint8_t *__restrict__ cls,
+                                                   int32_t *__restrict__ parent, uint8_t *__restrict__ mark)
+{
+    __shared__ CannySmem sm;
+    pdl_wait();
+    const int R0 = blockIdx.y * kCT, C0 = blockIdx.x * kCT, tid = threadIdx.x;
+    for (int k = tid; k < kCI * kCI; k += 256) {
+        const int y = k / kCI, x = k % kCI;
+        sm.in[y][x] = __ldg(gray + (int64_t)clampi_d(R0 - 4 + y, 0, H - 1) * pitch + clampi_d(C0 - 4 + x, 0, W - 1));
+    }
+    __syncthreads();
+    for (int k = tid; k < kCI * kCS; k += 256) {
+        const int y = k / kCS, xs = k % kCS;
+        const int o = clampi_d(C0 - 2 + xs, 0, W - 1) - C0 + 2;  // in-column of tap j = 0
+        sm.hs[y][xs] = sm.in[y][o] + 4 * sm.in[y][o + 1] + 6 * sm.in[y][o + 2] + 4 * sm.in[y][o + 3] +
+                       sm.in[y][o + 4];
+    }
+    __syncthreads();
+    for (int k = tid; k < kCS * kCS; k += 256) {
+        const int ys = k / kCS, xs = k % kCS;
+        const int o = clampi_d(R0 - 2 + ys, 0, H - 1) - R0 + 2;
+        sm.s[ys][xs] = sm.hs[o][xs] + 4 * sm.hs[o + 1][xs] + 6 * sm.hs[o + 2][xs] + 4 * sm.hs[o + 3][xs] +
+                       sm.hs[o + 4][xs];
+    }
+    __syncthreads();
+    for (int k = tid; k < kCM * kCM; k += 256) {
+        const int ym = k / kCM, xm = k % kCM;
+        const int y = R0 - 1 + ym, x = C0 - 1 + xm;
+        long long v = 0;
+        if (y >= 0 && y < H && x >= 0 && x < W) {
+            const long long gx = sm.s[ym + 1][xm + 2] - sm.s[ym + 1][xm];
+            const long long gy = sm.s[ym + 2][xm + 1] - sm.s[ym][xm + 1];
+            v = gx * gx + gy * gy;
+        }
+        sm.m2[ym][xm] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < kCT * kCT; k += 256) {
+        const int ty = k / kCT, tx = k % kCT;
+        const int r = R0 + ty, c = C0 + tx;
+        if (r >= H || c >= W) continue;
+        const long long gx = sm.s[ty + 2][tx + 3] - sm.s[ty + 2][tx + 1];
+        const long long gy = sm.s[ty + 3][tx + 2] - sm.s[ty + 1][tx + 2];
+        const long long ax = gx < 0 ? -gx : gx, ay = gy < 0 ? -gy : gy, s2 = (ax + ay) * (ax + ay);
+        int dr, dc;  // the neighbour on the "minus" side is (r - dr, c - dc)
+        if (s2 < 2 * ax * ax) {
+            dr = 0; dc = 1;
+        } else if (s2 < 2 * ay * ay) {
+            dr = 1; dc = 0;
+        } else if ((gx > 0) == (gy > 0)) {
+            dr = 1; dc = 1;
+        } else {
+            dr = -1; dc = 1;
+        }
+        const long long m = sm.m2[ty + 1][tx + 1];
+        const long long mm = sm.m2[ty + 1 - dr][tx + 1 - dc], mp = sm.m2[ty + 1 + dr][tx + 1 + dc];
+        uint8_t q = 0;
+        if (m > mm && m >= mp) q = m >= thi ? 2 : (m >= tlo ? 1 : 0);
+        const int64_t i = (int64_t)r * W + c;
+        cls[i] = q;
+        parent[i] = q ? (int32_t)i : -1;
+        mark[i] = 0;
+    }
+}
+
+__device__ __forceinline__ int32_t uf_find(const volatile int32_t *parent, int32_t x, int *err)
+{
+    for (int k = 0; k < kUfMaxSteps; ++k) {
+        const int32_t p = parent[x];
+        if (p == x) return x;
+        x = p;
+    }
+    atomicOr(err, 2);
+    return x;
+}
+
+__device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b, int *err)
+{
+    for (int k = 0; k < kUfMaxSteps; ++k) {
+        a = uf_find(parent, a, err);
+        b = uf_find(parent, b, err);
+        if (a == b) return;
+        if (a < b) {
+            const int32_t t = a;
+            a = b;
+            b = t;
+        }
+        const int32_t old = atomicMin(parent + a, b);
+        if (old == a) return;  // a was a root and now hangs under b
+        a = old;               // a had been re-parented meanwhile: join its new parent to b
+    }
+    atomicOr(err, 2);
+}
+
+__global__ void __launch_bounds__(256) k_canny_union(int H, int W, const uint8_t *__restrict__ cls,
+                                                     int32_t *parent, int *err)
+{
+    pdl_wait();
+    const int64_t total = (int64_t)H * W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        if (!cls[t]) continue;
+        const int r = (int)(t / W), c = (int)(t % W);
+        if (c > 0 && cls[t - 1]) uf_unite(parent, (int32_t)t, (int32_t)(t - 1), err);
+        if (r > 0) {
+            const int64_t u = t - W;
+            if (c > 0 && cls[u - 1]) uf_unite(parent, (int32_t)t, (int32_t)(u - 1), err);
+            if (cls[u]) uf_unite(parent, (int32_t)t, (int32_t)u, err);
+            if (c + 1 < W && cls[u + 1]) uf_unite(parent, (int32_t)t, (int32_t)(u + 1), err);
+        }
+    }
+}
+
+// Flattens each survivor's parent to its root and marks the roots of strong
+// survivors (all unions are complete when this kernel starts).
+__global__ void __launch_bounds__(256) k_canny_mark(int64_t total, const uint8_t *__restrict__ cls, int32_t *parent,
+                                                    uint8_t *mark, int *err)
+{
+    pdl_wait();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint8_t q = cls[t];
+        if (!q) continue;
+        const int32_t root = uf_find(parent, (int32_t)t, err);
+        parent[t] = root;
+        if (q == 2) mark[root] = 1;
+    }
+}
+
+// Canny edge pixel: a survivor whose (flattened) root is marked.
+__device__ __forceinline__ bool canny_edge(const uint8_t *cls, const int32_t *parent, const uint8_t *mark, int64_t i)
+{
+    return cls[i] && mark[parent[i]];
+}
+
+__global__ void __launch_bounds__(256) k_canny_edges(int H, int W, const uint8_t *__restrict__ cls,
+                                                     const int32_t *__restrict__ parent,
+                                                     const uint8_t *__restrict__ mark, uint8_t *__restrict__ edges,
+                                                     int64_t epitch)
 {
     pdl_wait();
     const int64_t total = (int64_t)H * W;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(t / W), c = (int)(t % W);
+        edges[(int64_t)r * epitch + c] = canny_edge(cls, parent, mark, t) ? 1 : 0;
+    }
+}
+
+// ---- steps 2-3: the window's own central-difference gradient at edge pixels
+__global__ void __launch_bounds__(256) k_phog_planes(const uint8_t *__restrict__ gray, int64_t pitch, int H, int W,
+                                                     const uint8_t *__restrict__ cls, const int32_t *__restrict__ parent,
+                                                     const uint8_t *__restrict__ mark, uint8_t *__restrict__ bins,
+                                                     int32_t *__restrict__ wt)
+{
+    pdl_wait();
+    const int64_t total = (int64_t)H * W;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(t / W), c = (int)(t % W);
+        const bool edge = canny_edge(cls, parent, mark, t);
         const uint8_t *row = gray + (int64_t)r * pitch;
         const int gx = (int)__ldg(row + min(c + 1, W - 1)) - (int)__ldg(row + max(c - 1, 0));
         const int gy = (int)__ldg(gray + (int64_t)min(r + 1, H - 1) * pitch + c) -
                        (int)__ldg(gray + (int64_t)max(r - 1, 0) * pitch + c);
         const int64_t m = isqrt_exact(256 * ((int64_t)gx * gx + (int64_t)gy * gy));
-        const bool edge = m >= 16 * (int64_t)tau;
         bins[t] = edge ? (uint8_t)orientation_bin9(gx, gy) : (uint8_t)255;
         wt[t] = edge ? (int32_t)m : 0;
     }
@@ -205,16 +399,54 @@ unsigned grid_for(int64_t total)
 
 }  // namespace
 
-int launch_phog_build(const uint8_t *gray, int64_t pitch, int H, int W, int tau, uint8_t *bins, int32_t *wt,
-                      int64_t P, int64_t *ih, cudaStream_t st, const Prof *prof)
+// Canny's detector into the scratch of one window (classes, parents, marks);
+// 3 launches.
+static void launch_canny(const uint8_t *gray, int64_t pitch, int H, int W, int lo, int hi, const CannyScratch &cs,
+                         int *err, cudaStream_t st)
+{
+    const long long tlo = (long long)(256 * lo) * (256 * lo), thi = (long long)(256 * hi) * (256 * hi);
+    const dim3 grid((W + kCT - 1) / kCT, (H + kCT - 1) / kCT);
+    launch_pdl(k_canny_nms, grid, 256, 0, st, gray, pitch, H, W, tlo, thi, cs.cls, cs.parent, cs.mark);
+    launch_pdl(k_canny_union, grid_for((int64_t)H * W), 256, 0, st, H, W, (const uint8_t *)cs.cls, cs.parent, err);
+    launch_pdl(k_canny_mark, grid_for((int64_t)H * W), 256, 0, st, (int64_t)H * W, (const uint8_t *)cs.cls,
+               cs.parent, cs.mark, err);
+}
+
+size_t canny_scratch_bytes(int H, int W) { return (size_t)H * W * 6 + 256; }
+
+CannyScratch carve_canny(void *base, int H, int W)
+{
+    const size_t px = (size_t)H * W;
+    CannyScratch cs;
+    cs.parent = static_cast<int32_t *>(base);
+    cs.cls = reinterpret_cast<uint8_t *>(cs.parent + px);
+    cs.mark = cs.cls + px;
+    return cs;
+}
+
+int launch_canny_edges(const uint8_t *gray, int64_t pitch, int H, int W, int lo, int hi, const CannyScratch &cs,
+                       uint8_t *edges, int64_t epitch, int *err, cudaStream_t st, const Prof *prof)
 {
     prof_mark(prof, KID_PHOG_BUILD, 0, st);
-    launch_pdl(k_phog_planes, grid_for((int64_t)H * W), 256, 0, st, gray, pitch, H, W, tau, bins, wt);
+    launch_canny(gray, pitch, H, W, lo, hi, cs, err, st);
+    launch_pdl(k_canny_edges, grid_for((int64_t)H * W), 256, 0, st, H, W, (const uint8_t *)cs.cls,
+               (const int32_t *)cs.parent, (const uint8_t *)cs.mark, edges, epitch);
+    prof_mark(prof, KID_PHOG_BUILD, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 4 : -1;
+}
+
+int launch_phog_build(const uint8_t *gray, int64_t pitch, int H, int W, int lo, int hi, const CannyScratch &cs,
+                      uint8_t *bins, int32_t *wt, int64_t P, int64_t *ih, int *err, cudaStream_t st, const Prof *prof)
+{
+    prof_mark(prof, KID_PHOG_BUILD, 0, st);
+    launch_canny(gray, pitch, H, W, lo, hi, cs, err, st);
+    launch_pdl(k_phog_planes, grid_for((int64_t)H * W), 256, 0, st, gray, pitch, H, W, (const uint8_t *)cs.cls,
+               (const int32_t *)cs.parent, (const uint8_t *)cs.mark, bins, wt);
     const int64_t warps = (int64_t)kPhogBins * H;
     launch_pdl(k_phog_rows, (unsigned)((warps + 7) / 8), 256, 0, st, bins, wt, H, W, P, ih);
     launch_pdl(k_phog_cols, grid_for((int64_t)kPhogBins * P), 256, 0, st, H, P, ih);
     prof_mark(prof, KID_PHOG_BUILD, 1, st);
-    return cudaPeekAtLastError() == cudaSuccess ? 3 : -1;
+    return cudaPeekAtLastError() == cudaSuccess ? 6 : -1;
 }
 
 int launch_phog_descriptors(const int64_t *ih, int H, int W, int64_t P, int L, const int32_t *wins, int64_t n,

@@ -37,7 +37,7 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
              "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
-             "ih_phog_match", "ih_profile_select", "ih_query")
+             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -124,7 +124,8 @@ def load_library(path: str = LIB_PATH):
             "ih_match_window": ([p, i32, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_accumulate": ([p, i32, i32, i32, p], i32),
             "ih_profile_select": ([p, p, i32], i32),
-            "ih_phog_build": ([p, p, i32, i32, i64, i32, ctypes.POINTER(i32), p], i32),
+            "ih_phog_build": ([p, p, i32, i32, i64, i32, i32, ctypes.POINTER(i32), p], i32),
+            "ih_canny_edges": ([p, p, i32, i32, i64, i32, i32, p, i64, p], i32),
             "ih_phog_descriptors": ([p, i32, i32, p, i64, p, p], i32),
             "ih_phog_match": ([p, i32, i32, p, i32, i32, p, p, p], i32),
             "ih_local_median": ([p, i32, i32, i32, i32, i32, p, p], i32),
@@ -261,18 +262,39 @@ def phog_descriptor_len(levels):
     return PHOG_BINS * sum(4 ** l for l in range(int(levels) + 1))
 
 
-def ih_phog_build(ctx, gray, tau, stream=None):
-    """Algorithm 2 steps 1-4 on a (H, W) uint8 CUDA tensor (rows may be
-    strided): returns the handle of the 9-bin magnitude-weighted orientation
-    integral histogram."""
+def _rows(gray):
+    """(tensor, row pitch) of an (H, W) uint8 CUDA tensor whose rows may be strided."""
     h, w = gray.shape
-    pitch = gray.stride(0) if gray.stride(1) == 1 else None
-    if pitch is None:
-        gray = gray.contiguous()
-        pitch = w
+    if gray.stride(1) == 1:
+        return gray, gray.stride(0)
+    return gray.contiguous(), w
+
+
+IH_CANNY_MAX_THRESHOLD = 1024
+
+
+def ih_canny_edges(ctx, gray, tau_low, tau_high, out, stream=None):
+    """Algorithm 2 step 1, Canny's detector, on a (H, W) uint8 CUDA tensor:
+    writes 1 on edge pixels and 0 elsewhere into out ((H, W) uint8 CUDA
+    tensor, rows may be strided)."""
+    h, w = gray.shape
+    gray, pitch = _rows(gray)
+    if out.element_size() != 1 or tuple(out.shape) != (h, w) or out.stride(1) != 1:
+        raise ValueError("out must be an (H, W) uint8 tensor with unit column stride")
+    _check(ctx, load_library().ih_canny_edges(ctx, _ptr(gray), int(h), int(w), int(pitch), int(tau_low),
+                                              int(tau_high), _ptr(out), int(out.stride(0)), _stream(stream)))
+    return out
+
+
+def ih_phog_build(ctx, gray, tau_low, tau_high, stream=None):
+    """Algorithm 2 steps 1-4 on a (H, W) uint8 CUDA tensor (rows may be
+    strided), with Canny thresholds tau_low <= tau_high: returns the handle of
+    the 9-bin magnitude-weighted orientation integral histogram."""
+    h, w = gray.shape
+    gray, pitch = _rows(gray)
     out = ctypes.c_int32(-1)
-    _check(ctx, load_library().ih_phog_build(ctx, _ptr(gray), int(h), int(w), int(pitch), int(tau),
-                                             ctypes.byref(out), _stream(stream)))
+    _check(ctx, load_library().ih_phog_build(ctx, _ptr(gray), int(h), int(w), int(pitch), int(tau_low),
+                                             int(tau_high), ctypes.byref(out), _stream(stream)))
     return out.value
 
 

@@ -20,14 +20,27 @@ def test_fmv_algorithmic_bytes():
     assert bench.algorithmic_bytes("tile_sums", B, Bw, 100_000, 4096) == 7 * hw
 
 
+def test_wami_algorithmic_bytes():
+    import bench
+    hw = 8192 * 8192
+    B = Bw = 32
+    tiles = hw + 4 * B * hw + hw + 4 * 8 * Bw * hw    # gray in (counts, moments), 32 int32 + 4 x 32 int64 out
+    assert bench.algorithmic_bytes("tiles/count+moments", B, Bw, 10 ** 6, 10 ** 5, hw, 1) == tiles
+    assert tiles == 77_443_629_056
+    assert bench.algorithmic_bytes("queries", B, Bw, 10 ** 6, 10 ** 5, hw, 1) == (
+        10 ** 6 * (16 + 16 * B + 4 * B) + 10 ** 5 * (16 + 4 * Bw * 36 + 4 * Bw))
+
+
 def test_traffic_only_for_the_profiled_sources(tmp_path, monkeypatch):
     import bench
-    d = {"source_digest": bench.source_digest(), "kernels": {"queries": {"dram_bytes_per_launch": 123.0}}}
+    d = {"source_digest": bench.source_digest(),
+         "workloads": {"fmv": {"kernels": {"queries": {"dram_bytes_per_launch": 123.0}}}}}
     (tmp_path / "profiles").mkdir()
     (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(d))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "source_digest", lambda: d["source_digest"])
     assert bench.dram_traffic("queries") == 123.0
+    assert bench.dram_traffic("queries", "wami") is None
     assert bench.dram_traffic("features") is None
     monkeypatch.setattr(bench, "source_digest", lambda: "another")
     assert bench.dram_traffic("queries") is None

@@ -566,15 +566,60 @@ def test_accumulate_refuses_mismatched_frames(ihlib, ctx):
 
 # ---------------------------------------------------------------- Algorithm 2: spatial pyramid of orientations
 
-@pytest.mark.parametrize("tau", [0, 6, 40])
-def test_phog_descriptors_vs_oracle(ihlib, ctx, tau):
+def _canny_images():
+    """Windows whose edges exercise every part of Canny's detector: blob
+    content, uniform noise (many short weak runs), a bright block (long
+    straight edges and corners), a constant window (no edges), single rows,
+    columns and pixels, and a window that spans several 32 x 32 tiles with a
+    ragged last tile."""
+    g = synth.blob_plane(131, 203, 130)
+    g[40:90, 60:150] = 235
+    return [synth.blob_plane(64, 64, 131), synth.uniform_plane(45, 77, 132), g, np.full((20, 30), 77, np.uint8),
+            synth.uniform_plane(1, 50, 133), synth.uniform_plane(50, 1, 134), np.zeros((1, 1), np.uint8),
+            synth.blob_plane(257, 300, 135)]
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 0), (2, 6), (6, 24), (30, 90)])
+def test_canny_edges_vs_oracle(ihlib, ctx, lo, hi):
+    """Algorithm 2 step 1 on the GPU (tiled smoothing, gradient, suppression,
+    union-find hysteresis) equals the oracle's sequential detector bit for
+    bit, on whole windows and on a window with a row pitch."""
+    for k, g in enumerate(_canny_images()):
+        h, w = g.shape
+        ref, _, _, _ = oracle.canny(g, lo, hi)
+        out = torch.full((h, w), 7, dtype=torch.uint8, device=DEV)
+        ihlib.ih_canny_edges(ctx, torch.from_numpy(g).to(DEV), lo, hi, out)
+        ihlib.ih_sync(ctx)
+        assert np.array_equal(out.cpu().numpy(), ref), (k, lo, hi)
+    g = _canny_images()[2]
+    buf = torch.zeros((g.shape[0], g.shape[1] + 13), dtype=torch.uint8, device=DEV)
+    buf[:, 5:5 + g.shape[1]] = torch.from_numpy(g).to(DEV)
+    eb = torch.full((g.shape[0], g.shape[1] + 9), 7, dtype=torch.uint8, device=DEV)
+    ihlib.ih_canny_edges(ctx, buf[:, 5:5 + g.shape[1]], lo, hi, eb[:, 3:3 + g.shape[1]])
+    ihlib.ih_sync(ctx)
+    e = eb.cpu().numpy()
+    assert np.array_equal(e[:, 3:3 + g.shape[1]], oracle.canny(g, lo, hi)[0])
+    assert (e[:, :3] == 7).all() and (e[:, 3 + g.shape[1]:] == 7).all()
+
+
+def test_canny_edges_refusals(ihlib, ctx):
+    g = torch.zeros((10, 10), dtype=torch.uint8, device=DEV)
+    out = torch.empty((10, 10), dtype=torch.uint8, device=DEV)
+    for lo, hi in ((-1, 4), (5, 4), (0, ihlib.IH_CANNY_MAX_THRESHOLD + 1)):
+        with pytest.raises(ihlib.IHError):
+            ihlib.ih_canny_edges(ctx, g, lo, hi, out)
+
+
+@pytest.mark.parametrize("lo,hi", [(0, 0), (2, 6), (8, 40)])
+def test_phog_descriptors_vs_oracle(ihlib, ctx, lo, hi):
     h, w = 130, 171
     g = synth.blob_plane(h, w, 120)
-    hdl = ihlib.ih_phog_build(ctx, torch.from_numpy(g).to(DEV), tau)
+    hdl = ihlib.ih_phog_build(ctx, torch.from_numpy(g).to(DEV), lo, hi)
     info = ihlib.ih_info(ctx, hdl)
     assert info["total_bins"] == 9 and info["count_bytes"] == 0
     assert info["moment_bytes"] == 9 * h * ((w + 3) // 4 * 4) * 8
-    bins, wt = oracle.phog_planes(g, tau)
+    bins, wt = oracle.phog_planes(g, lo, hi)
+    assert (bins < 9).any()
     wins = np.concatenate([synth.rects_side_range(h, w, 40, 1, 100, 121),
                            np.array([[0, 0, h - 1, w - 1], [5, 6, 5, 6], [3, 4, 66, 131]], np.int32)])
     for L in (0, 2, 3):
@@ -592,8 +637,8 @@ def test_phog_descriptors_vs_oracle(ihlib, ctx, tau):
 def test_phog_match_map_vs_oracle(ihlib, ctx):
     h, w = 96, 128
     g = synth.blob_plane(h, w, 122)
-    hdl = ihlib.ih_phog_build(ctx, torch.from_numpy(g).to(DEV), 5)
-    bins, wt = oracle.phog_planes(g, 5)
+    hdl = ihlib.ih_phog_build(ctx, torch.from_numpy(g).to(DEV), 2, 8)
+    bins, wt = oracle.phog_planes(g, 2, 8)
     L, wh, ww = 2, 32, 40
     target = oracle.phog_descriptor(bins, wt, L, 30, 50, wh, ww)
     search = (20, 40, 20 + 23, 40 + 30)
@@ -681,7 +726,8 @@ def test_record_layout_exact(ihlib, ctx, bins):
 @pytest.mark.parametrize("kernel", [0, 1, 2])
 def test_query_both_equals_separate_calls(ihlib, ctx, layout, kernel):
     """ih_query (one launch) returns exactly what ih_query_rects and
-    ih_query_weighted return, and the rectangles match the oracle."""
+    ih_query_weighted return; the rectangles match the oracle exactly and the
+    weighted windows the FP64 direct sum within 1e-5."""
     ih = ihlib
     h, w = 200, 611
     planes = np.stack([synth.blob_plane(h, w, 70 + k) for k in range(3)])
@@ -700,6 +746,8 @@ def test_query_both_equals_separate_calls(ihlib, ctx, layout, kernel):
     ih.ih_sync(ctx)
     assert torch.equal(r1, r2) and torch.equal(w1, w2)
     assert np.array_equal(r2.cpu().numpy(), oracle.frame_rect_hist(planes, chans, rects))
+    _assert_weighted(w2.cpu().numpy(), oracle.weighted_hist(planes[0], 16, wins, normalize=True, kernel=kernel,
+                                                            layers=3))
     ih.ih_release(ctx, hdl)
 
 

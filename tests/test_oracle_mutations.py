@@ -58,6 +58,25 @@ MUTANTS = [
      [lambda: pins.test_phog_descriptor_cells(2)]),
     ("pyramid_level_weight", "il / (double)(1 << (L - l + 1))", "il / (double)(1 << (L - l))",
      [pins.test_pyramid_match_kernel_forms_agree]),
+    ("canny_binomial_kernel", "or_binom5[5] = {1, 4, 6, 4, 1};", "or_binom5[5] = {1, 3, 6, 3, 1};",
+     [lambda: pins.test_canny_smoothing_is_binomial_convolution(0)]),
+    ("canny_gradient_axes", "int64_t gy = (int64_t)S[(int64_t)clampi(r + 1, 0, h - 1) * w + c] - S[(int64_t)clampi(r - 1, 0, h - 1) * w + c];\n            M[",
+     "int64_t gy = (int64_t)S[(int64_t)r * w + clampi(c + 1, 0, w - 1)] - S[(int64_t)clampi(r - 1, 0, h - 1) * w + c];\n            M[",
+     [lambda: pins.test_canny_gradient_of_the_smoothed_image(0)]),
+    ("canny_nms_diagonals_swapped", "dr = 1; dc = 1;            /* near 45 deg", "dr = -1; dc = 1;           /* near 45 deg",
+     [lambda: pins.test_canny_suppression_and_thresholds_by_angle(0), pins.test_canny_step_edges_are_one_pixel_wide]),
+    ("canny_nms_sector_test", "if (s2 < 2 * ax * ax) {", "if (s2 < 3 * ax * ax) {",
+     [lambda: pins.test_canny_suppression_and_thresholds_by_angle(0)]),
+    ("canny_nms_ties_kept", "if (m > mm && m >= mp)", "if (m >= mm && m >= mp)",
+     [pins.test_canny_step_edges_are_one_pixel_wide]),
+    ("canny_weak_threshold", "(m >= tlo ? 1 : 0)", "(m >= thi ? 1 : 0)",
+     [pins.test_canny_hysteresis_keeps_connected_weak_runs]),
+    ("canny_hysteresis_4_connected", "if ((a == 0 && b == 0) || y < 0", "if ((a == 0) == (b == 0) || y < 0",
+     [lambda: pins.test_canny_hysteresis_is_8_connected_components(0)]),
+    ("canny_hysteresis_off", "if (K[j] != 0 && !edges[j]) {", "if (K[j] == 2 && !edges[j]) {",
+     [pins.test_canny_hysteresis_keeps_connected_weak_runs]),
+    ("phog_edges_ignored", "int e = edge[(int64_t)r * w + c];", "int e = m > 0;",
+     [pins.test_phog_planes_follow_the_stencil]),
     ("wedding_shrink_axes", "int dr = j * hgt / (2 * layers), dc = j * wdt / (2 * layers);",
      "int dr = j * wdt / (2 * layers), dc = j * hgt / (2 * layers);",
      [lambda: pins.test_wedding_cake_is_sum_of_nested_windows(3)]),

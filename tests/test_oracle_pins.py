@@ -481,18 +481,142 @@ def test_isqrt_exhaustive_against_math_isqrt():
         assert oracle.isqrt(n) == math.isqrt(n)
 
 
+# Canny's detector (Algorithm 2 step 1; J. Canny 1986), pinned stage by stage
+# against library routines and independent formulations, and end to end on
+# images whose edges are known by construction.
+
+def _canny_case(k):
+    if k == 0:
+        return synth.blob_plane(41, 57, 90)
+    if k == 1:
+        return synth.uniform_plane(33, 29, 91)
+    g = synth.blob_plane(48, 64, 92)
+    g[10:30, 20:40] = 230  # a bright block: long straight edges and corners
+    return g
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_canny_smoothing_is_binomial_convolution(k):
+    from scipy import ndimage
+    g = _canny_case(k)
+    _, S, _, _ = oracle.canny(g, 5, 20)
+    b = np.array([1, 4, 6, 4, 1], np.int64)
+    ref = ndimage.convolve(g.astype(np.int64), np.outer(b, b), mode="nearest")
+    assert np.array_equal(S, ref)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_canny_gradient_of_the_smoothed_image(k):
+    g = _canny_case(k)
+    _, S, M, _ = oracle.canny(g, 5, 20)
+    p = np.pad(S.astype(np.int64), 1, mode="edge")
+    gx = p[1:-1, 2:] - p[1:-1, :-2]
+    gy = p[2:, 1:-1] - p[:-2, 1:-1]
+    assert np.array_equal(M, gx * gx + gy * gy)
+
+
+def _nms_by_angle(S):
+    """Non-maximum suppression by the gradient angle in degrees (numpy
+    arctan2), an independent formulation of the oracle's exact sector test."""
+    h, w = S.shape
+    p = np.pad(S.astype(np.int64), 1, mode="edge")
+    gx = p[1:-1, 2:] - p[1:-1, :-2]
+    gy = p[2:, 1:-1] - p[:-2, 1:-1]
+    m = gx * gx + gy * gy
+    ang = np.degrees(np.arctan2(gy, gx)) % 180.0
+    mp = np.pad(m, 1)  # neighbours outside the window count as 0
+    keep = np.zeros((h, w), bool)
+    for r in range(h):
+        for c in range(w):
+            a = ang[r, c]
+            if a < 22.5 or a >= 157.5:
+                lo_, hi_ = (r, c - 1), (r, c + 1)
+            elif a < 67.5:
+                lo_, hi_ = (r - 1, c - 1), (r + 1, c + 1)
+            elif a < 112.5:
+                lo_, hi_ = (r - 1, c), (r + 1, c)
+            else:
+                lo_, hi_ = (r + 1, c - 1), (r - 1, c + 1)
+            v = m[r, c]
+            keep[r, c] = v > mp[lo_[0] + 1, lo_[1] + 1] and v >= mp[hi_[0] + 1, hi_[1] + 1]
+    return keep, m
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_canny_suppression_and_thresholds_by_angle(k):
+    g = _canny_case(k)
+    lo, hi = 6, 24
+    _, S, _, cls = oracle.canny(g, lo, hi)
+    keep, m = _nms_by_angle(S)
+    ref = np.where(keep & (m >= (256 * hi) ** 2), 2, np.where(keep & (m >= (256 * lo) ** 2), 1, 0))
+    assert np.array_equal(cls, ref)
+    assert (cls == 1).any() and (cls == 2).any()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_canny_hysteresis_is_8_connected_components(k):
+    """Edge pixels = survivors in an 8-connected component of survivors that
+    holds a strong one (scipy.ndimage.label)."""
+    from scipy import ndimage
+    g = _canny_case(k)
+    edges, _, _, cls = oracle.canny(g, 6, 24)
+    lab, _ = ndimage.label(cls > 0, structure=np.ones((3, 3), int))
+    strong = np.unique(lab[cls == 2])
+    ref = np.isin(lab, strong[strong > 0]) & (cls > 0)
+    assert np.array_equal(edges.astype(bool), ref)
+    assert edges.sum() < (cls > 0).sum()  # some weak runs are dropped
+
+
+def test_canny_step_edges_are_one_pixel_wide():
+    v = np.zeros((12, 14), np.uint8)
+    v[:, 6:] = 255
+    e, _, _, _ = oracle.canny(v, 20, 60)
+    ref = np.zeros_like(e)
+    ref[:, 5] = 1  # the two-pixel plateau of |G| at columns 5 and 6 keeps column 5
+    assert np.array_equal(e, ref)
+    e, _, _, _ = oracle.canny(np.ascontiguousarray(v.T), 20, 60)
+    assert np.array_equal(e, np.ascontiguousarray(ref.T))
+    # a 45-degree step: the line stays on the two anti-diagonals next to it
+    rr, cc = np.mgrid[0:16, 0:16]
+    d = np.where(rr + cc >= 15, 255, 0).astype(np.uint8)
+    e, _, _, _ = oracle.canny(d, 20, 60)
+    assert e.sum() > 0 and set(np.unique((rr + cc)[e == 1])) == {14, 15}
+    for r in range(1, 15):  # every interior row: both pixels, one on each anti-diagonal
+        assert list(np.nonzero(e[r])[0]) == [14 - r, 15 - r]
+
+
+def test_canny_hysteresis_keeps_connected_weak_runs():
+    """A vertical step whose contrast falls from 200 to 40 down the rows:
+    strong above, weak below, one connected line -> all rows are edges; an
+    isolated weak run beside it is dropped; with a high threshold above every
+    magnitude nothing is kept."""
+    g = np.zeros((21, 20), np.uint8)
+    for r in range(21):
+        g[r, 8:] = 200 - 8 * r
+    e, _, _, cls = oracle.canny(g, 10, 60)
+    assert (cls[:, 8] == 2).sum() >= 5 and (cls[:, 8] == 1).sum() >= 5
+    ref = np.zeros_like(e)
+    ref[:, 8] = 1
+    assert np.array_equal(e, ref)
+    assert ((cls == 1) & (ref == 0)).any()  # the isolated weak run exists but is not an edge
+    e, _, _, cls = oracle.canny(g, 10, 130)
+    assert (cls == 1).sum() > 0 and (cls == 2).sum() == 0 and e.sum() == 0
+
+
 def test_phog_planes_follow_the_stencil():
+    """Algorithm 2 steps 2-3 on the Canny edge pixels of step 1."""
     import math
     g = synth.blob_plane(23, 31, 70)
-    tau = 6
-    bins, wt = oracle.phog_planes(g, tau)
+    lo, hi = 3, 9
+    bins, wt = oracle.phog_planes(g, lo, hi)
+    edges, _, _, _ = oracle.canny(g, lo, hi)
     p = np.pad(g.astype(np.int64), 1, mode="edge")
     gx = p[1:-1, 2:] - p[1:-1, :-2]
     gy = p[2:, 1:-1] - p[:-2, 1:-1]
     for r in range(23):
         for c in range(31):
             m = math.isqrt(256 * int(gx[r, c] ** 2 + gy[r, c] ** 2))
-            if m >= 16 * tau:
+            if edges[r, c]:
                 assert wt[r, c] == m and bins[r, c] == oracle.orientation_bin(int(gx[r, c]), int(gy[r, c]))
             else:
                 assert wt[r, c] == 0 and bins[r, c] == 255
@@ -501,7 +625,7 @@ def test_phog_planes_follow_the_stencil():
 
 def test_phog_ih_equals_cumsum():
     g = synth.blob_plane(30, 37, 71)
-    bins, wt = oracle.phog_planes(g, 4)
+    bins, wt = oracle.phog_planes(g, 2, 6)
     onehot = (bins[None] == np.arange(9)[:, None, None]) * wt[None].astype(np.int64)
     assert np.array_equal(oracle.phog_ih(bins, wt), onehot.cumsum(1).cumsum(2))
 
@@ -509,7 +633,7 @@ def test_phog_ih_equals_cumsum():
 @pytest.mark.parametrize("L", [0, 1, 2, 3])
 def test_phog_descriptor_cells(L):
     g = synth.blob_plane(70, 90, 72)
-    bins, wt = oracle.phog_planes(g, 5)
+    bins, wt = oracle.phog_planes(g, 2, 8)
     r0, c0, wh, ww = 6, 9, 48, 64
     d = oracle.phog_descriptor(bins, wt, L, r0, c0, wh, ww)
     assert d.shape == (9 * sum(4 ** l for l in range(L + 1)),)
@@ -533,7 +657,7 @@ def test_pyramid_match_kernel_forms_agree():
     I^0 / 2^L + sum_{l>=1} I^l / 2^(L-l+1); the oracle computes the second
     form, numpy the first; kappa(X, X) is X's total weight."""
     g = synth.blob_plane(80, 80, 73)
-    bins, wt = oracle.phog_planes(g, 5)
+    bins, wt = oracle.phog_planes(g, 2, 8)
     L = 3
     x = oracle.phog_descriptor(bins, wt, L, 4, 4, 64, 64)
     y = oracle.phog_descriptor(bins, wt, L, 10, 7, 64, 64)
