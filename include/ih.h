@@ -54,6 +54,7 @@ typedef enum {
     IH_ENOTBUILT = 6, /* the handle names no live frame */
     IH_ETOOBIG = 7,   /* ih_build_counts_static: the frame needs more carry
                          scratch than IH_STATIC_SCRATCH_BYTES */
+    IH_ECANCELLED = 8 /* a server request was cancelled (ih_server_cancel) */
 } ih_status;
 
 /* Binning function Q of one channel (Eq. 2.15). */
@@ -144,6 +145,20 @@ ih_status ih_create(const ih_config *cfg, ih_ctx **out);
  * built then), IH_ENOMEM / IH_ECUDA on allocation or launch failure. */
 ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_handles,
                    void *stream);
+
+/* The count build of ih_build (Eq. 2.15, Algorithm 5's tensor) with the
+ * tiles' 2-D prefixes computed on the tensor cores: for a 128 x 128 tile and
+ * bin b, H_local = T O_b T^t with O_b the tile's one-hot plane of b and T
+ * the lower-triangular ones, as two chained tcgen05 MMAs (kind::f16, bf16
+ * 0/1 operands, fp32 accumulators in tensor memory: exact, since a tile's
+ * counts stay below 2^24), plus the same tile carries as ih_build.  An
+ * alternative kernel of the count path, kept for measurement beside the
+ * scan-based tiles: the frame must use IH_INPUT_PLANES, IH_LAYOUT_BIN_MAJOR
+ * and no weighted channel (IH_EINVAL otherwise).  The frame it builds is an
+ * ordinary frame (*out_handle) for every query, export and release call.
+ * A bounded device-side wait that gives up makes the next ih_sync() return
+ * IH_ETIMEOUT. */
+ih_status ih_build_mma(ih_ctx *ctx, const ih_frame *frame, int32_t *out_handle, void *stream);
 
 /* Rectangle histograms by the four-corner rule of Eq. 2.16:
  *   h(R,b) = H(r1,c1,b) - H(r0-1,c1,b) - H(r1,c0-1,b) + H(r0-1,c0-1,b)
@@ -358,6 +373,10 @@ ih_status ih_profile_select(ih_ctx *ctx, const char *const *names, int32_t n);
  * are this library's own kernels). */
 int64_t ih_launch_count(ih_ctx *ctx);
 
+/* Bytes of the frames (count tensors and moment planes) the context owns now,
+ * the quantity its HBM budget bounds (0 for a NULL context). */
+uint64_t ih_memory_used(ih_ctx *ctx);
+
 /* One-line description of the last error of this context ("" if none). */
 const char *ih_last_error(ih_ctx *ctx);
 
@@ -460,6 +479,15 @@ ih_status ih_server_submit(ih_server *srv, const ih_request *req);
 /* Copies up to max completions (host) to out, waiting up to wait_ms for the
  * first one; returns how many were copied. */
 int32_t ih_server_poll(ih_server *srv, ih_completion *out, int32_t max, int32_t wait_ms);
+/* Cancels the request submitted with tag `user` (the first such request
+ * that has not completed).  A request still waiting for admission leaves
+ * the queue at once and completes with IH_ECANCELLED; it never holds budget.
+ * A request already on the device cannot be stopped: it completes with
+ * IH_ECANCELLED when its tick finishes, and its frame is released then
+ * instead of staying resident, which returns its bytes to the budget; its
+ * buffers stay in use until that completion.  Returns IH_OK, or IH_EINVAL
+ * when no uncompleted request carries the tag. */
+ih_status ih_server_cancel(ih_server *srv, uint64_t user);
 /* Waits until every submitted request has completed. */
 ih_status ih_server_drain(ih_server *srv);
 /* Seconds since the server started (host monotonic clock). */

@@ -80,7 +80,7 @@ const char *kernel_name(int kid)
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
                                            "local_median", "phog_build",     "phog_query",
-                                           "tile_sums", "queries"};
+                                           "tile_sums", "queries",      "tiles/mma"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -500,6 +500,58 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
         if (s != IH_OK) return s;
     }
     for (int k = 0; k < n; ++k) out_handles[k] = publish_frame(ctx, recs[k]);
+    return IH_OK;
+}
+
+ih_status ih_build_mma(ih_ctx *ctx, const ih_frame *f, int32_t *out_handle, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (!f || !out_handle) return fail(ctx, IH_EINVAL, "ih_build_mma: bad arguments");
+    ih_status s = validate(ctx, *f);
+    if (s != IH_OK) return s;
+    if (f->layout != IH_LAYOUT_BIN_MAJOR || f->input != IH_INPUT_PLANES || f->weighted_channel != -1)
+        return fail(ctx, IH_EINVAL, "ih_build_mma: bin-major planes without moment planes only");
+    DevGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    FrameRec fr;
+    frame_record(*f, fr);
+    if (ctx->budget && ctx->used + fr.count_bytes > ctx->budget)
+        return fail(ctx, IH_EBUDGET, "ih_build_mma: %llu bytes over the budget", (unsigned long long)fr.count_bytes);
+    cudaError_t e = pool_alloc(ctx, &fr.d_ih, fr.count_bytes, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tensor allocation");
+    const uint8_t *planes[kMaxChannels];
+    int64_t cpitch[kMaxChannels];
+    for (int c = 0; c < f->channels; ++c) {
+        planes[c] = f->d_pixels + c * (int64_t)f->height * f->pitch_bytes;
+        cpitch[c] = f->pitch_bytes;
+    }
+    PlaneSet ps;
+    if (!make_planeset(ctx, *f, fr, planes, cpitch, ps)) {
+        cudaFreeAsync(fr.d_ih, st);
+        return fail(ctx, IH_EINVAL, "too many bins for one build");
+    }
+    ps.g = make_grid(fr.H, fr.W, 128, 128);  // the tensor-core tile
+    ps.g.P = fr.P;
+    void *scratch = nullptr;
+    const size_t cb = carry_bytes(ps);
+    if (cb && (e = pool_alloc(ctx, &scratch, cb, st)) != cudaSuccess) {
+        cudaFreeAsync(fr.d_ih, st);
+        return cuda_fail(ctx, e, "scratch allocation");
+    }
+    carve_carries(ps, scratch);
+    int nl = launch_carries(ps, st, prof_of(ctx));
+    const int nm = nl < 0 ? -1 : launch_tiles_mma(ps, ctx->d_err, st, prof_of(ctx));
+    if (scratch) cudaFreeAsync(scratch, st);
+    if (nm < 0) {
+        cudaFreeAsync(fr.d_ih, st);
+        return cuda_fail(ctx, cudaGetLastError(), "build launch");
+    }
+    ctx->launches += nl + nm;
+    make_view(ps, fr.d_ih, fr.view);
+    fr.R = ps.g.R;
+    fr.Wc = ps.g.Wc;
+    *out_handle = publish_frame(ctx, fr);
     return IH_OK;
 }
 
@@ -923,6 +975,13 @@ int64_t ih_launch_count(ih_ctx *ctx)
     if (!ctx) return 0;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     return ctx->launches;
+}
+
+uint64_t ih_memory_used(ih_ctx *ctx)
+{
+    if (!ctx) return 0;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    return ctx->used;
 }
 
 const char *ih_last_error(ih_ctx *ctx)

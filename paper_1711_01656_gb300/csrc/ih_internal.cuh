@@ -70,7 +70,8 @@ enum KernelId {
     KID_PHOG_QUERY = 14,
     KID_SUMS_ALL = 15,  // tile sums of all windows of one frame in one launch
     KID_QUERY_BOTH = 16,  // rectangle and weighted queries of one frame in one launch
-    KID_COUNT = 17
+    KID_TILES_MMA = 17,   // count tiles as tensor-core products (k_mma.cu)
+    KID_COUNT = 18
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -192,6 +193,13 @@ void carve_carries(PlaneSet &ps, void *base);
 int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof);
 // One-time kernel attributes (shared-memory limits); call before a capture.
 void prepare_kernels();
+// The tile sums and the carry scan of a build alone (the first two kernels
+// of launch_build); returns the number of kernels launched, or -1.
+int launch_carries(const PlaneSet &ps, cudaStream_t st, const Prof *prof);
+// The count tiles of a bin-major frame on 128 x 128 tiles (ps.g.Wc == 128,
+// ps.g.R <= 128, no moment planes) as tcgen05 products (k_mma.cu), after
+// launch_carries.  A bounded wait that gives up sets bit 2 of *err.
+int launch_tiles_mma(const PlaneSet &ps, int *err, cudaStream_t st, const Prof *prof);
 
 // Batched build: every kernel runs once over the concatenated work of n
 // frames.  The prefix arrays (n + 1 entries, device) give each frame's first

@@ -10,7 +10,9 @@
 //      is free: a request is admitted if its tensors fit the context's
 //      budget, after evicting resident frames of completed requests (least
 //      recently completed first) if needed; a request larger than the whole
-//      budget completes with IH_EBUDGET;
+//      budget completes with IH_EBUDGET; a cancelled request leaves the
+//      queue (ih_server_cancel), or, once on the device, is released when
+//      its tick retires instead of staying resident;
 //   3. launches each new tick on the next of its CUDA streams: one upload of
 //      the tick's descriptor tables, one batched feature pre-pass, the five
 //      batched build kernels and the batched rectangle and weighted queries,
@@ -43,6 +45,7 @@ struct Req {
     double t_submit = 0;
     FrameRec fr;
     int handle = -1;
+    bool cancelled = false;  // set by ih_server_cancel while the request is on the device
 };
 
 struct Slot {
@@ -131,6 +134,13 @@ void retire(ih_server *s)
         cudaEventElapsedTime(&ms, s->ref, sl.done);
         const double t_done = s->t_ref + ms / 1e3;
         for (Req *q : sl.reqs) {
+            if (q->cancelled) {  // its result is dropped: release the frame now
+                release_handle(s->ctx, q->handle);
+                q->handle = -1;
+                complete(s, q, IH_ECANCELLED, sl.t_admit, t_done);
+                delete q;
+                continue;
+            }
             const int tr = q->r.tracker;
             auto it = s->resident.find(tr);
             if (it != s->resident.end()) {
@@ -460,6 +470,37 @@ int32_t ih_server_poll(ih_server *s, ih_completion *out, int32_t max, int32_t wa
         s->done.pop_front();
     }
     return n;
+}
+
+ih_status ih_server_cancel(ih_server *s, uint64_t user)
+{
+    if (!s) return IH_EINVAL;
+    Req *gone = nullptr;
+    {
+        // the scheduler holds ctx->mu while it moves requests into ticks
+        std::lock_guard<std::recursive_mutex> lc(s->ctx->mu);
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto it = s->pending.begin(); it != s->pending.end(); ++it)
+            if ((*it)->r.user == user) {
+                gone = *it;
+                s->pending.erase(it);
+                break;
+            }
+        if (!gone) {
+            for (Slot &sl : s->slots)
+                if (sl.busy)
+                    for (Req *q : sl.reqs)
+                        if (q->r.user == user && !q->cancelled) {
+                            q->cancelled = true;
+                            return IH_OK;
+                        }
+            return IH_EINVAL;
+        }
+    }
+    const double t = s->clock();
+    complete(s, gone, IH_ECANCELLED, t, t);
+    delete gone;
+    return IH_OK;
 }
 
 ih_status ih_server_drain(ih_server *s)

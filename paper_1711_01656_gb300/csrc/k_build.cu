@@ -1525,7 +1525,7 @@ void batch_counts(const PlaneSet &ps, int64_t *c)
     c[4] = ps.mom ? tiles * ps.chan[ps.wch].bins : 0;
 }
 
-int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+int launch_carries(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 {
     prepare_kernels();
     const TileGrid &g = ps.g;
@@ -1546,6 +1546,14 @@ int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
         prof_mark(prof, KID_SCAN, 1, st);
         ++n;
     }
+    return cudaPeekAtLastError() == cudaSuccess ? n : -1;
+}
+
+int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+{
+    const TileGrid &g = ps.g;
+    int n = launch_carries(ps, st, prof);
+    if (n < 0) return -1;
     const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;
     const unsigned blocks = (unsigned)((units + 3) / 4);
     if (ps.mom) {

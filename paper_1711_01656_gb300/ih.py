@@ -15,7 +15,7 @@ import threading
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libih.so")
 
-IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT, IH_ETOOBIG = range(8)
+IH_OK, IH_EINVAL, IH_ENOMEM, IH_EBUDGET, IH_ECUDA, IH_ETIMEOUT, IH_ENOTBUILT, IH_ETOOBIG, IH_ECANCELLED = range(9)
 IH_BIN_UNIFORM8, IH_BIN_INDEX = 0, 1
 IH_INPUT_PLANES, IH_INPUT_RGB_FEATURES = 0, 1
 IH_LAYOUT_BIN_MAJOR, IH_LAYOUT_SLAB, IH_LAYOUT_RECORD = 0, 1, 2
@@ -28,7 +28,7 @@ def IH_LAYERS(n):
     return (int(n) & 0xFF) << 8
 
 STATUS_NAMES = {0: "IH_OK", 1: "IH_EINVAL", 2: "IH_ENOMEM", 3: "IH_EBUDGET", 4: "IH_ECUDA",
-                5: "IH_ETIMEOUT", 6: "IH_ENOTBUILT", 7: "IH_ETOOBIG"}
+                5: "IH_ETIMEOUT", 6: "IH_ENOTBUILT", 7: "IH_ETOOBIG", 8: "IH_ECANCELLED"}
 
 # The exported C symbols (include/ih.h), checked by the test suite.
 C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih_destroy",
@@ -37,7 +37,7 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
              "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
-             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges")
+             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges", "ih_server_cancel", "ih_memory_used", "ih_build_mma")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
 IH_CFG_PROFILE = 1
 
@@ -138,6 +138,8 @@ def load_library(path: str = LIB_PATH):
             "ih_features": ([p, p, i32, i32, i64, p, p], i32),
             "ih_profile_read": ([p, ctypes.POINTER(ih_kernel_stat), i32, ctypes.POINTER(i32), i32], i32),
             "ih_launch_count": ([p], i64),
+            "ih_memory_used": ([p], ctypes.c_uint64),
+            "ih_build_mma": ([p, p, ctypes.POINTER(i32), p], i32),
             "ih_last_error": ([p], ctypes.c_char_p),
             "ih_build_counts_static": ([p, i32, i32, i64, i32, i32, p, i64, p], i32),
             "ih_batch_create": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(ih_batch_queries), u32,
@@ -149,6 +151,7 @@ def load_library(path: str = LIB_PATH):
             "ih_server_submit": ([p, ctypes.POINTER(ih_request)], i32),
             "ih_server_poll": ([p, ctypes.POINTER(ih_completion), i32, i32], i32),
             "ih_server_drain": ([p], i32),
+            "ih_server_cancel": ([p, ctypes.c_uint64], i32),
             "ih_server_clock": ([p], ctypes.c_double),
             "ih_server_destroy": ([p], i32),
         }
@@ -235,6 +238,15 @@ def ih_build(ctx, frames, stream=None):
     handles = (ctypes.c_int32 * len(cs))()
     _check(ctx, load_library().ih_build(ctx, arr, len(cs), handles, _stream(stream)))
     return list(handles)
+
+
+def ih_build_mma(ctx, frame, stream=None):
+    """The count build with tensor-core tiles (bin-major planes, no moment
+    planes): returns the frame's handle."""
+    cf, _keep = frame._c()
+    out = ctypes.c_int32(-1)
+    _check(ctx, load_library().ih_build_mma(ctx, ctypes.byref(cf), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def ih_query_rects(ctx, handle, rects, out, stream=None):
@@ -464,6 +476,12 @@ def ih_server_poll(srv, max=1024, wait_ms=0):
     return [{k: getattr(arr[i], k) for k, _ in ih_completion._fields_} for i in range(n)]
 
 
+def ih_server_cancel(srv, user):
+    """Cancels the uncompleted request tagged `user`; its completion carries
+    IH_ECANCELLED."""
+    _check(None, load_library().ih_server_cancel(srv, ctypes.c_uint64(int(user))))
+
+
 def ih_server_drain(srv):
     _check(None, load_library().ih_server_drain(srv))
 
@@ -474,6 +492,11 @@ def ih_server_clock(srv) -> float:
 
 def ih_server_destroy(srv):
     _check(None, load_library().ih_server_destroy(srv))
+
+
+def ih_memory_used(ctx) -> int:
+    """Bytes of frames the context owns (what its HBM budget bounds)."""
+    return int(load_library().ih_memory_used(ctx))
 
 
 def ih_launch_count(ctx) -> int:

@@ -819,3 +819,34 @@ np.save(d + "/out_" + sys.argv[3] + ".npy", np.concatenate([full.cpu().numpy().r
     feats = oracle.features(rgb)
     full = a[:91 * h * w].view(np.int32).reshape(91, h, w)
     assert np.array_equal(full, oracle.frame_integral_histogram(feats, synth.FMV_CHANNELS))
+
+
+# ---------------------------------------------------------------- tensor-core count tiles
+
+@pytest.mark.parametrize("h,w,bins", [(1, 1, 4), (37, 53, 16), (128, 128, 8), (129, 257, 32), (300, 700, 16),
+                                      (513, 385, 5)])
+def test_build_mma_exact(ihlib, ctx, h, w, bins):
+    """ih_build_mma (tiles as two chained tcgen05 products per bin) gives
+    Algorithm 5's tensor bit for bit: single tiles, ragged tiles, several
+    bands and strips of carries; its frame answers rectangle queries."""
+    img = synth.blob_plane(h, w, 300 + h)
+    hdl = ihlib.ih_build_mma(ctx, ihlib.Frame(torch.from_numpy(img).to(DEV)[None], [(bins, 0)]))
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.integral_histogram(img, bins))
+    rects = synth.rects_uniform_corners(h, w, 300, 301)
+    assert np.array_equal(_rects_gpu(ihlib, ctx, hdl, rects, bins).cpu().numpy(), oracle.rect_hist(img, bins, rects))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_build_mma_multichannel_and_refusals(ihlib, ctx):
+    h, w = 200, 333
+    planes = np.stack([synth.uniform_plane(h, w, 310), synth.blob_plane(h, w, 311)])
+    planes[1] %= 9
+    chans = [(24, 0), (9, 1)]
+    hdl = ihlib.ih_build_mma(ctx, ihlib.Frame(torch.from_numpy(planes).to(DEV), chans))
+    ref = oracle.frame_integral_histogram(planes, chans)
+    assert np.array_equal(_export(ihlib, ctx, hdl), ref)
+    ihlib.ih_release(ctx, hdl)
+    pix = torch.from_numpy(planes).to(DEV)
+    for bad in (ihlib.Frame(pix, chans, layout=ihlib.IH_LAYOUT_SLAB), ihlib.Frame(pix, chans, weighted_channel=0)):
+        with pytest.raises(ihlib.IHError):
+            ihlib.ih_build_mma(ctx, bad)

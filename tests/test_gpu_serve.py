@@ -146,3 +146,53 @@ def test_invalid_request_rejected_at_submit(ihlib, ctx):
                                 weighted_out=torch.empty((1, 4), device=DEV))
     finally:
         ih.ih_server_destroy(srv)
+
+
+def test_cancel_queued_and_inflight_requests(ihlib):
+    """ih_server_cancel: a queued request leaves the queue and completes with
+    IH_ECANCELLED; a request already on the device completes with
+    IH_ECANCELLED when its tick finishes and is not kept resident, so its
+    bytes return to the budget (a later request of the same size is admitted
+    and completes); the other requests complete with their results; an
+    unknown tag is refused."""
+    ih = ihlib
+    big = torch.from_numpy(synth.blob_plane(4096, 4096, 41)).to(DEV)[None]
+    fbig = ih.Frame(big, [(32, 0)], weighted_channel=0)
+    big_bytes = 4096 * 4096 * (32 * 4 + 4 * 32 * 8)
+    c = ih.ih_create(0, hbm_budget_bytes=int(big_bytes * 1.3))
+    small = [synth.blob_plane(96, 128, 50 + k) for k in range(3)]
+    outs = [torch.full((40, 8), -9, dtype=torch.int32, device=DEV) for _ in small]
+    rects = torch.from_numpy(synth.rects_uniform_corners(96, 128, 40, 51)).to(DEV)
+    srv = ih.ih_server_create(c, streams=1, max_inflight=1, max_batch=1)
+    try:
+        ih.ih_server_submit(c, srv, 0, fbig, user=100)
+        for k, img in enumerate(small):
+            ih.ih_server_submit(c, srv, 1 + k, ih.Frame(torch.from_numpy(img).to(DEV)[None], [(8, 0)]),
+                                rects=rects, rect_out=outs[k], user=200 + k)
+        ih.ih_server_cancel(srv, 201)  # queued behind the 4096 x 4096 frame
+        ih.ih_server_cancel(srv, 100)  # on the device, or about to be
+        with pytest.raises(ih.IHError):
+            ih.ih_server_cancel(srv, 999)
+        ih.ih_server_drain(srv)
+        done = {d["user"]: d for d in ih.ih_server_poll(srv, max=16)}
+        assert sorted(done) == [100, 200, 201, 202]
+        assert done[100]["status"] == ih.IH_ECANCELLED and done[100]["handle"] == -1
+        assert done[201]["status"] == ih.IH_ECANCELLED and done[201]["handle"] == -1
+        assert (outs[1] == -9).all()  # the cancelled request's queries never ran
+        for k in (0, 2):
+            assert done[200 + k]["status"] == 0
+            assert np.array_equal(outs[k].cpu().numpy(), oracle.rect_hist(small[k], 8, rects.cpu().numpy()))
+        with pytest.raises(ih.IHError):  # completed requests cannot be cancelled
+            ih.ih_server_cancel(srv, 200)
+        # only the two small frames stay resident: the cancelled frame is released
+        assert ih.ih_memory_used(c) == 2 * 8 * 96 * 128 * 4
+        # the cancelled frame's bytes are back in the budget: another frame of
+        # the same size fits (nothing resident is large enough to evict for it)
+        ih.ih_server_submit(c, srv, 5, fbig, user=300)
+        ih.ih_server_drain(srv)
+        last = ih.ih_server_poll(srv, max=4)
+        assert len(last) == 1 and last[0]["user"] == 300 and last[0]["status"] == 0
+    finally:
+        ih.ih_server_destroy(srv)
+        ih.ih_destroy(c)
+        torch.cuda.empty_cache()
