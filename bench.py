@@ -559,12 +559,14 @@ def run_engine(args):
     del flush
     torch.cuda.empty_cache()
 
-    batched = served = wami = plain = match = median = phog = None
+    batched = served = wami = plain = match = median = phog = mma = None
     sections = world == 1  # the side workloads run once, on a single GPU
     if sections and not args.no_wami:
         wami = wami_section(ih, dev, layout)
     if sections and not args.no_plain:
         plain = plain_section(ih, dev)
+    if sections and not args.no_mma:
+        mma = mma_section(ih, dev)
     if sections and not args.no_match:
         match = match_section(ih, dev, layout)
     if sections and not args.no_median:
@@ -597,7 +599,7 @@ def run_engine(args):
             "gpu_launches": m["gpu_launches"], "clocks": m["clocks"], "kernels": m["kernels"],
             "kernels_timed_in": "the warm-up steps (the timed steps carry events around the dominant kernel only)",
             "fmv": fmv, "wami_phases": wami, "plain": plain, "batched": batched, "served": served,
-            "match": match, "median": median, "phog": phog,
+            "match": match, "median": median, "phog": phog, "mma_tiles": mma,
         }
         print(json.dumps(line))
     if world > 1:
@@ -690,6 +692,61 @@ def wami_section(ih, dev, layout, reps=3):
         out["tiles_roofline"] = {"bound": "hbm", "kernel": "tiles/count+moments", "achieved": round(gbs, 1),
                                  "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4)}
     return out
+
+
+def mma_section(ih, dev, reps=3):
+    """The count tiles as tensor-core products (ih_build_mma: two chained
+    tcgen05 bf16 products per 128 x 128 tile and bin) against the scan-based
+    tiles kernel on the same frame: 8192 x 8192 gray, 32 bins, bin-major
+    counts, once on the scan path's own tile grid and once on the MMA's
+    128 x 128 grid.  Kernel times are CUDA-event averages over `reps` builds
+    after one warm-up; the tensors must be equal."""
+    import torch
+    from paper_1711_01656_gb300 import synth
+    hh = ww = 8192
+    B = 32
+    free, _ = torch.cuda.mem_get_info(dev)
+    if 3 * hh * ww * B * 4 > free * 0.8:
+        return {"skipped": "needs %.1f GB of HBM" % (3 * hh * ww * B * 4 / 1e9)}
+    img = torch.from_numpy(synth.blob_plane(hh, ww, synth.config_seed(3))).to(dev)[None]
+    frame = ih.Frame(img, [(B, 0)], layout=ih.IH_LAYOUT_BIN_MAJOR)
+    out = {}
+    tensors = []
+    for name in ("scan", "scan_128x128", "mma"):
+        ctx = ih.ih_create(dev.index or 0, flags=ih.IH_CFG_PROFILE)
+        if name == "scan_128x128":
+            ih.ih_tune_set(ctx, frame, 128, 128)
+        build = (lambda: ih.ih_build_mma(ctx, frame)) if name == "mma" else (lambda: ih.ih_build(ctx, frame)[0])
+        for rep in range(reps + 1):
+            h = build()
+            if rep == reps:
+                t = torch.empty((B, hh, ww), dtype=torch.int32, device=dev)
+                ih.ih_export(ctx, h, t)
+                tensors.append(t)
+            ih.ih_release(ctx, h)
+            ih.ih_sync(ctx)
+            if rep == 0:
+                ih.ih_profile_read(ctx, reset=True)
+        prof = ih.ih_profile_read(ctx, reset=True)
+        ih.ih_destroy(ctx)
+        out[name] = {k: round(v[1] / v[0], 4) for k, v in prof.items() if k != "export"}
+    equal = all(torch.equal(tensors[0], t) for t in tensors[1:])
+    del tensors
+    torch.cuda.empty_cache()
+    peak, _ = measured_peak()
+    abytes = hh * ww + 4.0 * B * hh * ww
+    res = {"workload": "8192x8192 gray, 32 bins, bin-major int32 counts (no moment planes)",
+           "kernel_ms": out, "tensors_equal": bool(equal)}
+    t_scan, t_scan128, t_mma = (out["scan"].get("tiles/count"), out["scan_128x128"].get("tiles/count"),
+                                out["mma"].get("tiles/mma"))
+    if t_scan and t_mma:
+        flops = 2 * 2 * 128.0 ** 3 * B * (hh // 128) * (ww // 128)
+        res.update({"scan_tiles_GBs": round(abytes / (t_scan / 1e3) / 1e9, 1),
+                    "scan_128x128_tiles_GBs": round(abytes / (t_scan128 / 1e3) / 1e9, 1) if t_scan128 else None,
+                    "mma_tiles_GBs": round(abytes / (t_mma / 1e3) / 1e9, 1),
+                    "mma_tiles_tensor_TFLOPs": round(flops / (t_mma / 1e3) / 1e12, 1),
+                    "mma_vs_scan_time": round(t_mma / t_scan, 3), "hbm_peak_GBs": peak})
+    return res
 
 
 def match_section(ih, dev, layout, runs=20):
@@ -853,16 +910,19 @@ def plain_section(ih, dev, runs=400):
         ih.ih_release(ctx, h)
 
     us_plain = timed(per_frame, runs)
-    batch, handles = ih.ih_batch_create(ctx, [frame], rects=rects, rect_counts=[rects.shape[0]],
-                                        rect_out=r_out.view(-1), batch_flags=ih.IH_BATCH_GRAPH)
-    us_graph = timed(lambda: ih.ih_batch_run(ctx, batch), runs)
-    ih.ih_batch_destroy(batch)
-    for h in handles:
-        ih.ih_release(ctx, h)
+    us = {}
+    for name, flags in (("graph", ih.IH_BATCH_GRAPH), ("persistent_graph", ih.IH_BATCH_GRAPH | ih.IH_BATCH_PERSISTENT)):
+        batch, handles = ih.ih_batch_create(ctx, [frame], rects=rects, rect_counts=[rects.shape[0]],
+                                            rect_out=r_out.view(-1), batch_flags=flags)
+        us[name] = timed(lambda: ih.ih_batch_run(ctx, batch), runs)
+        ih.ih_batch_destroy(batch)
+        for h in handles:
+            ih.ih_release(ctx, h)
+    us_graph = min(us.values())
     ih.ih_destroy(ctx)
     cells = B * hh * ww
     return {"workload": "plain 640x480 uniform gray, 16 bins, 10,000 rects", "per_frame_us": round(us_plain, 2),
-            "graph_us": round(us_graph, 2), "cells_per_s_per_frame": cells / (us_plain / 1e6),
+            "graph_us": round(us_graph, 2), "graph_modes_us": {k: round(v, 2) for k, v in us.items()}, "cells_per_s_per_frame": cells / (us_plain / 1e6),
             "cells_per_s_graph": cells / (us_graph / 1e6)}
 
 
@@ -904,16 +964,20 @@ def batched_section(ih, dev, layout, n_frames=64, runs=5):
         return float(np.median(ts))
 
     ctx = ih.ih_create(dev.index or 0)
-    batch, handles = ih.ih_batch_create(ctx, frames, windows=wins, window_counts=[nw] * n_frames,
-                                        weighted_out=w_out, batch_flags=ih.IH_BATCH_GRAPH | ih.IH_BATCH_AUTOTUNE)
-    timed(lambda: ih.ih_batch_run(ctx, batch), 2)
-    l0 = ih.ih_launch_count(ctx)
-    ms_b = timed(lambda: ih.ih_batch_run(ctx, batch), runs)
-    launches_b = (ih.ih_launch_count(ctx) - l0) // runs
-    ih.ih_batch_destroy(batch)
-    for h in handles:
-        ih.ih_release(ctx, h)
-    torch.cuda.synchronize()
+    res_b = {}
+    for name, flags in (("graph", ih.IH_BATCH_GRAPH | ih.IH_BATCH_AUTOTUNE),
+                        ("persistent", ih.IH_BATCH_GRAPH | ih.IH_BATCH_AUTOTUNE | ih.IH_BATCH_PERSISTENT)):
+        batch, handles = ih.ih_batch_create(ctx, frames, windows=wins, window_counts=[nw] * n_frames,
+                                            weighted_out=w_out, batch_flags=flags)
+        timed(lambda: ih.ih_batch_run(ctx, batch), 2)
+        l0 = ih.ih_launch_count(ctx)
+        res_b[name] = (timed(lambda: ih.ih_batch_run(ctx, batch), runs), (ih.ih_launch_count(ctx) - l0) // runs)
+        ih.ih_batch_destroy(batch)
+        for h in handles:
+            ih.ih_release(ctx, h)
+        torch.cuda.synchronize()
+    ih.ih_sync(ctx)
+    ms_b, launches_b = min(res_b.values())
 
     def per_frame():
         for k, f in enumerate(frames):
@@ -936,7 +1000,11 @@ def batched_section(ih, dev, layout, n_frames=64, runs=5):
             "batched_graph_ms": round(ms_b, 3), "per_frame_ms": round(ms_p, 3),
             "batched_cells_per_s": cells / (ms_b / 1e3), "per_frame_cells_per_s": cells / (ms_p / 1e3),
             "batched_output_GBs": round(gbytes / (ms_b / 1e3), 1), "speedup_vs_per_frame": round(ms_p / ms_b, 3),
-            "launches_per_batch": int(launches_b), "launches_per_frame_loop": int(launches_p)}
+            "launches_per_batch": int(launches_b), "launches_per_frame_loop": int(launches_p),
+            "modes": {k: {"ms": round(v[0], 3), "launches_per_batch": int(v[1]),
+                          "output_GBs": round(gbytes / (v[0] / 1e3), 1), "speedup_vs_per_frame": round(ms_p / v[0], 3)}
+                      for k, v in res_b.items()},
+            "fastest_mode": min(res_b, key=lambda k: res_b[k][0])}
 
 
 def served_section(ih, dev, layout, seconds=2.0, trackers=16, fps=30.0, budget_gb=60):
@@ -1029,6 +1097,7 @@ def main(argv=None):
     ap.add_argument("--no-wami", action="store_true", help="skip the per-phase timings of the wide-area frame")
     ap.add_argument("--no-plain", action="store_true", help="skip the 640x480 plain frame")
     ap.add_argument("--no-match", action="store_true", help="skip the sliding-window matching maps")
+    ap.add_argument("--no-mma", action="store_true", help="skip the tensor-core count tiles comparison")
     ap.add_argument("--no-median", action="store_true", help="skip the spatio-temporal median video")
     ap.add_argument("--no-phog", action="store_true", help="skip the pyramid-of-orientations matching")
     ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")

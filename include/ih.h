@@ -402,8 +402,16 @@ typedef struct {
 } ih_batch_queries;
 
 enum {
-    IH_BATCH_GRAPH = 1,   /* capture the run's launches in a CUDA graph */
-    IH_BATCH_AUTOTUNE = 2 /* ih_autotune every distinct frame shape first */
+    IH_BATCH_GRAPH = 1,      /* capture the run's launches in a CUDA graph */
+    IH_BATCH_AUTOTUNE = 2,   /* ih_autotune every distinct frame shape first */
+    IH_BATCH_PERSISTENT = 4  /* build every frame in ONE persistent launch:
+                                CTAs take the tile sums, carry scans and tiles
+                                of all frames by ticket, each frame's phases
+                                ordered by per-frame counters with bounded
+                                waits (a wait that gives up makes ih_sync
+                                return IH_ETIMEOUT); a run is then the feature
+                                pre-pass of the RGB frames, the build and the
+                                queries: 3 launches (2 without RGB frames) */
 };
 
 /* Plans a batch of n frames: allocates every frame's tensors (the frames are
@@ -428,6 +436,11 @@ ih_status ih_batch_destroy(ih_batch *batch);
  * frame of the same shape (size, channels, bins, input kind, weighted
  * channel, layout) with the fastest.  Synchronous. */
 ih_status ih_autotune(ih_ctx *ctx, const ih_frame *frame, void *stream);
+
+/* Makes the context build every later frame of `frame`'s shape (as for
+ * ih_autotune) on tiles of band_rows (1..128) x strip_cols (a multiple of
+ * 128) pixels, e.g. to compare kernels on one tile grid.  Host only. */
+ih_status ih_tune_set(ih_ctx *ctx, const ih_frame *frame, int32_t band_rows, int32_t strip_cols);
 
 /* ---- serving ---------------------------------------------------------- */
 

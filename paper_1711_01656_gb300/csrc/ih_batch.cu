@@ -11,6 +11,7 @@
 // five build kernels over all frames, and the rectangle and weighted queries
 // of all frames -- or replays the CUDA graph captured from that sequence.
 #include <algorithm>
+#include <array>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -35,6 +36,11 @@ struct ih_batch {
     QueryJob *d_q = nullptr;
     int64_t *d_pre_r = nullptr, *d_pre_w = nullptr;
     int64_t q_rects = 0, q_wins = 0;
+    // IH_BATCH_PERSISTENT: the build as one launch of k_build_persistent
+    bool persistent = false;
+    PersistDev pdev{};
+    int32_t *d_counters = nullptr;  // [3 n] done counters, then the ticket
+    size_t counter_bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int64_t launches_per_run = 0;
@@ -87,7 +93,12 @@ int enqueue_run(ih_batch *b, cudaStream_t st, const Prof *prof)
         if (k < 0) return -1;
         n += k;
     }
-    k = launch_build_batch(b->bd, b->totals, st, prof);
+    if (b->persistent) {
+        if (cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, st) != cudaSuccess) return -1;
+        k = launch_build_persistent(b->pdev, b->bd.max_R, st, prof);
+    } else {
+        k = launch_build_batch(b->bd, b->totals, st, prof);
+    }
     if (k < 0) return -1;
     n += k;
     if (b->q_rects || b->q_wins) {
@@ -216,13 +227,27 @@ ih_status ih_autotune(ih_ctx *ctx, const ih_frame *frame, void *stream)
     return tune_frame(ctx, *frame, static_cast<cudaStream_t>(stream));
 }
 
+ih_status ih_tune_set(ih_ctx *ctx, const ih_frame *frame, int32_t band_rows, int32_t strip_cols)
+{
+    if (!ctx || !frame) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    ih_status s = validate(ctx, *frame);
+    if (s != IH_OK) return s;
+    if (band_rows < 1 || band_rows > kMaxBandRows || strip_cols < kChunk || strip_cols % kChunk)
+        return fail(ctx, IH_EINVAL, "tile grid %d x %d (band rows 1..%d, strip columns a multiple of %d)", band_rows,
+                    strip_cols, kMaxBandRows, kChunk);
+    ctx->tuned[shape_key(*frame)] = std::make_pair((int)band_rows, (int)strip_cols);
+    return IH_OK;
+}
+
 ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const ih_batch_queries *q, uint32_t flags,
                           ih_batch **out, int32_t *out_handles)
 {
     if (!ctx) return IH_EINVAL;
     std::lock_guard<std::recursive_mutex> lk(ctx->mu);
     if (!frames || n < 1 || !out || !out_handles) return fail(ctx, IH_EINVAL, "ih_batch_create: bad arguments");
-    if (flags & ~(uint32_t)(IH_BATCH_GRAPH | IH_BATCH_AUTOTUNE)) return fail(ctx, IH_EINVAL, "batch flags %u", flags);
+    if (flags & ~(uint32_t)(IH_BATCH_GRAPH | IH_BATCH_AUTOTUNE | IH_BATCH_PERSISTENT))
+        return fail(ctx, IH_EINVAL, "batch flags %u", flags);
     if (q && ((q->d_rects && (!q->rects || !q->d_rect_out)) || (q->d_windows && (!q->windows || !q->d_weighted_out)) ||
               q->kernel > IH_K_WEDDING_CAKE || (q->flags & ~((uint32_t)IH_NORMALIZE | IH_LAYERS(0xff))) ||
               weighted_layers(q->flags) > 64))
@@ -387,7 +412,52 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
     b->d_feat_pre = d_pre + 7 * (n + 1);
     b->nfeat = (int)feats.size();
     b->feat_total = feat_pre.back();
-    if (n == 1) {
+    if (flags & IH_BATCH_PERSISTENT) {
+        // segments in phase order: every frame's tile sums (weighted windows
+        // first), then every frame's carry scan, then every frame's tiles; a
+        // frame's later phase waits only for its own earlier ones
+        std::vector<PersistSeg> segs;
+        std::vector<int64_t> seg_pre(1, 0);
+        std::vector<int32_t> need(3 * n, 0);
+        std::vector<std::array<int64_t, kPersistKinds>> cnt(n);
+        for (int k = 0; k < n; ++k) {
+            persistent_counts(sets[k], cnt[k].data());
+            need[3 * k] = (int32_t)(cnt[k][0] + cnt[k][1]);
+            need[3 * k + 1] = (int32_t)cnt[k][2];
+            need[3 * k + 2] = (int32_t)(cnt[k][3] + cnt[k][4]);
+        }
+        const int order[3][2] = {{0, 1}, {2, -1}, {3, 4}};
+        for (const auto &ph : order)
+            for (int k = 0; k < n; ++k)
+                for (int kind : ph)
+                    if (kind >= 0 && cnt[k][kind] > 0) {
+                        segs.push_back(PersistSeg{k, kind, 0, cnt[k][kind]});
+                        seg_pre.push_back(seg_pre.back() + cnt[k][kind]);
+                    }
+        PersistSeg *d_segs = nullptr;
+        int64_t *d_seg_pre = nullptr;
+        int32_t *d_need = nullptr;
+        b->counter_bytes = sizeof(int32_t) * (3 * (size_t)n + 1);
+        if ((e = batch_alloc(b, &d_segs, sizeof(PersistSeg) * segs.size(), st)) != cudaSuccess ||
+            (e = batch_alloc(b, &d_seg_pre, sizeof(int64_t) * seg_pre.size(), st)) != cudaSuccess ||
+            (e = batch_alloc(b, &d_need, sizeof(int32_t) * need.size(), st)) != cudaSuccess ||
+            (e = batch_alloc(b, &b->d_counters, b->counter_bytes, st)) != cudaSuccess)
+            return bail(cuda_fail(ctx, e, "persistent table allocation"));
+        cudaMemcpyAsync(d_segs, segs.data(), sizeof(PersistSeg) * segs.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_seg_pre, seg_pre.data(), sizeof(int64_t) * seg_pre.size(), cudaMemcpyHostToDevice, st);
+        cudaMemcpyAsync(d_need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, st);
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(ctx, e, "table upload"));
+        b->persistent = true;
+        b->pdev.sets = d_sets;
+        b->pdev.segs = d_segs;
+        b->pdev.seg_pre = d_seg_pre;
+        b->pdev.nsegs = (int32_t)segs.size();
+        b->pdev.total = seg_pre.back();
+        b->pdev.done = b->d_counters;
+        b->pdev.need = d_need;
+        b->pdev.ticket = reinterpret_cast<unsigned int *>(b->d_counters + 3 * (size_t)n);
+        b->pdev.err = ctx->d_err;
+    } else if (n == 1) {
         b->single = true;
         b->single_feat = !feats.empty();
         if (b->single_feat) b->feat0 = feats[0];

@@ -80,7 +80,7 @@ const char *kernel_name(int kid)
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
                                            "local_median", "phog_build",     "phog_query",
-                                           "tile_sums", "queries",      "tiles/mma"};
+                                           "tile_sums", "queries",      "tiles/mma", "persistent_build"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 

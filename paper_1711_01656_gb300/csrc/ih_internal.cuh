@@ -71,7 +71,8 @@ enum KernelId {
     KID_SUMS_ALL = 15,  // tile sums of all windows of one frame in one launch
     KID_QUERY_BOTH = 16,  // rectangle and weighted queries of one frame in one launch
     KID_TILES_MMA = 17,   // count tiles as tensor-core products (k_mma.cu)
-    KID_COUNT = 18
+    KID_PERSISTENT = 18,  // tile sums, carry scan and tiles of a batch in one persistent launch
+    KID_COUNT = 19
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -216,6 +217,32 @@ struct BatchDev {
 };
 // Work counts of one frame for the five batched kernels (host).
 void batch_counts(const PlaneSet &ps, int64_t *counts5);
+
+// Persistent batched build (k_build_persistent): a segment is `count` items
+// of one kind of one frame starting at item `first` of that kind; the items
+// of a launch are the segments in table order (tickets 0 .. total-1).
+// Kinds: 0 weighted-channel tile sums (one window, one tile), 1 count tile
+// sums (two (window, tile) units), 2 carry-scan chunks (256 scan items),
+// 3 count tiles, 4 moment tiles (8 warp units each).
+constexpr int kPersistKinds = 5;
+struct PersistSeg {
+    int32_t frame, kind;
+    int64_t first, count;
+};
+struct PersistDev {
+    const PlaneSet *sets;
+    const PersistSeg *segs;
+    const int64_t *seg_pre;  // [nsegs + 1] first ticket of each segment
+    int32_t nsegs;
+    int64_t total;           // items of the launch
+    int32_t *done;           // [n][3] finished items per frame and phase (sums, scan, tiles); zero before the launch
+    const int32_t *need;     // [n][3] items per frame and phase
+    unsigned int *ticket;    // zero before the launch
+    int *err;
+};
+// Items of each kind of one frame (host).
+void persistent_counts(const PlaneSet &ps, int64_t *counts5);
+int launch_build_persistent(const PersistDev &pd, int max_R, cudaStream_t st, const Prof *prof);
 // totals: the five totals over all frames (host).
 int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t st, const Prof *prof);
 

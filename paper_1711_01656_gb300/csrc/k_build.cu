@@ -1396,6 +1396,127 @@ __global__ void __launch_bounds__(128, 4) k_tiles_b(const BatchDev bd, unsigned 
     }
 }
 
+// ------------------------------------------------------------- persistent batched build
+//
+// One launch builds every frame of a batch: 256-thread CTAs, as many as fit
+// the GPU at once, take work items by ticket (an atomic counter) until the
+// batch's items run out.  The items are segments of one kind of work of one
+// frame -- weighted-channel tile sums (one window per item), count tile sums
+// (two windows per item, one per 128-thread half), carry-scan chunks (256
+// scan items), count tiles and moment tiles (8 warp units per item) -- in an
+// order the host chooses.  A frame's carry scan may start once all its tile
+// sums are done, its tiles once its carry scan is done: each finished item
+// adds one to its frame's counter for its phase (after a device-wide fence),
+// and an item whose phase depends on another reads that counter with acquire
+// semantics until it reaches the frame's total.  Every item it waits for has
+// a smaller ticket, so it was taken earlier by a CTA that is running it; the
+// wait is bounded all the same: a wait that gives up sets bit 2 of the error
+// word (ih_sync reports IH_ETIMEOUT) and the item goes on without the data.
+// Loads of data written inside the launch (the carries) are plain loads after
+// that acquire; pixels and feature planes are written before the launch.
+constexpr int kPThreads = 256;
+constexpr long kPSpinLimit = 1L << 24;
+
+enum PersistKind { PK_SUMS_W = 0, PK_SUMS_C = 1, PK_SCAN = 2, PK_TILES_C = 3, PK_TILES_M = 4 };
+
+__device__ __forceinline__ int persist_phase(int kind) { return kind <= PK_SUMS_C ? 0 : (kind == PK_SCAN ? 1 : 2); }
+
+__device__ __forceinline__ int ld_acquire_gpu(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const PersistDev pd)
+{
+    pdl_wait();
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ unsigned int s_t;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (;;) {
+        if (tid == 0) s_t = atomicAdd(pd.ticket, 1u);
+        __syncthreads();
+        const int64_t t = s_t;
+        if (t >= pd.total) return;
+        const int sg = find_frame(pd.seg_pre, pd.nsegs, t);
+        const PersistSeg seg = pd.segs[sg];
+        const int64_t idx = seg.first + (t - pd.seg_pre[sg]);
+        const PlaneSet &ps = pd.sets[seg.frame];
+        const int phase = persist_phase(seg.kind);
+        int32_t *done = pd.done + 3 * (int64_t)seg.frame;
+        if (tid == 0) {
+            int ok = 1;
+            if (phase > 0) {
+                const int need = pd.need[3 * (int64_t)seg.frame + phase - 1];
+                long spins = 0;
+                while (ld_acquire_gpu(done + phase - 1) < need) {
+                    if (++spins > kPSpinLimit) {
+                        ok = 0;
+                        atomicOr(pd.err, 2);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            s_abort = !ok;
+        }
+        __syncthreads();  // also: every thread has read s_t before it is taken again
+        if (!s_abort) {
+            const TileGrid &g = ps.g;
+            const int64_t per = (int64_t)g.ns * g.nb;
+            if (seg.kind == PK_SUMS_W) {
+                const int z = (int)(idx / per), rem = (int)(idx % per);
+                tile_sums_body<true>(ps, rem % g.ns, rem / g.ns, ps.nwin_count + z);
+            } else if (seg.kind == PK_SUMS_C) {
+                const int half = tid >> 7;
+                const int64_t u = 2 * idx + half;
+                if (u < per * ps.nwin_count) {
+                    const int z = (int)(u / per), rem = (int)(u % per);
+                    CountSumsSmem &sm = reinterpret_cast<CountSumsSmem *>(dsm)[half];
+                    tile_sums_count_group(ps, rem % g.ns, rem / g.ns, z, sm, tid & 127, 1 + half);
+                }
+            } else if (seg.kind == PK_SCAN) {
+                const int64_t u = idx * kPThreads + tid;
+                if (u < carry_scan_items(ps)) carry_scan_item(ps, u);
+            } else if (seg.kind == PK_TILES_C) {
+                CountSmem *cs = reinterpret_cast<CountSmem *>(dsm);
+                const int64_t u = idx * 8 + wid;
+                const int h = wid >> 2, w4 = wid & 3;
+                if (u < per * ps.ngroups) {
+                    if (ps.layout == LAYOUT_SLAB)
+                        tiles_count_dispatch<LAYOUT_SLAB, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                    else if (ps.layout == LAYOUT_RECORD)
+                        tiles_count_dispatch<LAYOUT_RECORD, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                    else
+                        tiles_count_dispatch<LAYOUT_BIN_MAJOR, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                }
+            } else {
+                MomentSmem *m = reinterpret_cast<MomentSmem *>(dsm);
+                const int Bw = ps.chan[ps.wch].bins;
+                const int64_t u = idx * 8 + wid;
+                const int h = wid >> 2, w4 = wid & 3;
+                if (u < per * Bw) {
+                    const int tile = (int)(u / Bw), wb = (int)(u % Bw);
+                    if (ps.mom32)
+                        tiles_moments_unit<true>(ps, tile / g.ns, tile % g.ns, wb, lane, m[h].RLn[w4], m[h].RLx[w4],
+                                                 m[h].RLxx[w4], m[h].stage[w4]);
+                    else if (ps.uni)
+                        tiles_moments_unit<false, true>(ps, tile / g.ns, tile % g.ns, wb, lane, m[h].RLn[w4],
+                                                        m[h].RLx[w4], m[h].RLxx[w4], m[h].stage[w4]);
+                    else
+                        tiles_moments_unit<false>(ps, tile / g.ns, tile % g.ns, wb, lane, m[h].RLn[w4], m[h].RLx[w4],
+                                                  m[h].RLxx[w4], m[h].stage[w4]);
+                }
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) atomicAdd(done + phase, 1);
+    }
+}
+
 template <typename F>
 void set_max_smem(F *f, size_t bytes)
 {
@@ -1462,6 +1583,8 @@ void carve_carries(PlaneSet &ps, void *base)
     }
 }
 
+size_t persistent_smem_bytes(int max_R);
+
 void prepare_kernels()
 {
     prepare_features();
@@ -1475,6 +1598,7 @@ void prepare_kernels()
     if (dev < 0 || dev >= 64 || done[dev]) return;
     set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
     set_max_smem(k_tile_sums_all_b, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
+    set_max_smem(k_build_persistent, persistent_smem_bytes(kMaxBandRows));
     done[dev] = true;
 }
 
@@ -1512,6 +1636,54 @@ int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t s
         ++n;
     }
     return cudaPeekAtLastError() == cudaSuccess ? n : -1;
+}
+
+size_t persistent_smem_bytes(int max_R)
+{
+    size_t b = std::max(sums_smem_bytes(max_R, true), 2 * sizeof(CountSumsSmem));
+    b = std::max(b, std::max(2 * sizeof(CountSmem), 2 * sizeof(MomentSmem)));
+    return b;
+}
+
+void persistent_counts(const PlaneSet &ps, int64_t *c)
+{
+    const int64_t tiles = (int64_t)ps.g.nb * ps.g.ns;
+    const bool carries = ps.colsum != nullptr;
+    c[PK_SUMS_W] = carries ? tiles * (ps.nwin - ps.nwin_count) : 0;
+    c[PK_SUMS_C] = carries ? (tiles * ps.nwin_count + 1) / 2 : 0;
+    c[PK_SCAN] = carries ? ((int64_t)ps.B * ps.g.W + (int64_t)ps.B * ps.g.H + (int64_t)ps.g.nb * ps.B + kPThreads - 1) /
+                               kPThreads
+                         : 0;
+    c[PK_TILES_C] = (tiles * ps.ngroups + 7) / 8;
+    c[PK_TILES_M] = ps.mom ? (tiles * ps.chan[ps.wch].bins + 7) / 8 : 0;
+}
+
+int persistent_ctas()
+{
+    prepare_kernels();
+    static int ctas[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 1;
+    if (!ctas[dev]) {
+        int per_sm = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_persistent, kPThreads,
+                                                      persistent_smem_bytes(kMaxBandRows));
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        ctas[dev] = std::max(1, per_sm) * std::max(1, nsm);
+    }
+    return ctas[dev];
+}
+
+int launch_build_persistent(const PersistDev &pd, int max_R, cudaStream_t st, const Prof *prof)
+{
+    prepare_kernels();
+    const int64_t ctas = std::min<int64_t>(pd.total, persistent_ctas());
+    if (ctas <= 0) return 0;
+    prof_mark(prof, KID_PERSISTENT, 0, st);
+    launch_pdl(k_build_persistent, (unsigned)ctas, kPThreads, persistent_smem_bytes(max_R), st, pd);
+    prof_mark(prof, KID_PERSISTENT, 1, st);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 void batch_counts(const PlaneSet &ps, int64_t *c)

@@ -37,8 +37,8 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
              "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
-             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges", "ih_server_cancel", "ih_memory_used", "ih_build_mma")
-IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE = 1, 2
+             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges", "ih_server_cancel", "ih_memory_used", "ih_build_mma", "ih_tune_set")
+IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE, IH_BATCH_PERSISTENT = 1, 2, 4
 IH_CFG_PROFILE = 1
 
 
@@ -140,6 +140,7 @@ def load_library(path: str = LIB_PATH):
             "ih_launch_count": ([p], i64),
             "ih_memory_used": ([p], ctypes.c_uint64),
             "ih_build_mma": ([p, p, ctypes.POINTER(i32), p], i32),
+            "ih_tune_set": ([p, p, i32, i32], i32),
             "ih_last_error": ([p], ctypes.c_char_p),
             "ih_build_counts_static": ([p, i32, i32, i64, i32, i32, p, i64, p], i32),
             "ih_batch_create": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(ih_batch_queries), u32,
@@ -437,6 +438,12 @@ def ih_batch_run(ctx, batch, stream=None):
 
 def ih_batch_destroy(batch):
     _check(None, load_library().ih_batch_destroy(batch))
+
+
+def ih_tune_set(ctx, frame, band_rows, strip_cols):
+    """Later frames of this frame's shape are built on band_rows x strip_cols tiles."""
+    cf, _keep = frame._c()
+    _check(ctx, load_library().ih_tune_set(ctx, ctypes.byref(cf), int(band_rows), int(strip_cols)))
 
 
 def ih_autotune(ctx, frame, stream=None):

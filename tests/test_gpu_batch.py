@@ -56,8 +56,12 @@ def _moments(ih, ctx, h):
     return torch.stack(outs)
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_equals_single_and_oracle(ihlib, ctx, graph):
+def test_batch_equals_single_and_oracle(ihlib, ctx, graph, persistent):
+    """Every frame of a batch -- one launch per kernel, or the whole build in
+    one persistent launch (IH_BATCH_PERSISTENT) -- equals its single build,
+    which equals the oracle; so do its queries; twice in a row."""
     ih = ihlib
     specs = _frames(ih, 11)
     frames = [s[0] for s in specs]
@@ -83,7 +87,8 @@ def test_batch_equals_single_and_oracle(ihlib, ctx, graph):
     w_out = torch.full((sum(n * b for n, b in zip(wc, Bw)),), -7.0, dtype=torch.float32, device=DEV)
     batch, handles = ih.ih_batch_create(ctx, frames, rects=d_rects, rect_counts=rc, rect_out=rect_out,
                                         windows=d_wins, window_counts=wc, weighted_out=w_out,
-                                        batch_flags=ih.IH_BATCH_GRAPH if graph else 0)
+                                        batch_flags=(ih.IH_BATCH_GRAPH if graph else 0) |
+                                        (ih.IH_BATCH_PERSISTENT if persistent else 0))
     try:
         for run in range(2):  # a second run (graph replay) gives the same results
             if run:
@@ -195,9 +200,10 @@ def test_batch_other_kernels_equal_single(ihlib, ctx, kernel, layers):
             ih.ih_release(ctx, hdl)
 
 
+@pytest.mark.parametrize("persistent", [False, True])
 @pytest.mark.parametrize("graph", [False, True])
 @pytest.mark.parametrize("layout", [0, 2])
-def test_one_frame_batch(ihlib, ctx, graph, layout):
+def test_one_frame_batch(ihlib, ctx, graph, layout, persistent):
     """A batch of one frame (run with the single-frame kernels) gives the
     same tensor, rectangles and weighted windows as ih_build + ih_query."""
     ih = ihlib
@@ -210,7 +216,8 @@ def test_one_frame_batch(ihlib, ctx, graph, layout):
     w_out = torch.full((120 * 16,), -7.0, dtype=torch.float32, device=DEV)
     batch, handles = ih.ih_batch_create(ctx, [f], rects=rects, rect_counts=[300], rect_out=r_out, windows=wins,
                                         window_counts=[120], weighted_out=w_out,
-                                        batch_flags=ih.IH_BATCH_GRAPH if graph else 0)
+                                        batch_flags=(ih.IH_BATCH_GRAPH if graph else 0) |
+                                        (ih.IH_BATCH_PERSISTENT if persistent else 0))
     try:
         ih.ih_batch_run(ctx, batch)
         ih.ih_sync(ctx)
@@ -224,6 +231,38 @@ def test_one_frame_batch(ihlib, ctx, graph, layout):
         feats = oracle.features(rgb.cpu().numpy())
         assert np.array_equal(sr.cpu().numpy(), oracle.frame_rect_hist(feats, synth.FMV_CHANNELS, rects.cpu().numpy()))
         ih.ih_release(ctx, single)
+    finally:
+        ih.ih_batch_destroy(batch)
+        for hd in handles:
+            ih.ih_release(ctx, hd)
+
+
+def test_persistent_batch_of_many_frames(ihlib, ctx):
+    """A persistent batch of 24 frames of mixed sizes (several waves of CTAs
+    over the work items, frames of one tile and of many) equals per-frame
+    builds, and ih_sync reports no device-side timeout."""
+    ih = ihlib
+    g = np.random.Generator(np.random.PCG64(77))
+    sizes = [(int(g.integers(1, 700)), int(g.integers(1, 900))) for _ in range(24)]
+    imgs = [synth.blob_plane(h, w, 900 + k) for k, (h, w) in enumerate(sizes)]
+    pix = [torch.from_numpy(x).to(DEV)[None] for x in imgs]
+    frames = [ih.Frame(p, [(int(g.integers(1, 64)), 0)], weighted_channel=0 if k % 3 == 0 else -1, layout=k % 3)
+              for k, p in enumerate(pix)]
+    batch, handles = ih.ih_batch_create(ctx, frames, batch_flags=ih.IH_BATCH_PERSISTENT | ih.IH_BATCH_GRAPH)
+    try:
+        for _ in range(3):
+            ih.ih_batch_run(ctx, batch)
+        ih.ih_sync(ctx)
+        for k, f in enumerate(frames):
+            single, = ih.ih_build(ctx, f)
+            assert torch.equal(_export(ih, ctx, handles[k]), _export(ih, ctx, single)), "frame %d" % k
+            gm, sm = _moments(ih, ctx, handles[k]), _moments(ih, ctx, single)
+            assert (gm is None) == (sm is None) and (gm is None or torch.equal(gm, sm))
+            ih.ih_release(ctx, single)
+        ih.ih_sync(ctx)
+        k = int(np.argmax([h * w for h, w in sizes]))
+        assert np.array_equal(_export(ih, ctx, handles[k]).cpu().numpy(),
+                              oracle.integral_histogram(imgs[k], frames[k].channels[0][0]))
     finally:
         ih.ih_batch_destroy(batch)
         for hd in handles:

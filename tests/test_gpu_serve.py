@@ -166,9 +166,10 @@ def test_cancel_queued_and_inflight_requests(ihlib):
     srv = ih.ih_server_create(c, streams=1, max_inflight=1, max_batch=1)
     try:
         ih.ih_server_submit(c, srv, 0, fbig, user=100)
-        for k, img in enumerate(small):
-            ih.ih_server_submit(c, srv, 1 + k, ih.Frame(torch.from_numpy(img).to(DEV)[None], [(8, 0)]),
-                                rects=rects, rect_out=outs[k], user=200 + k)
+        keep = [torch.from_numpy(img).to(DEV)[None] for img in small]  # valid until the requests complete
+        for k in range(len(small)):
+            ih.ih_server_submit(c, srv, 1 + k, ih.Frame(keep[k], [(8, 0)]), rects=rects, rect_out=outs[k],
+                                user=200 + k)
         ih.ih_server_cancel(srv, 201)  # queued behind the 4096 x 4096 frame
         ih.ih_server_cancel(srv, 100)  # on the device, or about to be
         with pytest.raises(ih.IHError):
