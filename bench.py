@@ -920,9 +920,33 @@ def plain_section(ih, dev, runs=400):
             ih.ih_release(ctx, h)
     us_graph = min(us.values())
     ih.ih_destroy(ctx)
+    # per-kernel device time of the plain per-frame calls and of the persistent build
+    ctxp = ih.ih_create(dev.index or 0, flags=ih.IH_CFG_PROFILE)
+    kern = {}
+    for name, flags in (("per_frame", None), ("persistent", ih.IH_BATCH_PERSISTENT)):
+        if flags is None:
+            run = lambda: (lambda h: (ih.ih_query_rects(ctxp, h, rects, r_out), ih.ih_release(ctxp, h)))(
+                ih.ih_build(ctxp, frame)[0])
+        else:
+            batch, handles = ih.ih_batch_create(ctxp, [frame], rects=rects, rect_counts=[rects.shape[0]],
+                                                rect_out=r_out.view(-1), batch_flags=flags)
+            run = lambda: ih.ih_batch_run(ctxp, batch)
+        for rep in range(21):
+            run()
+            if rep == 0:
+                ih.ih_sync(ctxp)
+                ih.ih_profile_read(ctxp, reset=True)
+        ih.ih_sync(ctxp)
+        kern[name] = {k: round(v[1] / v[0] * 1e3, 2) for k, v in ih.ih_profile_read(ctxp, reset=True).items()}
+        if flags is not None:
+            ih.ih_batch_destroy(batch)
+            for h in handles:
+                ih.ih_release(ctxp, h)
+    ih.ih_destroy(ctxp)
     cells = B * hh * ww
     return {"workload": "plain 640x480 uniform gray, 16 bins, 10,000 rects", "per_frame_us": round(us_plain, 2),
-            "graph_us": round(us_graph, 2), "graph_modes_us": {k: round(v, 2) for k, v in us.items()}, "cells_per_s_per_frame": cells / (us_plain / 1e6),
+            "graph_us": round(us_graph, 2), "graph_modes_us": {k: round(v, 2) for k, v in us.items()},
+            "kernel_us": kern, "cells_per_s_per_frame": cells / (us_plain / 1e6),
             "cells_per_s_graph": cells / (us_graph / 1e6)}
 
 

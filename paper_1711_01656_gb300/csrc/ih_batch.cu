@@ -39,6 +39,7 @@ struct ih_batch {
     // IH_BATCH_PERSISTENT: the build as one launch of k_build_persistent
     bool persistent = false;
     PersistDev pdev{};
+    int persist_layout = -1;  // the layout of every frame, or -1
     int32_t *d_counters = nullptr;  // [3 n] done counters, then the ticket
     size_t counter_bytes = 0;
     cudaGraph_t graph = nullptr;
@@ -95,7 +96,7 @@ int enqueue_run(ih_batch *b, cudaStream_t st, const Prof *prof)
     }
     if (b->persistent) {
         if (cudaMemsetAsync(b->d_counters, 0, b->counter_bytes, st) != cudaSuccess) return -1;
-        k = launch_build_persistent(b->pdev, b->bd.max_R, st, prof);
+        k = launch_build_persistent(b->pdev, b->persist_layout, b->bd.max_R, st, prof);
     } else {
         k = launch_build_batch(b->bd, b->totals, st, prof);
     }
@@ -448,6 +449,9 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
         cudaMemcpyAsync(d_need, need.data(), sizeof(int32_t) * need.size(), cudaMemcpyHostToDevice, st);
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return bail(cuda_fail(ctx, e, "table upload"));
         b->persistent = true;
+        b->persist_layout = sets[0].layout;
+        for (int k = 1; k < n; ++k)
+            if (sets[k].layout != b->persist_layout) b->persist_layout = -1;
         b->pdev.sets = d_sets;
         b->pdev.segs = d_segs;
         b->pdev.seg_pre = d_seg_pre;

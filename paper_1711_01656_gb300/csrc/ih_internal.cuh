@@ -164,8 +164,8 @@ struct PlaneSet {
     int16_t rec_w[kMaxGroups];     // words per pixel record of each plane
     int64_t slab_off[kMaxGroups];  // element offset of each plane
     int32_t *out;         // count tensor
-    int64_t *mom;         // moment planes [4][Bw][H][P] (w = c, r, c^2, r^2), or null;
-                          // uint32 (values mod 2^32) when mom32
+    int64_t *mom;         // moment planes as quads [Bw][H][P][4] (w = c, r, c^2, r^2 of
+                          // one pixel together), or null; uint32 (values mod 2^32) when mom32
     // carries (null when the frame is a single tile)
     int32_t *colsum;      // [nb][B][W]  column counts -> G0 after the scan
     int32_t *rowsum;      // [ns][B][H]  row counts    -> L0 after the scan
@@ -242,7 +242,8 @@ struct PersistDev {
 };
 // Items of each kind of one frame (host).
 void persistent_counts(const PlaneSet &ps, int64_t *counts5);
-int launch_build_persistent(const PersistDev &pd, int max_R, cudaStream_t st, const Prof *prof);
+// layout: the count layout of every frame, or -1 when the frames differ.
+int launch_build_persistent(const PersistDev &pd, int layout, int max_R, cudaStream_t st, const Prof *prof);
 // totals: the five totals over all frames (host).
 int launch_build_batch(const BatchDev &bd, const int64_t *totals, cudaStream_t st, const Prof *prof);
 
@@ -290,7 +291,7 @@ struct CountView {
 };
 struct MomentView {
     int32_t bin0;        // first bin of the weighted channel in the count tensor
-    const int64_t *m;    // [4][Bw][H][P]: w = c, r, c^2, r^2 (uint32 when m32)
+    const int64_t *m;    // quads [Bw][H][P][4]: w = c, r, c^2, r^2 (uint32 when m32)
     int32_t Bw;
     int32_t m32;
 };
@@ -363,7 +364,8 @@ int launch_phog_match(const int64_t *ih, int H, int64_t P, int L, const int64_t 
                       int sc0, int sr1, int sc1, float *out, cudaStream_t st, const Prof *prof);
 // Count tensor -> packed bin-major B x H x W int32.
 int launch_export(const CountView &v, int32_t *dst, cudaStream_t st, const Prof *prof);
-// Moment plane k of [4][Bw][H][P] (int64, or uint32 when m32) -> packed Bw x H x W int64.
+// Moment plane k (entry k of the quads [Bw][H][P][4], int64 or uint32 when
+// m32) -> packed Bw x H x W int64.
 int launch_export_moments(const void *m, int m32, int Bw, int H, int W, int64_t P, int k, int64_t *dst,
                           cudaStream_t st, const Prof *prof);
 

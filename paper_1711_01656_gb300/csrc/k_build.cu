@@ -1168,9 +1168,9 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
             });
     }
     __syncwarp();
-    const int64_t plane = (int64_t)Bw * g.H * g.P;
-    int64_t *mo = ps.mom + (int64_t)wb * g.H * g.P;
-    uint32_t *mo32 = reinterpret_cast<uint32_t *>(ps.mom) + (int64_t)wb * g.H * g.P;
+    // bin wb's quads: [H][P][4] (w = c, r, c^2, r^2 of one pixel together)
+    int64_t *mo = ps.mom + (int64_t)wb * g.H * g.P * 4;
+    uint32_t *mo32 = reinterpret_cast<uint32_t *>(ps.mom) + (int64_t)wb * g.H * g.P * 4;
     const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
 
     for (int cc = C0; cc < C1; cc += kChunk) {
@@ -1257,37 +1257,35 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                 if (c < g.P) {
                     const int64_t o = (int64_t)(R0 + rr) * g.P + c;
                     if (M32) {
-                        // the planes modulo 2^32: one 16-byte store per plane
+                        // the quads modulo 2^32: one 16-byte store per pixel
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            *reinterpret_cast<uint4 *>(mo32 + k * plane + o) =
-                                make_uint4((uint32_t)acc[k][0], (uint32_t)acc[k][1], (uint32_t)acc[k][2],
-                                           (uint32_t)acc[k][3]);
+                        for (int jj = 0; jj < 4; ++jj)
+                            *reinterpret_cast<uint4 *>(mo32 + (o + jj) * 4) =
+                                make_uint4((uint32_t)acc[0][jj], (uint32_t)acc[1][jj], (uint32_t)acc[2][jj],
+                                           (uint32_t)acc[3][jj]);
                     } else {
-                        // through the warp's stage: pair 2*lane+h holds columns
-                        // 4*lane+2h, +1; the two halves are written in an order
-                        // that alternates every 4 lanes (no bank conflicts), and
-                        // each store below writes 512 contiguous bytes
-                        const int h = (lane >> 2) & 1;
+                        // through the warp's stage: the row's 128 quads are 256
+                        // 16-byte units, unit u = 2 px + h holding planes 2h, 2h+1
+                        // of pixel px, at position u ^ ((u >> 3) & 7) so that
+                        // both the writes (8 units per lane) and the reads (32
+                        // consecutive units per store) hit distinct bank groups
+                        longlong2 *s2 = reinterpret_cast<longlong2 *>(stage);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            longlong2 *s2 = reinterpret_cast<longlong2 *>(stage + k * kChunk);
-                            const longlong2 lo = make_longlong2(acc[k][0], acc[k][1]);
-                            const longlong2 hi = make_longlong2(acc[k][2], acc[k][3]);
-                            s2[2 * lane + h] = h ? hi : lo;
-                            s2[2 * lane + 1 - h] = h ? lo : hi;
+                        for (int t = 0; t < 8; ++t) {
+                            const int u = 8 * lane + t, jj = t >> 1, h = t & 1;
+                            s2[u ^ ((u >> 3) & 7)] = make_longlong2(acc[2 * h][jj], acc[2 * h + 1][jj]);
                         }
                     }
                 }
                 if (!M32) {
                     __syncwarp();
-                    const int64_t orow = (int64_t)(R0 + rr) * g.P + cc;
+                    // each store writes 512 contiguous bytes of the row's 4 KB of quads
+                    longlong2 *dst = reinterpret_cast<longlong2 *>(mo + ((int64_t)(R0 + rr) * g.P + cc) * 4);
+                    const longlong2 *s2 = reinterpret_cast<const longlong2 *>(stage);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const longlong2 *s2 = reinterpret_cast<const longlong2 *>(stage + k * kChunk);
-                        longlong2 *dst = reinterpret_cast<longlong2 *>(mo + k * plane + orow);
-                        if (cc + 2 * lane < g.P) dst[lane] = s2[lane];
-                        if (cc + 64 + 2 * lane < g.P) dst[32 + lane] = s2[32 + lane];
+                    for (int m = 0; m < 8; ++m) {
+                        const int u = 32 * m + lane;
+                        if (cc + (u >> 1) < g.P) dst[u] = s2[u ^ ((u >> 3) & 7)];
                     }
                 }
                 __syncwarp();
@@ -1428,6 +1426,9 @@ __device__ __forceinline__ int ld_acquire_gpu(const int32_t *p)
     return v;
 }
 
+// LAYOUT: the count layout of every frame of the batch, or -1 for a batch of
+// several layouts (each count-tile item then dispatches on its frame's).
+template <int LAYOUT>
 __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const PersistDev pd)
 {
     pdl_wait();
@@ -1452,7 +1453,8 @@ __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const Persist
                 const int need = pd.need[3 * (int64_t)seg.frame + phase - 1];
                 long spins = 0;
                 while (ld_acquire_gpu(done + phase - 1) < need) {
-                    if (++spins > kPSpinLimit) {
+                    // after one wait has given up, no other waits: the run is void
+                    if (++spins > kPSpinLimit || (*(volatile int *)pd.err & 2)) {
                         ok = 0;
                         atomicOr(pd.err, 2);
                         break;
@@ -1485,12 +1487,16 @@ __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const Persist
                 const int64_t u = idx * 8 + wid;
                 const int h = wid >> 2, w4 = wid & 3;
                 if (u < per * ps.ngroups) {
-                    if (ps.layout == LAYOUT_SLAB)
-                        tiles_count_dispatch<LAYOUT_SLAB, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
-                    else if (ps.layout == LAYOUT_RECORD)
-                        tiles_count_dispatch<LAYOUT_RECORD, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
-                    else
-                        tiles_count_dispatch<LAYOUT_BIN_MAJOR, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                    if constexpr (LAYOUT >= 0) {
+                        tiles_count_dispatch<LAYOUT, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                    } else {
+                        if (ps.layout == LAYOUT_SLAB)
+                            tiles_count_dispatch<LAYOUT_SLAB, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                        else if (ps.layout == LAYOUT_RECORD)
+                            tiles_count_dispatch<LAYOUT_RECORD, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                        else
+                            tiles_count_dispatch<LAYOUT_BIN_MAJOR, false>(ps, u, lane, cs[h].RL[w4], cs[h].stage[w4]);
+                    }
                 }
             } else {
                 MomentSmem *m = reinterpret_cast<MomentSmem *>(dsm);
@@ -1511,9 +1517,13 @@ __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const Persist
                 }
             }
         }
-        __threadfence();
+        // the CTA's writes, ordered before thread 0 by the barrier, are
+        // released device-wide by its fence before the counter moves
         __syncthreads();
-        if (tid == 0) atomicAdd(done + phase, 1);
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(done + phase, 1);
+        }
     }
 }
 
@@ -1598,7 +1608,10 @@ void prepare_kernels()
     if (dev < 0 || dev >= 64 || done[dev]) return;
     set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
     set_max_smem(k_tile_sums_all_b, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
-    set_max_smem(k_build_persistent, persistent_smem_bytes(kMaxBandRows));
+    set_max_smem(k_build_persistent<-1>, persistent_smem_bytes(kMaxBandRows));
+    set_max_smem(k_build_persistent<LAYOUT_SLAB>, persistent_smem_bytes(kMaxBandRows));
+    set_max_smem(k_build_persistent<LAYOUT_RECORD>, persistent_smem_bytes(kMaxBandRows));
+    set_max_smem(k_build_persistent<LAYOUT_BIN_MAJOR>, persistent_smem_bytes(kMaxBandRows));
     done[dev] = true;
 }
 
@@ -1667,7 +1680,7 @@ int persistent_ctas()
     if (dev < 0 || dev >= 64) return 1;
     if (!ctas[dev]) {
         int per_sm = 0, nsm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_persistent, kPThreads,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_persistent<-1>, kPThreads,
                                                       persistent_smem_bytes(kMaxBandRows));
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         ctas[dev] = std::max(1, per_sm) * std::max(1, nsm);
@@ -1675,13 +1688,21 @@ int persistent_ctas()
     return ctas[dev];
 }
 
-int launch_build_persistent(const PersistDev &pd, int max_R, cudaStream_t st, const Prof *prof)
+int launch_build_persistent(const PersistDev &pd, int layout, int max_R, cudaStream_t st, const Prof *prof)
 {
     prepare_kernels();
     const int64_t ctas = std::min<int64_t>(pd.total, persistent_ctas());
     if (ctas <= 0) return 0;
+    const size_t smem = persistent_smem_bytes(max_R);
     prof_mark(prof, KID_PERSISTENT, 0, st);
-    launch_pdl(k_build_persistent, (unsigned)ctas, kPThreads, persistent_smem_bytes(max_R), st, pd);
+    if (layout == LAYOUT_SLAB)
+        launch_pdl(k_build_persistent<LAYOUT_SLAB>, (unsigned)ctas, kPThreads, smem, st, pd);
+    else if (layout == LAYOUT_RECORD)
+        launch_pdl(k_build_persistent<LAYOUT_RECORD>, (unsigned)ctas, kPThreads, smem, st, pd);
+    else if (layout == LAYOUT_BIN_MAJOR)
+        launch_pdl(k_build_persistent<LAYOUT_BIN_MAJOR>, (unsigned)ctas, kPThreads, smem, st, pd);
+    else
+        launch_pdl(k_build_persistent<-1>, (unsigned)ctas, kPThreads, smem, st, pd);
     prof_mark(prof, KID_PERSISTENT, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

@@ -20,6 +20,9 @@
 // The window's total weight has the closed form
 //     K = (4 w^2 h^2 + w^2 + h^2) / (6 w h),
 // used by IH_NORMALIZE.
+// The moment planes are stored as quads, [Bw][H][P][4]: the four moments
+// (w = c, r, c^2, r^2) of a bin at one pixel are 32 contiguous bytes (16 with
+// 32-bit moments), so a window corner costs one sector per bin.
 #include "ih_internal.cuh"
 
 namespace ih {
@@ -263,11 +266,66 @@ __device__ __forceinline__ void count_base(const CountView &v, int gb, int64_t &
     }
 }
 
+// The four moments (w = c, r, c^2, r^2) of one bin at (r, c): one quad, 32
+// bytes (int64) or 16 bytes (uint32), so each corner of a window costs one
+// sector per bin.
+__device__ __forceinline__ void quad_at(const long long *q, int64_t P, int r, int c, long long (&o)[4])
+{
+    const longlong2 *p = reinterpret_cast<const longlong2 *>(q + ((int64_t)r * P + c) * 4);
+    const longlong2 a = __ldg(p), b = __ldg(p + 1);
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+
+__device__ __forceinline__ uint4 quad_at_u32(const uint32_t *q, int64_t P, int r, int c)
+{
+    return __ldg(reinterpret_cast<const uint4 *>(q + ((int64_t)r * P + c) * 4));
+}
+
+// Four-corner differences of the four moments of a bin (Eq. 2.16 on Eq. 3.4's
+// planes); q points at the bin's quads.
+__device__ __forceinline__ void four_corner_quad(const long long *q, int64_t P, int r0, int c0, int r1, int c1,
+                                                 long long (&S)[4])
+{
+    long long a[4];
+    quad_at(q, P, r1, c1, a);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) S[k] = a[k];
+    if (r0 > 0) {
+        quad_at(q, P, r0 - 1, c1, a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S[k] -= a[k];
+    }
+    if (c0 > 0) {
+        quad_at(q, P, r1, c0 - 1, a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S[k] -= a[k];
+    }
+    if (r0 > 0 && c0 > 0) {
+        quad_at(q, P, r0 - 1, c0 - 1, a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) S[k] += a[k];
+    }
+}
+
+// The same modulo 2^32.
+__device__ __forceinline__ uint4 four_corner_quad_u32(const uint32_t *q, int64_t P, int r0, int c0, int r1, int c1)
+{
+    uint4 s = quad_at_u32(q, P, r1, c1);
+    auto sub = [&](uint4 a) { s.x -= a.x; s.y -= a.y; s.z -= a.z; s.w -= a.w; };
+    auto add = [&](uint4 a) { s.x += a.x; s.y += a.y; s.z += a.z; s.w += a.w; };
+    if (r0 > 0) sub(quad_at_u32(q, P, r0 - 1, c1));
+    if (c0 > 0) sub(quad_at_u32(q, P, r1, c0 - 1));
+    if (r0 > 0 && c0 > 0) add(quad_at_u32(q, P, r0 - 1, c0 - 1));
+    return s;
+}
+
 __device__ __forceinline__ void weighted_item(const CountView &v, const MomentView &m, const int32_t *__restrict__ wins,
                                               int normalize, float *__restrict__ out, int64_t t, int *err)
 {
     const int64_t plane = (int64_t)v.H * v.P;
-    const int64_t mplane = (int64_t)m.Bw * plane;
     const int64_t qi = t / m.Bw;
     const int b = (int)(t - qi * m.Bw);
     const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
@@ -285,28 +343,22 @@ __device__ __forceinline__ void weighted_item(const CountView &v, const MomentVi
                         (r0 > 0 ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + c1) * px) : 0) -
                         (c0 > 0 ? (long long)__ldg(cp + ((int64_t)r1 * v.P + (c0 - 1)) * px) : 0) +
                         ((r0 > 0 && c0 > 0) ? (long long)__ldg(cp + ((int64_t)(r0 - 1) * v.P + (c0 - 1)) * px) : 0);
-    const int64_t mo = b * plane;
+    const int64_t mo = b * plane * 4;  // bin b's quads
     const long long w = c1 - c0 + 1, h = r1 - r0 + 1;
     const long long mc = c0 + c1, mr = r0 + r1;
     long long X2, Y2;
     if (m.m32) {
-        // planes modulo 2^32: the centred sums X2, Y2 < 2^32 for sides <= 256,
+        // moments modulo 2^32: the centred sums X2, Y2 < 2^32 for sides <= 256,
         // so computing them modulo 2^32 gives them exactly
-        const uint32_t *m32 = reinterpret_cast<const uint32_t *>(m.m);
-        const uint32_t Sc = four_corner_u32(m32 + 0 * mplane + mo, v.P, r0, c0, r1, c1);
-        const uint32_t Sr = four_corner_u32(m32 + 1 * mplane + mo, v.P, r0, c0, r1, c1);
-        const uint32_t Scc = four_corner_u32(m32 + 2 * mplane + mo, v.P, r0, c0, r1, c1);
-        const uint32_t Srr = four_corner_u32(m32 + 3 * mplane + mo, v.P, r0, c0, r1, c1);
+        const uint4 S = four_corner_quad_u32(reinterpret_cast<const uint32_t *>(m.m) + mo, v.P, r0, c0, r1, c1);
         const uint32_t n32 = (uint32_t)N, mc32 = (uint32_t)mc, mr32 = (uint32_t)mr;
-        X2 = (long long)(uint32_t)(4u * Scc - 4u * mc32 * Sc + mc32 * mc32 * n32);
-        Y2 = (long long)(uint32_t)(4u * Srr - 4u * mr32 * Sr + mr32 * mr32 * n32);
+        X2 = (long long)(uint32_t)(4u * S.z - 4u * mc32 * S.x + mc32 * mc32 * n32);
+        Y2 = (long long)(uint32_t)(4u * S.w - 4u * mr32 * S.y + mr32 * mr32 * n32);
     } else {
-        const long long Sc = four_corner(m.m + 0 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Sr = four_corner(m.m + 1 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Scc = four_corner(m.m + 2 * mplane + mo, v.P, r0, c0, r1, c1);
-        const long long Srr = four_corner(m.m + 3 * mplane + mo, v.P, r0, c0, r1, c1);
-        X2 = 4 * Scc - 4 * mc * Sc + mc * mc * N;
-        Y2 = 4 * Srr - 4 * mr * Sr + mr * mr * N;
+        long long S[4];  // w = c, r, c^2, r^2
+        four_corner_quad(reinterpret_cast<const long long *>(m.m) + mo, v.P, r0, c0, r1, c1, S);
+        X2 = 4 * S[2] - 4 * mc * S[0] + mc * mc * N;
+        Y2 = 4 * S[3] - 4 * mr * S[1] + mr * mr * N;
     }
     const long long A = 2 * w * w, Bh = 2 * h * h;
     const long long qx = X2 / A, rx = X2 - qx * A;
@@ -377,7 +429,6 @@ __device__ __forceinline__ void weighted_item_alt(const CountView &v, const Mome
                                                   int normalize, float *__restrict__ out, int64_t t, int *err)
 {
     const int64_t plane = (int64_t)v.H * v.P;
-    const int64_t mplane = (int64_t)m.Bw * plane;
     const int64_t qi = t / m.Bw;
     const int b = (int)(t - qi * m.Bw);
     const int r0 = __ldg(wins + 4 * qi), c0 = __ldg(wins + 4 * qi + 1);
@@ -396,14 +447,14 @@ __device__ __forceinline__ void weighted_item_alt(const CountView &v, const Mome
     if (kernel == IH_KERNEL_MANHATTAN) {
         const long long Sr = r0 + r1, Sc = c0 + c1;
         const int y[3] = {r0 - 1, (r0 + r1) >> 1, r1}, x[3] = {c0 - 1, (c0 + c1) >> 1, c1};
-        const int64_t mo = b * plane;
+        const int64_t mo = b * plane * 4;  // bin b's quads; w = c and w = r are their first two entries
         long long S;
         if (m.m32) {
-            const uint32_t *m32 = reinterpret_cast<const uint32_t *>(m.m);
+            const uint32_t *m32 = reinterpret_cast<const uint32_t *>(m.m) + mo;
             uint32_t N[3][3], C[3][3], R[3][3];
             grid_load(N, y, x, [&](int r, int c) { return (uint32_t)count_at(r, c); });
-            grid_load(C, y, x, [&](int r, int c) { return __ldg(m32 + 0 * mplane + mo + (int64_t)r * v.P + c); });
-            grid_load(R, y, x, [&](int r, int c) { return __ldg(m32 + 1 * mplane + mo + (int64_t)r * v.P + c); });
+            grid_load(C, y, x, [&](int r, int c) { return __ldg(m32 + ((int64_t)r * v.P + c) * 4); });
+            grid_load(R, y, x, [&](int r, int c) { return __ldg(m32 + ((int64_t)r * v.P + c) * 4 + 1); });
             uint32_t s = 0;
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -417,8 +468,17 @@ __device__ __forceinline__ void weighted_item_alt(const CountView &v, const Mome
         } else {
             long long N[3][3], C[3][3], R[3][3];
             grid_load(N, y, x, count_at);
-            grid_load(C, y, x, [&](int r, int c) { return (long long)__ldg(m.m + 0 * mplane + mo + (int64_t)r * v.P + c); });
-            grid_load(R, y, x, [&](int r, int c) { return (long long)__ldg(m.m + 1 * mplane + mo + (int64_t)r * v.P + c); });
+            const long long *mq = reinterpret_cast<const long long *>(m.m) + mo;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    longlong2 a = make_longlong2(0, 0);
+                    if (y[i] >= 0 && x[j] >= 0)
+                        a = __ldg(reinterpret_cast<const longlong2 *>(mq + ((int64_t)y[i] * v.P + x[j]) * 4));
+                    C[i][j] = a.x;
+                    R[i][j] = a.y;
+                }
             S = 0;
 #pragma unroll
             for (int i = 0; i < 2; ++i)
@@ -662,11 +722,10 @@ __global__ void __launch_bounds__(256) k_export_moments(const void *__restrict__
 {
     pdl_wait();
     const int64_t total = (int64_t)Bw * H * W;
-    const int64_t plane = (int64_t)Bw * H * P;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t c = t % W, rb = t / W;
-        const int64_t o = k * plane + rb * P + c;
+        const int64_t o = (rb * P + c) * 4 + k;  // entry k of the quad of (bin, row) rb, column c
         dst[t] = m32 ? (int64_t)__ldg(static_cast<const uint32_t *>(m) + o) : __ldg(static_cast<const int64_t *>(m) + o);
     }
 }
