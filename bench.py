@@ -105,13 +105,16 @@ WAMI_RECTS = 1_000_000
 WAMI_WINDOWS = 100_000
 
 
-def make_wami_inputs(seed: int):
+def make_wami_inputs(seed: int, side: int = WAMI_H):
     """The wide-area frame: one 8192 x 8192 blob plane, 1,000,000 rectangles
-    of side 16..256 inside it and 100,000 windows of side 32..256."""
+    of side 16..256 inside it and 100,000 windows of side 32..256 (a smaller
+    square side, for profiling captures, scales the query counts with the
+    area)."""
     from paper_1711_01656_gb300 import synth
-    img = synth.blob_plane(WAMI_H, WAMI_W, seed)
-    rects = synth.rects_side_range(WAMI_H, WAMI_W, WAMI_RECTS, 16, 256, seed + 100)
-    wins = synth.rects_side_range(WAMI_H, WAMI_W, WAMI_WINDOWS, 32, 256, seed + 200)
+    frac = side * side / float(WAMI_H * WAMI_W)
+    img = synth.blob_plane(side, side, seed)
+    rects = synth.rects_side_range(side, side, max(1, int(WAMI_RECTS * frac)), 16, min(256, side), seed + 100)
+    wins = synth.rects_side_range(side, side, max(1, int(WAMI_WINDOWS * frac)), 32, min(256, side), seed + 200)
     return img, rects, wins
 
 
@@ -189,7 +192,7 @@ class Spec:
     one ih_query call (every rectangle and every weighted window) and
     ih_release, on one frame."""
 
-    def __init__(self, kind: str, seed: int, layout: int):
+    def __init__(self, kind: str, seed: int, layout: int, side: int = 0):
         from paper_1711_01656_gb300 import synth
         self.kind, self.seed, self.layout = kind, seed, layout
         if kind == "fmv":
@@ -200,13 +203,16 @@ class Spec:
             self.planes = 7          # channel planes the tile kernels read
             self.workload = WORKLOAD
         elif kind == "wami":
-            img, self.rects, self.wins = make_wami_inputs(seed)
+            side = side or WAMI_H
+            img, self.rects, self.wins = make_wami_inputs(seed, side)
             self.frame = img[None]
             self.chans = [(WAMI_BINS, 0)]
             self.rgb_input, self.wch = False, 0
-            self.H, self.W = WAMI_H, WAMI_W
+            self.H = self.W = side
             self.planes = 1
-            self.workload = WAMI_WORKLOAD
+            self.workload = WAMI_WORKLOAD if side == WAMI_H else (
+                "profiling case of the WAMI step: %dx%d gray, 32 bins, int64 moments, %d rects, %d windows"
+                % (side, side, len(self.rects), len(self.wins)))
         else:
             raise ValueError(kind)
         self.B = sum(b for b, _ in self.chans)
@@ -545,7 +551,10 @@ def run_engine(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     layout = LAYOUTS[args.layout][0]
     # the headline: the wide-area frame, each rank its own frame
-    head = Spec("wami", rank_seed(synth.config_seed(3), rank), layout)
+    if args.workload == "fmv":  # the FMV step as the line's workload (profiling captures)
+        head = Spec("fmv", rank_seed(synth.config_seed(2), rank), layout)
+    else:
+        head = Spec("wami", rank_seed(synth.config_seed(3), rank), layout, args.wami_side)
     m = measure_step(ih, dev, head, args.steps, args.warmup, world, flush, barrier)
     # the full-motion-video step, the same measurement
     fmv_spec = fmv = None
@@ -566,7 +575,7 @@ def run_engine(args):
     if sections and not args.no_plain:
         plain = plain_section(ih, dev)
     if sections and not args.no_mma:
-        mma = mma_section(ih, dev)
+        mma = mma_section(ih, dev, side=args.mma_side)
     if sections and not args.no_match:
         match = match_section(ih, dev, layout)
     if sections and not args.no_median:
@@ -694,7 +703,7 @@ def wami_section(ih, dev, layout, reps=3):
     return out
 
 
-def mma_section(ih, dev, reps=3):
+def mma_section(ih, dev, reps=3, side=8192):
     """The count tiles as tensor-core products (ih_build_mma: two chained
     tcgen05 bf16 products per 128 x 128 tile and bin) against the scan-based
     tiles kernel on the same frame: 8192 x 8192 gray, 32 bins, bin-major
@@ -703,7 +712,7 @@ def mma_section(ih, dev, reps=3):
     after one warm-up; the tensors must be equal."""
     import torch
     from paper_1711_01656_gb300 import synth
-    hh = ww = 8192
+    hh = ww = side
     B = 32
     free, _ = torch.cuda.mem_get_info(dev)
     if 3 * hh * ww * B * 4 > free * 0.8:
@@ -735,7 +744,7 @@ def mma_section(ih, dev, reps=3):
     torch.cuda.empty_cache()
     peak, _ = measured_peak()
     abytes = hh * ww + 4.0 * B * hh * ww
-    res = {"workload": "8192x8192 gray, 32 bins, bin-major int32 counts (no moment planes)",
+    res = {"workload": "%dx%d gray, 32 bins, bin-major int32 counts (no moment planes)" % (hh, ww),
            "kernel_ms": out, "tensors_equal": bool(equal)}
     t_scan, t_scan128, t_mma = (out["scan"].get("tiles/count"), out["scan_128x128"].get("tiles/count"),
                                 out["mma"].get("tiles/mma"))
@@ -1125,6 +1134,11 @@ def main(argv=None):
     ap.add_argument("--no-median", action="store_true", help="skip the spatio-temporal median video")
     ap.add_argument("--no-phog", action="store_true", help="skip the pyramid-of-orientations matching")
     ap.add_argument("--layout", choices=sorted(LAYOUTS), default="record", help="count-tensor layout")
+    ap.add_argument("--workload", choices=["wami", "fmv"], default="wami",
+                    help="the workload of the line (wami: the headline; fmv for profiling captures)")
+    ap.add_argument("--wami-side", type=int, default=WAMI_H,
+                    help="side of the headline frame (smaller only for profiling captures)")
+    ap.add_argument("--mma-side", type=int, default=8192, help="side of the frame of the mma_tiles section")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
         ap.error("--warmup must be >= 3")

@@ -373,6 +373,14 @@ ih_status ih_profile_select(ih_ctx *ctx, const char *const *names, int32_t n);
  * are this library's own kernels). */
 int64_t ih_launch_count(ih_ctx *ctx);
 
+/* Checks the device-side wait that the persistent batched build and the
+ * tensor-core tiles use: one thread waits, on `stream`, for a counter that
+ * nothing raises and gives up after `polls` polls (1..2^24, a few dozen ns
+ * apart), exactly as a wait whose producer never finishes would.  The next
+ * ih_sync() then returns IH_ETIMEOUT and clears the error; the context stays
+ * usable.  No GPU fault is involved. */
+ih_status ih_wait_selftest(ih_ctx *ctx, int32_t polls, void *stream);
+
 /* Bytes of the frames (count tensors and moment planes) the context owns now,
  * the quantity its HBM budget bounds (0 for a NULL context). */
 uint64_t ih_memory_used(ih_ctx *ctx);

@@ -977,6 +977,24 @@ int64_t ih_launch_count(ih_ctx *ctx)
     return ctx->launches;
 }
 
+ih_status ih_wait_selftest(ih_ctx *ctx, int32_t polls, void *stream)
+{
+    if (!ctx) return IH_EINVAL;
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    if (polls < 1 || polls > (1 << 24)) return fail(ctx, IH_EINVAL, "ih_wait_selftest: polls %d (1..2^24)", polls);
+    DevGuard dg(ctx->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int32_t *never = nullptr;
+    cudaError_t e = pool_alloc(ctx, &never, sizeof(int32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(never, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "self-test counter");
+    const int k = launch_wait_selftest(never, polls, ctx->d_err, st);
+    cudaFreeAsync(never, st);
+    if (k < 0) return cuda_fail(ctx, cudaGetLastError(), "self-test launch");
+    ctx->launches += k;
+    return IH_OK;
+}
+
 uint64_t ih_memory_used(ih_ctx *ctx)
 {
     if (!ctx) return 0;

@@ -242,6 +242,9 @@ struct PersistDev {
 };
 // Items of each kind of one frame (host).
 void persistent_counts(const PlaneSet &ps, int64_t *counts5);
+// One thread waits (bounded, `limit` polls) for *never >= 1; it gives up and
+// sets bit 2 of *err unless something raises the counter.
+int launch_wait_selftest(const int32_t *never, long limit, int *err, cudaStream_t st);
 // layout: the count layout of every frame, or -1 when the frames differ.
 int launch_build_persistent(const PersistDev &pd, int layout, int max_R, cudaStream_t st, const Prof *prof);
 // totals: the five totals over all frames (host).

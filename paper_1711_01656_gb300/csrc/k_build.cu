@@ -1428,6 +1428,31 @@ __device__ __forceinline__ int ld_acquire_gpu(const int32_t *p)
 
 // LAYOUT: the count layout of every frame of the batch, or -1 for a batch of
 // several layouts (each count-tile item then dispatches on its frame's).
+// Waits until *counter >= need, reading it with acquire semantics, for at
+// most `limit` polls (a few dozen ns apart); gives up early once bit 2 of
+// the error word is set (another wait gave up: the run is void).  On giving
+// up it sets bit 2 and returns false.  One thread of a CTA calls it.
+__device__ __forceinline__ bool bounded_wait_geq(const int32_t *counter, int need, long limit, int *err)
+{
+    long spins = 0;
+    while (ld_acquire_gpu(counter) < need) {
+        if (++spins > limit || (*(volatile int *)err & 2)) {
+            atomicOr(err, 2);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// Self-test of the bounded wait: one thread waits for a counter that nothing
+// raises and gives up after `limit` polls.
+__global__ void k_wait_selftest(const int32_t *never, long limit, int *err)
+{
+    pdl_wait();
+    if (threadIdx.x == 0 && blockIdx.x == 0) bounded_wait_geq(never, 1, limit, err);
+}
+
 template <int LAYOUT>
 __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const PersistDev pd)
 {
@@ -1447,23 +1472,9 @@ __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const Persist
         const PlaneSet &ps = pd.sets[seg.frame];
         const int phase = persist_phase(seg.kind);
         int32_t *done = pd.done + 3 * (int64_t)seg.frame;
-        if (tid == 0) {
-            int ok = 1;
-            if (phase > 0) {
-                const int need = pd.need[3 * (int64_t)seg.frame + phase - 1];
-                long spins = 0;
-                while (ld_acquire_gpu(done + phase - 1) < need) {
-                    // after one wait has given up, no other waits: the run is void
-                    if (++spins > kPSpinLimit || (*(volatile int *)pd.err & 2)) {
-                        ok = 0;
-                        atomicOr(pd.err, 2);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
-            }
-            s_abort = !ok;
-        }
+        if (tid == 0)
+            s_abort = phase > 0 && !bounded_wait_geq(done + phase - 1, pd.need[3 * (int64_t)seg.frame + phase - 1],
+                                                     kPSpinLimit, pd.err);
         __syncthreads();  // also: every thread has read s_t before it is taken again
         if (!s_abort) {
             const TileGrid &g = ps.g;
@@ -1686,6 +1697,12 @@ int persistent_ctas()
         ctas[dev] = std::max(1, per_sm) * std::max(1, nsm);
     }
     return ctas[dev];
+}
+
+int launch_wait_selftest(const int32_t *never, long limit, int *err, cudaStream_t st)
+{
+    launch_pdl(k_wait_selftest, 1, 32, 0, st, never, limit, err);
+    return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }
 
 int launch_build_persistent(const PersistDev &pd, int layout, int max_R, cudaStream_t st, const Prof *prof)

@@ -37,7 +37,7 @@ C_SYMBOLS = ("ih_create", "ih_build", "ih_query_rects", "ih_query_weighted", "ih
              "ih_batch_destroy", "ih_autotune", "ih_server_create", "ih_server_submit", "ih_server_poll",
              "ih_server_drain", "ih_server_clock", "ih_server_destroy", "ih_build_counts_static",
              "ih_match_window", "ih_accumulate", "ih_local_median", "ih_phog_build", "ih_phog_descriptors",
-             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges", "ih_server_cancel", "ih_memory_used", "ih_build_mma", "ih_tune_set")
+             "ih_phog_match", "ih_profile_select", "ih_query", "ih_canny_edges", "ih_server_cancel", "ih_memory_used", "ih_build_mma", "ih_tune_set", "ih_wait_selftest")
 IH_BATCH_GRAPH, IH_BATCH_AUTOTUNE, IH_BATCH_PERSISTENT = 1, 2, 4
 IH_CFG_PROFILE = 1
 
@@ -141,6 +141,7 @@ def load_library(path: str = LIB_PATH):
             "ih_memory_used": ([p], ctypes.c_uint64),
             "ih_build_mma": ([p, p, ctypes.POINTER(i32), p], i32),
             "ih_tune_set": ([p, p, i32, i32], i32),
+            "ih_wait_selftest": ([p, i32, p], i32),
             "ih_last_error": ([p], ctypes.c_char_p),
             "ih_build_counts_static": ([p, i32, i32, i64, i32, i32, p, i64, p], i32),
             "ih_batch_create": ([p, ctypes.POINTER(ih_frame), i32, ctypes.POINTER(ih_batch_queries), u32,
@@ -499,6 +500,12 @@ def ih_server_clock(srv) -> float:
 
 def ih_server_destroy(srv):
     _check(None, load_library().ih_server_destroy(srv))
+
+
+def ih_wait_selftest(ctx, polls, stream=None):
+    """A device-side wait on a counter nothing raises, given up after `polls`
+    polls: the next ih_sync raises IHError(IH_ETIMEOUT)."""
+    _check(ctx, load_library().ih_wait_selftest(ctx, int(polls), _stream(stream)))
 
 
 def ih_memory_used(ctx) -> int:

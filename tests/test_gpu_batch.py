@@ -267,3 +267,21 @@ def test_persistent_batch_of_many_frames(ihlib, ctx):
         ih.ih_batch_destroy(batch)
         for hd in handles:
             ih.ih_release(ctx, hd)
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(ihlib, ctx):
+    """The device-side wait of the persistent build gives up after its poll
+    limit when its producer never finishes (here: a counter nothing raises):
+    ih_sync reports IH_ETIMEOUT once, and the context then builds exactly."""
+    ih = ihlib
+    ih.ih_wait_selftest(ctx, 20000)
+    with pytest.raises(ih.IHError) as e:
+        ih.ih_sync(ctx)
+    assert e.value.status == ih.IH_ETIMEOUT
+    ih.ih_sync(ctx)  # the error word was cleared
+    img = synth.blob_plane(70, 90, 5)
+    h, = ih.ih_build(ctx, ih.Frame(torch.from_numpy(img).to(DEV)[None], [(8, 0)]))
+    assert np.array_equal(_export(ih, ctx, h).cpu().numpy(), oracle.integral_histogram(img, 8))
+    ih.ih_release(ctx, h)
+    with pytest.raises(ih.IHError):
+        ih.ih_wait_selftest(ctx, 0)
