@@ -80,7 +80,7 @@ const char *kernel_name(int kid)
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
                                            "local_median", "phog_build",     "phog_query",
-                                           "tile_sums", "queries",      "tiles/mma", "persistent_build"};
+                                           "tile_sums", "queries",      "tiles/mma", "persistent_build", "onepass_build"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -336,6 +336,7 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
     ps.out = fr.d_ih;
     ps.mom = fr.d_mom;
     ps.mom32 = fr.mbits == 32;
+    ps.err = ctx->d_err;
     ps.uni = 1;
     for (int c = 0; c < fr.nchan; ++c)
         if (f.chan[c].mode != 0) ps.uni = 0;

@@ -72,7 +72,8 @@ enum KernelId {
     KID_QUERY_BOTH = 16,  // rectangle and weighted queries of one frame in one launch
     KID_TILES_MMA = 17,   // count tiles as tensor-core products (k_mma.cu)
     KID_PERSISTENT = 18,  // tile sums, carry scan and tiles of a batch in one persistent launch
-    KID_COUNT = 19
+    KID_ONEPASS = 19,     // the one-pass build of a small frame
+    KID_COUNT = 20
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -182,8 +183,17 @@ struct PlaneSet {
     int64_t *l_c;         // [ns][Bw][H] L for w = c and c^2 (int64)
     int64_t *l_cc;
     int64_t *corner_w;    // [nb][ns][Bw][4] corners for w = c, r, c^2, r^2
+    // one-pass build of small frames (onepass_ok): per band and bin the
+    // published column counts (agg) and inclusive column prefixes (incl),
+    // [nb][B][W]; per band and group a flag, then a ticket counter
+    int32_t *agg, *incl, *flags;
+    int *err;             // the context's error word (bounded waits)
 };
 
+// True when a frame is built by the one-pass kernel (k_build_onepass): no
+// moment planes, bin-major or slab layout, bands of <= 32 rows, strips of
+// 128 columns, at most 16 strips, several tiles, and at most 2^26 count cells.
+bool onepass_ok(const PlaneSet &ps);
 // Bytes of carry scratch a plane set needs (0 for a single tile), and the
 // carving of one scratch block into the carry arrays.
 size_t carry_bytes(const PlaneSet &ps);

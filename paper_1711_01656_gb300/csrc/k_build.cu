@@ -781,9 +781,12 @@ __device__ __forceinline__ void store_record_staged(int32_t *row, int rec_w, int
 // LAYOUT_RECORD: NB = 8 is the group's width in the record and its
 // nb + nb1 <= NB real bins may come from two channels (SEG2); the padding
 // fields are never hit and hold 0.
+// tr: when not null, the tile's corner H(R0-1, C0-1) per bin of the group
+// (the one-pass build computes it in its CTA) instead of the sum of the
+// per-band corners of the bands above.
 template <int LAYOUT, int NB, bool SEG2, bool PAIR, bool UNI = false>
 __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int j, int gi, int lane,
-                                                 int32_t (*RL)[kGroupBins], int4 *stage)
+                                                 int32_t (*RL)[kGroupBins], int4 *stage, const int32_t *tr = nullptr)
 {
     const TileGrid &g = ps.g;
     const GroupDev gr = ps.grp[gi];
@@ -801,10 +804,14 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
     }
     int TR[NB];  // H(R0-1, chunk start - 1) per bin: the tile corner to begin with
 #pragma unroll
-    for (int b = 0; b < NB; ++b)
-        TR[b] = (ps.corner && b < nbr) ? sum_bands_above<int>(i, lane, [&](int ib) {
-            return ps.corner[((int64_t)ib * g.ns + j) * ps.B + bg0 + b];
-        }) : 0;
+    for (int b = 0; b < NB; ++b) {
+        if (tr)
+            TR[b] = b < nbr ? tr[b] : 0;
+        else
+            TR[b] = (ps.corner && b < nbr) ? sum_bands_above<int>(i, lane, [&](int ib) {
+                return ps.corner[((int64_t)ib * g.ns + j) * ps.B + bg0 + b];
+            }) : 0;
+    }
     __syncwarp();
 
     // the channels' descriptors in registers for the row loop
@@ -1068,6 +1075,24 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
 // groups and the tail of the grid is made of the cheapest units.
 // LAYOUT_RECORD: unit = tile * groups + group, so the groups sharing a
 // plane's records write them at about the same time.
+// The count unit of tile (i, j), group gi, with the group's template
+// arguments chosen at run time (non-record layouts).
+template <int LAYOUT, bool PAIR>
+__device__ __forceinline__ void tiles_count_at(const PlaneSet &ps, int i, int j, int gi, int lane,
+                                               int32_t (*RL)[kGroupBins], int4 *stage, const int32_t *tr)
+{
+    switch (ps.grp[gi].nb) {
+    case 1: tiles_count_unit<LAYOUT, 1, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    case 2: tiles_count_unit<LAYOUT, 2, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    case 3: tiles_count_unit<LAYOUT, 3, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    case 4: tiles_count_unit<LAYOUT, 4, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    case 5: tiles_count_unit<LAYOUT, 5, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    case 6: tiles_count_unit<LAYOUT, 6, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    case 7: tiles_count_unit<LAYOUT, 7, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    default: tiles_count_unit<LAYOUT, 8, false, PAIR>(ps, i, j, gi, lane, RL, stage, tr); break;
+    }
+}
+
 template <int LAYOUT, bool PAIR>
 __device__ __forceinline__ void tiles_count_dispatch(const PlaneSet &ps, int64_t unit, int lane,
                                                      int32_t (*RL)[kGroupBins], int4 *stage)
@@ -1538,6 +1563,194 @@ __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const Persist
     }
 }
 
+// ------------------------------------------------------------- one-pass build of small frames
+//
+// A frame without moment planes, in the bin-major or slab layout, cut into
+// bands of at most 32 rows and strips of 128 columns (at most 16 strips), is
+// built in ONE launch: CTA (band i, bin group g), one warp per strip.
+//  1. Each warp reads its strip of the band once: the column counts of the
+//     group's bins (8-bit fields) and, row by row, the strip's row counts
+//     (packed-field warp reductions, into shared memory).  The CTA publishes
+//     its column counts (the band's aggregate) and raises its flag to 1.
+//  2. Decoupled look-back over the bands above (Merrill & Garland, "Single-
+//     pass parallel prefix scan with decoupled look-back", NVIDIA 2016):
+//     each warp walks bands i-1, i-2, ..., adding a band's published
+//     inclusive column prefix (flag 2) and stopping, or its aggregate (flag
+//     1) and going on.  The sum is G: the column counts over all rows above
+//     the band.  The CTA publishes G plus its own counts and raises its flag
+//     to 2.  Flags are read with acquire semantics and the published sums
+//     with L2-only loads; every poll loop is bounded (a wait that gives up
+//     sets bit 2 of the error word: ih_sync reports IH_ETIMEOUT).
+//  3. In shared memory: each strip's row carries L (prefix over the strips to
+//     its left of the row counts, stored where the tiles body reads them)
+//     and its corner H(R0-1, C0-1) (prefix over the strips to its left of
+//     the totals of G).
+//  4. Each warp runs the count-tile body on its tile with those carries.
+// CTAs take (band, group) by ticket in band order, so every band a CTA
+// looks back at was taken by a CTA that is running or done.
+constexpr int kOneMaxStrips = 16;
+constexpr int kOneMaxRows = 32;
+constexpr long kOneSpinLimit = 1L << 22;
+
+struct OneSmem {
+    int32_t rowtot[kOneMaxStrips][kOneMaxRows][kGroupBins];  // row counts per strip
+    int32_t gtot[kOneMaxStrips][kGroupBins];                 // totals of G per strip
+    int32_t tr[kOneMaxStrips][kGroupBins];                   // corners
+    int32_t RL[kOneMaxStrips][kOneMaxRows][kGroupBins];      // the tiles body's row-carry buffers
+};
+
+__device__ __forceinline__ int ld_acquire_flag(const int32_t *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_flag(int32_t *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(kOneMaxStrips * 32) k_build_onepass(const __grid_constant__ PlaneSet ps)
+{
+    extern __shared__ __align__(16) unsigned char dsm[];
+    OneSmem &sm = *reinterpret_cast<OneSmem *>(dsm);
+    int4 *stages = reinterpret_cast<int4 *>(dsm + ((sizeof(OneSmem) + 15) & ~size_t(15)));
+    __shared__ unsigned int s_t;
+    pdl_wait();
+    const TileGrid &g = ps.g;
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_t = atomicAdd(reinterpret_cast<unsigned int *>(ps.flags) + g.nb * ps.ngroups, 1u);
+    __syncthreads();
+    const int i = (int)(s_t / ps.ngroups), gi = (int)(s_t % ps.ngroups);
+    const GroupDev gr = ps.grp[gi];
+    const ChanDev &ch = ps.chan[gr.chan];
+    const int nbg = gr.nb;
+    const int64_t bg0 = ch.bin_off + gr.b_lo;
+    const int R0 = i * g.R, nr = min(g.R, g.H - R0);
+    const int C0 = j * kChunk, c = C0 + 4 * lane;
+    const int nvalid = max(0, min(4, g.W - c));
+    const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
+    int32_t *flag = ps.flags + (int64_t)i * ps.ngroups + gi;
+
+    // 1. column counts (bins 0-3 and 4-7 of each column in 8-bit fields) and row counts
+    uint32_t colw[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int rr = 0; rr < nr; ++rr) {
+        const uint32_t px = load4(ch.plane, ch.pitch, R0 + rr, c, g.W, vec_ok);
+        uint32_t rw0 = 0, rw1 = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int b = bin_of((px >> (8 * q)) & 0xff, ch.bins, ch.mode) - gr.b_lo;
+            if (q < nvalid && b >= 0 && b < nbg) {
+                const uint32_t inc = 1u << (8 * (b & 3));
+                if (b < 4) {
+                    colw[q][0] += inc;
+                    rw0 += inc;
+                } else {
+                    colw[q][1] += inc;
+                    rw1 += inc;
+                }
+            }
+        }
+        rw0 = __reduce_add_sync(kFull, rw0);
+        rw1 = __reduce_add_sync(kFull, rw1);
+        if (lane < kGroupBins) sm.rowtot[j][rr][lane] = (int)(((lane < 4 ? rw0 : rw1) >> (8 * (lane & 3))) & 0xff);
+    }
+    int cnt[kGroupBins][4];
+#pragma unroll
+    for (int b = 0; b < kGroupBins; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cnt[b][q] = (int)((colw[q][b >> 2] >> (8 * (b & 3))) & 0xff);
+    const int64_t rowstride = (int64_t)g.W;
+    auto at = [&](int32_t *base, int band, int b, int q) { return base + ((int64_t)band * ps.B + bg0 + b) * rowstride + c + q; };
+    if (i + 1 < g.nb) {  // the last band's aggregate is never read
+#pragma unroll
+        for (int b = 0; b < kGroupBins; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (b < nbg && q < nvalid) *at(ps.agg, i, b, q) = cnt[b][q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && i + 1 < g.nb) {
+        __threadfence();
+        st_release_flag(flag, 1);
+    }
+    // 2. look-back: G = column counts of the rows above the band
+    int G[kGroupBins][4];
+#pragma unroll
+    for (int b = 0; b < kGroupBins; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) G[b][q] = 0;
+    bool ok = true;
+    for (int k = i - 1; k >= 0 && ok; --k) {
+        int f = 0;
+        if (lane == 0) {
+            const int32_t *fk = ps.flags + (int64_t)k * ps.ngroups + gi;
+            long spins = 0;
+            while ((f = ld_acquire_flag(fk)) == 0) {
+                if (++spins > kOneSpinLimit || (*(volatile int *)ps.err & 2)) {
+                    atomicOr(ps.err, 2);
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        f = __shfl_sync(kFull, f, 0);
+        if (f == 0) {
+            ok = false;
+            break;
+        }
+        int32_t *src = f == 2 ? ps.incl : ps.agg;
+#pragma unroll
+        for (int b = 0; b < kGroupBins; ++b)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (b < nbg && q < nvalid) G[b][q] += __ldcg(at(src, k, b, q));
+        if (f == 2) break;
+    }
+    // publish the inclusive prefix; G is the tiles' column carry
+#pragma unroll
+    for (int b = 0; b < kGroupBins; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (b < nbg && q < nvalid) {
+                if (i + 1 < g.nb) *at(ps.incl, i, b, q) = G[b][q] + cnt[b][q];
+                *at(ps.colsum, i, b, q) = G[b][q];
+            }
+    // strip totals of G for the corners
+#pragma unroll
+    for (int b = 0; b < kGroupBins; ++b) {
+        const int t = __reduce_add_sync(kFull, G[b][0] + G[b][1] + G[b][2] + G[b][3]);
+        if (lane == b) sm.gtot[j][b] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && i + 1 < g.nb) {
+        __threadfence();
+        st_release_flag(flag, 2);
+    }
+    // 3. corners and row carries of this warp's tile
+    if (lane < kGroupBins) {
+        int t = 0;
+        for (int jj = 0; jj < j; ++jj) t += sm.gtot[jj][lane];
+        sm.tr[j][lane] = t;
+    }
+    for (int k = lane; k < nr * kGroupBins; k += 32) {
+        const int rr = k / kGroupBins, b = k % kGroupBins;
+        int t = 0;
+        for (int jj = 0; jj < j; ++jj) t += sm.rowtot[jj][rr][b];
+        if (b < nbg) ps.rowsum[((int64_t)j * ps.B + bg0 + b) * g.H + R0 + rr] = t;
+    }
+    __syncwarp();
+    // 4. the tile (the body reads colsum[i], rowsum[j] of this band: written above by this CTA)
+    __syncthreads();
+    if (ok && C0 < g.W)
+        tiles_count_at<LAYOUT, false>(ps, i, j, gi, lane, sm.RL[j], stages + j * (32 * SlabStage<kGroupBins>::S),
+                                     sm.tr[j]);
+}
+
+size_t onepass_smem_bytes() { return ((sizeof(OneSmem) + 15) & ~size_t(15)) + sizeof(int4) * kOneMaxStrips * 32 * SlabStage<kGroupBins>::S; }
+
 template <typename F>
 void set_max_smem(F *f, size_t bytes)
 {
@@ -1557,12 +1770,24 @@ bool pdl_enabled()
     return on;
 }
 
+bool onepass_ok(const PlaneSet &ps)
+{
+    static const bool on = [] {
+        const char *e = getenv("IH_ONEPASS");
+        return !(e && e[0] == '0');
+    }();
+    const TileGrid &g = ps.g;
+    return on && !ps.mom && ps.wch < 0 && ps.layout != LAYOUT_RECORD && g.Wc == kChunk && g.R <= kOneMaxRows &&
+           g.ns <= kOneMaxStrips && (int64_t)g.nb * g.ns > 1 && (int64_t)ps.B * g.H * g.W <= ((int64_t)1 << 26);
+}
+
 size_t carry_bytes(const PlaneSet &ps)
 {
     const TileGrid &g = ps.g;
     if ((int64_t)g.nb * g.ns <= 1) return 0;
     const size_t B = ps.B, W = g.W, H = g.H, nb = g.nb, ns = g.ns;
     size_t n = r256(4 * B * W * nb) + r256(4 * B * H * ns) + 2 * r256(4 * nb * ns * B);
+    if (onepass_ok(ps)) n += 2 * r256(4 * B * W * nb) + r256(4 * (nb * (size_t)ps.ngroups + 1));
     if (ps.wch >= 0) {
         const size_t Bw = ps.chan[ps.wch].bins;
         n += 2 * r256(4 * Bw * W * nb) + 2 * r256(4 * Bw * H * ns) + r256(32 * nb * ns * Bw);
@@ -1575,6 +1800,7 @@ void carve_carries(PlaneSet &ps, void *base)
 {
     const TileGrid &g = ps.g;
     ps.colsum = ps.rowsum = ps.tilesum = ps.corner = nullptr;
+    ps.agg = ps.incl = ps.flags = nullptr;
     ps.col_su = ps.col_suu = ps.row_sv = ps.row_svv = nullptr;
     ps.tile_w = ps.g_r = ps.g_rr = ps.l_c = ps.l_cc = ps.corner_w = nullptr;
     if (!base || (int64_t)g.nb * g.ns <= 1) return;
@@ -1589,6 +1815,11 @@ void carve_carries(PlaneSet &ps, void *base)
     ps.rowsum = reinterpret_cast<int32_t *>(take(4 * B * H * ns));
     ps.tilesum = reinterpret_cast<int32_t *>(take(4 * nb * ns * B));
     ps.corner = reinterpret_cast<int32_t *>(take(4 * nb * ns * B));
+    if (onepass_ok(ps)) {
+        ps.agg = reinterpret_cast<int32_t *>(take(4 * B * W * nb));
+        ps.incl = reinterpret_cast<int32_t *>(take(4 * B * W * nb));
+        ps.flags = reinterpret_cast<int32_t *>(take(4 * (nb * (size_t)ps.ngroups + 1)));
+    }
     if (ps.wch >= 0) {
         const size_t Bw = ps.chan[ps.wch].bins;
         ps.col_su = reinterpret_cast<int32_t *>(take(4 * Bw * W * nb));
@@ -1619,6 +1850,8 @@ void prepare_kernels()
     if (dev < 0 || dev >= 64 || done[dev]) return;
     set_max_smem(k_tile_sums_all, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
     set_max_smem(k_tile_sums_all_b, std::max(sums_smem_bytes(kMaxBandRows, true), 2 * sizeof(CountSumsSmem)));
+    set_max_smem(k_build_onepass<LAYOUT_SLAB>, onepass_smem_bytes());
+    set_max_smem(k_build_onepass<LAYOUT_BIN_MAJOR>, onepass_smem_bytes());
     set_max_smem(k_build_persistent<-1>, persistent_smem_bytes(kMaxBandRows));
     set_max_smem(k_build_persistent<LAYOUT_SLAB>, persistent_smem_bytes(kMaxBandRows));
     set_max_smem(k_build_persistent<LAYOUT_RECORD>, persistent_smem_bytes(kMaxBandRows));
@@ -1762,6 +1995,20 @@ int launch_carries(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 {
     const TileGrid &g = ps.g;
+    if (ps.flags && ps.err && onepass_ok(ps)) {
+        prepare_kernels();
+        // flags and ticket start at zero; then one launch builds the frame
+        if (cudaMemsetAsync(ps.flags, 0, 4 * ((size_t)g.nb * ps.ngroups + 1), st) != cudaSuccess) return -1;
+        prof_mark(prof, KID_ONEPASS, 0, st);
+        if (ps.layout == LAYOUT_SLAB)
+            launch_pdl(k_build_onepass<LAYOUT_SLAB>, (unsigned)(g.nb * ps.ngroups), 32 * g.ns, onepass_smem_bytes(),
+                       st, ps);
+        else
+            launch_pdl(k_build_onepass<LAYOUT_BIN_MAJOR>, (unsigned)(g.nb * ps.ngroups), 32 * g.ns,
+                       onepass_smem_bytes(), st, ps);
+        prof_mark(prof, KID_ONEPASS, 1, st);
+        return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
+    }
     int n = launch_carries(ps, st, prof);
     if (n < 0) return -1;
     const int64_t units = (int64_t)g.nb * g.ns * ps.ngroups;

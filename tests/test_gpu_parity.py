@@ -850,3 +850,63 @@ def test_build_mma_multichannel_and_refusals(ihlib, ctx):
     for bad in (ihlib.Frame(pix, chans, layout=ihlib.IH_LAYOUT_SLAB), ihlib.Frame(pix, chans, weighted_channel=0)):
         with pytest.raises(ihlib.IHError):
             ihlib.ih_build_mma(ctx, bad)
+
+
+# ---------------------------------------------------------------- one-pass build of small frames
+
+@pytest.mark.parametrize("h,w,chans,layout", [
+    (480, 640, [(16, 0)], 0),            # the plain 640 x 480 frame
+    (9, 130, [(8, 0)], 0),               # two bands, two strips, ragged
+    (257, 2048, [(5, 0), (12, 1)], 1),   # 16 strips, slab layout, index channel
+    (33, 129, [(40, 0)], 0),             # 5 groups of 8 bins
+    (700, 300, [(3, 0)], 1),             # many bands: long look-back chains
+])
+def test_onepass_build_exact(ihlib, ctx, h, w, chans, layout):
+    """Small frames without moment planes are built in one launch (column
+    carries by look-back over bands): the tensor equals Algorithm 5 and the
+    rectangles the enumeration."""
+    planes = np.stack([synth.blob_plane(h, w, 400 + k) for k in range(len(chans))])
+    for k, (b, m) in enumerate(chans):
+        if m == 1:
+            planes[k] %= b + 2  # some values fall in no bin
+    hdl, _ = _build(ihlib, ctx, planes, chans, layout=layout)
+    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.frame_integral_histogram(planes, chans))
+    B = sum(b for b, _ in chans)
+    rects = synth.rects_uniform_corners(h, w, 400, 401)
+    assert np.array_equal(_rects_gpu(ihlib, ctx, hdl, rects, B).cpu().numpy(), oracle.frame_rect_hist(planes, chans, rects))
+    ihlib.ih_release(ctx, hdl)
+
+
+def test_onepass_and_three_kernel_builds_agree(ihlib, ctx, tmp_path):
+    """IH_ONEPASS=0 (read once per process) builds small frames with the tile
+    sums, carry scan and tiles kernels: the same bits as the one-pass build."""
+    import os
+    import subprocess
+    import sys
+    imgs = [synth.uniform_plane(480, 640, 410), synth.blob_plane(100, 1030, 411)]
+    for k, x in enumerate(imgs):
+        np.save(tmp_path / ("img%d.npy" % k), x)
+    script = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_01656_gb300 import ih
+d = sys.argv[2]
+dev = torch.device("cuda:0")
+c = ih.ih_create(0)
+outs = []
+for k in range(2):
+    img = np.load(d + "/img%d.npy" % k)
+    hd, = ih.ih_build(c, ih.Frame(torch.from_numpy(img).to(dev)[None], [(16, 0)]))
+    t = torch.empty((16,) + img.shape, dtype=torch.int32, device=dev)
+    ih.ih_export(c, hd, t)
+    ih.ih_sync(c)
+    outs.append(t.cpu().numpy().ravel())
+np.save(d + "/out_" + sys.argv[3] + ".npy", np.concatenate(outs))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for tag, one in (("one", "1"), ("three", "0")):
+        env = dict(os.environ, IH_ONEPASS=one)
+        subprocess.run([sys.executable, "-c", script, root, str(tmp_path), tag], env=env, check=True, timeout=600)
+    a, b = np.load(tmp_path / "out_one.npy"), np.load(tmp_path / "out_three.npy")
+    assert np.array_equal(a, b)
+    assert np.array_equal(a[:16 * 480 * 640].reshape(16, 480, 640), oracle.integral_histogram(imgs[0], 16))
