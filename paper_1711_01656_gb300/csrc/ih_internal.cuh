@@ -185,14 +185,16 @@ struct PlaneSet {
     int64_t *corner_w;    // [nb][ns][Bw][4] corners for w = c, r, c^2, r^2
     // one-pass build of small frames (onepass_ok): per band and bin the
     // published column counts (agg) and inclusive column prefixes (incl),
-    // [nb][B][W]; per band and group a flag, then a ticket counter
+    // [nb][B][P]; per band and group a flag, then a ticket counter
     int32_t *agg, *incl, *flags;
     int *err;             // the context's error word (bounded waits)
 };
 
-// True when a frame is built by the one-pass kernel (k_build_onepass): no
-// moment planes, bin-major or slab layout, bands of <= 32 rows, strips of
-// 128 columns, at most 16 strips, several tiles, and at most 2^26 count cells.
+// True when a frame is built by the one-pass kernel (k_build_onepass): a
+// context's frame (an error word for its bounded waits), no moment planes,
+// bin-major or slab layout, bands of <= 32 rows, strips of 128 columns, at
+// most 16 strips, several tiles, and at most 2^26 count cells.  IH_ONEPASS=0
+// in the environment (read once) turns it off.
 bool onepass_ok(const PlaneSet &ps);
 // Bytes of carry scratch a plane set needs (0 for a single tile), and the
 // carving of one scratch block into the carry arrays.

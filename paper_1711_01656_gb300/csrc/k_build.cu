@@ -1573,12 +1573,13 @@ __global__ void __launch_bounds__(kPThreads, 2) k_build_persistent(const Persist
 //     (packed-field warp reductions, into shared memory).  The CTA publishes
 //     its column counts (the band's aggregate) and raises its flag to 1.
 //  2. Decoupled look-back over the bands above (Merrill & Garland, "Single-
-//     pass parallel prefix scan with decoupled look-back", NVIDIA 2016):
-//     each warp walks bands i-1, i-2, ..., adding a band's published
-//     inclusive column prefix (flag 2) and stopping, or its aggregate (flag
-//     1) and going on.  The sum is G: the column counts over all rows above
-//     the band.  The CTA publishes G plus its own counts and raises its flag
-//     to 2.  Flags are read with acquire semantics and the published sums
+//     pass parallel prefix scan with decoupled look-back", NVIDIA 2016), 32
+//     bands at a time: each lane of a warp polls one band's flag; the
+//     nearest band whose inclusive column prefix is published (flag 2) ends
+//     the walk, and the aggregates (flag 1) of the bands before it are summed
+//     with independent loads.  The sum is G: the column counts over all rows
+//     above the band.  The CTA publishes G plus its own counts and raises its
+//     flag to 2.  Flags are read with acquire semantics and the published sums
 //     with L2-only loads; every poll loop is bounded (a wait that gives up
 //     sets bit 2 of the error word: ih_sync reports IH_ETIMEOUT).
 //  3. In shared memory: each strip's row carries L (prefix over the strips to
@@ -1662,31 +1663,35 @@ __global__ void __launch_bounds__(kOneMaxStrips * 32) k_build_onepass(const __gr
     for (int b = 0; b < kGroupBins; ++b)
 #pragma unroll
         for (int q = 0; q < 4; ++q) cnt[b][q] = (int)((colw[q][b >> 2] >> (8 * (b & 3))) & 0xff);
-    const int64_t rowstride = (int64_t)g.W;
-    auto at = [&](int32_t *base, int band, int b, int q) { return base + ((int64_t)band * ps.B + bg0 + b) * rowstride + c + q; };
-    if (i + 1 < g.nb) {  // the last band's aggregate is never read
+    // published sums: [band][bin][P] int32, 16-byte rows of 4 columns per lane
+    auto pub = [&](int32_t *base, int band, int b) {
+        return reinterpret_cast<int4 *>(base + ((int64_t)band * ps.B + bg0 + b) * g.P + c);
+    };
+    const bool inrow = c < g.P;
+    if (i + 1 < g.nb && inrow) {  // the last band's aggregate is never read
 #pragma unroll
         for (int b = 0; b < kGroupBins; ++b)
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (b < nbg && q < nvalid) *at(ps.agg, i, b, q) = cnt[b][q];
+            if (b < nbg) *pub(ps.agg, i, b) = make_int4(cnt[b][0], cnt[b][1], cnt[b][2], cnt[b][3]);
     }
     __syncthreads();
     if (threadIdx.x == 0 && i + 1 < g.nb) {
         __threadfence();
         st_release_flag(flag, 1);
     }
-    // 2. look-back: G = column counts of the rows above the band
+    // 2. warp-parallel look-back, 32 bands at a time: lane l polls band
+    // k_hi - l; the nearest band with its inclusive prefix published (flag 2)
+    // ends the walk, and the aggregates of the bands before it are summed
     int G[kGroupBins][4];
 #pragma unroll
     for (int b = 0; b < kGroupBins; ++b)
 #pragma unroll
         for (int q = 0; q < 4; ++q) G[b][q] = 0;
     bool ok = true;
-    for (int k = i - 1; k >= 0 && ok; --k) {
-        int f = 0;
-        if (lane == 0) {
-            const int32_t *fk = ps.flags + (int64_t)k * ps.ngroups + gi;
+    for (int k_hi = i - 1; k_hi >= 0;) {
+        const int kb = k_hi - lane;
+        int f = 2;  // bands before the first one count as a published zero prefix
+        if (kb >= 0) {
+            const int32_t *fk = ps.flags + (int64_t)kb * ps.ngroups + gi;
             long spins = 0;
             while ((f = ld_acquire_flag(fk)) == 0) {
                 if (++spins > kOneSpinLimit || (*(volatile int *)ps.err & 2)) {
@@ -1696,28 +1701,52 @@ __global__ void __launch_bounds__(kOneMaxStrips * 32) k_build_onepass(const __gr
                 __nanosleep(32);
             }
         }
-        f = __shfl_sync(kFull, f, 0);
-        if (f == 0) {
+        const unsigned lost = __ballot_sync(kFull, f == 0);
+        if (lost) {
             ok = false;
             break;
         }
-        int32_t *src = f == 2 ? ps.incl : ps.agg;
+        const unsigned incl = __ballot_sync(kFull, f == 2);
+        const int stop = incl ? __ffs(incl) - 1 : 32;  // bands k_hi .. k_hi - stop + 1: aggregates
+        if (inrow) {
+            for (int l = 0; l < stop; ++l) {
 #pragma unroll
-        for (int b = 0; b < kGroupBins; ++b)
+                for (int b = 0; b < kGroupBins; ++b)
+                    if (b < nbg) {
+                        const int4 v = __ldcg(pub(ps.agg, k_hi - l, b));
+                        G[b][0] += v.x;
+                        G[b][1] += v.y;
+                        G[b][2] += v.z;
+                        G[b][3] += v.w;
+                    }
+            }
+            if (stop < 32 && k_hi - stop >= 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (b < nbg && q < nvalid) G[b][q] += __ldcg(at(src, k, b, q));
-        if (f == 2) break;
+                for (int b = 0; b < kGroupBins; ++b)
+                    if (b < nbg) {
+                        const int4 v = __ldcg(pub(ps.incl, k_hi - stop, b));
+                        G[b][0] += v.x;
+                        G[b][1] += v.y;
+                        G[b][2] += v.z;
+                        G[b][3] += v.w;
+                    }
+            }
+        }
+        if (stop < 32) break;
+        k_hi -= 32;
     }
+    const int64_t rowstride = (int64_t)g.W;
+    auto at = [&](int32_t *base, int band, int b, int q) { return base + ((int64_t)band * ps.B + bg0 + b) * rowstride + c + q; };
     // publish the inclusive prefix; G is the tiles' column carry
 #pragma unroll
-    for (int b = 0; b < kGroupBins; ++b)
+    for (int b = 0; b < kGroupBins; ++b) {
+        if (b < nbg && i + 1 < g.nb && inrow)
+            *pub(ps.incl, i, b) = make_int4(G[b][0] + cnt[b][0], G[b][1] + cnt[b][1], G[b][2] + cnt[b][2],
+                                            G[b][3] + cnt[b][3]);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (b < nbg && q < nvalid) {
-                if (i + 1 < g.nb) *at(ps.incl, i, b, q) = G[b][q] + cnt[b][q];
-                *at(ps.colsum, i, b, q) = G[b][q];
-            }
+            if (b < nbg && q < nvalid) *at(ps.colsum, i, b, q) = G[b][q];
+    }
     // strip totals of G for the corners
 #pragma unroll
     for (int b = 0; b < kGroupBins; ++b) {
@@ -1777,7 +1806,7 @@ bool onepass_ok(const PlaneSet &ps)
         return !(e && e[0] == '0');
     }();
     const TileGrid &g = ps.g;
-    return on && !ps.mom && ps.wch < 0 && ps.layout != LAYOUT_RECORD && g.Wc == kChunk && g.R <= kOneMaxRows &&
+    return on && ps.err && !ps.mom && ps.wch < 0 && ps.layout != LAYOUT_RECORD && g.Wc == kChunk && g.R <= kOneMaxRows &&
            g.ns <= kOneMaxStrips && (int64_t)g.nb * g.ns > 1 && (int64_t)ps.B * g.H * g.W <= ((int64_t)1 << 26);
 }
 
@@ -1787,7 +1816,7 @@ size_t carry_bytes(const PlaneSet &ps)
     if ((int64_t)g.nb * g.ns <= 1) return 0;
     const size_t B = ps.B, W = g.W, H = g.H, nb = g.nb, ns = g.ns;
     size_t n = r256(4 * B * W * nb) + r256(4 * B * H * ns) + 2 * r256(4 * nb * ns * B);
-    if (onepass_ok(ps)) n += 2 * r256(4 * B * W * nb) + r256(4 * (nb * (size_t)ps.ngroups + 1));
+    if (onepass_ok(ps)) n += 2 * r256(4 * B * (size_t)g.P * nb) + r256(4 * (nb * (size_t)ps.ngroups + 1));
     if (ps.wch >= 0) {
         const size_t Bw = ps.chan[ps.wch].bins;
         n += 2 * r256(4 * Bw * W * nb) + 2 * r256(4 * Bw * H * ns) + r256(32 * nb * ns * Bw);
@@ -1816,8 +1845,8 @@ void carve_carries(PlaneSet &ps, void *base)
     ps.tilesum = reinterpret_cast<int32_t *>(take(4 * nb * ns * B));
     ps.corner = reinterpret_cast<int32_t *>(take(4 * nb * ns * B));
     if (onepass_ok(ps)) {
-        ps.agg = reinterpret_cast<int32_t *>(take(4 * B * W * nb));
-        ps.incl = reinterpret_cast<int32_t *>(take(4 * B * W * nb));
+        ps.agg = reinterpret_cast<int32_t *>(take(4 * B * (size_t)g.P * nb));
+        ps.incl = reinterpret_cast<int32_t *>(take(4 * B * (size_t)g.P * nb));
         ps.flags = reinterpret_cast<int32_t *>(take(4 * (nb * (size_t)ps.ngroups + 1)));
     }
     if (ps.wch >= 0) {
@@ -1995,7 +2024,7 @@ int launch_carries(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 {
     const TileGrid &g = ps.g;
-    if (ps.flags && ps.err && onepass_ok(ps)) {
+    if (ps.flags && onepass_ok(ps)) {
         prepare_kernels();
         // flags and ticket start at zero; then one launch builds the frame
         if (cudaMemsetAsync(ps.flags, 0, 4 * ((size_t)g.nb * ps.ngroups + 1), st) != cudaSuccess) return -1;
