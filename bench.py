@@ -460,6 +460,17 @@ def measure_step(ih, dev, spec, steps: int, warmup: int, world: int, flush, barr
         ih.ih_sync(ctx)
         prof = ih.ih_profile_read(ctx, reset=True)
         ih.ih_profile_select(ctx, [])
+        # the build alone (ih_build, events around it; release outside), L2 flushed
+        nb_ = max(3, min(steps, 20))
+        evb = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nb_)]
+        for k in range(nb_):
+            flush.fill_(k & 0xFF)
+            evb[k][0].record()
+            h, = ih.ih_build(ctx, spec.ih_frame(ih, d_in))
+            evb[k][1].record()
+            ih.ih_release(ctx, h)
+        torch.cuda.synchronize()
+        build_ms = sorted(a.elapsed_time(b) for a, b in evb)[nb_ // 2]
         del d_in
 
         h_in = torch.from_numpy(spec.frame).pin_memory()
@@ -522,7 +533,12 @@ def measure_step(ih, dev, spec, steps: int, warmup: int, world: int, flush, barr
     kernels = {k: {"launches": v[0], "total_ms": round(v[1], 4), "share": round(v[1] / total_ms, 4),
                    "gbs": round(spec_bytes(spec, k) / (v[1] / v[0] / 1e3) / 1e9, 1)}
                for k, v in sorted(prof_all.items(), key=lambda kv: -kv[1][1])}
+    build_bytes = spec_bytes(spec, "tiles/count+moments") + (3 * spec.H * spec.W if spec.rgb_input else 0)
     return {"value": spec.cells * steps * world / dev_max, "ms_per_step": 1e3 * dev_max / steps,
+            "build": {"ms_median": round(build_ms, 4), "algorithmic_bytes": build_bytes,
+                      "GBs": round(build_bytes / (build_ms / 1e3) / 1e9, 1),
+                      "frac_of_peak": round(build_bytes / (build_ms / 1e3) / 1e9 / measured_peak()[0], 4),
+                      "what": "ih_build alone (every build kernel of the frame), CUDA events, L2 flushed"},
             "e2e": {"value": spec.cells * steps * world / e2e_max, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": round(1e3 * e2e_max / steps, 4)},
             "roofline": roof, "kernels": kernels, "gpu_launches": int(launches),
@@ -563,7 +579,7 @@ def run_engine(args):
         fmv = measure_step(ih, dev, fmv_spec, args.fmv_steps, args.warmup, world, flush, barrier,
                            sample_clocks=False)
         fmv = {"workload": fmv_spec.workload, "value": fmv["value"], "unit": UNIT,
-               "ms_per_step": fmv["ms_per_step"], "steps": args.fmv_steps, "e2e": fmv["e2e"],
+               "ms_per_step": fmv["ms_per_step"], "steps": args.fmv_steps, "e2e": fmv["e2e"], "build": fmv["build"],
                "roofline": fmv["roofline"], "kernels": fmv["kernels"], "gpu_launches": fmv["gpu_launches"]}
     del flush
     torch.cuda.empty_cache()
@@ -604,7 +620,7 @@ def run_engine(args):
                        "e2e_pipeline": "dual buffering over two streams (Algorithm 10)",
                        "parallelism": "replicas: one frame per GPU, no collective",
                        "layout": LAYOUTS[args.layout][1]},
-            "roofline": m["roofline"], "cpu_baseline": cpu, "e2e": m["e2e"],
+            "roofline": m["roofline"], "cpu_baseline": cpu, "e2e": m["e2e"], "build": m["build"],
             "gpu_launches": m["gpu_launches"], "clocks": m["clocks"], "kernels": m["kernels"],
             "kernels_timed_in": "the warm-up steps (the timed steps carry events around the dominant kernel only)",
             "fmv": fmv, "wami_phases": wami, "plain": plain, "batched": batched, "served": served,

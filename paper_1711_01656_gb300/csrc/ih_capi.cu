@@ -337,6 +337,14 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
     ps.mom = fr.d_mom;
     ps.mom32 = fr.mbits == 32;
     ps.err = ctx->d_err;
+    if (it == ctx->tuned.end()) {
+        // a small frame built in one pass takes 16-row bands: fewer bands to
+        // look back over (the tiles of 128 columns stay)
+        PlaneSet t = ps;
+        t.g = make_grid(fr.H, fr.W, 16, kChunk);
+        t.g.P = fr.P;
+        if (onepass_ok(t)) ps.g = t.g;
+    }
     ps.uni = 1;
     for (int c = 0; c < fr.nchan; ++c)
         if (f.chan[c].mode != 0) ps.uni = 0;

@@ -193,8 +193,9 @@ struct PlaneSet {
 // True when a frame is built by the one-pass kernel (k_build_onepass): a
 // context's frame (an error word for its bounded waits), no moment planes,
 // bin-major or slab layout, bands of <= 32 rows, strips of 128 columns, at
-// most 16 strips, several tiles, and at most 2^26 count cells.  IH_ONEPASS=0
-// in the environment (read once) turns it off.
+// most 16 strips, several tiles, and at most 2^26 count cells, when
+// IH_ONEPASS=1 is in the environment (read once): measured slower than the
+// three-kernel build on the 640 x 480 frame, so it is off by default.
 bool onepass_ok(const PlaneSet &ps);
 // Bytes of carry scratch a plane set needs (0 for a single tile), and the
 // carving of one scratch block into the carry arrays.

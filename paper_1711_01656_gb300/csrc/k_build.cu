@@ -1637,8 +1637,16 @@ __global__ void __launch_bounds__(kOneMaxStrips * 32) k_build_onepass(const __gr
 
     // 1. column counts (bins 0-3 and 4-7 of each column in 8-bit fields) and row counts
     uint32_t colw[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int rr = 0; rr < nr; ++rr) {
-        const uint32_t px = load4(ch.plane, ch.pitch, R0 + rr, c, g.W, vec_ok);
+    for (int r8 = 0; r8 < nr; r8 += 8) {
+      // the loads of 8 rows in flight at once
+      uint32_t pxs[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) pxs[k] = r8 + k < nr ? load4(ch.plane, ch.pitch, R0 + r8 + k, c, g.W, vec_ok) : 0u;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int rr = r8 + k;
+        if (rr >= nr) break;
+        const uint32_t px = pxs[k];
         uint32_t rw0 = 0, rw1 = 0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -1657,6 +1665,7 @@ __global__ void __launch_bounds__(kOneMaxStrips * 32) k_build_onepass(const __gr
         rw0 = __reduce_add_sync(kFull, rw0);
         rw1 = __reduce_add_sync(kFull, rw1);
         if (lane < kGroupBins) sm.rowtot[j][rr][lane] = (int)(((lane < 4 ? rw0 : rw1) >> (8 * (lane & 3))) & 0xff);
+      }
     }
     int cnt[kGroupBins][4];
 #pragma unroll
@@ -1774,7 +1783,7 @@ __global__ void __launch_bounds__(kOneMaxStrips * 32) k_build_onepass(const __gr
     // 4. the tile (the body reads colsum[i], rowsum[j] of this band: written above by this CTA)
     __syncthreads();
     if (ok && C0 < g.W)
-        tiles_count_at<LAYOUT, false>(ps, i, j, gi, lane, sm.RL[j], stages + j * (32 * SlabStage<kGroupBins>::S),
+        tiles_count_at<LAYOUT, true>(ps, i, j, gi, lane, sm.RL[j], stages + j * (32 * SlabStage<kGroupBins>::S),
                                      sm.tr[j]);
 }
 
@@ -1803,7 +1812,7 @@ bool onepass_ok(const PlaneSet &ps)
 {
     static const bool on = [] {
         const char *e = getenv("IH_ONEPASS");
-        return !(e && e[0] == '0');
+        return e && e[0] == '1';
     }();
     const TileGrid &g = ps.g;
     return on && ps.err && !ps.mom && ps.wch < 0 && ps.layout != LAYOUT_RECORD && g.Wc == kChunk && g.R <= kOneMaxRows &&

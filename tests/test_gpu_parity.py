@@ -854,59 +854,64 @@ def test_build_mma_multichannel_and_refusals(ihlib, ctx):
 
 # ---------------------------------------------------------------- one-pass build of small frames
 
-@pytest.mark.parametrize("h,w,chans,layout", [
+_ONEPASS_CASES = [
     (480, 640, [(16, 0)], 0),            # the plain 640 x 480 frame
-    (9, 130, [(8, 0)], 0),               # two bands, two strips, ragged
+    (9, 130, [(8, 0)], 0),               # one band, two strips, ragged
     (257, 2048, [(5, 0), (12, 1)], 1),   # 16 strips, slab layout, index channel
     (33, 129, [(40, 0)], 0),             # 5 groups of 8 bins
     (700, 300, [(3, 0)], 1),             # many bands: long look-back chains
-])
-def test_onepass_build_exact(ihlib, ctx, h, w, chans, layout):
-    """Small frames without moment planes are built in one launch (column
-    carries by look-back over bands): the tensor equals Algorithm 5 and the
-    rectangles the enumeration."""
-    planes = np.stack([synth.blob_plane(h, w, 400 + k) for k in range(len(chans))])
-    for k, (b, m) in enumerate(chans):
-        if m == 1:
-            planes[k] %= b + 2  # some values fall in no bin
-    hdl, _ = _build(ihlib, ctx, planes, chans, layout=layout)
-    assert np.array_equal(_export(ihlib, ctx, hdl), oracle.frame_integral_histogram(planes, chans))
-    B = sum(b for b, _ in chans)
-    rects = synth.rects_uniform_corners(h, w, 400, 401)
-    assert np.array_equal(_rects_gpu(ihlib, ctx, hdl, rects, B).cpu().numpy(), oracle.frame_rect_hist(planes, chans, rects))
-    ihlib.ih_release(ctx, hdl)
+]
 
-
-def test_onepass_and_three_kernel_builds_agree(ihlib, ctx, tmp_path):
-    """IH_ONEPASS=0 (read once per process) builds small frames with the tile
-    sums, carry scan and tiles kernels: the same bits as the one-pass build."""
-    import os
-    import subprocess
-    import sys
-    imgs = [synth.uniform_plane(480, 640, 410), synth.blob_plane(100, 1030, 411)]
-    for k, x in enumerate(imgs):
-        np.save(tmp_path / ("img%d.npy" % k), x)
-    script = r'''
+_ONEPASS_SCRIPT = r'''
 import sys, numpy as np, torch
 sys.path.insert(0, sys.argv[1])
 from paper_1711_01656_gb300 import ih
-d = sys.argv[2]
+d, n = sys.argv[2], int(sys.argv[4])
 dev = torch.device("cuda:0")
 c = ih.ih_create(0)
-outs = []
-for k in range(2):
-    img = np.load(d + "/img%d.npy" % k)
-    hd, = ih.ih_build(c, ih.Frame(torch.from_numpy(img).to(dev)[None], [(16, 0)]))
-    t = torch.empty((16,) + img.shape, dtype=torch.int32, device=dev)
+for k in range(n):
+    z = np.load(d + "/case%d.npz" % k)
+    planes, bins, modes, layout, rects = z["planes"], z["bins"], z["modes"], int(z["layout"]), z["rects"]
+    chans = [(int(b), int(m)) for b, m in zip(bins, modes)]
+    hd, = ih.ih_build(c, ih.Frame(torch.from_numpy(planes).to(dev), chans, layout=layout))
+    B = int(bins.sum())
+    t = torch.empty((B,) + planes.shape[1:], dtype=torch.int32, device=dev)
     ih.ih_export(c, hd, t)
+    r = torch.empty((len(rects), B), dtype=torch.int32, device=dev)
+    ih.ih_query_rects(c, hd, torch.from_numpy(rects).to(dev), r)
     ih.ih_sync(c)
-    outs.append(t.cpu().numpy().ravel())
-np.save(d + "/out_" + sys.argv[3] + ".npy", np.concatenate(outs))
+    np.savez(d + "/out%d_%s.npz" % (k, sys.argv[3]), t=t.cpu().numpy(), r=r.cpu().numpy())
+    ih.ih_release(c, hd)
+ih.ih_destroy(c)
 '''
+
+
+def test_onepass_build_exact_and_equal_to_three_kernels(ihlib, tmp_path):
+    """IH_ONEPASS=1 (read once per process) builds small frames without
+    moment planes in one launch (column carries by decoupled look-back over
+    bands): the tensors equal Algorithm 5, the rectangles the enumeration,
+    and both equal the three-kernel build (IH_ONEPASS=0) bit for bit."""
+    import os
+    import subprocess
+    import sys
+    cases = []
+    for k, (h, w, chans, layout) in enumerate(_ONEPASS_CASES):
+        planes = np.stack([synth.blob_plane(h, w, 400 + 10 * k + c) for c in range(len(chans))])
+        for c, (b, m) in enumerate(chans):
+            if m == 1:
+                planes[c] %= b + 2  # some values fall in no bin
+        rects = synth.rects_uniform_corners(h, w, 300, 401 + k)
+        np.savez(tmp_path / ("case%d.npz" % k), planes=planes, bins=np.array([b for b, _ in chans]),
+                 modes=np.array([m for _, m in chans]), layout=layout, rects=rects)
+        cases.append((planes, chans, rects))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for tag, one in (("one", "1"), ("three", "0")):
         env = dict(os.environ, IH_ONEPASS=one)
-        subprocess.run([sys.executable, "-c", script, root, str(tmp_path), tag], env=env, check=True, timeout=600)
-    a, b = np.load(tmp_path / "out_one.npy"), np.load(tmp_path / "out_three.npy")
-    assert np.array_equal(a, b)
-    assert np.array_equal(a[:16 * 480 * 640].reshape(16, 480, 640), oracle.integral_histogram(imgs[0], 16))
+        subprocess.run([sys.executable, "-c", _ONEPASS_SCRIPT, root, str(tmp_path), tag, str(len(cases))], env=env,
+                       check=True, timeout=600)
+    for k, (planes, chans, rects) in enumerate(cases):
+        one = np.load(tmp_path / ("out%d_one.npz" % k))
+        three = np.load(tmp_path / ("out%d_three.npz" % k))
+        assert np.array_equal(one["t"], three["t"]) and np.array_equal(one["r"], three["r"]), k
+        assert np.array_equal(one["t"], oracle.frame_integral_histogram(planes, chans)), k
+        assert np.array_equal(one["r"], oracle.frame_rect_hist(planes, chans, rects)), k
