@@ -1280,14 +1280,18 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                     acc[3][jj] += r2 * (long long)N;
                 }
                 if (c < g.P) {
-                    const int64_t o = (int64_t)(R0 + rr) * g.P + c;
                     if (M32) {
-                        // the quads modulo 2^32: one 16-byte store per pixel
+                        // the quads modulo 2^32 (16 bytes per pixel) through the
+                        // warp's stage: unit u = px at position u ^ ((u >> 3) & 7)
+                        // (conflict-free writes of 4 units per lane and reads of
+                        // 32 consecutive units per store)
+                        uint4 *s4 = reinterpret_cast<uint4 *>(stage);
 #pragma unroll
-                        for (int jj = 0; jj < 4; ++jj)
-                            *reinterpret_cast<uint4 *>(mo32 + (o + jj) * 4) =
-                                make_uint4((uint32_t)acc[0][jj], (uint32_t)acc[1][jj], (uint32_t)acc[2][jj],
-                                           (uint32_t)acc[3][jj]);
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int u = 4 * lane + jj;
+                            s4[u ^ ((u >> 3) & 7)] = make_uint4((uint32_t)acc[0][jj], (uint32_t)acc[1][jj],
+                                                                (uint32_t)acc[2][jj], (uint32_t)acc[3][jj]);
+                        }
                     } else {
                         // through the warp's stage: the row's 128 quads are 256
                         // 16-byte units, unit u = 2 px + h holding planes 2h, 2h+1
@@ -1302,7 +1306,17 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                         }
                     }
                 }
-                if (!M32) {
+                if (M32) {
+                    __syncwarp();
+                    // each store writes 512 contiguous bytes of the row's 2 KB of quads
+                    uint4 *dst = reinterpret_cast<uint4 *>(mo32 + ((int64_t)(R0 + rr) * g.P + cc) * 4);
+                    const uint4 *s4 = reinterpret_cast<const uint4 *>(stage);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int u = 32 * m + lane;
+                        if (cc + u < g.P) dst[u] = s4[u ^ ((u >> 3) & 7)];
+                    }
+                } else {
                     __syncwarp();
                     // each store writes 512 contiguous bytes of the row's 4 KB of quads
                     longlong2 *dst = reinterpret_cast<longlong2 *>(mo + ((int64_t)(R0 + rr) * g.P + cc) * 4);
@@ -1956,10 +1970,12 @@ void persistent_counts(const PlaneSet &ps, int64_t *c)
 int persistent_ctas()
 {
     prepare_kernels();
+    static std::mutex mu;
     static int ctas[64] = {0};
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64) return 1;
+    std::lock_guard<std::mutex> lk(mu);
     if (!ctas[dev]) {
         int per_sm = 0, nsm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_persistent<-1>, kPThreads,

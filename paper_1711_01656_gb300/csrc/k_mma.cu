@@ -33,6 +33,8 @@
 // returns.
 #include <stdint.h>
 
+#include <mutex>
+
 #include "ih_internal.cuh"
 
 namespace ih {
@@ -330,10 +332,18 @@ size_t mma_smem_bytes() { return sizeof(MmaSmem) + 1024; }
 
 int launch_tiles_mma(const PlaneSet &ps, int *err, cudaStream_t st, const Prof *prof)
 {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_tiles_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma_smem_bytes());
-        attr = true;
+    // the shared-memory limit is an attribute of the kernel on the current
+    // device: set it once per device, under a lock
+    static std::mutex mu;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev >= 0 && dev < 64 && !done[dev]) {
+            cudaFuncSetAttribute(k_tiles_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mma_smem_bytes());
+            done[dev] = true;
+        }
     }
     prof_mark(prof, KID_TILES_MMA, 0, st);
     launch_pdl(k_tiles_mma, dim3(ps.g.ns, ps.g.nb, ps.nchan), kMThreads, mma_smem_bytes(), st, ps, err);
