@@ -321,7 +321,10 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
         const uint8_t *planes[kMaxChannels];
         int64_t cpitch[kMaxChannels];
         frame_planes(f, feat, fp, planes, cpitch);
-        if (!make_planeset(ctx, f, fr, planes, cpitch, sets[k])) return bail(fail(ctx, IH_EINVAL, "too many bins"));
+        // a one-frame batch runs the single-frame kernels, the small-frame build included
+        const bool one = n == 1 && !(flags & IH_BATCH_PERSISTENT);
+        if (!make_planeset(ctx, f, fr, planes, cpitch, sets[k], one))
+            return bail(fail(ctx, IH_EINVAL, "too many bins"));
     }
     batch_grids(sets.data(), n, ctx->nsm);
     for (int k = 0; k < n; ++k) carry_total += (carry_bytes(sets[k]) + 255) & ~size_t(255);

@@ -80,7 +80,8 @@ const char *kernel_name(int kid)
                                            "query_rects",   "query_weighted",  "export",
                                            "tiles/count+moments", "match_window", "accumulate",
                                            "local_median", "phog_build",     "phog_query",
-                                           "tile_sums", "queries",      "tiles/mma", "persistent_build", "onepass_build"};
+                                           "tile_sums", "queries",      "tiles/mma", "persistent_build", "onepass_build",
+                                           "small_build"};
     return (kid >= 0 && kid < KID_COUNT) ? names[kid] : "?";
 }
 
@@ -309,7 +310,7 @@ std::string shape_key(const ih_frame &f)
 }
 
 bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uint8_t *const *planes,
-                   const int64_t *cpitch, PlaneSet &ps)
+                   const int64_t *cpitch, PlaneSet &ps, bool small)
 {
     memset(&ps, 0, sizeof ps);
     ps.B = fr.B;
@@ -348,6 +349,9 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
     ps.uni = 1;
     for (int c = 0; c < fr.nchan; ++c)
         if (f.chan[c].mode != 0) ps.uni = 0;
+    // a single frame too small to fill the GPU with the three-kernel build
+    // is built by one cooperative launch (its own tile grid)
+    if (small && it == ctx->tuned.end() && !onepass_ok(ps)) small_plan(ps, ctx->nsm);
     return true;
 }
 
@@ -487,7 +491,8 @@ ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_
             }
         }
         PlaneSet ps;
-        if (!make_planeset(ctx, f, fr, planes, cpitch, ps)) return fail(ctx, IH_EINVAL, "too many bins for one build");
+        if (!make_planeset(ctx, f, fr, planes, cpitch, ps, true))
+            return fail(ctx, IH_EINVAL, "too many bins for one build");
         void *scratch = nullptr;
         const size_t cb = carry_bytes(ps);
         if (cb) {

@@ -97,9 +97,10 @@ int record_plan(const int *bins, int nchan, GroupDev *sp, int max_sp, int16_t *r
 void frame_record(const ih_frame &f, FrameRec &fr);
 // The plane set of one frame: channels, bin groups, tile grid (tuned if the
 // context has a tuned grid for this shape), slab offsets, outputs.  Carries
-// are left null.
+// are left null.  small: a single frame that may take the small-frame build
+// (one cooperative launch, small_plan) when it qualifies.
 bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uint8_t *const *planes,
-                   const int64_t *cpitch, PlaneSet &ps);
+                   const int64_t *cpitch, PlaneSet &ps, bool small = false);
 std::string shape_key(const ih_frame &f);
 void make_view(const PlaneSet &ps, const int32_t *d, CountView &v);
 FrameRec *get_frame(ih_ctx *ctx, int32_t handle);

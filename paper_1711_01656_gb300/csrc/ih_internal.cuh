@@ -73,7 +73,8 @@ enum KernelId {
     KID_TILES_MMA = 17,   // count tiles as tensor-core products (k_mma.cu)
     KID_PERSISTENT = 18,  // tile sums, carry scan and tiles of a batch in one persistent launch
     KID_ONEPASS = 19,     // the one-pass build of a small frame
-    KID_COUNT = 20
+    KID_SMALL = 20,       // the small-frame build (one cooperative launch)
+    KID_COUNT = 21
 };
 
 // Optional launch hook: mark(ctx, kid, 0, st) before a kernel is launched on
@@ -187,6 +188,15 @@ struct PlaneSet {
     // published column counts (agg) and inclusive column prefixes (incl),
     // [nb][B][P]; per band and group a flag, then a ticket counter
     int32_t *agg, *incl, *flags;
+    // small-frame build (small_plan): rows per warp (0: not planned), and per
+    // tile its packed column counts [ngroups][nb][ns][256], per strip its
+    // packed row counts [ns][ngroups][H][2], per tile its bin totals
+    // [nb][ns][ngroups][8], and the grid barrier's arrival counter (zero
+    // before the launch)
+    int32_t small;
+    uint32_t *sm_col, *sm_row;
+    int32_t *sm_tot;
+    unsigned int *sm_bar;
     int *err;             // the context's error word (bounded waits)
 };
 
@@ -197,6 +207,18 @@ struct PlaneSet {
 // IH_ONEPASS=1 is in the environment (read once): measured slower than the
 // three-kernel build on the 640 x 480 frame, so it is off by default.
 bool onepass_ok(const PlaneSet &ps);
+// Small-frame build (k_small.cu): when a count-only frame in the bin-major
+// or slab layout is small enough that every tile of a 128-column grid fits
+// the GPU at once, picks the band height (ps.g) and rows per warp
+// (ps.small) and returns true; the frame is then built by one cooperative
+// launch.  IH_SMALL=0 in the environment (read once) turns it off.
+bool small_plan(PlaneSet &ps, int nsm);
+// Scratch bytes of a small-frame build, and its carving.
+size_t small_bytes(const PlaneSet &ps);
+void carve_small(PlaneSet &ps, void *base);
+// The small-frame build (memset of the barrier counter + one launch);
+// returns the number of kernels launched, or -1.
+int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof);
 // Bytes of carry scratch a plane set needs (0 for a single tile), and the
 // carving of one scratch block into the carry arrays.
 size_t carry_bytes(const PlaneSet &ps);

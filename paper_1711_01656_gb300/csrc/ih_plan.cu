@@ -48,6 +48,7 @@ void batch_grids(PlaneSet *sets, int n, int nsm)
     // supply the parallelism, and large tiles carry less (the 64-frame FMV
     // batch: 35.1 ms with per-shape tuned tiles, 32.8 ms with 128 x 512)
     long long units = 0;
+    if (n == 1 && sets[0].small) return;  // a single small frame keeps its own grid
     for (int k = 0; k < n; ++k) {
         const TileGrid g = make_grid(sets[k].g.H, sets[k].g.W, kBatchR, kBatchWc);
         units += (long long)g.nb * g.ns * sets[k].ngroups;

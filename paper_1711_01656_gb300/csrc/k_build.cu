@@ -47,12 +47,12 @@
 #include <stdlib.h>
 
 #include "ih_internal.cuh"
+#include "k_tilecore.cuh"
 
 namespace ih {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
 // count tiles: two rows in flight per step (more ILP) or one (fewer
 // registers, so that 4 CTAs fit an SM); the record layout's units, whose
 // group may draw on two channels, take the second
@@ -61,42 +61,6 @@ constexpr bool pair_rows() { return LAYOUT != LAYOUT_RECORD; }
 // (the batched kernel, which serves every layout with one register budget,
 // always takes the first)
 constexpr int kQStride = kSumCols + 4;  // padded row of the staged byte tile
-
-// Eq. 2.15's Q: the channel-local bin of value v, or -1 for none.
-__device__ __forceinline__ int bin_of(int v, int bins, int mode)
-{
-    if (mode == 0) return (v * bins) >> 8;
-    return v < bins ? v : -1;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_incl_scan(T x, int lane)
-{
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const T y = __shfl_up_sync(kFull, x, d);
-        if (lane >= d) x += y;
-    }
-    return x;
-}
-
-// The 4 pixels (r, c..c+3) of a channel as packed bytes (pixel j in byte j);
-// bytes at or beyond `cend` are 0 and must be masked by the caller.
-__device__ __forceinline__ uint32_t load4(const uint8_t *plane, int64_t pitch, int r, int c, int cend, bool vec_ok)
-{
-    const uint8_t *row = plane + (int64_t)r * pitch;
-    if (vec_ok && c + 3 < cend) return __ldg(reinterpret_cast<const unsigned int *>(row + c));
-    uint32_t v = 0;
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj)
-        if (c + jj < cend) v |= (uint32_t)__ldg(row + c + jj) << (8 * jj);
-    return v;
-}
-
-__device__ __forceinline__ uint32_t load4(const ChanDev &ch, int r, int c, int cend, bool vec_ok)
-{
-    return load4(ch.plane, ch.pitch, r, c, cend, vec_ok);
-}
 
 // ------------------------------------------------------------- tile sums
 
@@ -703,79 +667,6 @@ __device__ __forceinline__ T sum_bands_above(int i, int lane, F at)
 }
 
 // ------------------------------------------------------------- count tiles
-
-// Slab-layout row store through a per-warp shared buffer.  Lane L's 4
-// pixel records (NB int4 units) go to units L*S + k, S the smallest odd
-// number > NB, so that both the writes and the reads below hit 8 distinct
-// 16-byte bank groups per 8 lanes; the warp then stores the row segment
-// (32*NB units, contiguous in global memory) with lane L writing units
-// 32m + L: every store instruction covers 512 contiguous bytes.
-template <int NB>
-struct SlabStage {
-    static constexpr int S = (NB + 1) | 1;
-};
-
-template <int NB>
-__device__ __forceinline__ void store_slab_staged(int32_t *seg, int npx, const int (&acc)[NB][4], int4 *stage,
-                                                  int lane)
-{
-    constexpr int S = SlabStage<NB>::S;
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        int v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int f = 4 * k + e;  // flat index: pixel f / NB, bin f % NB
-            v[e] = acc[f % NB][f / NB];
-        }
-        stage[lane * S + k] = make_int4(v[0], v[1], v[2], v[3]);
-    }
-    __syncwarp();
-    // units of pixels below npx (the segment's valid pixels, a multiple of 4)
-    const int nunits = npx / 4 * NB;
-#pragma unroll
-    for (int m = 0; m < NB; ++m) {
-        const int u = 32 * m + lane;
-        if (u < nunits) reinterpret_cast<int4 *>(seg)[u] = stage[(u / NB) * S + (u % NB)];
-    }
-}
-
-// Record-layout row store through the same per-warp buffer.  Each of the
-// segment's npx pixels owns an NB-word chunk (NB = 8: one whole 32-byte
-// sector, so no sector is shared with another warp) at a stride of rec_w
-// words; unit u = 32m + L of the row is quarter u % (NB/4) of pixel
-// u / (NB/4), so consecutive lanes write consecutive 16-byte pieces of
-// consecutive chunks.
-template <int NB>
-__device__ __forceinline__ void store_record_staged(int32_t *row, int rec_w, int npx, const int (&acc)[NB][4],
-                                                    int4 *stage, int lane)
-{
-    static_assert(NB == 4 || NB == 8, "record chunks are 4 or 8 words");
-    constexpr int S = SlabStage<NB>::S, Q = NB / 4;
-    __syncwarp();
-#pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        int v[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int f = 4 * k + e;  // flat index: pixel f / NB, bin f % NB
-            v[e] = acc[f % NB][f / NB];
-        }
-        stage[lane * S + k] = make_int4(v[0], v[1], v[2], v[3]);
-    }
-    __syncwarp();
-    const int nunits = npx * Q;
-#pragma unroll
-    for (int m = 0; m < NB; ++m) {
-        const int u = 32 * m + lane;
-        if (u < nunits) {
-            const int L = u / NB, k = u % NB;
-            const int px = 4 * L + k / Q, q = k % Q;
-            *reinterpret_cast<int4 *>(row + (int64_t)px * rec_w + 4 * q) = stage[L * S + k];
-        }
-    }
-}
 
 // One warp-unit of the count tiles: tile (i, j), group gi of exactly NB bins.
 // LAYOUT_RECORD: NB = 8 is the group's width in the record and its
@@ -1836,6 +1727,7 @@ bool onepass_ok(const PlaneSet &ps)
 size_t carry_bytes(const PlaneSet &ps)
 {
     const TileGrid &g = ps.g;
+    if (ps.small) return small_bytes(ps);
     if ((int64_t)g.nb * g.ns <= 1) return 0;
     const size_t B = ps.B, W = g.W, H = g.H, nb = g.nb, ns = g.ns;
     size_t n = r256(4 * B * W * nb) + r256(4 * B * H * ns) + 2 * r256(4 * nb * ns * B);
@@ -1855,6 +1747,13 @@ void carve_carries(PlaneSet &ps, void *base)
     ps.agg = ps.incl = ps.flags = nullptr;
     ps.col_su = ps.col_suu = ps.row_sv = ps.row_svv = nullptr;
     ps.tile_w = ps.g_r = ps.g_rr = ps.l_c = ps.l_cc = ps.corner_w = nullptr;
+    ps.sm_col = ps.sm_row = nullptr;
+    ps.sm_tot = nullptr;
+    ps.sm_bar = nullptr;
+    if (base && ps.small) {
+        carve_small(ps, base);
+        return;
+    }
     if (!base || (int64_t)g.nb * g.ns <= 1) return;
     char *s = static_cast<char *>(base);
     const size_t B = ps.B, W = g.W, H = g.H, nb = g.nb, ns = g.ns;
@@ -2049,6 +1948,7 @@ int launch_carries(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 int launch_build(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 {
     const TileGrid &g = ps.g;
+    if (ps.small && ps.sm_bar) return launch_build_small(ps, st, prof);
     if (ps.flags && onepass_ok(ps)) {
         prepare_kernels();
         // flags and ticket start at zero; then one launch builds the frame

@@ -906,7 +906,7 @@ def test_onepass_build_exact_and_equal_to_three_kernels(ihlib, tmp_path):
         cases.append((planes, chans, rects))
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     for tag, one in (("one", "1"), ("three", "0")):
-        env = dict(os.environ, IH_ONEPASS=one)
+        env = dict(os.environ, IH_ONEPASS=one, IH_SMALL="0")
         subprocess.run([sys.executable, "-c", _ONEPASS_SCRIPT, root, str(tmp_path), tag, str(len(cases))], env=env,
                        check=True, timeout=600)
     for k, (planes, chans, rects) in enumerate(cases):
@@ -915,3 +915,109 @@ def test_onepass_build_exact_and_equal_to_three_kernels(ihlib, tmp_path):
         assert np.array_equal(one["t"], three["t"]) and np.array_equal(one["r"], three["r"]), k
         assert np.array_equal(one["t"], oracle.frame_integral_histogram(planes, chans)), k
         assert np.array_equal(one["r"], oracle.frame_rect_hist(planes, chans, rects)), k
+
+
+# ---------------------------------------------------------------- small-frame build (one cooperative launch)
+
+_SMALL_CASES = [
+    (480, 640, [(16, 0)], 0),            # the plain 640 x 480 frame
+    (9, 130, [(8, 0)], 0),               # one band, two strips, the second 2 columns wide
+    (257, 2048, [(5, 0), (12, 1)], 1),   # 16 strips, slab layout, index channel, groups of 5 and 6 bins
+    (33, 129, [(40, 0)], 0),             # 5 groups of 8 bins
+    (700, 300, [(3, 0)], 1),             # many bands
+    (1, 1, [(4, 0)], 0),                 # one pixel
+    (2, 3, [(2, 0)], 1),                 # the hand-worked frame's shape
+    (1023, 1001, [(16, 0)], 0),          # ragged bands and strips, more rows per warp
+    (720, 1280, [(16, 0)], 1),           # slab, eight rows per warp
+]
+
+_SMALL_SCRIPT = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1711_01656_gb300 import ih
+d, n = sys.argv[2], int(sys.argv[4])
+dev = torch.device("cuda:0")
+c = ih.ih_create(0, flags=ih.IH_CFG_PROFILE)
+for k in range(n):
+    z = np.load(d + "/case%d.npz" % k)
+    planes, bins, modes, layout, rects = z["planes"], z["bins"], z["modes"], int(z["layout"]), z["rects"]
+    chans = [(int(b), int(m)) for b, m in zip(bins, modes)]
+    ih.ih_profile_read(c, reset=True)
+    hd, = ih.ih_build(c, ih.Frame(torch.from_numpy(planes).to(dev), chans, layout=layout))
+    B = int(bins.sum())
+    t = torch.empty((B,) + planes.shape[1:], dtype=torch.int32, device=dev)
+    ih.ih_export(c, hd, t)
+    r = torch.empty((len(rects), B), dtype=torch.int32, device=dev)
+    ih.ih_query_rects(c, hd, torch.from_numpy(rects).to(dev), r)
+    ih.ih_sync(c)
+    kern = sorted(ih.ih_profile_read(c, reset=True))
+    np.savez(d + "/out%d_%s.npz" % (k, sys.argv[3]), t=t.cpu().numpy(), r=r.cpu().numpy(),
+             small=int("small_build" in kern))
+    ih.ih_release(c, hd)
+ih.ih_destroy(c)
+'''
+
+
+def test_small_build_exact_and_equal_to_three_kernels(ihlib, tmp_path):
+    """Count-only frames that fit the GPU at once are built by one
+    cooperative launch (tile sums, a bounded grid barrier, carries summed
+    from the published sums, tiles): the tensors equal Algorithm 5, the
+    rectangles the enumeration, and both equal the three-kernel build
+    (IH_SMALL=0, read once per process) bit for bit."""
+    import os
+    import subprocess
+    import sys
+    cases = []
+    for k, (h, w, chans, layout) in enumerate(_SMALL_CASES):
+        planes = np.stack([synth.blob_plane(h, w, 500 + 10 * k + c) for c in range(len(chans))])
+        for c, (b, m) in enumerate(chans):
+            if m == 1:
+                planes[c] %= b + 2  # some values fall in no bin
+        rects = synth.rects_uniform_corners(h, w, 300, 501 + k)
+        np.savez(tmp_path / ("case%d.npz" % k), planes=planes, bins=np.array([b for b, _ in chans]),
+                 modes=np.array([m for _, m in chans]), layout=layout, rects=rects)
+        cases.append((planes, chans, rects))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for tag, on in (("small", "1"), ("three", "0")):
+        env = dict(os.environ, IH_SMALL=on, IH_ONEPASS="0")
+        subprocess.run([sys.executable, "-c", _SMALL_SCRIPT, root, str(tmp_path), tag, str(len(cases))], env=env,
+                       check=True, timeout=600)
+    for k, (planes, chans, rects) in enumerate(cases):
+        small = np.load(tmp_path / ("out%d_small.npz" % k))
+        three = np.load(tmp_path / ("out%d_three.npz" % k))
+        assert int(small["small"]) == 1 and int(three["small"]) == 0, k
+        assert np.array_equal(small["t"], oracle.frame_integral_histogram(planes, chans)), k
+        assert np.array_equal(small["r"], oracle.frame_rect_hist(planes, chans, rects)), k
+        assert np.array_equal(small["t"], three["t"]) and np.array_equal(small["r"], three["r"]), k
+
+
+def test_small_build_repeated_and_graphed(ihlib, ctx):
+    """The grid barrier's counter is zeroed before every launch: repeated
+    builds, and a one-frame batch replayed as a CUDA graph, give the same
+    tensor and queries each time."""
+    h, w = 480, 640
+    img = synth.uniform_plane(h, w, synth.config_seed(1) + 7)
+    rects = synth.rects_uniform_corners(h, w, 2000, 77)
+    ref = oracle.integral_histogram(img, 16, threads=8)
+    rref = oracle.rect_hist(img, 16, rects)
+    pix = torch.from_numpy(img).to(DEV)[None]
+    for _ in range(3):
+        hdl, = ihlib.ih_build(ctx, ihlib.Frame(pix, [(16, 0)]))
+        assert np.array_equal(_export(ihlib, ctx, hdl), ref)
+        ihlib.ih_release(ctx, hdl)
+    d_rects = torch.from_numpy(rects).to(DEV)
+    r_out = torch.full((len(rects), 16), -7, dtype=torch.int32, device=DEV)
+    batch, handles = ihlib.ih_batch_create(ctx, [ihlib.Frame(pix, [(16, 0)])], rects=d_rects,
+                                           rect_counts=[len(rects)], rect_out=r_out.view(-1),
+                                           batch_flags=ihlib.IH_BATCH_GRAPH)
+    try:
+        for _ in range(5):
+            r_out.fill_(-7)
+            ihlib.ih_batch_run(ctx, batch)
+            ihlib.ih_sync(ctx)
+            assert np.array_equal(r_out.cpu().numpy(), rref)
+        assert np.array_equal(_export(ihlib, ctx, handles[0]), ref)
+    finally:
+        ihlib.ih_batch_destroy(batch)
+        for hd in handles:
+            ihlib.ih_release(ctx, hd)
