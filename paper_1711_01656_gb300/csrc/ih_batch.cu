@@ -469,6 +469,12 @@ ih_status ih_batch_create(ih_ctx *ctx, const ih_frame *frames, int32_t n, const 
         b->single_feat = !feats.empty();
         if (b->single_feat) b->feat0 = feats[0];
         b->set0 = sets[0];
+        if (b->set0.small && b->set0.sm_bar) {
+            // the small-frame build's barrier counters: zeroed once here, left zero by every run
+            if ((e = cudaMemsetAsync(b->set0.sm_bar, 0, 2 * sizeof(unsigned int), st)) != cudaSuccess)
+                return bail(cuda_fail(ctx, e, "counter initialisation"));
+            b->set0.sm_zeroed = 1;
+        }
         b->view0 = recs[0].view;
         b->q0 = qj[0];
     }

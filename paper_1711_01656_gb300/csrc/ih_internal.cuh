@@ -191,9 +191,11 @@ struct PlaneSet {
     // small-frame build (small_plan): rows per warp (0: not planned), and per
     // tile its packed column counts [ngroups][nb][ns][256], per strip its
     // packed row counts [ns][ngroups][H][2], per tile its bin totals
-    // [nb][ns][ngroups][8], and the grid barrier's arrival counter (zero
-    // before the launch)
-    int32_t small;
+    // [nb][ns][ngroups][8], and the grid barrier's arrival and exit counters
+    // (zero before a launch; every launch leaves them zero).  sm_zeroed: the
+    // counters are known to be zero (scratch kept from launch to launch), so
+    // the launch needs no memset first.
+    int32_t small, sm_zeroed;
     uint32_t *sm_col, *sm_row;
     int32_t *sm_tot;
     unsigned int *sm_bar;
@@ -335,8 +337,13 @@ struct MomentView {
 };
 int launch_query_rects(const CountView &v, const int32_t *rects, int64_t n, int32_t *out,
                        int *err, cudaStream_t st, const Prof *prof);
-// Work items of one rectangle query (threads per rectangle).
-inline int64_t rect_items(const CountView &v) { return v.layout == LAYOUT_RECORD ? v.nquarters : v.ngroups; }
+// Work items of one rectangle query (threads per rectangle): a 4-word
+// quarter of the pixel record (record layout), a bin (bin-major) or a bin
+// group (slab).
+inline int64_t rect_items(const CountView &v)
+{
+    return v.layout == LAYOUT_RECORD ? v.nquarters : v.layout == LAYOUT_BIN_MAJOR ? v.B : v.ngroups;
+}
 // Queries of one frame of a batch (device table).
 struct QueryJob {
     const CountView *v;   // device copy of the frame's view

@@ -60,6 +60,28 @@ __device__ __forceinline__ uint32_t four_corner_u32(const uint32_t *p, int64_t P
     return a - b - c + d;
 }
 
+// LAYOUT_BIN_MAJOR: one thread per (rectangle, bin), item t = rect * B + bin:
+// four independent loads, one store.
+__device__ __forceinline__ void rect_item_bin(const CountView &v, const int32_t *__restrict__ rects,
+                                              int32_t *__restrict__ out, int64_t t, int *err)
+{
+    const int64_t qi = t / v.B;
+    const int b = (int)(t - qi * v.B);
+    const int r0 = __ldg(rects + 4 * qi), c0 = __ldg(rects + 4 * qi + 1);
+    const int r1 = __ldg(rects + 4 * qi + 2), c1 = __ldg(rects + 4 * qi + 3);
+    if (!box_ok(r0, c0, r1, c1, v.H, v.W)) {
+        out[t] = -1;
+        if (b == 0) atomicOr(err, 1);
+        return;
+    }
+    const int32_t *p = v.d + (int64_t)b * v.H * v.P;
+    int32_t s = __ldg(p + (int64_t)r1 * v.P + c1);
+    if (r0 > 0) s -= __ldg(p + (int64_t)(r0 - 1) * v.P + c1);
+    if (c0 > 0) s -= __ldg(p + (int64_t)r1 * v.P + (c0 - 1));
+    if (r0 > 0 && c0 > 0) s += __ldg(p + (int64_t)(r0 - 1) * v.P + (c0 - 1));
+    out[t] = s;
+}
+
 // One thread per (rectangle, bin group): the group's bins of each corner
 // are nb_g contiguous words in the slab layout.
 template <typename TN>
@@ -201,6 +223,12 @@ __device__ __forceinline__ void query_rects_cta(const CountView &v, const int32_
             rect_item_record(v, s_off, s_rw, s_w0, s_qp, s_wb, rects, out, t, err);
         return;
     }
+    if (v.layout == LAYOUT_BIN_MAJOR) {
+        const int64_t total = n * v.B;
+        for (int64_t t = bx * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nbx * blockDim.x)
+            rect_item_bin(v, rects, out, t, err);
+        return;
+    }
     const int64_t total = n * v.ngroups;
     for (int64_t t = bx * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)nbx * blockDim.x)
         rect_item(v, s_off, s_nb, s_b0, rects, out, t, err);
@@ -241,6 +269,8 @@ __device__ __forceinline__ void query_rects_b_cta(const QueryJob *__restrict__ j
         if (v.layout == LAYOUT_RECORD)
             rect_item_record(v, v.slab_off, v.group_nb, v.plane_w0, v.quarter_plane, v.word_bin, jb.rects,
                              jb.rect_out, t - pre[f], err);
+        else if (v.layout == LAYOUT_BIN_MAJOR)
+            rect_item_bin(v, jb.rects, jb.rect_out, t - pre[f], err);
         else
             rect_item(v, v.slab_off, v.group_nb, v.group_bin0, jb.rects, jb.rect_out, t - pre[f], err);
     }

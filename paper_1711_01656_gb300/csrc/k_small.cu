@@ -9,24 +9,26 @@
 // warp w owns rows [R0 + w RPW, R0 + (w+1) RPW) of the tile (RPW = 1..8 rows
 // per warp), a lane 4 adjacent columns.  The chains are RPW rows long and
 // every tile runs at once:
-//  1. Tile sums.  Each warp bins its rows once (the pixel words stay in
-//     registers) into packed 8-bit one-hot fields: the column counts of its
-//     rows and, row by row, the strip's row counts (warp reductions).  The
-//     CTA turns the warps' column counts into an exclusive prefix over the
-//     warps (shared memory) and publishes the tile's column counts, its row
-//     counts and its bin totals.
+//  1. Before the barrier, from the tile's own pixels: each warp bins its
+//     rows once (the pixel words stay in registers) into packed 8-bit
+//     one-hot fields: the column counts of its rows, the strip's row counts
+//     (warp reductions) and its rows' 2-D sums D_w(c) over columns [C0, c]
+//     (16-bit pairs, one in-lane prefix and four warp scans).  The CTA
+//     publishes the band's column counts, its row counts and its bin
+//     totals, and keeps the exclusive prefix over the warps of D_w.
 //  2. Grid barrier.  The launch is cooperative, so every CTA is resident;
 //     a CTA arrives once its sums are published and waits for all others
 //     (bounded: a wait that gives up sets bit 2 of the error word, and
-//     ih_sync reports IH_ETIMEOUT).
+//     ih_sync reports IH_ETIMEOUT).  The last CTA past the barrier zeroes
+//     its counters for the next launch.
 //  3. Carries as direct sums of the published tile sums: the column carry G
 //     (the bands above), the row carries L (the strips to the left) and the
-//     tile corner (the tiles above and to the left).
-//  4. Each warp seeds its columns with H(r-1, c) -- the corner, the row
-//     carries of the band's rows above its own, and the row prefix of G plus
-//     the column counts of the warps above -- and writes its rows like the
-//     count tiles kernel: per row a packed one-hot, one in-lane prefix and
-//     two warp scans, each cell stored once.
+//     tile corner (the tiles above and to the left); from them the band's
+//     top row H(R0-1, c) = corner + row prefix of G, one warp per bin.
+//  4. Each warp seeds its columns with H(R0 + rw - 1, c) = H(R0-1, c) +
+//     sum_{w' < w} D_w'(c) + the row carries of the band's rows above it,
+//     and writes its rows like the count tiles kernel: per row a packed
+//     one-hot, one in-lane prefix and two warp scans, each cell stored once.
 // Per cell the arithmetic is the split of Eq. 2.15 at the tile's edges:
 //   H(r,c) = H(R0-1, C0-1) + sum_{C0<=c'<=c} G(c')
 //          + sum_{R0<=r'<=r} ( L(r') + sum_{C0<=c'<=c} Q(r',c') ).
@@ -51,13 +53,18 @@ constexpr int kSmMaxStrips = 16;
 constexpr long kSmSpinLimit = 1L << 22;
 
 struct SmallSmem {
-    uint32_t colw[kSmWarps][kSmThreads];  // per warp: word k of lane L at [k * 32 + L]; then the
-                                          // exclusive prefix over the warps
+    uint32_t colw[kSmWarps][kSmThreads];  // per warp: packed column counts, word k of lane L at
+                                          // [k * 32 + L] (k = 2 q + h: column 4L + q, bins 4h..4h+3)
+    uint32_t D[kSmWarps][2 * kSmThreads]; // per warp: its rows' 2-D sums over columns [C0, c] as
+                                          // 16-bit pairs, then the exclusive prefix over the warps
     uint32_t G[2][kSmThreads];            // column carry at the band's top: 16-bit fields of
                                           // bytes 0, 2 ([0]) and 1, 3 ([1]) of word [k * 32 + L]
+    uint32_t Gp[4][kSmThreads][2];        // its partial sums over four slices of the bands
+    int32_t Htop[kGroupBins][kChunk];     // H(R0 - 1, c) of the strip's columns
     uint32_t rowcnt[kSmMaxRows][2];       // row counts over the strip, packed (bins 0-3, 4-7)
     int32_t L[kSmMaxRows][kGroupBins];    // row carries
     int32_t cpart[kSmWarps][kGroupBins];  // partial corners
+    int32_t LS[kSmWarps][kGroupBins];     // per warp: the row carries of the band's rows above it
     int ok;
 };
 
@@ -115,7 +122,7 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
     const bool vec_ok = ((ch.pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(ch.plane) & 3) == 0);
 
     // 1. the warp's rows: pixel words, column counts (bins 0-3 and 4-7 of
-    // each of the lane's columns) and row counts
+    // each of the lane's columns, fields <= RPW) and row counts
     uint32_t px[kSmMaxRpw];
 #pragma unroll
     for (int k = 0; k < kSmMaxRpw; ++k) px[k] = k < nrw ? load4(ch.plane, ch.pitch, R0 + rw + k, c, g.W, vec_ok) : 0u;
@@ -144,24 +151,57 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
         r1w = __reduce_add_sync(kFull, r1w);
         if (lane < 2) sm.rowcnt[rw + k][lane] = lane ? r1w : r0w;  // rows past the frame's end: 0
     }
+    // the warp's 2-D sums D(b, c) = sum over its rows and columns [C0, c] as
+    // 16-bit pairs (fields <= RPW * 128): pair word m = 2h + o holds bins
+    // 4h + o (low half) and 4h + o + 2 (high half)
+    {
+        uint32_t pw[4][4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        sm.colw[w][(2 * q) * 32 + lane] = colw[q][0];
-        sm.colw[w][(2 * q + 1) * 32 + lane] = colw[q][1];
+        for (int q = 0; q < 4; ++q) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                pw[q][2 * h] = colw[q][h] & 0x00ff00ffu;
+                pw[q][2 * h + 1] = (colw[q][h] >> 8) & 0x00ff00ffu;
+            }
+            sm.colw[w][(2 * q) * 32 + lane] = colw[q][0];
+            sm.colw[w][(2 * q + 1) * 32 + lane] = colw[q][1];
+        }
+#pragma unroll
+        for (int q = 1; q < 4; ++q)
+#pragma unroll
+            for (int m = 0; m < 4; ++m) pw[q][m] += pw[q - 1][m];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const uint32_t ex = warp_incl_scan(pw[3][m], lane) - pw[3][m];
+            uint4 v;
+            v.x = ex + pw[0][m];
+            v.y = ex + pw[1][m];
+            v.z = ex + pw[2][m];
+            v.w = ex + pw[3][m];
+            reinterpret_cast<uint4 *>(sm.D[w])[m * 32 + lane] = v;
+        }
     }
     __syncthreads();
 
     // the tile's sums: exclusive prefix of the column counts over the warps
-    // (fields <= R <= 64), published with the tile's total; row counts; bin totals
+    // gives the band's column counts (fields <= R <= 64), published; the
+    // exclusive prefix over the warps of D (fields <= R * 128); row counts;
+    // bin totals
     {
         uint32_t run = 0u;
 #pragma unroll
-        for (int ww = 0; ww < kSmWarps; ++ww) {
-            const uint32_t v = sm.colw[ww][tid];
-            sm.colw[ww][tid] = run;
-            run += v;
-        }
+        for (int ww = 0; ww < kSmWarps; ++ww) run += sm.colw[ww][tid];
         ps.sm_col[(int64_t)blockIdx.x * kSmThreads + tid] = run;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t e = 0u;
+#pragma unroll
+            for (int ww = 0; ww < kSmWarps; ++ww) {
+                const uint32_t v = sm.D[ww][h * kSmThreads + tid];
+                sm.D[ww][h * kSmThreads + tid] = e;
+                e += v;
+            }
+        }
     }
     if (tid < 2 * nr)
         ps.sm_row[(((int64_t)j * ps.ngroups + gi) * g.H + R0 + (tid >> 1)) * 2 + (tid & 1)] = sm.rowcnt[tid >> 1][tid & 1];
@@ -175,39 +215,71 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
     // 2. every CTA's sums are published
     if (tid == 0) sm.ok = grid_arrive_wait(ps.sm_bar, gridDim.x, ps.err) ? 1 : 0;
     __syncthreads();
-    if (!sm.ok) return;
+    if (!sm.ok) {
+        if (tid == 0 && atomicAdd(ps.sm_bar + 1, 1u) == gridDim.x - 1) {
+            ps.sm_bar[0] = 0u;
+            ps.sm_bar[1] = 0u;
+        }
+        return;
+    }
 
     // 3. carries: G over the bands above (16-bit pair fields, <= H), the row
-    // carries of the band's rows over the strips to the left, the corner
+    // carries of the band's rows over the strips to the left, the corner.
+    // Loads are issued 8 at a time before they are summed (one L2 round
+    // trip per 8): thread = (slice tid >> 6 of the bands, 4 words 4s..4s+3).
     {
-        uint32_t lo = 0u, hi = 0u;
-        const uint32_t *src = ps.sm_col + ((int64_t)gi * ntiles + j) * kSmThreads + tid;
-        int ib = 0;
-        for (; ib + 4 <= i; ib += 4) {
-            uint32_t v[4];
+        const int sl = tid >> 6, s4 = tid & 63;
+        const uint4 *src = reinterpret_cast<const uint4 *>(ps.sm_col + ((int64_t)gi * ntiles + j) * kSmThreads) + s4;
+        const int64_t stride = (int64_t)g.ns * (kSmThreads / 4);
+        const bool pack8 = 8 * g.R <= 255;  // 8 bands add up packed
+        uint32_t lo[4] = {0u, 0u, 0u, 0u}, hi[4] = {0u, 0u, 0u, 0u};
+        for (int base = 0; base < i; base += 32) {
+            uint4 v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = __ldcg(src + (int64_t)(ib + u) * g.ns * kSmThreads);
+            for (int u = 0; u < 8; ++u) {
+                const int ib = base + sl + 4 * u;
+                v[u] = ib < i ? __ldcg(src + ib * stride) : make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (pack8) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                lo += v[u] & 0x00ff00ffu;
-                hi += (v[u] >> 8) & 0x00ff00ffu;
+                for (int u = 1; u < 8; ++u) {
+                    v[0].x += v[u].x;
+                    v[0].y += v[u].y;
+                    v[0].z += v[u].z;
+                    v[0].w += v[u].w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (pack8 && u > 0) break;
+                const uint32_t vw[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    lo[e] += vw[e] & 0x00ff00ffu;
+                    hi[e] += (vw[e] >> 8) & 0x00ff00ffu;
+                }
             }
         }
-        for (; ib < i; ++ib) {
-            const uint32_t v = __ldcg(src + (int64_t)ib * g.ns * kSmThreads);
-            lo += v & 0x00ff00ffu;
-            hi += (v >> 8) & 0x00ff00ffu;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            sm.Gp[sl][4 * s4 + e][0] = lo[e];
+            sm.Gp[sl][4 * s4 + e][1] = hi[e];
         }
-        sm.G[0][tid] = lo;
-        sm.G[1][tid] = hi;
     }
     if (tid < 2 * nr) {
         const int r = tid >> 1, h = tid & 1;
         uint32_t lo = 0u, hi = 0u;
-        for (int jj = 0; jj < j; ++jj) {
-            const uint32_t v = __ldcg(ps.sm_row + (((int64_t)jj * ps.ngroups + gi) * g.H + R0 + r) * 2 + h);
-            lo += v & 0x00ff00ffu;
-            hi += (v >> 8) & 0x00ff00ffu;
+        const uint32_t *src = ps.sm_row + ((int64_t)gi * g.H + R0 + r) * 2 + h;
+        const int64_t stride = (int64_t)ps.ngroups * g.H * 2;
+        for (int base = 0; base < j; base += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = base + u < j ? __ldcg(src + (base + u) * stride) : 0u;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                lo += v[u] & 0x00ff00ffu;
+                hi += (v[u] >> 8) & 0x00ff00ffu;
+            }
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) sm.L[r][4 * h + e] = pair_field(lo, hi, e);
@@ -217,57 +289,93 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
         for (int e = 0; e < 4; ++e) sm.L[r][4 * h + e] = 0;
     }
     {
-        // corner: tiles (i', j') with i' < i, j' < j; thread = (bin tid & 7, slice tid >> 3)
-        const int b = tid & 7, s = tid >> 3, n = i * j;
+        // corner: tiles (i', j') with i' < i, j' < j; thread = (bin tid & 7,
+        // bands i' = tid >> 3, + 32, ...), then a reduction over the bands
+        const int b = tid & 7;
         int t = 0;
-        for (int k = s; k < n; k += kSmThreads / 8) {
-            const int ii = k / j, jj = k - (k / j) * j;
-            t += __ldcg(ps.sm_tot + ((int64_t)(ii * g.ns + jj) * ps.ngroups + gi) * kGroupBins + b);
+        for (int ii = tid >> 3; ii < i; ii += kSmThreads / 8) {
+            const int32_t *src = ps.sm_tot + ((int64_t)ii * g.ns * ps.ngroups + gi) * kGroupBins + b;
+            for (int base = 0; base < j; base += 8) {
+                int v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = base + u < j ? __ldcg(src + (int64_t)(base + u) * ps.ngroups * kGroupBins) : 0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) t += v[u];
+            }
         }
         t += __shfl_xor_sync(kFull, t, 8);
         t += __shfl_xor_sync(kFull, t, 16);
         if (lane < 8) sm.cpart[w][lane] = t;
     }
     __syncthreads();
-
-    // 4. the warp's rows
-    if (nrw == 0) return;
-    int TR[NB];
+    sm.G[0][tid] = sm.Gp[0][tid][0] + sm.Gp[1][tid][0] + sm.Gp[2][tid][0] + sm.Gp[3][tid][0];
+    sm.G[1][tid] = sm.Gp[0][tid][1] + sm.Gp[1][tid][1] + sm.Gp[2][tid][1] + sm.Gp[3][tid][1];
+    __syncthreads();
+    if (w < NB) {
+        // H(R0 - 1, c) of bin w: the corner plus the row prefix of G
+        int corner = 0;
 #pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        int t = 0;
-#pragma unroll
-        for (int ww = 0; ww < kSmWarps; ++ww) t += sm.cpart[ww][b];
-        for (int r = 0; r < rw; ++r) t += sm.L[r][b];
-        TR[b] = t;  // H(R0 + rw - 1, C0 - 1)
-    }
-    int acc[NB][4];
-#pragma unroll
-    for (int b = 0; b < NB; ++b) {
-        // column counts over rows [0, R0 + rw) of the lane's 4 columns
+        for (int k = 0; k < kSmWarps; ++k) corner += sm.cpart[k][w];
         int p[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int k = (2 * q + (b >> 2)) * 32 + lane;
-            p[q] = pair_field(sm.G[0][k], sm.G[1][k], b & 3) + (int)((sm.colw[w][k] >> (8 * (b & 3))) & 0xff);
-            if (q >= nvalid) p[q] = 0;
+            const int k = (2 * q + (w >> 2)) * 32 + lane;
+            p[q] = pair_field(sm.G[0][k], sm.G[1][k], w & 3);
         }
         p[1] += p[0];
         p[2] += p[1];
         p[3] += p[2];
-        const int incl = warp_incl_scan(p[3], lane);
-        const int base = TR[b] + (incl - p[3]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[b][q] = p[q] + base;
+        const int base = corner + warp_incl_scan(p[3], lane) - p[3];
+        *reinterpret_cast<int4 *>(&sm.Htop[w][4 * lane]) = make_int4(base + p[0], base + p[1], base + p[2], base + p[3]);
     }
+    if (tid < kSmWarps * kGroupBins) {
+        // the row carries of the band's rows above each warp
+        const int ww = tid >> 3, b = tid & 7;
+        int t = 0;
+        for (int r = 0; r < ww * rpw; ++r) t += sm.L[r][b];
+        sm.LS[ww][b] = t;
+    }
+    __syncthreads();
+
+    // the last CTA to get here zeroes the barrier counters for the next launch
+    if (tid == 0 && atomicAdd(ps.sm_bar + 1, 1u) == gridDim.x - 1) {
+        ps.sm_bar[0] = 0u;
+        ps.sm_bar[1] = 0u;
+    }
+
+    // 4. the warp's rows, seeded with H(R0 + rw - 1, c) = H(R0 - 1, c) + the
+    // 2-D sums of the warps above + the row carries of the rows above
+    if (nrw == 0) return;
+    int acc[NB][4];
+    {
+        uint4 dv[4];
 #pragma unroll
-    for (int k = 0; k < kSmMaxRpw; ++k) {
-        if (k >= nrw) break;
+        for (int m = 0; m < 4; ++m) dv[m] = reinterpret_cast<const uint4 *>(sm.D[w])[m * 32 + lane];
+        const int4 s0 = *reinterpret_cast<const int4 *>(&sm.LS[w][0]);
+        const int4 s1 = *reinterpret_cast<const int4 *>(&sm.LS[w][4]);
+        const int ls[8] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            const int4 ht = *reinterpret_cast<const int4 *>(&sm.Htop[b][4 * lane]);
+            const uint4 d = dv[2 * (b >> 2) + (b & 1)];
+            const int sh = (b & 2) ? 16 : 0;
+            acc[b][0] = ht.x + ls[b] + (int)((d.x >> sh) & 0xffffu);
+            acc[b][1] = ht.y + ls[b] + (int)((d.y >> sh) & 0xffffu);
+            acc[b][2] = ht.z + ls[b] + (int)((d.z >> sh) & 0xffffu);
+            acc[b][3] = ht.w + ls[b] + (int)((d.w >> sh) & 0xffffu);
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < nrw; ++k) {
         const int r = R0 + rw + k;
+        const uint32_t pk = px[0];
+#pragma unroll
+        for (int u = 0; u + 1 < kSmMaxRpw; ++u) px[u] = px[u + 1];  // the next row's word to the front
         uint32_t P0[4], P1[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const int qb = bin_of((px[k] >> (8 * q)) & 0xff, bins, mode);
+            const int qb = bin_of((pk >> (8 * q)) & 0xff, bins, mode);
             const unsigned d = (q < nvalid && qb >= 0) ? (unsigned)(qb - blo) : 0xFFFFFFFFu;
             P0[q] = (q ? P0[q - 1] : 0u) + (d < 4u ? (1u << (d << 3)) : 0u);
             P1[q] = (q ? P1[q - 1] : 0u) + ((d - 4u) < 4u ? (1u << ((d - 4u) << 3)) : 0u);
@@ -394,7 +502,7 @@ size_t small_bytes(const PlaneSet &ps)
     const TileGrid &g = ps.g;
     const size_t tiles = (size_t)g.nb * g.ns * ps.ngroups;
     return r256(4 * tiles * kSmThreads) + r256(8 * (size_t)g.ns * ps.ngroups * g.H) + r256(4 * tiles * kGroupBins) +
-           r256(4);
+           r256(8);
 }
 
 void carve_small(PlaneSet &ps, void *base)
@@ -413,7 +521,8 @@ void carve_small(PlaneSet &ps, void *base)
 
 int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
 {
-    if (cudaMemsetAsync(ps.sm_bar, 0, sizeof(unsigned int), st) != cudaSuccess) return -1;
+    // the counters of fresh scratch are zeroed here; a launch leaves them zero
+    if (!ps.sm_zeroed && cudaMemsetAsync(ps.sm_bar, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) return -1;
     const unsigned ctas = (unsigned)((int64_t)ps.g.nb * ps.g.ns * ps.ngroups);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ctas);
