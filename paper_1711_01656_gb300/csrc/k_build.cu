@@ -271,13 +271,14 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
         }
         __syncthreads();
     }
-    for (int k = tid; k < nbw * nr; k += kSumThreads) {
-        const int b = k / nr, rr = k % nr;
-        ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = row_cnt[b * R + rr];
-        if (WT) {
-            const int64_t o = ((int64_t)j * Bw + wd.b_lo + b) * g.H + R0 + rr;
-            ps.row_sv[o] = row_sv[b * R + rr];
-            ps.row_svv[o] = row_svv[b * R + rr];
+    for (int b = tid >> 5; b < nbw; b += kSumThreads / 32) {
+        for (int rr = tid & 31; rr < nr; rr += 32) {
+            ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = row_cnt[b * R + rr];
+            if (WT) {
+                const int64_t o = ((int64_t)j * Bw + wd.b_lo + b) * g.H + R0 + rr;
+                ps.row_sv[o] = row_sv[b * R + rr];
+                ps.row_svv[o] = row_svv[b * R + rr];
+            }
         }
     }
     if (tid < nbw) {
@@ -307,10 +308,12 @@ __device__ __forceinline__ void tile_sums_body(const PlaneSet &ps, int j, int i,
 
 // Tile sums of a window of an unweighted channel, 4 warps per (band, strip,
 // window).  Row rr of the band goes to warp rr % 4; a lane holds 4 adjacent
-// columns of the 128-column pass.  A pixel's window-local bin is one 8-bit
-// field of NW packed words (4 bins per word): a lane's per-column words add
-// up its rows (at most 32 per field), and a row's words over the warp are
-// one redux.sync.add each (at most 128 per field), so no field overflows.
+// columns of the 128-column pass.  A pixel's window-local bin is one 4-bit
+// field of two words (8 bins per word), so a pixel costs a shift and two
+// adds; a lane's per-column fields add up at most 15 rows before they are
+// spread into NW byte words (at most 32 rows per field), and a row's fields
+// over the warp are spread into bytes and reduced by one redux.sync.add per
+// word (at most 128 per field), so no field overflows.
 constexpr int kCntThreads = 128;
 
 // The 128 threads of one group (a whole CTA, or half of a 256-thread CTA:
@@ -338,7 +341,11 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
     const int bins = ch.bins, mode = ch.mode;
     const bool vec_ok = ((pt & 3) == 0) && ((reinterpret_cast<uintptr_t>(pl) & 3) == 0);
 
-    for (int k = tid; k < nbw * nr; k += kCntThreads) rows[k / nr][k % nr] = 0;
+    {
+        // zero the row counters (no division by nr: all of rows[][], 16-byte stores)
+        int4 *r4 = reinterpret_cast<int4 *>(&rows[0][0]);
+        for (int k = tid; k < kWindowBins * kMaxBandRows / 4; k += kCntThreads) r4[k] = make_int4(0, 0, 0, 0);
+    }
     group_sync(bar);
     for (int cp = C0; cp < C1; cp += kChunk) {
         const int c = cp + lane * 4;
@@ -348,38 +355,69 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
         for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
             for (int k = 0; k < NW; ++k) col[jj][k] = 0u;
-        // two rows of this warp in flight
+        // two rows of this warp in flight.  A pixel's bin d (0..15) is a 4-bit
+        // field of two words (lo: d < 8, hi: d >= 8); a column's fields add up
+        // at most 15 rows before they are spread into the byte words col[jj]
+        // (word 2h + o holds bins 8h + o, 8h + o + 2, 8h + o + 4, 8h + o + 6)
         uint32_t pa = wid < nr ? load4(pl, pt, R0 + wid, c, C1, vec_ok) : 0u;
         uint32_t pb = wid + 4 < nr ? load4(pl, pt, R0 + wid + 4, c, C1, vec_ok) : 0u;
+        uint32_t nib[4][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}, {0u, 0u}};
+        int pend = 0;
         for (int rr = wid; rr < nr; rr += 4) {
             const uint32_t px = pa;
             pa = pb;
             if (rr + 8 < nr) pb = load4(pl, pt, R0 + rr + 8, c, C1, vec_ok);
-            uint32_t rw[NW];
-#pragma unroll
-            for (int k = 0; k < NW; ++k) rw[k] = 0u;
+            uint32_t rlo = 0u, rhi = 0u;
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
                 const int q = bin_of((px >> (8 * jj)) & 0xff, bins, mode) - blo;
-                const unsigned d = (jj < nvalid && q >= 0 && q < nbw) ? (unsigned)q : 0xFFFFFFFFu;
-                const uint32_t e = 1u << ((d & 3u) << 3);
-#pragma unroll
-                for (int k = 0; k < NW; ++k) {
-                    const uint32_t v = (d >> 2) == (unsigned)k ? e : 0u;
-                    col[jj][k] += v;
-                    rw[k] += v;
+                const unsigned d = (jj < nvalid && q >= 0 && q < nbw) ? (unsigned)q : 16u;
+                const uint32_t e = 1u << ((d & 7u) << 2);
+                const uint32_t el = d < 8u ? e : 0u;
+                rlo += el;
+                nib[jj][0] += el;
+                if (NW > 2) {
+                    const uint32_t eh = (d - 8u) < 8u ? e : 0u;
+                    rhi += eh;
+                    nib[jj][1] += eh;
                 }
             }
+            if (++pend == 15) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) rw[k] = __reduce_add_sync(kFull, rw[k]);
+                for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+                    for (int h = 0; h < NW / 2; ++h) {
+                        col[jj][2 * h] += nib[jj][h] & 0x0F0F0F0Fu;
+                        col[jj][2 * h + 1] += (nib[jj][h] >> 4) & 0x0F0F0F0Fu;
+                        nib[jj][h] = 0u;
+                    }
+                pend = 0;
+            }
+            // the row's counts over the pass: fields <= 4 per lane, spread
+            // into bytes and reduced over the warp (<= 128 per field)
+            uint32_t rw[NW];
+            rw[0] = __reduce_add_sync(kFull, rlo & 0x0F0F0F0Fu);
+            rw[1] = __reduce_add_sync(kFull, (rlo >> 4) & 0x0F0F0F0Fu);
+            if (NW > 2) {
+                rw[2] = __reduce_add_sync(kFull, rhi & 0x0F0F0F0Fu);
+                rw[3] = __reduce_add_sync(kFull, (rhi >> 4) & 0x0F0F0F0Fu);
+            }
             if (lane < nbw) {
+                const int wsel = ((lane >> 3) << 1) | (lane & 1);
                 uint32_t w = rw[0];
 #pragma unroll
                 for (int k = 1; k < NW; ++k)
-                    if ((lane >> 2) == k) w = rw[k];
-                rows[lane][rr] += (int32_t)((w >> ((lane & 3) << 3)) & 0xFFu);
+                    if (wsel == k) w = rw[k];
+                rows[lane][rr] += (int32_t)((w >> (((lane & 7) >> 1) << 3)) & 0xFFu);
             }
         }
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj)
+#pragma unroll
+            for (int h = 0; h < NW / 2; ++h) {
+                col[jj][2 * h] += nib[jj][h] & 0x0F0F0F0Fu;
+                col[jj][2 * h + 1] += (nib[jj][h] >> 4) & 0x0F0F0F0Fu;
+            }
 #pragma unroll
         for (int jj = 0; jj < 4; ++jj)
 #pragma unroll
@@ -397,14 +435,15 @@ __device__ __forceinline__ void tile_sums_count_body(const PlaneSet &ps, int j, 
                 int32_t *dst = ps.colsum + ((int64_t)i * ps.B + bglob) * g.W + cp + cc;
 #pragma unroll
                 for (int b = 0; b < 4 * NW; ++b)
-                    if (b < nbw) dst[(int64_t)b * g.W] = (int32_t)((sw[b >> 2] >> ((b & 3) << 3)) & 0xFFu);
+                    if (b < nbw)
+                        dst[(int64_t)b * g.W] = (int32_t)((sw[((b >> 3) << 1) | (b & 1)] >> (((b & 7) >> 1) << 3)) & 0xFFu);
             }
         }
         group_sync(bar);
     }
-    for (int k = tid; k < nbw * nr; k += kCntThreads) {
-        const int b = k / nr, rr = k % nr;
-        ps.rowsum[((int64_t)j * ps.B + bglob + b) * g.H + R0 + rr] = rows[b][rr];
+    for (int b = wid; b < nbw; b += 4) {
+        int32_t *dst = ps.rowsum + ((int64_t)j * ps.B + bglob + b) * g.H + R0;
+        for (int rr = lane; rr < nr; rr += 32) dst[rr] = rows[b][rr];
     }
     for (int b = wid; b < nbw; b += 4) {
         int32_t t = 0;
