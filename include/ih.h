@@ -537,7 +537,9 @@ ih_status ih_server_destroy(ih_server *srv);
  * array's device address and prepares the build kernels for that device,
  * which SYNCHRONISES THE DEVICE once; make that first call before any stream
  * capture begins and before the loop that must not stall.  Later calls only
- * enqueue kernels, on the same kernel path as ih_build.  All calls share the
+ * enqueue kernels: the three-kernel build of ih_build (tile sums, carry scan,
+ * count tiles), also for the small frames that ih_build builds in one
+ * cooperative launch.  All calls share the
  * array: calls whose work overlaps on the GPU race on it and must be ordered
  * by the caller (one stream, or events).  Returns IH_EINVAL for bad arguments,
  * IH_ETOOBIG when even the largest tiles need more than the array holds
