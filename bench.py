@@ -1152,9 +1152,17 @@ def main(argv=None):
     ap.add_argument("--wami-side", type=int, default=WAMI_H,
                     help="side of the headline frame (smaller only for profiling captures)")
     ap.add_argument("--mma-side", type=int, default=8192, help="side of the frame of the mma_tiles section")
+    ap.add_argument("--only-plain", type=int, default=0, metavar="RUNS",
+                    help="profiling captures: run only the 640x480 plain-frame section with RUNS timed "
+                         "repetitions and print its JSON (no bench line)")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "engine":
         ap.error("--warmup must be >= 3")
+    if args.only_plain > 0:
+        import torch
+        from paper_1711_01656_gb300 import ih
+        print(json.dumps(plain_section(ih, torch.device("cuda", 0), runs=args.only_plain)))
+        return 0
     return run_reference(args) if args.impl == "reference" else run_engine(args)
 
 
