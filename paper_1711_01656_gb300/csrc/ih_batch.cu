@@ -76,11 +76,17 @@ int enqueue_run(ih_batch *b, cudaStream_t st, const Prof *prof)
             if (k < 0) return -1;
             n += k;
         }
+        const QueryJob &q = b->q0;
+        const int64_t nr = q.rects ? b->q_rects / rect_items(b->view0) : 0, nw = q.wins ? b->q_wins / q.m.Bw : 0;
+        if (b->set0.small && b->set0.sm_bar && nr && !nw) {
+            // a small frame and its rectangles in one launch
+            const SmallQuery sq{q.rects, nr, q.rect_out};
+            k = launch_build_small(b->set0, st, prof, &sq);
+            return k < 0 ? -1 : n + k;
+        }
         k = launch_build(b->set0, st, prof);
         if (k < 0) return -1;
         n += k;
-        const QueryJob &q = b->q0;
-        const int64_t nr = q.rects ? b->q_rects / rect_items(b->view0) : 0, nw = q.wins ? b->q_wins / q.m.Bw : 0;
         if (nr || nw) {
             k = launch_query_both(b->view0, q.m, q.rects, nr, q.rect_out, q.wins, nw, q.kernel, q.layers, q.normalize,
                                   q.wout, b->ctx->d_err, st, prof);

@@ -218,9 +218,17 @@ bool small_plan(PlaneSet &ps, int nsm);
 // Scratch bytes of a small-frame build, and its carving.
 size_t small_bytes(const PlaneSet &ps);
 void carve_small(PlaneSet &ps, void *base);
-// The small-frame build (memset of the barrier counter + one launch);
-// returns the number of kernels launched, or -1.
-int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof);
+// Rectangle queries answered by the small-frame build's own launch (after a
+// second grid barrier): n x 4 rectangles in, n x B counts out.
+struct SmallQuery {
+    const int32_t *rects;
+    int64_t n;
+    int32_t *out;
+};
+// The small-frame build (a memset of the barrier counters unless
+// ps.sm_zeroed, then one launch), with the frame's rectangle queries when
+// `queries` is given; returns the number of kernels launched, or -1.
+int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof, const SmallQuery *queries = nullptr);
 // Bytes of carry scratch a plane set needs (0 for a single tile), and the
 // carving of one scratch block into the carry arrays.
 size_t carry_bytes(const PlaneSet &ps);

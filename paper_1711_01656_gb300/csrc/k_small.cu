@@ -76,12 +76,17 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned int *p)
 }
 
 // One thread of each CTA: publish the CTA's writes (ordered before this
-// thread by the caller's __syncthreads), arrive, and wait until `target`
-// CTAs have arrived.  False when the wait gave up.
-__device__ __forceinline__ bool grid_arrive_wait(unsigned int *bar, unsigned target, int *err)
+// thread by the caller's __syncthreads) and arrive.
+__device__ __forceinline__ void grid_arrive(unsigned int *bar)
 {
     __threadfence();
     atomicAdd(bar, 1u);
+}
+
+// ... and wait until the counter reaches `target`.  False when the wait gave
+// up (or another CTA's did).
+__device__ __forceinline__ bool grid_wait(unsigned int *bar, unsigned target, int *err)
+{
     long spins = 0;
     while (ld_acquire_u32(bar) < target) {
         if (++spins > kSmSpinLimit || (*(volatile int *)err & 2)) {
@@ -213,15 +218,12 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
     __syncthreads();
 
     // 2. every CTA's sums are published
-    if (tid == 0) sm.ok = grid_arrive_wait(ps.sm_bar, gridDim.x, ps.err) ? 1 : 0;
-    __syncthreads();
-    if (!sm.ok) {
-        if (tid == 0 && atomicAdd(ps.sm_bar + 1, 1u) == gridDim.x - 1) {
-            ps.sm_bar[0] = 0u;
-            ps.sm_bar[1] = 0u;
-        }
-        return;
+    if (tid == 0) {
+        grid_arrive(ps.sm_bar);
+        sm.ok = grid_wait(ps.sm_bar, gridDim.x, ps.err) ? 1 : 0;
     }
+    __syncthreads();
+    if (!sm.ok) return;
 
     // 3. carries: G over the bands above (16-bit pair fields, <= H), the row
     // carries of the band's rows over the strips to the left, the corner.
@@ -338,12 +340,6 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
     }
     __syncthreads();
 
-    // the last CTA to get here zeroes the barrier counters for the next launch
-    if (tid == 0 && atomicAdd(ps.sm_bar + 1, 1u) == gridDim.x - 1) {
-        ps.sm_bar[0] = 0u;
-        ps.sm_bar[1] = 0u;
-    }
-
     // 4. the warp's rows, seeded with H(R0 + rw - 1, c) = H(R0 - 1, c) + the
     // 2-D sums of the warps above + the row carries of the rows above
     if (nrw == 0) return;
@@ -406,8 +402,80 @@ __device__ __forceinline__ void small_body(const PlaneSet &ps, SmallSmem &sm, in
     }
 }
 
+// 5. Rectangle queries of the frame (Eq. 2.16) after a second grid barrier,
+// over every CTA, one item per (rectangle, bin): bin-major, item k = bin;
+// slab, item k = 8 g + b (bin b < nb_g of group g; consecutive items read
+// consecutive words of a corner's record).  The tensor was written by other
+// CTAs of this launch, so its corners are read through L2 (ld.global.cg).
+// An invalid rectangle writes -1 over its row and sets bit 0 of the error
+// word.
 template <int LAYOUT>
-__global__ void __launch_bounds__(kSmThreads, 2) k_build_small(const __grid_constant__ PlaneSet ps)
+__device__ __forceinline__ void small_queries(const PlaneSet &ps, const SmallQuery &q)
+{
+    const TileGrid &g = ps.g;
+    const int64_t per = LAYOUT == LAYOUT_BIN_MAJOR ? ps.B : (int64_t)ps.ngroups * kGroupBins;
+    const int64_t total = q.n * per, step = (int64_t)gridDim.x * kSmThreads;
+    // two items per pass, every load of both issued before any is used
+    for (int64_t t0 = (int64_t)blockIdx.x * kSmThreads + threadIdx.x; t0 < total; t0 += 2 * step) {
+        int32_t *o[2] = {nullptr, nullptr};
+        int32_t v[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+        int rc[2][4];
+        bool use[2], ok[2];
+        int kk[2];
+        const int32_t *pl[2];
+        int64_t stride[2], word[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int64_t t = t0 + u * step;
+            use[u] = t < total;
+            const int64_t qi = use[u] ? t / per : 0;
+            const int k = use[u] ? (int)(t - qi * per) : 0;
+            kk[u] = k;
+            int64_t bin;
+            if (LAYOUT == LAYOUT_BIN_MAJOR) {
+                bin = k;
+                pl[u] = ps.out + (int64_t)k * g.H * g.P;
+                stride[u] = 1;
+                word[u] = 0;
+            } else {
+                const GroupDev gr = ps.grp[k >> 3];
+                if ((k & 7) >= gr.nb) use[u] = false;
+                bin = ps.chan[gr.chan].bin_off + gr.b_lo + (k & 7);
+                pl[u] = ps.out + ps.slab_off[gr.plane];
+                stride[u] = gr.nb;
+                word[u] = k & 7;
+            }
+            o[u] = q.out + qi * ps.B + bin;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) rc[u][e] = use[u] ? __ldg(q.rects + 4 * qi + e) : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int r0 = rc[u][0], c0 = rc[u][1], r1 = rc[u][2], c1 = rc[u][3];
+            ok[u] = use[u] && r0 >= 0 && c0 >= 0 && r0 <= r1 && c0 <= c1 && r1 < g.H && c1 < g.W;
+            if (ok[u]) {
+                v[u][0] = __ldcg(pl[u] + ((int64_t)r1 * g.P + c1) * stride[u] + word[u]);
+                if (r0 > 0) v[u][1] = __ldcg(pl[u] + ((int64_t)(r0 - 1) * g.P + c1) * stride[u] + word[u]);
+                if (c0 > 0) v[u][2] = __ldcg(pl[u] + ((int64_t)r1 * g.P + (c0 - 1)) * stride[u] + word[u]);
+                if (r0 > 0 && c0 > 0)
+                    v[u][3] = __ldcg(pl[u] + ((int64_t)(r0 - 1) * g.P + (c0 - 1)) * stride[u] + word[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!use[u]) continue;
+            if (ok[u]) {
+                *o[u] = v[u][0] - v[u][1] - v[u][2] + v[u][3];
+            } else {
+                *o[u] = -1;
+                if (kk[u] == 0) atomicOr(ps.err, 1);
+            }
+        }
+    }
+}
+
+template <int LAYOUT>
+__global__ void __launch_bounds__(kSmThreads, 2) k_build_small(const __grid_constant__ PlaneSet ps, const SmallQuery q)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     SmallSmem &sm = *reinterpret_cast<SmallSmem *>(dsm);
@@ -423,6 +491,22 @@ __global__ void __launch_bounds__(kSmThreads, 2) k_build_small(const __grid_cons
     case 6: small_body<LAYOUT, 6>(ps, sm, stage); break;
     case 7: small_body<LAYOUT, 7>(ps, sm, stage); break;
     default: small_body<LAYOUT, 8>(ps, sm, stage); break;
+    }
+    if (q.n > 0) {
+        // a CTA whose first wait gave up still arrives (without waiting), so
+        // that no other CTA waits for it
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            grid_arrive(ps.sm_bar);
+            sm.ok = (sm.ok && grid_wait(ps.sm_bar, 2 * gridDim.x, ps.err)) ? 1 : 0;
+        }
+        __syncthreads();
+        if (sm.ok) small_queries<LAYOUT>(ps, q);
+    }
+    // the last CTA past the barriers zeroes their counters for the next launch
+    if (threadIdx.x == 0 && atomicAdd(ps.sm_bar + 1, 1u) == gridDim.x - 1) {
+        ps.sm_bar[0] = 0u;
+        ps.sm_bar[1] = 0u;
     }
 }
 
@@ -519,8 +603,9 @@ void carve_small(PlaneSet &ps, void *base)
     ps.sm_bar = reinterpret_cast<unsigned int *>(s);
 }
 
-int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
+int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof, const SmallQuery *queries)
 {
+    const SmallQuery q = queries ? *queries : SmallQuery{nullptr, 0, nullptr};
     // the counters of fresh scratch are zeroed here; a launch leaves them zero
     if (!ps.sm_zeroed && cudaMemsetAsync(ps.sm_bar, 0, 2 * sizeof(unsigned int), st) != cudaSuccess) return -1;
     const unsigned ctas = (unsigned)((int64_t)ps.g.nb * ps.g.ns * ps.ngroups);
@@ -536,9 +621,9 @@ int launch_build_small(const PlaneSet &ps, cudaStream_t st, const Prof *prof)
     cfg.numAttrs = 1;
     prof_mark(prof, KID_SMALL, 0, st);
     if (ps.layout == LAYOUT_SLAB)
-        cudaLaunchKernelEx(&cfg, k_build_small<LAYOUT_SLAB>, ps);
+        cudaLaunchKernelEx(&cfg, k_build_small<LAYOUT_SLAB>, ps, q);
     else
-        cudaLaunchKernelEx(&cfg, k_build_small<LAYOUT_BIN_MAJOR>, ps);
+        cudaLaunchKernelEx(&cfg, k_build_small<LAYOUT_BIN_MAJOR>, ps, q);
     prof_mark(prof, KID_SMALL, 1, st);
     return cudaPeekAtLastError() == cudaSuccess ? 1 : -1;
 }

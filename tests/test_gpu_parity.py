@@ -991,10 +991,12 @@ def test_small_build_exact_and_equal_to_three_kernels(ihlib, tmp_path):
         assert np.array_equal(small["t"], three["t"]) and np.array_equal(small["r"], three["r"]), k
 
 
-def test_small_build_repeated_and_graphed(ihlib, ctx):
-    """The grid barrier's counter is zeroed before every launch: repeated
-    builds, and a one-frame batch replayed as a CUDA graph, give the same
-    tensor and queries each time."""
+@pytest.mark.parametrize("layout", [0, 1])
+def test_small_build_repeated_and_graphed(ihlib, ctx, layout):
+    """The grid barriers' counters are left zero by every launch: repeated
+    builds, and a one-frame batch replayed as a CUDA graph (build and
+    rectangles in one launch), give the same tensor and queries each time;
+    an invalid rectangle's row is -1 and the status IH_EINVAL."""
     h, w = 480, 640
     img = synth.uniform_plane(h, w, synth.config_seed(1) + 7)
     rects = synth.rects_uniform_corners(h, w, 2000, 77)
@@ -1002,22 +1004,36 @@ def test_small_build_repeated_and_graphed(ihlib, ctx):
     rref = oracle.rect_hist(img, 16, rects)
     pix = torch.from_numpy(img).to(DEV)[None]
     for _ in range(3):
-        hdl, = ihlib.ih_build(ctx, ihlib.Frame(pix, [(16, 0)]))
+        hdl, = ihlib.ih_build(ctx, ihlib.Frame(pix, [(16, 0)], layout=layout))
         assert np.array_equal(_export(ihlib, ctx, hdl), ref)
         ihlib.ih_release(ctx, hdl)
-    d_rects = torch.from_numpy(rects).to(DEV)
-    r_out = torch.full((len(rects), 16), -7, dtype=torch.int32, device=DEV)
-    batch, handles = ihlib.ih_batch_create(ctx, [ihlib.Frame(pix, [(16, 0)])], rects=d_rects,
-                                           rect_counts=[len(rects)], rect_out=r_out.view(-1),
-                                           batch_flags=ihlib.IH_BATCH_GRAPH)
-    try:
-        for _ in range(5):
-            r_out.fill_(-7)
-            ihlib.ih_batch_run(ctx, batch)
-            ihlib.ih_sync(ctx)
-            assert np.array_equal(r_out.cpu().numpy(), rref)
-        assert np.array_equal(_export(ihlib, ctx, handles[0]), ref)
-    finally:
-        ihlib.ih_batch_destroy(batch)
-        for hd in handles:
-            ihlib.ih_release(ctx, hd)
+    bad = rects.copy()
+    bad[5] = [10, 10, 9, 20]    # r0 > r1
+    bad[1999] = [0, 0, h, 3]    # past the last row
+    for rr, want in ((rects, rref), (bad, None)):
+        d_rects = torch.from_numpy(rr).to(DEV)
+        r_out = torch.full((len(rr), 16), -7, dtype=torch.int32, device=DEV)
+        batch, handles = ihlib.ih_batch_create(ctx, [ihlib.Frame(pix, [(16, 0)], layout=layout)], rects=d_rects,
+                                               rect_counts=[len(rr)], rect_out=r_out.view(-1),
+                                               batch_flags=ihlib.IH_BATCH_GRAPH)
+        try:
+            for _ in range(5):
+                r_out.fill_(-7)
+                ihlib.ih_batch_run(ctx, batch)
+                if want is not None:
+                    ihlib.ih_sync(ctx)
+                    assert np.array_equal(r_out.cpu().numpy(), want)
+                else:
+                    with pytest.raises(ihlib.IHError) as ei:
+                        ihlib.ih_sync(ctx)
+                    assert ei.value.status == ihlib.IH_EINVAL
+                    g = r_out.cpu().numpy()
+                    assert (g[5] == -1).all() and (g[1999] == -1).all()
+                    keep = np.ones(len(rr), bool)
+                    keep[[5, 1999]] = False
+                    assert np.array_equal(g[keep], rref[keep])
+            assert np.array_equal(_export(ihlib, ctx, handles[0]), ref)
+        finally:
+            ihlib.ih_batch_destroy(batch)
+            for hd in handles:
+                ihlib.ih_release(ctx, hd)
