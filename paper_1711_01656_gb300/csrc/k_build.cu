@@ -886,9 +886,10 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                                                 rw, (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
                     }
                 }
-                // the last lane's inclusive sums are the chunk's row totals
+                // the last lane's inclusive sums are the chunk's row totals (the
+                // next chunk's row carries; none when this chunk ends the strip)
                 __syncwarp();
-                if (lane == 31) {
+                if (lane == 31 && cc + kChunk < C1) {
                     int4 a, b4;
                     a.x = rla[0] + (int)__byte_perm(ia0, 0, 0x4440);
                     a.y = rla[1] + (int)__byte_perm(ia0, 0, 0x4441);
@@ -981,7 +982,7 @@ __device__ __forceinline__ void tiles_count_unit(const PlaneSet &ps, int i, int 
                                         rw, (int)(g.P - cc < kChunk ? g.P - cc : kChunk), acc, stage, lane);
             }
             __syncwarp();
-            if (lane == 31) {
+            if (lane == 31 && cc + kChunk < C1) {  // the next chunk's row carries
                 int4 a, b4;
                 a.x = rla[0] + (int)__byte_perm(ia0, 0, 0x4440);
                 a.y = rla[1] + (int)__byte_perm(ia0, 0, 0x4441);
@@ -1258,7 +1259,7 @@ __device__ __forceinline__ void tiles_moments_unit(const PlaneSet &ps, int i, in
                     }
                 }
                 __syncwarp();
-                if (lane == 0) {
+                if (lane == 0 && cc + kChunk < C1) {  // the next chunk's row carries
                     const long long tn = t1 & 0xFF, tu = t1 >> 8, tuu = t2;
                     RLn[rr] = rn + (int)tn;
                     RLx[rr] = rx + Cb * tn + tu;

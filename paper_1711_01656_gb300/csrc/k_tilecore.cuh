@@ -108,15 +108,17 @@ __device__ __forceinline__ void store_record_staged(int32_t *row, int rec_w, int
         stage[lane * S + k] = make_int4(v[0], v[1], v[2], v[3]);
     }
     __syncwarp();
+    // unit u = 32m + L' is word chunk k = L' % NB (the same for every m) of
+    // lane-pixel group u / NB = (32/NB) m + L' / NB: its destination and its
+    // stage slot are a per-lane constant plus m times a stride
     const int nunits = npx * Q;
+    const int kk = lane % NB;
+    const int64_t c0 = (int64_t)(4 * (lane / NB) + kk / Q) * rec_w + 4 * (kk % Q);
+    const int64_t dm = (int64_t)(128 / NB) * rec_w;
+    const int s0 = (lane / NB) * S + kk;
 #pragma unroll
     for (int m = 0; m < NB; ++m) {
-        const int u = 32 * m + lane;
-        if (u < nunits) {
-            const int L = u / NB, k = u % NB;
-            const int px = 4 * L + k / Q, q = k % Q;
-            *reinterpret_cast<int4 *>(row + (int64_t)px * rec_w + 4 * q) = stage[L * S + k];
-        }
+        if (32 * m + lane < nunits) *reinterpret_cast<int4 *>(row + c0 + m * dm) = stage[s0 + m * (32 / NB) * S];
     }
 }
 
