@@ -351,7 +351,7 @@ bool make_planeset(ih_ctx *ctx, const ih_frame &f, const FrameRec &fr, const uin
         if (f.chan[c].mode != 0) ps.uni = 0;
     // a single frame too small to fill the GPU with the three-kernel build
     // is built by one cooperative launch (its own tile grid)
-    if (small && it == ctx->tuned.end() && !onepass_ok(ps)) small_plan(ps, ctx->nsm);
+    if (small && it == ctx->tuned.end() && !onepass_ok(ps)) small_plan(ps);
     return true;
 }
 

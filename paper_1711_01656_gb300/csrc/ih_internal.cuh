@@ -214,7 +214,7 @@ bool onepass_ok(const PlaneSet &ps);
 // the GPU at once, picks the band height (ps.g) and rows per warp
 // (ps.small) and returns true; the frame is then built by one cooperative
 // launch.  IH_SMALL=0 in the environment (read once) turns it off.
-bool small_plan(PlaneSet &ps, int nsm);
+bool small_plan(PlaneSet &ps);
 // Scratch bytes of a small-frame build, and its carving.
 size_t small_bytes(const PlaneSet &ps);
 void carve_small(PlaneSet &ps, void *base);

@@ -553,13 +553,12 @@ int small_capacity(int layout)
 
 }  // namespace
 
-bool small_plan(PlaneSet &ps, int nsm)
+bool small_plan(PlaneSet &ps)
 {
     static const bool on = [] {
         const char *e = getenv("IH_SMALL");
         return !(e && e[0] == '0');
     }();
-    (void)nsm;
     const int H = ps.g.H, W = ps.g.W;
     if (!on || !ps.err || ps.mom || ps.wch >= 0) return false;
     if (ps.layout != LAYOUT_BIN_MAJOR && ps.layout != LAYOUT_SLAB) return false;
