@@ -19,6 +19,8 @@
 //   H_w(r,c) = corner_w + sum_{C0<=c'<=c} G_w(c')
 //            + sum_{R0<=r'<=r} ( L_w(r') + sum_{C0<=c'<=c} w(r',c') Q(r',c') )
 // which is Eq. 3.4 (Eq. 2.15 for w = 1) split at the tile's top and left edges.
+// A single count-only frame whose tiles all fit the GPU at once takes the
+// same split in one cooperative launch instead (small_plan, k_small.cu).
 #pragma once
 
 #include <cuda_runtime.h>

@@ -39,8 +39,12 @@
 // launch (k_tiles_count when the frame has no moment planes); k_tiles_b does
 // the same over the frames of a batch.
 //
-// No kernel waits on another CTA; the only inter-CTA data flow is through the
-// carry arrays between launches on one stream.
+// These kernels wait on no other CTA: the only inter-CTA data flow is through
+// the carry arrays between launches on one stream.  Two opt-in kernels at the
+// end of this file do wait, with bounded polls: the persistent batched build
+// (per-frame phase counters) and the one-pass build of small frames
+// (decoupled look-back over bands); the default small-frame build is in
+// k_small.cu (one grid barrier in a cooperative launch).
 #include <algorithm>
 #include <mutex>
 
