@@ -140,9 +140,14 @@ ih_status ih_create(const ih_config *cfg, ih_ctx **out);
  * whose weighted_channel >= 0, and enqueues the work on `stream`.
  * out_handles (host, n entries) receives one handle per frame.  The tensors
  * are owned by the context.  The pixels must stay valid until the stream
- * passes the build.  Returns IH_EINVAL for an invalid descriptor,
- * IH_EBUDGET if the frames' bytes would exceed the HBM budget (no frame is
- * built then), IH_ENOMEM / IH_ECUDA on allocation or launch failure. */
+ * passes the build.  A frame without moment planes in the bin-major or slab
+ * layout, small enough that all its tiles fit the GPU at once (a 640 x 480
+ * frame, say), is built by one cooperative launch whose CTAs meet at a
+ * bounded grid barrier (IH_SMALL=0 in the environment turns this off); a
+ * barrier wait that gives up makes the next ih_sync return IH_ETIMEOUT.
+ * Returns IH_EINVAL for an invalid descriptor, IH_EBUDGET if the frames'
+ * bytes would exceed the HBM budget (no frame is built then), IH_ENOMEM /
+ * IH_ECUDA on allocation or launch failure. */
 ih_status ih_build(ih_ctx *ctx, const ih_frame *frames, int32_t n, int32_t *out_handles,
                    void *stream);
 
